@@ -1,0 +1,128 @@
+"""Pins of the oracle's MINRES (Sec. 4) against dense solves, scipy's MINRES and
+the qualitative results the paper prints (Fig. 1, Fig. 3)."""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import gl_inputs as gi
+
+BH3 = gi.WORKLOADS["cube128"][3]
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.mark.parametrize("dim,N", [(2, 14), (3, 5)])
+def test_minres_matches_dense_solve(oracle_mod, dim, N):
+    """On at most 200 nodes the R_1-MINRES solution matches a direct solve of the
+    realified 2n x 2n system (Remark rmk:isometry); the oracle's own LU is checked
+    against numpy's solver."""
+    m = oracle_mod.Mesh(dim, N, 1.0, BH3 if dim == 3 else (0, 0, 1))
+    assert m.n <= 200
+    psi, b = gi.disk(m.n, 1), gi.complex_normal(m.n, 1)
+    xd = m.dense_solve(psi, b)
+    Jr = m.jacobian_dense_real(psi)
+    xn = np.linalg.solve(Jr, np.concatenate([b.real, b.imag]))
+    np.testing.assert_allclose(xd, xn[: m.n] + 1j * xn[m.n:], rtol=1e-12, atol=1e-12)
+    for mc in (512, 16):  # one level (exact inverse) and a real hierarchy
+        # 1e-11 is near the FP64 attainable accuracy kappa(J) * eps of these systems
+        x, info = m.solve(psi, b, tol=1e-11, max_coarse=mc)
+        assert info.converged and info.true_relres <= 1e-11
+        assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
+
+
+def test_unpreconditioned_minres_matches_scipy(oracle_mod):
+    """Without a preconditioner (k = 0 in Fig. 1) MINRES in <.,.>_R is plain MINRES on
+    D^(1/2) J D^(-1/2) realified; its iterates must match scipy's MINRES."""
+    m = oracle_mod.Mesh(2, 10, 1.2)
+    psi, b = gi.disk(m.n, 2), gi.complex_normal(m.n, 3)
+    vol = np.concatenate([m.volumes()] * 2)
+    Jr = m.jacobian_dense_real(psi)
+    S = np.sqrt(vol)[:, None] * Jr / np.sqrt(vol)[None, :]
+    c = np.sqrt(vol) * np.concatenate([b.real, b.imag])
+    for k in (5, 12):
+        y, _ = spla.minres(S, c, maxiter=k, rtol=1e-300)
+        xs = y / np.sqrt(vol)
+        x, info = m.solve(psi, b, cycles=0, maxit=k, tol=1e-300)
+        assert info.iters == k
+        np.testing.assert_allclose(x, xs[: m.n] + 1j * xs[m.n:], rtol=1e-9, atol=1e-11)
+
+
+def test_minres_residual_monotone_and_estimate_is_preconditioned_norm(oracle_mod):
+    """MINRES minimises the R_1-norm of the residual: the estimate never increases
+    and equals sqrt(<r, R_1 r>_R) / sqrt(<b, R_1 b>_R) of the actual iterate."""
+    m = oracle_mod.Mesh(2, 33, 1.0)
+    psi, b = gi.disk(m.n, 5), gi.complex_normal(m.n, 6)
+    P = oracle_mod.Precond(m, psi, max_coarse=32)
+    prev = np.inf
+    nb = np.sqrt(m.inner_r(b, P.apply(b)))
+    for k in range(1, 12, 2):
+        P.opts.maxit = k
+        P.opts.tol = 1e-300
+        x, info = P.minres(b)
+        r = b - m.jacobian(psi, x)
+        est = np.sqrt(m.inner_r(r, P.apply(r))) / nb
+        assert info.est_relres == pytest.approx(est, rel=1e-6)
+        assert info.est_relres <= prev * (1 + 1e-12)
+        prev = info.est_relres
+
+
+def read_fig3():
+    rows = {}
+    with open(os.path.join(GOLDEN, "fig3_cube_az_iterations.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, *vals = line.split()
+            rows[name] = [int(v) for v in vals]
+    return rows
+
+
+@pytest.mark.slow
+def test_mesh_independent_iterations_like_fig3(oracle_mod):
+    """Fig. 3 (cube, A_z, psi = 1, tol 1e-11): unpreconditioned counts grow with the
+    mesh; R_1 counts stay flat; R_inf needs fewer iterations than R_1.  The same
+    shape must appear here (the paper's exact counts are not a target: its mesh and
+    AMG parameters differ)."""
+    fig = read_fig3()
+    assert fig["unprec"][-1] > 3 * fig["unprec"][1]
+    assert max(fig["R1"][1:]) - min(fig["R1"][1:]) <= 1 and max(fig["Rinf"][1:]) < min(fig["R1"][1:])
+    it1, itinf, it0 = [], [], []
+    for N in (10, 16, 24):
+        m = oracle_mod.Mesh(3, N, 1.0, (0, 0, 1))
+        psi = np.ones(m.n, complex)
+        b = gi.complex_normal(m.n, 5)
+        it1.append(m.solve(psi, b, tol=1e-11, max_coarse=64)[1].iters)
+        itinf.append(m.solve(psi, b, tol=1e-11, max_coarse=64, cycles=10)[1].iters)
+        it0.append(m.solve(psi, b, tol=1e-11, cycles=0, maxit=2000)[1].iters)
+    assert max(it1) - min(it1) <= 3, it1
+    assert all(a < b for a, b in zip(itinf, it1)), (itinf, it1)
+    assert it0[-1] > 1.5 * it0[0] and min(it0) > max(it1), (it0, it1)
+
+
+def test_mesh_independent_iterations_2d(oracle_mod):
+    """R_1 iteration counts to 1e-10 do not grow with the mesh (Sec. 4, 2D)."""
+    its = []
+    for N in (32, 64, 128):
+        m = oracle_mod.Mesh(2, N, 1.0)
+        x, info = m.solve(gi.disk(m.n, 1), gi.complex_normal(m.n, 1))
+        assert info.converged and info.true_relres <= 1e-10
+        its.append(info.iters)
+    assert max(its) - min(its) <= 4 and max(its) <= 30, its
+
+
+def test_fig1_shape_more_cycles_fewer_iterations(oracle_mod):
+    """Fig. 1: with more V-cycles per iteration MINRES needs fewer iterations, but the
+    cost in matvec equivalents (1 + k x cycle cost per iteration) is lowest for k = 1."""
+    m = oracle_mod.Mesh(2, 65, 1.0)
+    psi = np.ones(m.n, complex)
+    b = np.ones(m.n, complex)
+    its = {}
+    for k in (1, 2, 5):
+        x, info = m.solve(psi, b, cycles=k, max_coarse=32, tol=1e-10)
+        assert info.converged
+        its[k] = info.iters
+    assert its[1] > its[2] > its[5]
+    cyc = 3.31  # the paper's cost of one V-cycle in matvecs (Fig. 1 caption)
+    cost = {k: its[k] * (1 + k * cyc) for k in its}
+    assert cost[1] < cost[2] < cost[5]
