@@ -1,0 +1,343 @@
+#!/usr/bin/env python3
+"""Benchmark: Jacobian solves per second at a relative residual of 1e-10 on the
+3D unit cube with 128^3 nodes (2,097,152 complex unknowns), field mu = 1 along
+(1,1,1)/sqrt(3), psi == 1 (the state of the paper's Sec. 4 experiments), random
+complex-normal right-hand side (seed 5).
+
+One step = one R_1-preconditioned MINRES solve of J(psi) x = b from x = 0 until
+the FP64 true residual ||b - J x||_D / ||b||_D <= 1e-10.  The preconditioner is
+set up once for psi before the timed region (setup-exclusive solves/s).  The
+headline form is GL_MIXED (FP32 applies and V-cycles inside FP64 defect
+correction); the FP64 form is timed beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+Multi-GPU (one rank per GPU via torch.distributed.run): every rank solves its
+own copy of the workload (replicas, no exchange); value = solves of all ranks
+divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gl_inputs as gi  # noqa: E402
+
+METRIC = "Jacobian solves/s @1e-10 rel-res (3D 128^3): mixed+learned vs FP64 GPU; %HBM"
+UNIT = "solves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--N", type=int, default=128, help="nodes per side of the cube")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--max-coarse", type=int, default=512, help="coarsest-level size bound of the AMG hierarchy")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, name in enumerate(names):
+                if len(r) > 5 + k and "Active" in r[5 + k] and "Not" not in r[5 + k]:
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def workload(N):
+    dim, _, mu, bh = gi.WORKLOADS["cube128"]
+    n = N ** 3
+    return dim, mu, bh, n
+
+
+def cpu_baseline(N, b, x_gpu):
+    """The oracle's FP64 R_1-MINRES solve of the same system on the host (setup
+    excluded, like the GPU number); also the GPU solution's error against it."""
+    import oracle
+
+    dim, mu, bh, n = workload(N)
+    t0 = time.perf_counter()
+    m = oracle.Mesh(dim, N, mu, bh)
+    psi = np.ones(n, complex)
+    P = oracle.Precond(m, psi)
+    t1 = time.perf_counter()
+    x, info = P.minres(b)
+    t2 = time.perf_counter()
+    err = float(np.linalg.norm(x_gpu - x) / np.linalg.norm(x)) if x_gpu is not None else None
+    return {
+        "value": 1.0 / (t2 - t1), "unit": UNIT, "cores": 1, "kind": "oracle",
+        "sample": f"one full FP64 R_1-MINRES solve of the {N}^3 cube system on 1 host thread "
+                  f"({info.iters} iterations, true relres {info.true_relres:.2e}; "
+                  f"mesh+setup {t1 - t0:.1f} s untimed)",
+        "iters": info.iters,
+    }, err
+
+
+def run_reference(args):
+    """The oracle timed on the host cores, in the bench's metric and config.  Each
+    step is a bounded sample: 3 MINRES iterations, scaled by the iteration count of
+    one full oracle solve done during warm-up."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    N = args.N
+    dim, mu, bh, n = workload(N)
+    m = oracle.Mesh(dim, N, mu, bh)
+    psi = np.ones(n, complex)
+    b = gi.complex_normal(n, 5)
+    P = oracle.Precond(m, psi)
+    x, info = P.minres(b)
+    full_iters = info.iters
+    per_it = []
+    P.opts.tol = 1e-300
+    P.opts.maxit = 3
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        P.minres(b)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            per_it.append(dt / 3)
+    t_it = float(np.mean(per_it))
+    value = 1.0 / (t_it * full_iters)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_it * full_iters,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"cube{N}^3 mu=1 bhat=(1,1,1)/sqrt3 psi=1 b=CN(0,1) seed 5",
+                   "n": n, "tol": 1e-10, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"3 MINRES iterations per step x {full_iters} iterations per full solve"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    import paper_1204_5125_gb300 as gl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+
+    N = args.N
+    dim, mu, bh, n = workload(N)
+    b_host = gi.complex_normal(n, 5)
+    psi = torch.ones(n, dtype=torch.complex128, device=dev)
+    b = torch.from_numpy(b_host).to(dev)
+    x = torch.zeros_like(b)
+
+    t0 = time.perf_counter()
+    mesh = gl.gl_mesh_create(dim, N, mu, bh)
+    t1 = time.perf_counter()
+    opts_mixed = gl.options(precision=gl.GL_MIXED, max_coarse=args.max_coarse)
+    opts_fp64 = gl.options(precision=gl.GL_FP64, max_coarse=args.max_coarse)
+    prec = gl.gl_precond_setup(mesh, psi, opts_mixed)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    nlev = gl.gl_precond_levels(prec)
+    levels = [gl.gl_precond_level_info(prec, l) for l in range(nlev)]
+
+    def solve(opts):
+        x.zero_()
+        st, info = gl.gl_jacobian_solve(mesh, psi, prec, b, x, opts)
+        if st != 0:
+            raise RuntimeError(f"solve failed: status {st} {info.as_dict()}")
+        return info
+
+    def timed(opts, steps, warm, profile_class=None):
+        for _ in range(warm):
+            solve(opts)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if profile_class:
+            gl.gl_profile_begin(profile_class, 1 << 16)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        infos = [solve(opts) for _ in range(steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        prof = gl.gl_profile_end() if profile_class else None
+        ms = ev0.elapsed_time(ev1)
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos, prof
+
+    # FP64 GPU form (context and the ratio the metric asks for)
+    ms64, infos64, _ = timed(opts_fp64, max(1, args.steps // 2), max(1, args.warmup // 2))
+    x64 = x.clone()
+    # the two mixed forms: FP32 inner solves in FP64 defect correction, and an
+    # FP32 V-cycle inside FP64 MINRES; the faster one is the headline
+    forms = {"mixed_inner": opts_mixed, "mixed_precond": gl.options(precision=gl.GL_MIXED_PRECOND,
+                                                                     max_coarse=args.max_coarse)}
+    quick = {}
+    for name, o in forms.items():
+        q_ms, q_inf, _ = timed(o, 2, 1)
+        quick[name] = {"solves_per_s": 2e3 / q_ms, "iters": [i.iters for i in q_inf],
+                       "outer": [i.outer_iters for i in q_inf], "true_relres": max(i.true_relres for i in q_inf)}
+    head = max(quick, key=lambda k: quick[k]["solves_per_s"])
+    opts_head = forms[head]
+    # headline: the chosen mixed form, with the dominant kernel timed live by CUDA events
+    with Clocks(dev.index if world == 1 else local) as clk:
+        ms, infos, prof = timed(opts_head, args.steps, args.warmup, profile_class="gs0")
+    x_mixed = x.clone()
+    err_mixed_vs_fp64 = float(torch.linalg.norm(x_mixed - x64) / torch.linalg.norm(x64))
+
+    # end to end through the C ABI with host buffers: H2D of b, solve, D2H of x
+    e2e = None
+    if not args.no_e2e:
+        b_pin = torch.from_numpy(b_host).pin_memory()
+        x_pin = torch.empty_like(b_pin).pin_memory()
+        for _ in range(1):
+            b.copy_(b_pin, non_blocking=True)
+            solve(opts_head)
+            x_pin.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        te0 = time.perf_counter()
+        for _ in range(args.steps):
+            b.copy_(b_pin, non_blocking=True)
+            solve(opts_head)
+            x_pin.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - te0
+        if dist:
+            t = torch.tensor([te], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * args.steps / te, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
+               "d2h_bytes_per_step": 16 * n}
+
+    value = world * args.steps / (ms / 1e3)
+    value64 = world * len(infos64) / (ms64 / 1e3)
+    peak, peak_kind = peaks()
+    achieved = prof["bytes"] / (prof["ms"] / 1e3) / 1e9 if prof and prof["ms"] > 0 else None
+    per_launch_bytes = prof["bytes"] / prof["timed"] if prof and prof["timed"] else None
+    roofline = {
+        "bound": "hbm", "kernel": "k_gs (Gauss-Seidel colour sweep, finest level, FP32)",
+        "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": achieved / peak if achieved else None, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+        "traffic": None, "alg_bytes_per_launch": per_launch_bytes,
+        "launches_timed": prof["timed"] if prof else None,
+        "avg_launch_us": 1e3 * prof["ms"] / prof["timed"] if prof and prof["timed"] else None,
+    }
+
+    cpu = None
+    err_vs_oracle = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, err_vs_oracle = cpu_baseline(N, b_host, x_mixed.cpu().numpy())
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64/f64", "data": "synthetic",
+            "config": {"workload": f"cube{N}^3 mu=1 bhat=(1,1,1)/sqrt3 psi=1 b=CN(0,1) seed 5",
+                       "n": n, "tol": 1e-10, "form": head, "max_coarse": args.max_coarse,
+                       "l2": "inputs larger than L2 (operators ~0.5 GB)", "levels": [lv["n"] for lv in levels],
+                       "colors": [lv["ncolors"] for lv in levels], "parallelism": f"replicas x{world}"},
+            "iters_mixed": [i.iters for i in infos], "outer_mixed": [i.outer_iters for i in infos],
+            "mixed_forms": quick,
+            "true_relres_mixed": max(i.true_relres for i in infos),
+            "fp64_value": value64, "iters_fp64": [i.iters for i in infos64],
+            "true_relres_fp64": max(i.true_relres for i in infos64),
+            "mixed_over_fp64": value / value64, "err_mixed_vs_fp64_gpu": err_mixed_vs_fp64,
+            "err_mixed_vs_fp64_oracle": err_vs_oracle,
+            "setup_s": {"mesh": t1 - t0, "precond": t2 - t1},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": prof["launches"] if prof else None, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    gl.gl_precond_destroy(prec)
+    gl.gl_mesh_destroy(mesh)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * gl.h -- C ABI of the GB300 library for the Jacobian solve of the extreme
+ * type-II Ginzburg-Landau problem (Schloemer & Vanroose, "An optimal linear
+ * solver for the Jacobian system of the extreme type-II Ginzburg-Landau
+ * problem", arXiv:1204.5125).
+ *
+ * Conventions shared by every call below.
+ *   - Complex vectors are arrays of n interleaved (re, im) FP64 pairs
+ *     (C99 double complex / numpy complex128 layout), n = number of mesh nodes.
+ *     Node j = i + N*(j_y + N*k) for lattice coordinates (i, j_y, k), x fastest.
+ *   - Every pointer named *_dev is a device pointer of the current CUDA device;
+ *     the caller allocates and owns it.  Pointers named *_host are host memory,
+ *     also owned by the caller.  No call retains a caller pointer after it
+ *     returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls that only launch work return as soon as it is queued; the
+ *     caller synchronises the stream before reading results.  Calls that return
+ *     host values (setup, solve, info) synchronise the stream themselves.
+ *   - The library owns gl_mesh and gl_prec handles (all their device memory)
+ *     until the matching *_destroy call.
+ *   - Every call returns a gl_status.  On failure gl_last_error() returns a
+ *     message (per host thread) and outputs are unspecified unless stated.
+ *   - Only structured meshes are supported: the unit square (dim 2) or cube
+ *     (dim 3) centred at the origin with N nodes per side, spacing h = 1/(N-1),
+ *     split into right triangles along the (i,j)-(i+1,j+1) diagonal in 2D and
+ *     into Kuhn (Freudenthal) tetrahedra along the main diagonal in 3D.
+ */
+#ifndef GL_GB300_H
+#define GL_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GL_API __attribute__((visibility("default")))
+#else
+#define GL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gl_mesh_s *gl_mesh;
+typedef struct gl_prec_s *gl_prec;
+
+typedef enum {
+    GL_OK = 0,
+    GL_ERR_ARG = 1,           /* invalid argument (null handle, bad size, ...) */
+    GL_ERR_CUDA = 2,          /* a CUDA runtime call or kernel failed */
+    GL_ERR_OOM = 3,           /* device allocation failed */
+    GL_ERR_NOT_CONVERGED = 4, /* solve stopped at maxit; x holds the last iterate */
+    GL_ERR_BREAKDOWN = 5,     /* preconditioner not positive definite (<v, R v>_R < 0) */
+    GL_ERR_NAN = 6,           /* a non-finite residual or scalar appeared */
+    GL_ERR_TIMEOUT = 7,       /* a bounded device-side wait ran out */
+    GL_ERR_CAPACITY = 8       /* an internal per-row or per-level limit was exceeded */
+} gl_status;
+
+typedef enum {
+    GL_FP64 = 0,          /* everything in FP64 complex */
+    GL_MIXED = 1,         /* FP64 defect correction around inner MINRES solves whose vectors,
+                             Jacobian applies and V-cycles are FP32 complex */
+    GL_MIXED_PRECOND = 2  /* FP64 MINRES and Jacobian applies; the V-cycle of R_k runs in FP32 */
+} gl_precision;
+
+/* Solver options.  Fill with gl_options_default() and override fields. */
+typedef struct {
+    double tol;          /* target ||b - J x||_D / ||b||_D (default 1e-10) */
+    int maxit;           /* MINRES iteration cap (inner cap in GL_MIXED) (default 500) */
+    int cycles;          /* k in R_k = AMG_k(...) (Eq. prec2); 0 = no preconditioner (default 1) */
+    int max_coarse;      /* stop coarsening at or below this many nodes (default 512, max 4096) */
+    int max_levels;      /* hierarchy depth cap (default 10, max 16) */
+    int power_its;       /* power iterations for rho(D^-1 A) in prolongator smoothing (default 20) */
+    int precision;       /* gl_precision (default GL_FP64); the coarsest solve is FP64 in every mode */
+    double inner_tol;    /* GL_MIXED: relative reduction asked of each FP32 inner solve (default 1e-5) */
+    int max_outer;       /* GL_MIXED: cap on FP64 refinement steps (default 20) */
+    int check_every;     /* host polls the device convergence flag every this many iterations (default 6) */
+} gl_options;
+
+/* Per-solve report. */
+typedef struct {
+    int iters;           /* MINRES iterations (summed over inner solves in GL_MIXED) */
+    int outer_iters;     /* FP64 refinement steps (GL_MIXED), 1 in GL_FP64 */
+    int converged;       /* 1 if true_relres <= tol */
+    double true_relres;  /* ||b - J x||_D / ||b||_D computed in FP64 at the end */
+    double est_relres;   /* last MINRES recurrence estimate (preconditioned norm) */
+    double setup_ms;     /* preconditioner setup time inside this call (0 if a gl_prec was given) */
+    double solve_ms;     /* wall time of the Krylov part */
+    int warmstart_used;  /* reserved: 1 if x was taken from a learned initial guess */
+} gl_solve_info;
+
+/* Default options (values listed in gl_options).  Returns GL_ERR_ARG on NULL. */
+GL_API gl_status gl_options_default(gl_options *opt);
+
+/* Builds the finite-volume discretisation of Sec. 3 on the structured mesh:
+ * edge coefficients alpha_jk summed over simplices (Eq. fhat; cotangent formula
+ * for triangles, M alpha = b of Cor. "simplex" for tetrahedra), control volumes
+ * |V_j| (Eq. mass lumping), link phases theta_jk = integral of A from x_j to x_k
+ * (Eq. link variable) for A(x) = (mu/2) bhat x x (Eq. mvp0 scaled by mu, field
+ * along the unit vector bhat), and K-hat with (K-hat psi)_j = sum_k alpha_jk
+ * (psi_j - exp(-i theta_jk) psi_k) (Eq. discr kin energy, Remark rmk:dk).
+ * Edges with |alpha| <= 1e-12 max|alpha| are dropped.
+ * dim: 2 or 3.  n_per_side: N >= 2 (n = N^dim < 2^31).  bhat: 3 doubles (host),
+ * normalised internally; NULL means (0,0,1).  Runs on `stream` and
+ * synchronises it.  *out receives a new handle. */
+GL_API gl_status gl_mesh_create(int dim, int n_per_side, double mu, const double *bhat_host, void *stream,
+                         gl_mesh *out);
+GL_API gl_status gl_mesh_destroy(gl_mesh mesh);
+
+/* n = number of nodes; nnz = stored entries of K-hat (diagonal included);
+ * volumes_dev (nullable): receives |V_j| as n doubles.  Synchronises `stream`
+ * only when volumes_dev is given (copy on the legacy stream). */
+GL_API gl_status gl_mesh_info(gl_mesh mesh, int64_t *n, int64_t *nnz, double *volumes_dev);
+
+/* Discrete GL residual (Eq. discr ginla): r_i = (K psi)_i - psi_i (1 - |psi_i|^2),
+ * K = D^-1 K-hat.  psi_dev, r_dev: n complex (FP64); may not alias. */
+GL_API gl_status gl_residual(gl_mesh mesh, const void *psi_dev, void *r_dev, void *stream);
+
+/* Discrete Jacobian (Sec. 3):
+ *   y_i = (K phi)_i + (-1 + 2|psi_i|^2) phi_i + psi_i^2 conj(phi_i).
+ * psi, phi, y: n complex FP64; y may not alias psi or phi.  With GL_MIXED the
+ * operator and arithmetic are FP32 (inputs rounded to FP32, output widened). */
+GL_API gl_status gl_jacobian_apply(gl_mesh mesh, const void *psi_dev, const void *phi_dev, void *y_dev,
+                            int precision, void *stream);
+
+/* Sets up R_k(psi) = AMG_k(K-hat + 2 D |psi|^2, D .) (Eq. prec2, Sec. 4.1):
+ * smoothed-aggregation AMG with symmetric Gauss-Seidel smoothing.  Uses
+ * opt->cycles, max_coarse, max_levels, power_its, precision (GL_MIXED also
+ * builds FP32 copies of every level).  Synchronises `stream`. */
+GL_API gl_status gl_precond_setup(gl_mesh mesh, const void *psi_dev, const gl_options *opt, void *stream,
+                           gl_prec *out);
+
+/* z = R_k x: k V-cycles for (K-hat + 2 D|psi|^2) z = D x from z = 0 (Eq. prec2).
+ * x_dev, z_dev: n complex FP64, may not alias.  FP64 arithmetic. */
+GL_API gl_status gl_precond_apply(gl_prec prec, const void *x_dev, void *z_dev, void *stream);
+GL_API gl_status gl_precond_destroy(gl_prec prec);
+
+/* Hierarchy introspection (for parity checks).  Level 0 is the finest.
+ * Node numbering is the canonical one: the mesh's node ids on level 0 and the
+ * aggregate ids (roots in ascending id order) below.  Host outputs. */
+GL_API gl_status gl_precond_levels(gl_prec prec, int *nlevels);
+GL_API gl_status gl_precond_level_info(gl_prec prec, int level, int64_t *n, int64_t *nnz, int32_t *ncolors,
+                                int64_t *p_nnz, double *omega);
+/* agg_host: n int32, the coarse node of each node of this level (not the coarsest). */
+GL_API gl_status gl_precond_level_aggregates(gl_prec prec, int level, int32_t *agg_host);
+/* color_host: n int32 smoothing colours of this level. */
+GL_API gl_status gl_precond_level_colors(gl_prec prec, int level, int32_t *color_host);
+/* CSR of the level operator (Hermitian; level 0 = K-hat + 2 D|psi|^2), columns
+ * ascending: rp_host n+1 int64, ci_host nnz int32, v_host nnz complex FP64. */
+GL_API gl_status gl_precond_level_matrix(gl_prec prec, int level, int64_t *rp_host, int32_t *ci_host, void *v_host);
+/* CSR of the prolongator from level+1 to level: n rows, p_nnz entries. */
+GL_API gl_status gl_precond_level_P(gl_prec prec, int level, int64_t *rp_host, int32_t *ci_host, void *v_host);
+
+/* Mesh introspection (host outputs): edges (j < k) in lexicographic order with
+ * alpha and theta; and K-hat as CSR with ascending columns. */
+GL_API gl_status gl_mesh_nedges(gl_mesh mesh, int64_t *nedges);
+GL_API gl_status gl_mesh_edges(gl_mesh mesh, int32_t *ej_host, int32_t *ek_host, double *alpha_host,
+                        double *theta_host);
+GL_API gl_status gl_mesh_khat(gl_mesh mesh, int64_t *rp_host, int32_t *ci_host, void *v_host);
+
+/* Solves J(psi) x = b (the Newton system, Eq. Newton system) by preconditioned
+ * MINRES in <.,.>_R = Re sum |V_i| conj(x_i) y_i (Sec. 4, Eq. disc inner2) with
+ * preconditioner R_k(psi).  prec: a handle set up for the same psi, or NULL to
+ * set one up inside the call (timed in info->setup_ms).  x_dev: on entry the
+ * initial guess (zeros for x0 = 0), on exit the solution.  The iteration stops
+ * once the recurrence estimate and then the FP64 true residual
+ * ||b - J x||_D / ||b||_D are both <= opt->tol.  GL_MIXED: FP64 defect
+ * correction around FP32 inner MINRES solves.  Returns GL_ERR_NOT_CONVERGED at
+ * the iteration cap with x the last iterate.  Synchronises `stream`. */
+GL_API gl_status gl_jacobian_solve(gl_mesh mesh, const void *psi_dev, gl_prec prec, const void *b_dev, void *x_dev,
+                            const gl_options *opt, gl_solve_info *info, void *stream);
+
+/* One Newton step (Eq. Newton system): r = GL(psi), solve J(psi) d = -r with
+ * R_k(psi), psi <- psi + d.  *gl_norm_out (nullable) = ||GL(psi)||_R of the
+ * state on entry.  Synchronises `stream`. */
+GL_API gl_status gl_newton_step(gl_mesh mesh, void *psi_dev, const gl_options *opt, gl_solve_info *info,
+                         double *gl_norm_out, void *stream);
+
+/* Solves count independent systems J(psi_s) x_s = b_s on their own meshes with
+ * their own R_1(psi_s), all on one stream.  infos: count entries (nullable).
+ * Returns the first non-GL_OK status (all instances are still attempted). */
+GL_API gl_status gl_batch_solve(int count, const gl_mesh *meshes, const void *const *psi_dev, const void *const *b_dev,
+                         void *const *x_dev, const gl_options *opt, gl_solve_info *infos, void *stream);
+
+/* Measurement instrumentation (no counterpart in the paper).
+ * gl_profile_begin resets the count of hot-path kernel launches and, when
+ * kernel_class is not NULL, records a pair of CUDA events on the launching
+ * stream around each of the next max_launches launches of that class:
+ *   "gs0"  Gauss-Seidel colour sweeps on the finest level (byte model: per row
+ *          the diagonal, b and the written x; the stored off-diagonals as value +
+ *          32-bit column; each neighbour value once)
+ *   "jz"   the fused Jacobian apply + dot of MINRES (byte model: stored
+ *          off-diagonals, K_ii, |V|, psi, z and the written result per row)
+ *   "gs", "resid0", "resid", "restrict", "prolong" (timed, no byte model).
+ * gl_profile_end synchronises the device and returns the launches since
+ * begin, the number of timed launches, their summed duration in ms and their
+ * summed algorithmic bytes.  Not thread-safe; one profile at a time. */
+GL_API gl_status gl_profile_begin(const char *kernel_class, int max_launches);
+GL_API gl_status gl_profile_end(int64_t *launches, int64_t *timed, double *total_ms, double *alg_bytes);
+
+/* Message describing the last failure on this host thread ("" if none). */
+GL_API const char *gl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GL_GB300_H */

@@ -1,0 +1,305 @@
+"""Python binding of the GB300 Ginzburg-Landau Jacobian-solve library.
+
+Thin ctypes marshalling over the C ABI in ``include/gl.h``: every function
+below has the name of the C entry point it calls, takes torch tensors (CUDA,
+complex128, contiguous) for device buffers and numpy arrays for host outputs,
+and raises :class:`GLError` on a non-GL_OK status.  All arithmetic happens in
+the CUDA library ``_build/libgl_gb300.so``; nothing here falls back to the CPU.
+If the library cannot be loaded, importing the functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from .build import LIB, build as _build
+
+__all__ = [
+    "GLError", "Options", "SolveInfo", "GL_FP64", "GL_MIXED", "GL_MIXED_PRECOND", "library", "options",
+    "gl_options_default", "gl_mesh_create", "gl_mesh_destroy", "gl_mesh_info", "gl_mesh_nedges", "gl_mesh_edges",
+    "gl_mesh_khat", "gl_residual", "gl_jacobian_apply", "gl_precond_setup", "gl_precond_apply",
+    "gl_precond_destroy", "gl_precond_levels", "gl_precond_level_info", "gl_precond_level_aggregates",
+    "gl_precond_level_colors", "gl_precond_level_matrix", "gl_precond_level_P", "gl_jacobian_solve",
+    "gl_newton_step", "gl_batch_solve", "gl_profile_begin", "gl_profile_end", "gl_last_error", "EXPORTED",
+]
+
+GL_FP64, GL_MIXED, GL_MIXED_PRECOND = 0, 1, 2
+STATUS = {0: "GL_OK", 1: "GL_ERR_ARG", 2: "GL_ERR_CUDA", 3: "GL_ERR_OOM", 4: "GL_ERR_NOT_CONVERGED",
+          5: "GL_ERR_BREAKDOWN", 6: "GL_ERR_NAN", 7: "GL_ERR_TIMEOUT", 8: "GL_ERR_CAPACITY"}
+
+# every entry point declared in include/gl.h
+EXPORTED = [
+    "gl_options_default", "gl_mesh_create", "gl_mesh_destroy", "gl_mesh_info", "gl_residual", "gl_jacobian_apply",
+    "gl_precond_setup", "gl_precond_apply", "gl_precond_destroy", "gl_precond_levels", "gl_precond_level_info",
+    "gl_precond_level_aggregates", "gl_precond_level_colors", "gl_precond_level_matrix", "gl_precond_level_P",
+    "gl_mesh_nedges", "gl_mesh_edges", "gl_mesh_khat", "gl_jacobian_solve", "gl_newton_step", "gl_batch_solve",
+    "gl_profile_begin", "gl_profile_end", "gl_last_error",
+]
+
+
+class GLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("tol", C.c_double), ("maxit", C.c_int), ("cycles", C.c_int), ("max_coarse", C.c_int),
+        ("max_levels", C.c_int), ("power_its", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double),
+        ("max_outer", C.c_int), ("check_every", C.c_int),
+    ]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int), ("outer_iters", C.c_int), ("converged", C.c_int), ("true_relres", C.c_double),
+        ("est_relres", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
+        ("warmstart_used", C.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+vp = C.c_void_p
+i64p = C.POINTER(C.c_int64)
+
+
+def library(build_if_missing: bool = True):
+    """Loads (building first if needed) the CUDA library and declares signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build() if build_if_missing else LIB
+        if not os.path.exists(path):
+            raise OSError(f"CUDA library not built: {path}")
+        L = C.CDLL(path)
+        sig = {
+            "gl_options_default": [C.POINTER(Options)],
+            "gl_mesh_create": [C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double), vp, C.POINTER(vp)],
+            "gl_mesh_destroy": [vp],
+            "gl_mesh_info": [vp, i64p, i64p, vp],
+            "gl_mesh_nedges": [vp, i64p],
+            "gl_mesh_edges": [vp, vp, vp, vp, vp],
+            "gl_mesh_khat": [vp, vp, vp, vp],
+            "gl_residual": [vp, vp, vp, vp],
+            "gl_jacobian_apply": [vp, vp, vp, vp, C.c_int, vp],
+            "gl_precond_setup": [vp, vp, C.POINTER(Options), vp, C.POINTER(vp)],
+            "gl_precond_apply": [vp, vp, vp, vp],
+            "gl_precond_destroy": [vp],
+            "gl_precond_levels": [vp, C.POINTER(C.c_int)],
+            "gl_precond_level_info": [vp, C.c_int, i64p, i64p, C.POINTER(C.c_int32), i64p, C.POINTER(C.c_double)],
+            "gl_precond_level_aggregates": [vp, C.c_int, vp],
+            "gl_precond_level_colors": [vp, C.c_int, vp],
+            "gl_precond_level_matrix": [vp, C.c_int, vp, vp, vp],
+            "gl_precond_level_P": [vp, C.c_int, vp, vp, vp],
+            "gl_jacobian_solve": [vp, vp, vp, vp, vp, C.POINTER(Options), C.POINTER(SolveInfo), vp],
+            "gl_newton_step": [vp, vp, C.POINTER(Options), C.POINTER(SolveInfo), C.POINTER(C.c_double), vp],
+            "gl_batch_solve": [C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                               C.POINTER(Options), C.POINTER(SolveInfo), vp],
+            "gl_profile_begin": [C.c_char_p, C.c_int],
+            "gl_profile_end": [i64p, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.gl_last_error.restype = C.c_char_p
+        L.gl_last_error.argtypes = []
+        _lib = L
+        return L
+
+
+def gl_last_error() -> str:
+    return library().gl_last_error().decode()
+
+
+def _check(st: int):
+    if st != 0:
+        raise GLError(st, gl_last_error())
+
+
+def _ptr(t):
+    """Device pointer of a contiguous complex128/float64 CUDA tensor."""
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError("tensor must live on the GPU")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def gl_options_default() -> Options:
+    o = Options()
+    _check(library().gl_options_default(C.byref(o)))
+    return o
+
+
+def options(**kw) -> Options:
+    o = gl_options_default()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def gl_mesh_create(dim: int, n_per_side: int, mu: float, bhat=(0.0, 0.0, 1.0), stream=None):
+    b = (C.c_double * 3)(*bhat)
+    out = C.c_void_p()
+    _check(library().gl_mesh_create(dim, n_per_side, float(mu), b, _stream(stream), C.byref(out)))
+    return out
+
+
+def gl_mesh_destroy(mesh):
+    _check(library().gl_mesh_destroy(mesh))
+
+
+def gl_mesh_info(mesh, volumes=None):
+    n, nnz = C.c_int64(), C.c_int64()
+    _check(library().gl_mesh_info(mesh, C.byref(n), C.byref(nnz), _ptr(volumes) if volumes is not None else None))
+    return n.value, nnz.value
+
+
+def gl_mesh_nedges(mesh) -> int:
+    ne = C.c_int64()
+    _check(library().gl_mesh_nedges(mesh, C.byref(ne)))
+    return ne.value
+
+
+def gl_mesh_edges(mesh):
+    ne = gl_mesh_nedges(mesh)
+    ej, ek = np.zeros(ne, np.int32), np.zeros(ne, np.int32)
+    al, th = np.zeros(ne), np.zeros(ne)
+    _check(library().gl_mesh_edges(mesh, ej.ctypes.data, ek.ctypes.data, al.ctypes.data, th.ctypes.data))
+    return ej, ek, al, th
+
+
+def gl_mesh_khat(mesh):
+    n, nnz = gl_mesh_info(mesh)
+    rp, ci, v = np.zeros(n + 1, np.int64), np.zeros(nnz, np.int32), np.zeros(nnz, np.complex128)
+    _check(library().gl_mesh_khat(mesh, rp.ctypes.data, ci.ctypes.data, v.ctypes.data))
+    return rp, ci, v
+
+
+def gl_residual(mesh, psi, r, stream=None):
+    _check(library().gl_residual(mesh, _ptr(psi), _ptr(r), _stream(stream)))
+
+
+def gl_jacobian_apply(mesh, psi, phi, y, precision=GL_FP64, stream=None):
+    _check(library().gl_jacobian_apply(mesh, _ptr(psi), _ptr(phi), _ptr(y), int(precision), _stream(stream)))
+
+
+def gl_precond_setup(mesh, psi, opts: Options | None = None, stream=None):
+    out = C.c_void_p()
+    o = opts if opts is not None else gl_options_default()
+    _check(library().gl_precond_setup(mesh, _ptr(psi), C.byref(o), _stream(stream), C.byref(out)))
+    return out
+
+
+def gl_precond_apply(prec, x, z, stream=None):
+    _check(library().gl_precond_apply(prec, _ptr(x), _ptr(z), _stream(stream)))
+
+
+def gl_precond_destroy(prec):
+    _check(library().gl_precond_destroy(prec))
+
+
+def gl_precond_levels(prec) -> int:
+    n = C.c_int()
+    _check(library().gl_precond_levels(prec, C.byref(n)))
+    return n.value
+
+
+def gl_precond_level_info(prec, level: int) -> dict:
+    n, nnz, pnnz = C.c_int64(), C.c_int64(), C.c_int64()
+    nc = C.c_int32()
+    om = C.c_double()
+    _check(library().gl_precond_level_info(prec, level, C.byref(n), C.byref(nnz), C.byref(nc), C.byref(pnnz),
+                                           C.byref(om)))
+    return dict(n=n.value, nnz=nnz.value, ncolors=nc.value, p_nnz=pnnz.value, omega=om.value)
+
+
+def gl_precond_level_aggregates(prec, level: int):
+    a = np.zeros(gl_precond_level_info(prec, level)["n"], np.int32)
+    _check(library().gl_precond_level_aggregates(prec, level, a.ctypes.data))
+    return a
+
+
+def gl_precond_level_colors(prec, level: int):
+    a = np.zeros(gl_precond_level_info(prec, level)["n"], np.int32)
+    _check(library().gl_precond_level_colors(prec, level, a.ctypes.data))
+    return a
+
+
+def gl_precond_level_matrix(prec, level: int):
+    info = gl_precond_level_info(prec, level)
+    rp, ci, v = np.zeros(info["n"] + 1, np.int64), np.zeros(info["nnz"], np.int32), np.zeros(info["nnz"], complex)
+    _check(library().gl_precond_level_matrix(prec, level, rp.ctypes.data, ci.ctypes.data, v.ctypes.data))
+    return rp, ci, v
+
+
+def gl_precond_level_P(prec, level: int):
+    info = gl_precond_level_info(prec, level)
+    rp, ci, v = np.zeros(info["n"] + 1, np.int64), np.zeros(info["p_nnz"], np.int32), np.zeros(info["p_nnz"], complex)
+    _check(library().gl_precond_level_P(prec, level, rp.ctypes.data, ci.ctypes.data, v.ctypes.data))
+    return rp, ci, v
+
+
+def gl_jacobian_solve(mesh, psi, prec, b, x, opts: Options | None = None, stream=None, raise_on_fail=True):
+    """Solves J(psi) x = b in place (x holds the initial guess). Returns (status, SolveInfo)."""
+    o = opts if opts is not None else gl_options_default()
+    info = SolveInfo()
+    st = library().gl_jacobian_solve(mesh, _ptr(psi), prec if prec is not None else None, _ptr(b), _ptr(x),
+                                     C.byref(o), C.byref(info), _stream(stream))
+    if raise_on_fail and st not in (0, 4):
+        _check(st)
+    return st, info
+
+
+def gl_newton_step(mesh, psi, opts: Options | None = None, stream=None):
+    o = opts if opts is not None else gl_options_default()
+    info = SolveInfo()
+    gn = C.c_double()
+    st = library().gl_newton_step(mesh, _ptr(psi), C.byref(o), C.byref(info), C.byref(gn), _stream(stream))
+    if st not in (0, 4):
+        _check(st)
+    return st, info, gn.value
+
+
+def gl_batch_solve(meshes, psis, bs, xs, opts: Options | None = None, stream=None):
+    k = len(meshes)
+    o = opts if opts is not None else gl_options_default()
+    arr = lambda xs_: (vp * k)(*[x.value if isinstance(x, C.c_void_p) else _ptr(x).value for x in xs_])
+    infos = (SolveInfo * k)()
+    st = library().gl_batch_solve(k, arr(meshes), arr(psis), arr(bs), arr(xs), C.byref(o), infos, _stream(stream))
+    if st not in (0, 4):
+        _check(st)
+    return st, list(infos)
+
+
+def gl_profile_begin(kernel_class: str | None = None, max_launches: int = 0):
+    _check(library().gl_profile_begin(kernel_class.encode() if kernel_class else None, int(max_launches)))
+
+
+def gl_profile_end() -> dict:
+    la, ti = C.c_int64(), C.c_int64()
+    ms, by = C.c_double(), C.c_double()
+    _check(library().gl_profile_end(C.byref(la), C.byref(ti), C.byref(ms), C.byref(by)))
+    return dict(launches=la.value, timed=ti.value, ms=ms.value, bytes=by.value)

@@ -1,0 +1,426 @@
+// gl_api.cu -- the extern "C" boundary declared in include/gl.h.  Every entry
+// point validates its arguments, runs the GPU work on the caller's stream, and
+// turns exceptions into gl_status codes with a per-thread message.
+#include <chrono>
+
+#include "gl_internal.cuh"
+#include "gl_profile.cuh"
+
+using namespace gl;
+
+namespace {
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+template <typename F>
+gl_status guard(F &&f) {
+    try {
+        set_error("");
+        return f();
+    } catch (const Error &e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return GL_ERR_OOM;
+    } catch (const std::exception &e) {
+        set_error(e.what());
+        return GL_ERR_CUDA;
+    }
+}
+
+void check_opts(const gl_options *o) {
+    GL_REQUIRE(o, GL_ERR_ARG, "options must not be NULL");
+    GL_REQUIRE(o->tol >= 0, GL_ERR_ARG, "tol must be >= 0");
+    GL_REQUIRE(o->maxit >= 0, GL_ERR_ARG, "maxit must be >= 0");
+    GL_REQUIRE(o->cycles >= 0 && o->cycles <= 64, GL_ERR_ARG, "cycles must be in [0, 64]");
+    GL_REQUIRE(o->precision == GL_FP64 || o->precision == GL_MIXED || o->precision == GL_MIXED_PRECOND, GL_ERR_ARG,
+               "unknown precision");
+    GL_REQUIRE(o->max_coarse <= MAX_COARSE_DENSE, GL_ERR_ARG, "max_coarse must be <= 4096");
+}
+
+void ensure_tmp(gl_mesh_s *m) {
+    if (m->t0.n != (size_t)m->n) {
+        m->t0.alloc(m->n);
+        m->t1.alloc(m->n);
+        m->t2.alloc(m->n);
+    }
+}
+
+void copy_csr_to_host(const CsrDev &A, int64_t *rp, int32_t *ci, void *v) {
+    GL_REQUIRE(rp && ci && v, GL_ERR_ARG, "output pointers must not be NULL");
+    GL_CUDA(cudaMemcpy(rp, A.rp.get(), (A.n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    GL_CUDA(cudaMemcpy(ci, A.ci.get(), A.nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    GL_CUDA(cudaMemcpy(v, A.v.get(), A.nnz * sizeof(double2), cudaMemcpyDeviceToHost));
+}
+
+}  // namespace
+
+extern "C" {
+
+gl_status gl_options_default(gl_options *o) {
+    if (!o) return GL_ERR_ARG;
+    o->tol = 1e-10;
+    o->maxit = 500;
+    o->cycles = 1;
+    o->max_coarse = 512;
+    o->max_levels = 10;
+    o->power_its = 20;
+    o->precision = GL_FP64;
+    o->inner_tol = 1e-5;
+    o->max_outer = 20;
+    o->check_every = 6;
+    return GL_OK;
+}
+
+const char *gl_last_error(void) { return last_error(); }
+
+gl_status gl_mesh_create(int dim, int n_per_side, double mu, const double *bhat, void *stream, gl_mesh *out) {
+    return guard([&] {
+        GL_REQUIRE(out, GL_ERR_ARG, "out must not be NULL");
+        *out = nullptr;
+        auto *m = new gl_mesh_s();
+        try {
+            mesh_create(m, dim, n_per_side, mu, bhat, as_stream(stream));
+        } catch (...) {
+            delete m;
+            throw;
+        }
+        *out = m;
+        return GL_OK;
+    });
+}
+
+gl_status gl_mesh_destroy(gl_mesh m) {
+    return guard([&] {
+        if (m) {
+            cudaDeviceSynchronize();
+            delete m;
+        }
+        return GL_OK;
+    });
+}
+
+gl_status gl_mesh_info(gl_mesh m, int64_t *n, int64_t *nnz, double *volumes_dev) {
+    return guard([&] {
+        GL_REQUIRE(m, GL_ERR_ARG, "mesh must not be NULL");
+        if (n) *n = m->n;
+        if (nnz) *nnz = m->khat.nnz;
+        if (volumes_dev)
+            GL_CUDA(cudaMemcpy(volumes_dev, m->vol.get(), m->n * sizeof(double), cudaMemcpyDeviceToDevice));
+        return GL_OK;
+    });
+}
+
+gl_status gl_mesh_nedges(gl_mesh m, int64_t *ne) {
+    return guard([&] {
+        GL_REQUIRE(m && ne, GL_ERR_ARG, "NULL argument");
+        *ne = m->nedges;
+        return GL_OK;
+    });
+}
+
+gl_status gl_mesh_edges(gl_mesh m, int32_t *ej, int32_t *ek, double *alpha, double *theta) {
+    return guard([&] {
+        GL_REQUIRE(m && ej && ek && alpha && theta, GL_ERR_ARG, "NULL argument");
+        size_t ne = (size_t)m->nedges;
+        GL_CUDA(cudaMemcpy(ej, m->ej.get(), ne * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        GL_CUDA(cudaMemcpy(ek, m->ek.get(), ne * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        GL_CUDA(cudaMemcpy(alpha, m->ealpha.get(), ne * sizeof(double), cudaMemcpyDeviceToHost));
+        GL_CUDA(cudaMemcpy(theta, m->etheta.get(), ne * sizeof(double), cudaMemcpyDeviceToHost));
+        return GL_OK;
+    });
+}
+
+gl_status gl_mesh_khat(gl_mesh m, int64_t *rp, int32_t *ci, void *v) {
+    return guard([&] {
+        GL_REQUIRE(m, GL_ERR_ARG, "mesh must not be NULL");
+        copy_csr_to_host(m->khat, rp, ci, v);
+        return GL_OK;
+    });
+}
+
+gl_status gl_residual(gl_mesh m, const void *psi, void *r, void *stream) {
+    return guard([&] {
+        GL_REQUIRE(m && psi && r, GL_ERR_ARG, "NULL argument");
+        GL_REQUIRE(psi != r, GL_ERR_ARG, "psi and r must not alias");
+        cudaStream_t s = as_stream(stream);
+        ensure_tmp(m);
+        permute_in(m->n, m->perm.get(), (const double2 *)psi, m->t0.get(), s);
+        residual_p(m, m->t0.get(), m->t1.get(), s);
+        permute_out(m->n, m->perm.get(), m->t1.get(), (double2 *)r, s);
+        return GL_OK;
+    });
+}
+
+gl_status gl_jacobian_apply(gl_mesh m, const void *psi, const void *phi, void *y, int precision, void *stream) {
+    return guard([&] {
+        GL_REQUIRE(m && psi && phi && y, GL_ERR_ARG, "NULL argument");
+        GL_REQUIRE(y != psi && y != phi, GL_ERR_ARG, "y must not alias psi or phi");
+        GL_REQUIRE(precision == GL_FP64 || precision == GL_MIXED, GL_ERR_ARG, "unknown precision");
+        cudaStream_t s = as_stream(stream);
+        ensure_tmp(m);
+        permute_in(m->n, m->perm.get(), (const double2 *)psi, m->t0.get(), s);
+        permute_in(m->n, m->perm.get(), (const double2 *)phi, m->t1.get(), s);
+        if (precision == GL_MIXED) {
+            mesh_ensure_fp32(m, s);
+            jacobian_apply_p32(m, m->t0.get(), m->t1.get(), m->t2.get(), s);
+        } else {
+            jacobian_apply_p(m, m->t0.get(), m->t1.get(), m->t2.get(), s);
+        }
+        permute_out(m->n, m->perm.get(), m->t2.get(), (double2 *)y, s);
+        return GL_OK;
+    });
+}
+
+gl_status gl_precond_setup(gl_mesh m, const void *psi, const gl_options *opt, void *stream, gl_prec *out) {
+    return guard([&] {
+        GL_REQUIRE(m && psi && out, GL_ERR_ARG, "NULL argument");
+        check_opts(opt);
+        *out = nullptr;
+        auto *p = new gl_prec_s();
+        try {
+            precond_setup(p, m, (const double2 *)psi, *opt, as_stream(stream));
+        } catch (...) {
+            cudaDeviceSynchronize();
+            delete p;
+            throw;
+        }
+        *out = p;
+        return GL_OK;
+    });
+}
+
+gl_status gl_precond_apply(gl_prec p, const void *x, void *z, void *stream) {
+    return guard([&] {
+        GL_REQUIRE(p && x && z, GL_ERR_ARG, "NULL argument");
+        GL_REQUIRE(x != z, GL_ERR_ARG, "x and z must not alias");
+        gl_mesh_s *m = p->mesh;
+        cudaStream_t s = as_stream(stream);
+        ensure_tmp(m);
+        permute_in(m->n, m->perm.get(), (const double2 *)x, m->t0.get(), s);
+        precond_apply_p(p, m->t0.get(), m->t1.get(), nullptr, s);
+        permute_out(m->n, m->perm.get(), m->t1.get(), (double2 *)z, s);
+        return GL_OK;
+    });
+}
+
+gl_status gl_precond_destroy(gl_prec p) {
+    return guard([&] {
+        if (p) {
+            cudaDeviceSynchronize();
+            delete p;
+        }
+        return GL_OK;
+    });
+}
+
+gl_status gl_precond_levels(gl_prec p, int *nlev) {
+    return guard([&] {
+        GL_REQUIRE(p && nlev, GL_ERR_ARG, "NULL argument");
+        *nlev = p->nlev;
+        return GL_OK;
+    });
+}
+
+gl_status gl_precond_level_info(gl_prec p, int l, int64_t *n, int64_t *nnz, int32_t *ncolors, int64_t *p_nnz,
+                                double *omega) {
+    return guard([&] {
+        GL_REQUIRE(p && l >= 0 && l < p->nlev, GL_ERR_ARG, "bad level");
+        const Level &L = p->L[l];
+        bool last = (l == p->nlev - 1);
+        if (n) *n = L.n;
+        if (nnz) *nnz = L.A_can.nnz;
+        if (ncolors) *ncolors = L.ncolors;
+        if (p_nnz) *p_nnz = last ? 0 : L.P_can.nnz;
+        if (omega) *omega = last ? 0.0 : L.omega;
+        return GL_OK;
+    });
+}
+
+gl_status gl_precond_level_aggregates(gl_prec p, int l, int32_t *agg) {
+    return guard([&] {
+        GL_REQUIRE(p && agg && l >= 0 && l < p->nlev - 1, GL_ERR_ARG, "bad level");
+        GL_CUDA(cudaMemcpy(agg, p->L[l].agg.get(), p->L[l].n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        return GL_OK;
+    });
+}
+
+gl_status gl_precond_level_colors(gl_prec p, int l, int32_t *col) {
+    return guard([&] {
+        GL_REQUIRE(p && col && l >= 0 && l < p->nlev, GL_ERR_ARG, "bad level");
+        GL_CUDA(cudaMemcpy(col, p->L[l].color.get(), p->L[l].n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        return GL_OK;
+    });
+}
+
+gl_status gl_precond_level_matrix(gl_prec p, int l, int64_t *rp, int32_t *ci, void *v) {
+    return guard([&] {
+        GL_REQUIRE(p && l >= 0 && l < p->nlev, GL_ERR_ARG, "bad level");
+        copy_csr_to_host(p->L[l].A_can, rp, ci, v);
+        return GL_OK;
+    });
+}
+
+gl_status gl_precond_level_P(gl_prec p, int l, int64_t *rp, int32_t *ci, void *v) {
+    return guard([&] {
+        GL_REQUIRE(p && l >= 0 && l < p->nlev - 1, GL_ERR_ARG, "bad level");
+        copy_csr_to_host(p->L[l].P_can, rp, ci, v);
+        return GL_OK;
+    });
+}
+
+gl_status gl_jacobian_solve(gl_mesh m, const void *psi, gl_prec prec, const void *b, void *x, const gl_options *opt,
+                            gl_solve_info *info, void *stream) {
+    return guard([&] {
+        GL_REQUIRE(m && psi && b && x, GL_ERR_ARG, "NULL argument");
+        check_opts(opt);
+        GL_REQUIRE(!prec || prec->mesh == m, GL_ERR_ARG, "preconditioner belongs to another mesh");
+        cudaStream_t s = as_stream(stream);
+        gl_solve_info inf{};
+        gl_prec_s *p = prec;
+        gl_prec_s *own = nullptr;
+        if (!p && opt->cycles > 0) {
+            auto t0 = std::chrono::steady_clock::now();
+            own = new gl_prec_s();
+            try {
+                precond_setup(own, m, (const double2 *)psi, *opt, s);
+            } catch (...) {
+                cudaDeviceSynchronize();
+                delete own;
+                throw;
+            }
+            p = own;
+            inf.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        }
+        gl_status st;
+        try {
+            ensure_tmp(m);
+            double2 *psi_p = p ? p->psi_p.get() : m->t0.get();
+            if (!p) permute_in(m->n, m->perm.get(), (const double2 *)psi, m->t0.get(), s);
+            permute_in(m->n, m->perm.get(), (const double2 *)b, m->t1.get(), s);
+            permute_in(m->n, m->perm.get(), (const double2 *)x, m->t2.get(), s);
+            st = jacobian_solve_p(m, p, psi_p, m->t1.get(), m->t2.get(), *opt, &inf, s);
+            permute_out(m->n, m->perm.get(), m->t2.get(), (double2 *)x, s);
+            GL_CUDA(cudaStreamSynchronize(s));
+        } catch (...) {
+            if (own) {
+                cudaDeviceSynchronize();
+                delete own;
+            }
+            throw;
+        }
+        if (own) delete own;
+        if (info) *info = inf;
+        if (st != GL_OK) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "solve stopped after %d iterations at relative residual %.3e", inf.iters,
+                     inf.true_relres);
+            set_error(buf);
+        }
+        return st;
+    });
+}
+
+gl_status gl_newton_step(gl_mesh m, void *psi, const gl_options *opt, gl_solve_info *info, double *gl_norm_out,
+                         void *stream) {
+    return guard([&] {
+        GL_REQUIRE(m && psi, GL_ERR_ARG, "NULL argument");
+        check_opts(opt);
+        cudaStream_t s = as_stream(stream);
+        int64_t n = m->n;
+        DBuf<double2> r(n), d(n);
+        GL_REQUIRE(gl_residual(m, psi, r.get(), stream) == GL_OK, GL_ERR_CUDA, last_error());
+        // ||GL||_R and the right-hand side -GL(psi)
+        std::vector<double2> hr(n);
+        std::vector<double> hv(n);
+        GL_CUDA(cudaMemcpyAsync(hr.data(), r.get(), n * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        GL_CUDA(cudaMemcpyAsync(hv.data(), m->vol.get(), n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GL_CUDA(cudaStreamSynchronize(s));
+        double g2 = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            g2 += hv[i] * (hr[i].x * hr[i].x + hr[i].y * hr[i].y);
+            hr[i].x = -hr[i].x;
+            hr[i].y = -hr[i].y;
+        }
+        if (gl_norm_out) *gl_norm_out = std::sqrt(g2);
+        GL_CUDA(cudaMemcpyAsync(r.get(), hr.data(), n * sizeof(double2), cudaMemcpyHostToDevice, s));
+        GL_CUDA(cudaMemsetAsync(d.get(), 0, n * sizeof(double2), s));
+        gl_status st = gl_jacobian_solve(m, psi, nullptr, r.get(), d.get(), opt, info, stream);
+        if (st != GL_OK && st != GL_ERR_NOT_CONVERGED) return st;
+        std::vector<double2> hp(n), hd(n);
+        GL_CUDA(cudaMemcpyAsync(hp.data(), psi, n * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        GL_CUDA(cudaMemcpyAsync(hd.data(), d.get(), n * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        GL_CUDA(cudaStreamSynchronize(s));
+        for (int64_t i = 0; i < n; ++i) {
+            hp[i].x += hd[i].x;
+            hp[i].y += hd[i].y;
+        }
+        GL_CUDA(cudaMemcpyAsync(psi, hp.data(), n * sizeof(double2), cudaMemcpyHostToDevice, s));
+        GL_CUDA(cudaStreamSynchronize(s));
+        return st;
+    });
+}
+
+gl_status gl_batch_solve(int count, const gl_mesh *meshes, const void *const *psi, const void *const *b,
+                         void *const *x, const gl_options *opt, gl_solve_info *infos, void *stream) {
+    return guard([&] {
+        GL_REQUIRE(count >= 0 && (count == 0 || (meshes && psi && b && x)), GL_ERR_ARG, "NULL argument");
+        check_opts(opt);
+        gl_status first = GL_OK;
+        for (int i = 0; i < count; ++i) {
+            gl_solve_info inf{};
+            gl_status st = gl_jacobian_solve(meshes[i], psi[i], nullptr, b[i], x[i], opt, &inf, stream);
+            if (infos) infos[i] = inf;
+            if (st != GL_OK && first == GL_OK) first = st;
+        }
+        return first;
+    });
+}
+
+gl_status gl_profile_begin(const char *kernel_class, int max_launches) {
+    return guard([&] {
+        GL_REQUIRE(max_launches >= 0 && max_launches <= (1 << 20), GL_ERR_ARG, "max_launches out of range");
+        Profiler &p = profiler();
+        GL_CUDA(cudaDeviceSynchronize());
+        for (auto e : p.ev) cudaEventDestroy(e);
+        p.ev.clear();
+        p.name = kernel_class ? kernel_class : "";
+        int slots = p.name.empty() ? 0 : max_launches;
+        p.ev.resize(2 * (size_t)slots);
+        for (auto &e : p.ev) GL_CUDA(cudaEventCreate(&e));
+        p.slot_bytes.assign(slots, 0.0);
+        p.free_slots.clear();
+        for (int i = slots - 1; i >= 0; --i) p.free_slots.push_back(i);
+        p.pending.clear();
+        p.capture = nullptr;
+        p.total_ms = p.total_bytes = 0;
+        p.timed = p.dropped = 0;
+        p.launches.store(0);
+        p.generation += 1;
+        p.active = true;
+        return GL_OK;
+    });
+}
+
+gl_status gl_profile_end(int64_t *launches, int64_t *timed, double *total_ms, double *alg_bytes) {
+    return guard([&] {
+        Profiler &p = profiler();
+        GL_REQUIRE(p.active, GL_ERR_ARG, "gl_profile_begin was not called");
+        GL_CUDA(cudaDeviceSynchronize());
+        p.harvest_direct();
+        if (launches) *launches = p.launches.load();
+        if (timed) *timed = p.timed;
+        if (total_ms) *total_ms = p.total_ms;
+        if (alg_bytes) *alg_bytes = p.total_bytes;
+        for (auto e : p.ev) cudaEventDestroy(e);
+        p.ev.clear();
+        p.free_slots.clear();
+        p.active = false;
+        p.name.clear();
+        p.generation += 1;
+        return GL_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// gl_internal.cuh -- handle layouts of gl_mesh / gl_prec and the internal entry
+// points shared between the translation units of the library.
+#pragma once
+
+#include "gl_common.cuh"
+
+struct gl_mesh_s {
+    int dim = 0, N = 0;
+    int64_t n = 0;
+    double h = 0, mu = 0, bhat[3] = {0, 0, 1};
+    // canonical (node-order) data
+    gl::CsrDev khat;                      // K-hat, columns ascending
+    gl::DBuf<double> vol;                 // |V_j|
+    int64_t nedges = 0;
+    gl::DBuf<int32_t> ej, ek;             // edges j < k, lexicographic
+    gl::DBuf<double> ealpha, etheta;
+    gl::DBuf<int32_t> color0;             // red-black colour of each node
+    // solve ordering: position p holds node perm[p]; red nodes occupy [0, nred)
+    int64_t nred = 0;
+    gl::DBuf<int32_t> perm, iperm;
+    gl::Sell<double2> K;                  // off-diagonals of K = D^-1 K-hat (solve ordering)
+    gl::DBuf<double> kdiag, volp;         // K_ii and |V_i| (solve ordering)
+    bool has32 = false;
+    gl::Sell<float2> K32;
+    gl::DBuf<float> kdiag32, volp32;
+    // scratch for the node-order public calls
+    gl::DBuf<double2> t0, t1, t2;
+};
+
+namespace gl {
+
+constexpr int MAX_LEVELS = 16;
+constexpr int MAX_COARSE_DENSE = 4096;
+
+struct Level {
+    int64_t n = 0;
+    int ncolors = 0;
+    std::vector<int64_t> cstart;    // colour c occupies solve positions [cstart[c], cstart[c+1])
+    std::vector<int64_t> cnnz;      // stored off-diagonals of the rows of each colour
+    // canonical numbering
+    CsrDev A_can;                   // Hermitian level operator (level 0: K-hat + 2 D |psi|^2)
+    DBuf<int32_t> agg;              // coarse node of each node (not on the coarsest level)
+    DBuf<int32_t> color;
+    DBuf<double> B;                 // near-null candidate
+    CsrDev P_can;                   // prolongator from level + 1
+    double rho = 0, omega = 0;
+    // solve ordering (colour-major)
+    DBuf<int32_t> perm_own, iperm_own;  // coarse levels own theirs; level 0 uses the mesh's
+    const int32_t *perm = nullptr, *iperm = nullptr;
+    Sell<double2> A_own;            // coarse levels: off-diagonals of A
+    const Sell<double2> *A = nullptr;  // level 0 points at the mesh's K (row-scaled)
+    DBuf<double> diag;              // level 0: K_ii + 2|psi_i|^2; else A_ii
+    Sell<double2> P, PH;            // permuted prolongator / its adjoint
+    CsrG<double2> Ag, PHg;          // grouped-CSR forms: coarse-level A (ell >= 1) and P^H
+    DBuf<int64_t> cstart_dev;       // cstart on the device (cooperative sweeps)
+    DBuf<unsigned> barrier;         // grid-barrier state of the cooperative sweeps
+    DBuf<double2> b, x, r;          // level vectors (solve ordering)
+    DBuf<double2> Ainv;             // coarsest: dense inverse, row-major
+    // FP32 copies (mixed precision)
+    Sell<float2> A32_own;
+    const Sell<float2> *A32 = nullptr;
+    DBuf<float> diag32;
+    Sell<float2> P32, PH32;
+    CsrG<float2> Ag32, PHg32;
+    DBuf<float2> b32, x32, r32;
+    DBuf<float2> Ainv32;            // unused: the coarsest solve stays FP64
+};
+
+}  // namespace gl
+
+struct gl_prec_s {
+    int64_t uid = 0;                  // unique per handle (keys cached CUDA graphs)
+    gl_mesh_s *mesh = nullptr;
+    gl::DBuf<int> err;                // set by a device-side wait that ran out
+    int nlev = 0;
+    int cycles = 1;
+    bool has32 = false;
+    gl::Level L[gl::MAX_LEVELS];
+    gl::DBuf<double2> psi_p;          // psi in solve ordering
+    gl::DBuf<double2> cyc_r, cyc_e;   // work vectors for k > 1 cycles
+    gl::DBuf<float2> cyc_r32, cyc_e32;
+    gl::DBuf<float2> mp_in, mp_out;   // FP32 V-cycle input/output inside FP64 MINRES
+    gl::DBuf<double2> coarse_b64, coarse_x64;  // FP64 coarsest solve in mixed mode
+};
+
+namespace gl {
+
+// gl_mesh.cu
+void mesh_create(gl_mesh_s *m, int dim, int N, double mu, const double *bhat, cudaStream_t s);
+void mesh_ensure_fp32(gl_mesh_s *m, cudaStream_t s);
+template <typename C>
+void build_sell(int64_t nrows, int64_t ncols, const int32_t *perm, const int32_t *icol, const CsrDev &A,
+                const double *row_scale, bool drop_diag, Sell<C> &out, double *diag_out, cudaStream_t s);
+void to_float(const double *in, float *out, int64_t n, cudaStream_t s);
+template <typename C>
+void build_csrg(int64_t nrows, const int32_t *perm, const int32_t *icol, const CsrDev &A, bool drop_diag,
+                CsrG<C> &out, double *diag_out, cudaStream_t s);
+
+// gl_setup.cu
+void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_options &o, cudaStream_t s);
+void precond_ensure_fp32(gl_prec_s *p, cudaStream_t s);
+
+// gl_ops.cu (solve ordering)
+void permute_in(int64_t n, const int32_t *perm, const double2 *nat, double2 *sol, cudaStream_t s);
+void permute_out(int64_t n, const int32_t *perm, const double2 *sol, double2 *nat, cudaStream_t s);
+void jacobian_apply_p(const gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s);
+void jacobian_apply_p32(const gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s);
+void residual_p(const gl_mesh_s *m, const double2 *psi, double2 *r, cudaStream_t s);
+
+// gl_vcycle.cu: z = R_k v in solve ordering; `stop` (nullable) is a device flag
+// that turns every kernel into a no-op when nonzero.
+void precond_apply_p(gl_prec_s *p, const double2 *v, double2 *z, const int *stop, cudaStream_t s);
+void precond_apply_p32(gl_prec_s *p, const float2 *v, float2 *z, const int *stop, cudaStream_t s);
+// z = R_k v with FP64 vectors and an FP32 V-cycle
+void precond_apply_p64_via32(gl_prec_s *p, const double2 *v, double2 *z, const int *stop, cudaStream_t s);
+
+// gl_solve.cu
+gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, const double2 *b_p, double2 *x_p,
+                           const gl_options &o, gl_solve_info *info, cudaStream_t s);
+
+}  // namespace gl

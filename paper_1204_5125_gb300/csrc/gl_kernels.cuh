@@ -1,0 +1,76 @@
+// gl_kernels.cuh -- device building blocks shared by the operator, V-cycle and
+// Krylov kernels.
+#pragma once
+
+#include "gl_common.cuh"
+
+namespace gl {
+
+// sum_k A[p][k] * x[col[p][k]] over the stored off-diagonals of row p of a sliced
+// ELL matrix (a warp reads 32 consecutive entries per k)
+template <typename C, typename X>
+__device__ __forceinline__ C sell_row(const SellView<C> &A, int64_t p, const X *__restrict__ x) {
+    int64_t s = p >> 5;
+    int lane = (int)(p & 31);
+    int64_t beg = __ldg(A.sptr + s);
+    int w = (int)((__ldg(A.sptr + s + 1) - beg) >> 5);
+    const int32_t *cp = A.col + beg + lane;
+    const C *vp = A.val + beg + lane;
+    C acc;
+    acc.x = 0;
+    acc.y = 0;
+#pragma unroll 4
+    for (int k = 0; k < w; ++k) {
+        int32_t c = __ldg(cp + (int64_t)k * SELL_C);
+        C a = vp[(int64_t)k * SELL_C];
+        X xv = x[c];
+        C xc;
+        xc.x = xv.x;
+        xc.y = xv.y;
+        cfma(acc, a, xc);
+    }
+    return acc;
+}
+
+// same, over the columns below `lo` only: on the first Gauss-Seidel pass from a
+// zero guess the colours before the current one hold values, the current colour
+// has no couplings to itself (a proper colouring) and the later colours are
+// still zero.  Padding entries point at the row itself, which lies in the
+// current colour, so they are skipped too (its x is not yet written).
+template <typename C, typename X>
+__device__ __forceinline__ C sell_row_before(const SellView<C> &A, int64_t p, const X *__restrict__ x, int64_t lo) {
+    int64_t s = p >> 5;
+    int lane = (int)(p & 31);
+    int64_t beg = __ldg(A.sptr + s);
+    int w = (int)((__ldg(A.sptr + s + 1) - beg) >> 5);
+    const int32_t *cp = A.col + beg + lane;
+    const C *vp = A.val + beg + lane;
+    C acc;
+    acc.x = 0;
+    acc.y = 0;
+    for (int k = 0; k < w; ++k) {
+        int32_t c = __ldg(cp + (int64_t)k * SELL_C);
+        if (c >= lo) continue;
+        C a = vp[(int64_t)k * SELL_C];
+        X xv = x[c];
+        C xc;
+        xc.x = xv.x;
+        xc.y = xv.y;
+        cfma(acc, a, xc);
+    }
+    return acc;
+}
+
+// Jacobian row given the off-diagonal sum: acc + (K_ii - 1 + 2|psi|^2) phi + psi^2 conj(phi)
+template <typename C, typename R>
+__device__ __forceinline__ C jacobian_epilogue(C acc, R kd, C ps, C ph) {
+    R a2 = ps.x * ps.x + ps.y * ps.y;
+    R d = kd - (R)1 + (R)2 * a2;
+    C p2 = mk(ps.x * ps.x - ps.y * ps.y, (R)2 * ps.x * ps.y);  // psi^2
+    C r;
+    r.x = acc.x + d * ph.x + (p2.x * ph.x + p2.y * ph.y);  // psi^2 conj(phi): (a+ib)(c-id)
+    r.y = acc.y + d * ph.y + (p2.y * ph.x - p2.x * ph.y);
+    return r;
+}
+
+}  // namespace gl

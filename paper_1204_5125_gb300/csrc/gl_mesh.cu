@@ -1,0 +1,627 @@
+// gl_mesh.cu -- assembly of the finite-volume discretisation (Sec. 3 of
+// Schloemer & Vanroose) on structured square/cube meshes, entirely on the GPU:
+//   * per-simplex edge coefficients: the cotangent formula for triangles (Remark
+//     after Cor. "simplex") and the SPD system M alpha = b, M_ij = <e_i,e_j>^2,
+//     b_i = |S| ||e_i||^2 for tetrahedra (Cor. "simplex"),
+//   * alpha_jk summed over the simplices adjacent to edge jk (Eq. fhat),
+//   * control volumes |V_j| (Eq. mass lumping) and link phases
+//     theta_jk = integral of A from x_j to x_k (Eq. link variable, midpoint rule,
+//     exact for the affine A = (mu/2) bhat x x),
+//   * K-hat (Eq. discr kin energy, Remark rmk:dk) as a CSR in node order, and
+//     K = D^-1 K-hat as a sliced-ELL in the red-black solve ordering.
+#include "gl_internal.cuh"
+
+namespace gl {
+
+// ---------------------------------------------------------------- lattice geometry
+struct Lattice {
+    int dim, N;
+    double h, mu, b[3];
+    __device__ __host__ int64_t id(int i, int j, int k) const { return (int64_t)i + (int64_t)N * ((int64_t)j + (int64_t)N * k); }
+    __device__ __host__ void coords(int64_t v, int &i, int &j, int &k) const {
+        i = (int)(v % N);
+        int64_t r = v / N;
+        j = (int)(r % N);
+        k = (int)(r / N);
+    }
+    __device__ void pos(int i, int j, int k, double *x) const {
+        x[0] = -0.5 + i * h;
+        x[1] = -0.5 + j * h;
+        x[2] = (dim == 3) ? -0.5 + k * h : 0.0;
+    }
+};
+
+// local vertex offsets (0/1 per axis) of the simplices of one cell
+// 2D: two triangles split along the (0,0)-(1,1) diagonal
+__constant__ int c_tri[2][3][2] = {{{0, 0}, {1, 0}, {1, 1}}, {{0, 0}, {1, 1}, {0, 1}}};
+// 3D: Kuhn tetrahedra, one per axis order, walking from (0,0,0) to (1,1,1)
+__constant__ int c_kuhn_order[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+__device__ void simplex_local(int dim, int s, int v, int off[3]) {
+    off[0] = off[1] = off[2] = 0;
+    if (dim == 2) {
+        off[0] = c_tri[s][v][0];
+        off[1] = c_tri[s][v][1];
+        return;
+    }
+    for (int st = 0; st < v; ++st) off[c_kuhn_order[s][st]] += 1;
+}
+
+// edge e of a simplex with d+1 vertices: (0,1),(0,2),..,(0,d),(1,2),...
+__device__ void simplex_edge(int dim, int e, int &a, int &b) {
+    int q = 0;
+    for (int i = 0; i <= dim; ++i)
+        for (int j = i + 1; j <= dim; ++j) {
+            if (q == e) {
+                a = i;
+                b = j;
+                return;
+            }
+            ++q;
+        }
+}
+
+// Edge coefficients of one simplex (vertices p, 3 doubles each).
+__device__ void simplex_alpha(int dim, const double p[4][3], double *alpha) {
+    if (dim == 2) {
+        // 1/2 t / sqrt(1 - t^2), t = cosine of the angle opposite the edge
+        for (int e = 0; e < 3; ++e) {
+            int a, b;
+            simplex_edge(2, e, a, b);
+            int k = 3 - a - b;
+            double u0 = p[a][0] - p[k][0], u1 = p[a][1] - p[k][1];
+            double v0 = p[b][0] - p[k][0], v1 = p[b][1] - p[k][1];
+            double t = (u0 * v0 + u1 * v1) / sqrt((u0 * u0 + u1 * u1) * (v0 * v0 + v1 * v1));
+            alpha[e] = 0.5 * t / sqrt(1.0 - t * t);
+        }
+        return;
+    }
+    double ev[6][3];
+    for (int e = 0; e < 6; ++e) {
+        int a, b;
+        simplex_edge(3, e, a, b);
+        for (int c = 0; c < 3; ++c) ev[e][c] = p[b][c] - p[a][c];
+    }
+    double e1[3], e2[3], e3[3];
+    for (int c = 0; c < 3; ++c) {
+        e1[c] = p[1][c] - p[0][c];
+        e2[c] = p[2][c] - p[0][c];
+        e3[c] = p[3][c] - p[0][c];
+    }
+    double det = e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) - e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
+                 e1[2] * (e2[0] * e3[1] - e2[1] * e3[0]);
+    double vol = fabs(det) / 6.0;
+    double M[6][6], rhs[6];
+    for (int i = 0; i < 6; ++i) {
+        for (int j = 0; j < 6; ++j) {
+            double d = ev[i][0] * ev[j][0] + ev[i][1] * ev[j][1] + ev[i][2] * ev[j][2];
+            M[i][j] = d * d;
+        }
+        rhs[i] = vol * (ev[i][0] * ev[i][0] + ev[i][1] * ev[i][1] + ev[i][2] * ev[i][2]);
+    }
+    // Cholesky M = L L^T (in place, lower), then two triangular solves
+    for (int j = 0; j < 6; ++j) {
+        double s = M[j][j];
+        for (int k = 0; k < j; ++k) s -= M[j][k] * M[j][k];
+        double l = sqrt(s);
+        M[j][j] = l;
+        for (int i = j + 1; i < 6; ++i) {
+            double t = M[i][j];
+            for (int k = 0; k < j; ++k) t -= M[i][k] * M[j][k];
+            M[i][j] = t / l;
+        }
+    }
+    double y[6];
+    for (int i = 0; i < 6; ++i) {
+        double s = rhs[i];
+        for (int k = 0; k < i; ++k) s -= M[i][k] * y[k];
+        y[i] = s / M[i][i];
+    }
+    for (int i = 5; i >= 0; --i) {
+        double s = y[i];
+        for (int k = i + 1; k < 6; ++k) s -= M[k][i] * alpha[k];
+        alpha[i] = s / M[i][i];
+    }
+}
+
+// alphaT[cell][simplex][edge] for every cell of the lattice
+__global__ void k_simplex_alpha(Lattice L, int64_t ncell, double *alphaT) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int M = L.N - 1;
+    int i = (int)(c % M), j = (int)((c / M) % M), k = (L.dim == 3) ? (int)(c / ((int64_t)M * M)) : 0;
+    int ns = (L.dim == 2) ? 2 : 6, ne = (L.dim == 2) ? 3 : 6;
+    for (int s = 0; s < ns; ++s) {
+        double p[4][3];
+        for (int v = 0; v <= L.dim; ++v) {
+            int off[3];
+            simplex_local(L.dim, s, v, off);
+            L.pos(i + off[0], j + off[1], k + off[2], p[v]);
+        }
+        double al[6];
+        simplex_alpha(L.dim, p, al);
+        for (int e = 0; e < ne; ++e) alphaT[(c * ns + s) * ne + e] = al[e];
+    }
+}
+
+// positive directions of the candidate edges (2D: x, y, xy; 3D: x, y, z, xy, xz, yz, xyz)
+__constant__ int c_dir2[3][3] = {{1, 0, 0}, {0, 1, 0}, {1, 1, 0}};
+__constant__ int c_dir3[7][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}};
+
+__device__ void dir_vec(int dim, int d, int v[3]) {
+    for (int c = 0; c < 3; ++c) v[c] = (dim == 2) ? c_dir2[d][c] : c_dir3[d][c];
+}
+
+// Eq. fhat: alpha of edge (node, node + dir) = sum over the simplices containing
+// it, gathered in a fixed order (cells by local offset, simplices, edges).
+__global__ void k_edge_alpha(Lattice L, int64_t n, int ndir, const double *alphaT, double *ealpha) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * ndir) return;
+    int64_t v = t / ndir;
+    int d = (int)(t % ndir);
+    int i, j, k;
+    L.coords(v, i, j, k);
+    int dv[3];
+    dir_vec(L.dim, d, dv);
+    int x0[3] = {i, j, k};
+    double acc = 0;
+    bool inside = (i + dv[0] < L.N) && (j + dv[1] < L.N) && (L.dim == 2 || k + dv[2] < L.N);
+    if (inside) {
+        int M = L.N - 1;
+        int ns = (L.dim == 2) ? 2 : 6, ne = (L.dim == 2) ? 3 : 6;
+        int ncand = 1 << L.dim;
+        for (int q = 0; q < ncand; ++q) {
+            int va[3] = {q & 1, (q >> 1) & 1, (L.dim == 3) ? (q >> 2) & 1 : 0};
+            bool ok = true;
+            int cc[3];
+            for (int a = 0; a < L.dim; ++a) {
+                if (va[a] + dv[a] > 1) ok = false;
+                cc[a] = x0[a] - va[a];
+                if (cc[a] < 0 || cc[a] >= M) ok = false;
+            }
+            if (!ok) continue;
+            int64_t cell = (int64_t)cc[0] + (int64_t)M * ((int64_t)cc[1] + (L.dim == 3 ? (int64_t)M * cc[2] : 0));
+            for (int s = 0; s < ns; ++s)
+                for (int e = 0; e < ne; ++e) {
+                    int a, b;
+                    simplex_edge(L.dim, e, a, b);
+                    int oa[3], ob[3];
+                    simplex_local(L.dim, s, a, oa);
+                    simplex_local(L.dim, s, b, ob);
+                    bool fwd = true, bwd = true;
+                    for (int c = 0; c < 3; ++c) {
+                        if (oa[c] != va[c] || ob[c] != va[c] + dv[c]) fwd = false;
+                        if (ob[c] != va[c] || oa[c] != va[c] + dv[c]) bwd = false;
+                    }
+                    if (fwd || bwd) acc += alphaT[(cell * ns + s) * ne + e];
+                }
+        }
+    }
+    ealpha[t] = acc;
+}
+
+// Neighbour list of a node: up to 2 ndir candidate edges, in ascending column order.
+struct Nbr {
+    int64_t col;
+    double alpha;
+};
+
+__device__ int node_neighbours(const Lattice &L, int64_t v, int ndir, const double *ealpha, double cut, Nbr *out) {
+    int i, j, k;
+    L.coords(v, i, j, k);
+    int x0[3] = {i, j, k};
+    int cnt = 0;
+    for (int d = 0; d < ndir; ++d) {
+        int dv[3];
+        dir_vec(L.dim, d, dv);
+        int64_t off = (int64_t)dv[0] + (int64_t)L.N * ((int64_t)dv[1] + (int64_t)L.N * dv[2]);
+        // forward edge (v, v + dir)
+        double a = ealpha[v * ndir + d];
+        if (fabs(a) > cut) out[cnt++] = Nbr{v + off, a};
+        // backward edge (v - dir, v)
+        bool ok = true;
+        for (int c = 0; c < L.dim; ++c)
+            if (x0[c] - dv[c] < 0) ok = false;
+        if (ok) {
+            double b = ealpha[(v - off) * ndir + d];
+            if (fabs(b) > cut) out[cnt++] = Nbr{v - off, b};
+        }
+    }
+    for (int s = 1; s < cnt; ++s) {  // insertion sort by column
+        Nbr key = out[s];
+        int r = s - 1;
+        while (r >= 0 && out[r].col > key.col) {
+            out[r + 1] = out[r];
+            --r;
+        }
+        out[r + 1] = key;
+    }
+    return cnt;
+}
+
+__global__ void k_row_len(Lattice L, int64_t n, int ndir, const double *ealpha, double cut, int64_t *len,
+                          int64_t *fwd) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    Nbr nb[16];
+    int c = node_neighbours(L, v, ndir, ealpha, cut, nb);
+    len[v] = c + 1;
+    int64_t f = 0;
+    for (int s = 0; s < c; ++s) f += (nb[s].col > v);
+    fwd[v] = f;
+}
+
+// integral of A = (mu/2) bhat x x along the straight edge from xa to xb (midpoint rule)
+__device__ double edge_phase(const Lattice &L, const double *xa, const double *xb) {
+    double m[3], d[3];
+    for (int c = 0; c < 3; ++c) {
+        m[c] = 0.5 * (xa[c] + xb[c]);
+        d[c] = xb[c] - xa[c];
+    }
+    double A0 = 0.5 * L.mu * (L.b[1] * m[2] - L.b[2] * m[1]);
+    double A1 = 0.5 * L.mu * (L.b[2] * m[0] - L.b[0] * m[2]);
+    double A2 = 0.5 * L.mu * (L.b[0] * m[1] - L.b[1] * m[0]);
+    return A0 * d[0] + A1 * d[1] + A2 * d[2];
+}
+
+// CSR row of K-hat: K-hat_vv = sum alpha, K-hat_vk = -alpha exp(-i theta_vk)
+__global__ void k_fill_khat(Lattice L, int64_t n, int ndir, const double *ealpha, double cut, const int64_t *rp,
+                            int32_t *ci, double2 *val, const int64_t *erp, int32_t *ej, int32_t *ek, double *eal,
+                            double *eth) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    Nbr nb[16];
+    int c = node_neighbours(L, v, ndir, ealpha, cut, nb);
+    int i, j, k;
+    L.coords(v, i, j, k);
+    double xv[3];
+    L.pos(i, j, k, xv);
+    int64_t q = rp[v], e = erp[v];
+    double diag = 0;
+    bool diag_done = false;
+    for (int s = 0; s < c; ++s) diag += nb[s].alpha;
+    for (int s = 0; s < c; ++s) {
+        if (!diag_done && nb[s].col > v) {
+            ci[q] = (int32_t)v;
+            val[q++] = make_double2(diag, 0.0);
+            diag_done = true;
+        }
+        int a, b, cc;
+        L.coords(nb[s].col, a, b, cc);
+        double xk[3];
+        L.pos(a, b, cc, xk);
+        double th = edge_phase(L, xv, xk);
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        ci[q] = (int32_t)nb[s].col;
+        val[q++] = make_double2(-nb[s].alpha * cs, nb[s].alpha * sn);
+        if (nb[s].col > v) {
+            ej[e] = (int32_t)v;
+            ek[e] = (int32_t)nb[s].col;
+            eal[e] = nb[s].alpha;
+            eth[e] = th;
+            ++e;
+        }
+    }
+    if (!diag_done) {
+        ci[q] = (int32_t)v;
+        val[q] = make_double2(diag, 0.0);
+    }
+}
+
+__global__ void k_volumes(Lattice L, int64_t n, double *vol) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int i, j, k;
+    L.coords(v, i, j, k);
+    int nb = (i == 0 || i == L.N - 1) + (j == 0 || j == L.N - 1);
+    if (L.dim == 3) nb += (k == 0 || k == L.N - 1);
+    double hd = (L.dim == 2) ? L.h * L.h : L.h * L.h * L.h;
+    vol[v] = hd / (double)(1 << nb);
+}
+
+// red-black colour of each lattice node: (i + j + k) mod 2
+__global__ void k_lattice_parity(Lattice L, int64_t n, int32_t *color, int64_t *is_red) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int i, j, k;
+    L.coords(v, i, j, k);
+    int c = (i + j + k) & 1;
+    color[v] = c;
+    is_red[v] = (c == 0);
+}
+
+// solve ordering: red nodes (ascending) first, then black nodes (ascending)
+__global__ void k_rb_perm(int64_t n, const int32_t *color, const int64_t *red_rank, int64_t nred, int32_t *perm,
+                          int32_t *iperm) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int64_t p = (color[v] == 0) ? red_rank[v] : nred + (v - red_rank[v]);
+    perm[p] = (int32_t)v;
+    iperm[v] = (int32_t)p;
+}
+
+__global__ void k_permute_real(int64_t n, const int32_t *perm, const double *in, double *out) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < n) out[p] = in[perm[p]];
+}
+
+// ---------------------------------------------------------------- sliced ELL builder
+__global__ void k_sell_rowlen(int64_t nrows, const int32_t *perm, const int64_t *rp, const int32_t *ci, bool drop_diag,
+                              int32_t *len) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= nrows) return;
+    int64_t r = perm ? perm[p] : p;
+    int64_t l = rp[r + 1] - rp[r];
+    if (drop_diag)
+        for (int64_t q = rp[r]; q < rp[r + 1]; ++q)
+            if (ci[q] == r) --l;
+    len[p] = (int32_t)l;
+}
+
+__global__ void k_sell_width(int64_t nrows, int64_t nslices, const int32_t *len, int64_t *ssize) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= nslices) return;
+    int w = 0;
+    for (int l = 0; l < SELL_C; ++l) {
+        int64_t p = s * SELL_C + l;
+        if (p < nrows) w = max(w, len[p]);
+    }
+    ssize[s] = (int64_t)w * SELL_C;
+}
+
+template <typename C>
+__global__ void k_sell_fill(int64_t nrows, int64_t ncols, const int32_t *perm, const int32_t *icol, const int64_t *rp,
+                            const int32_t *ci, const double2 *v, const double *row_scale, bool drop_diag,
+                            const int64_t *sptr, int32_t *scol, C *sval, double *diag_out) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= nrows) return;
+    int64_t r = perm ? perm[p] : p;
+    int64_t s = p / SELL_C;
+    int lane = (int)(p % SELL_C);
+    int64_t base = sptr[s] + lane;
+    int w = (int)((sptr[s + 1] - sptr[s]) / SELL_C);
+    double sc = row_scale ? 1.0 / row_scale[r] : 1.0;
+    int k = 0;
+    double dg = 0;
+    for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
+        int64_t c = ci[q];
+        double2 a = v[q];
+        if (drop_diag && c == r) {
+            dg = a.x * sc;
+            continue;
+        }
+        scol[base + (int64_t)k * SELL_C] = icol ? icol[c] : (int32_t)c;
+        C val;
+        val.x = a.x * sc;
+        val.y = a.y * sc;
+        sval[base + (int64_t)k * SELL_C] = val;
+        ++k;
+    }
+    int32_t pad = (int32_t)(p < ncols ? p : ncols - 1);
+    for (; k < w; ++k) {
+        scol[base + (int64_t)k * SELL_C] = pad;
+        C z;
+        z.x = 0;
+        z.y = 0;
+        sval[base + (int64_t)k * SELL_C] = z;
+    }
+    if (diag_out) diag_out[p] = dg;
+}
+
+template <typename C>
+void build_sell(int64_t nrows, int64_t ncols, const int32_t *perm, const int32_t *icol, const CsrDev &A,
+                const double *row_scale, bool drop_diag, Sell<C> &out, double *diag_out, cudaStream_t s) {
+    out.nrows = nrows;
+    out.nslices = (nrows + SELL_C - 1) / SELL_C;
+    DBuf<int32_t> len(nrows > 0 ? nrows : 1);
+    out.sptr.alloc(out.nslices + 1);
+    k_sell_rowlen<<<grid_for(nrows, 256), 256, 0, s>>>(nrows, perm, A.rp.get(), A.ci.get(), drop_diag, len.get());
+    GL_LAUNCH_CHECK();
+    k_sell_width<<<grid_for(out.nslices, 256), 256, 0, s>>>(nrows, out.nslices, len.get(), out.sptr.get());
+    GL_LAUNCH_CHECK();
+    scan_exclusive(out.sptr.get(), out.sptr.get(), out.nslices, true, s);
+    int64_t total = 0;
+    GL_CUDA(cudaMemcpyAsync(&total, out.sptr.get() + out.nslices, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaStreamSynchronize(s));
+    out.nnz_stored = total;
+    out.nnz_real = A.nnz - (drop_diag ? nrows : 0);
+    out.col.alloc(total > 0 ? total : 1);
+    out.val.alloc(total > 0 ? total : 1);
+    k_sell_fill<C><<<grid_for(nrows, 256), 256, 0, s>>>(nrows, ncols, perm, icol, A.rp.get(), A.ci.get(), A.v.get(),
+                                                        row_scale, drop_diag, out.sptr.get(), out.col.get(),
+                                                        out.val.get(), diag_out);
+    GL_LAUNCH_CHECK();
+    GL_CUDA(cudaStreamSynchronize(s));
+}
+
+template void build_sell<double2>(int64_t, int64_t, const int32_t *, const int32_t *, const CsrDev &, const double *,
+                                  bool, Sell<double2> &, double *, cudaStream_t);
+template void build_sell<float2>(int64_t, int64_t, const int32_t *, const int32_t *, const CsrDev &, const double *,
+                                 bool, Sell<float2> &, double *, cudaStream_t);
+
+// ---------------------------------------------------------------- grouped CSR builder
+__global__ void k_csrg_len(int64_t nrows, const int32_t *perm, const int64_t *rp, const int32_t *ci, bool drop_diag,
+                           int64_t *len) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= nrows) return;
+    int64_t r = perm ? perm[p] : p;
+    int64_t l = rp[r + 1] - rp[r];
+    if (drop_diag)
+        for (int64_t q = rp[r]; q < rp[r + 1]; ++q)
+            if (ci[q] == r) --l;
+    len[p] = l;
+}
+
+template <typename C>
+__global__ void k_csrg_fill(int64_t nrows, const int32_t *perm, const int32_t *icol, const int64_t *rp,
+                            const int32_t *ci, const double2 *v, bool drop_diag, const int64_t *orp, int32_t *ocol,
+                            C *oval, double *diag_out) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= nrows) return;
+    int64_t r = perm ? perm[p] : p;
+    int64_t o = orp[p];
+    double dg = 0;
+    for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
+        int64_t c = ci[q];
+        if (drop_diag && c == r) {
+            dg = v[q].x;
+            continue;
+        }
+        ocol[o] = icol ? icol[c] : (int32_t)c;
+        C val;
+        val.x = v[q].x;
+        val.y = v[q].y;
+        oval[o] = val;
+        ++o;
+    }
+    if (diag_out) diag_out[p] = dg;
+}
+
+template <typename C>
+void build_csrg(int64_t nrows, const int32_t *perm, const int32_t *icol, const CsrDev &A, bool drop_diag,
+                CsrG<C> &out, double *diag_out, cudaStream_t s) {
+    out.nrows = nrows;
+    DBuf<int64_t> len(nrows + 1);
+    k_csrg_len<<<grid_for(nrows, 256), 256, 0, s>>>(nrows, perm, A.rp.get(), A.ci.get(), drop_diag, len.get());
+    GL_LAUNCH_CHECK();
+    out.rp.alloc(nrows + 1);
+    scan_exclusive(len.get(), out.rp.get(), nrows, true, s);
+    GL_CUDA(cudaMemcpyAsync(&out.nnz, out.rp.get() + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaStreamSynchronize(s));
+    out.col.alloc(out.nnz > 0 ? out.nnz : 1);
+    out.val.alloc(out.nnz > 0 ? out.nnz : 1);
+    k_csrg_fill<C><<<grid_for(nrows, 256), 256, 0, s>>>(nrows, perm, icol, A.rp.get(), A.ci.get(), A.v.get(),
+                                                        drop_diag, out.rp.get(), out.col.get(), out.val.get(),
+                                                        diag_out);
+    GL_LAUNCH_CHECK();
+    GL_CUDA(cudaStreamSynchronize(s));
+    // lanes per row: the power of two nearest a quarter of the mean row length
+    double avg = nrows > 0 ? (double)out.nnz / nrows : 0;
+    int G = 1;
+    while (G < 32 && 2 * G * 4 <= avg * 1.5) G *= 2;
+    out.G = G;
+}
+
+template void build_csrg<double2>(int64_t, const int32_t *, const int32_t *, const CsrDev &, bool, CsrG<double2> &,
+                                  double *, cudaStream_t);
+template void build_csrg<float2>(int64_t, const int32_t *, const int32_t *, const CsrDev &, bool, CsrG<float2> &,
+                                 double *, cudaStream_t);
+
+__global__ void k_d2f(int64_t n, const double *in, float *out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
+}
+void to_float(const double *in, float *out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    k_d2f<<<grid_for(n, 256), 256, 0, s>>>(n, in, out);
+    GL_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------- mesh creation
+void mesh_create(gl_mesh_s *m, int dim, int N, double mu, const double *bhat, cudaStream_t s) {
+    GL_REQUIRE(dim == 2 || dim == 3, GL_ERR_ARG, "dim must be 2 or 3");
+    GL_REQUIRE(N >= 2, GL_ERR_ARG, "n_per_side must be >= 2");
+    double nd = (dim == 2) ? (double)N * N : (double)N * N * N;
+    GL_REQUIRE(nd < 2147483647.0, GL_ERR_ARG, "too many nodes for int32 indices");
+    Lattice L;
+    L.dim = dim;
+    L.N = N;
+    L.h = 1.0 / (N - 1);
+    L.mu = mu;
+    double b[3] = {0, 0, 1};
+    if (bhat) {
+        double nb = std::sqrt(bhat[0] * bhat[0] + bhat[1] * bhat[1] + bhat[2] * bhat[2]);
+        GL_REQUIRE(nb > 0, GL_ERR_ARG, "bhat must be nonzero");
+        for (int c = 0; c < 3; ++c) b[c] = bhat[c] / nb;
+    }
+    for (int c = 0; c < 3; ++c) L.b[c] = m->bhat[c] = b[c];
+    m->dim = dim;
+    m->N = N;
+    m->h = L.h;
+    m->mu = mu;
+    int64_t n = (int64_t)nd;
+    m->n = n;
+    int ndir = (dim == 2) ? 3 : 7;
+
+    // per-simplex coefficients, then per-edge sums
+    int64_t ncell = (dim == 2) ? (int64_t)(N - 1) * (N - 1) : (int64_t)(N - 1) * (N - 1) * (N - 1);
+    int ns = (dim == 2) ? 2 : 6, ne = (dim == 2) ? 3 : 6;
+    DBuf<double> ealpha(n * ndir);
+    {
+        DBuf<double> alphaT(ncell * ns * ne > 0 ? ncell * ns * ne : 1);
+        if (ncell > 0) {
+            k_simplex_alpha<<<grid_for(ncell, 128), 128, 0, s>>>(L, ncell, alphaT.get());
+            GL_LAUNCH_CHECK();
+        }
+        k_edge_alpha<<<grid_for(n * ndir, 256), 256, 0, s>>>(L, n, ndir, alphaT.get(), ealpha.get());
+        GL_LAUNCH_CHECK();
+        GL_CUDA(cudaStreamSynchronize(s));
+    }
+    double amax = reduce_max_abs(ealpha.get(), n * ndir, s);
+    double cut = 1e-12 * amax;
+
+    // K-hat CSR in node order, plus the edge list
+    DBuf<int64_t> len(n + 1), fwd(n + 1);
+    k_row_len<<<grid_for(n, 128), 128, 0, s>>>(L, n, ndir, ealpha.get(), cut, len.get(), fwd.get());
+    GL_LAUNCH_CHECK();
+    CsrDev &K = m->khat;
+    K.n = K.m = n;
+    K.rp.alloc(n + 1);
+    scan_exclusive(len.get(), K.rp.get(), n, true, s);
+    GL_CUDA(cudaMemcpyAsync(&K.nnz, K.rp.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    DBuf<int64_t> erp(n + 1);
+    scan_exclusive(fwd.get(), erp.get(), n, true, s);
+    GL_CUDA(cudaMemcpyAsync(&m->nedges, erp.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaStreamSynchronize(s));
+    K.ci.alloc(K.nnz);
+    K.v.alloc(K.nnz);
+    int64_t nem = m->nedges > 0 ? m->nedges : 1;
+    m->ej.alloc(nem);
+    m->ek.alloc(nem);
+    m->ealpha.alloc(nem);
+    m->etheta.alloc(nem);
+    k_fill_khat<<<grid_for(n, 128), 128, 0, s>>>(L, n, ndir, ealpha.get(), cut, K.rp.get(), K.ci.get(), K.v.get(),
+                                                  erp.get(), m->ej.get(), m->ek.get(), m->ealpha.get(),
+                                                  m->etheta.get());
+    GL_LAUNCH_CHECK();
+    m->vol.alloc(n);
+    k_volumes<<<grid_for(n, 256), 256, 0, s>>>(L, n, m->vol.get());
+    GL_LAUNCH_CHECK();
+
+    // red-black solve ordering
+    m->color0.alloc(n);
+    DBuf<int64_t> isred(n + 1);
+    k_lattice_parity<<<grid_for(n, 256), 256, 0, s>>>(L, n, m->color0.get(), isred.get());
+    GL_LAUNCH_CHECK();
+    scan_exclusive(isred.get(), isred.get(), n, true, s);
+    GL_CUDA(cudaMemcpyAsync(&m->nred, isred.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaStreamSynchronize(s));
+    m->perm.alloc(n);
+    m->iperm.alloc(n);
+    k_rb_perm<<<grid_for(n, 256), 256, 0, s>>>(n, m->color0.get(), isred.get(), m->nred, m->perm.get(),
+                                               m->iperm.get());
+    GL_LAUNCH_CHECK();
+
+    // K = D^-1 K-hat, off-diagonals as sliced ELL in the solve ordering
+    m->kdiag.alloc(n);
+    build_sell<double2>(n, n, m->perm.get(), m->iperm.get(), K, m->vol.get(), true, m->K, m->kdiag.get(), s);
+    m->volp.alloc(n);
+    k_permute_real<<<grid_for(n, 256), 256, 0, s>>>(n, m->perm.get(), m->vol.get(), m->volp.get());
+    GL_LAUNCH_CHECK();
+    GL_CUDA(cudaStreamSynchronize(s));
+}
+
+// FP32 copies of the fine operator for the mixed-precision path (built on demand)
+void mesh_ensure_fp32(gl_mesh_s *m, cudaStream_t s) {
+    if (m->has32) return;
+    build_sell<float2>(m->n, m->n, m->perm.get(), m->iperm.get(), m->khat, m->vol.get(), true, m->K32, nullptr, s);
+    m->kdiag32.alloc(m->n);
+    m->volp32.alloc(m->n);
+    to_float(m->kdiag.get(), m->kdiag32.get(), m->n, s);
+    to_float(m->volp.get(), m->volp32.get(), m->n, s);
+    GL_CUDA(cudaStreamSynchronize(s));
+    m->has32 = true;
+}
+
+}  // namespace gl

@@ -1,0 +1,86 @@
+// gl_ops.cu -- the fused sliced-ELL operators of the discrete GL problem in the
+// solve ordering (red nodes first, then black):
+//   Jacobian (Sec. 3): y_i = (K phi)_i + (-1 + 2|psi_i|^2) phi_i + psi_i^2 conj(phi_i)
+//   residual (Eq. discr ginla): r_i = (K psi)_i - psi_i (1 - |psi_i|^2)
+// with K = D^-1 K-hat (Remark rmk:dk) stored as off-diagonals + diagonal.
+#include "gl_internal.cuh"
+#include "gl_kernels.cuh"
+
+namespace gl {
+
+__global__ void k_gather(int64_t n, const int32_t *__restrict__ perm, const double2 *__restrict__ nat,
+                         double2 *__restrict__ sol) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < n) sol[p] = nat[perm[p]];
+}
+__global__ void k_scatter(int64_t n, const int32_t *__restrict__ perm, const double2 *__restrict__ sol,
+                          double2 *__restrict__ nat) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < n) nat[perm[p]] = sol[p];
+}
+
+void permute_in(int64_t n, const int32_t *perm, const double2 *nat, double2 *sol, cudaStream_t s) {
+    k_gather<<<grid_for(n, 256), 256, 0, s>>>(n, perm, nat, sol);
+    GL_LAUNCH_CHECK();
+}
+void permute_out(int64_t n, const int32_t *perm, const double2 *sol, double2 *nat, cudaStream_t s) {
+    k_scatter<<<grid_for(n, 256), 256, 0, s>>>(n, perm, sol, nat);
+    GL_LAUNCH_CHECK();
+}
+
+// y = J(psi) phi, FP64
+__global__ void k_jacobian64(int64_t n, SellView<double2> K, const double *__restrict__ kdiag,
+                             const double2 *__restrict__ psi, const double2 *__restrict__ phi,
+                             double2 *__restrict__ y) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double2 acc = sell_row<double2, double2>(K, p, phi);
+    y[p] = jacobian_epilogue(acc, kdiag[p], psi[p], phi[p]);
+}
+
+// y = J(psi) phi with the FP32 operator and FP32 arithmetic (FP64 in/out)
+__global__ void k_jacobian32(int64_t n, SellView<float2> K, const float *__restrict__ kdiag,
+                             const double2 *__restrict__ psi, const double2 *__restrict__ phi,
+                             double2 *__restrict__ y) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int64_t s = p >> 5;
+    int lane = (int)(p & 31);
+    int64_t beg = K.sptr[s];
+    int w = (int)((K.sptr[s + 1] - beg) >> 5);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int k = 0; k < w; ++k) {
+        int64_t q = beg + (int64_t)k * SELL_C + lane;
+        cfma(acc, K.val[q], to32(phi[K.col[q]]));
+    }
+    float2 r = jacobian_epilogue(acc, kdiag[p], to32(psi[p]), to32(phi[p]));
+    y[p] = to64(r);
+}
+
+// r = GL(psi), FP64
+__global__ void k_residual64(int64_t n, SellView<double2> K, const double *__restrict__ kdiag,
+                             const double2 *__restrict__ psi, double2 *__restrict__ r) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double2 acc = sell_row<double2, double2>(K, p, psi);
+    double2 ps = psi[p];
+    double a2 = ps.x * ps.x + ps.y * ps.y;
+    // (K psi)_i - psi_i (1 - |psi_i|^2) = offdiag + (K_ii - 1 + |psi_i|^2) psi_i
+    double d = kdiag[p] - 1.0 + a2;
+    r[p] = mk(acc.x + d * ps.x, acc.y + d * ps.y);
+}
+
+void jacobian_apply_p(const gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s) {
+    k_jacobian64<<<grid_for(m->n, 256), 256, 0, s>>>(m->n, m->K.view(), m->kdiag.get(), psi, phi, y);
+    GL_LAUNCH_CHECK();
+}
+void jacobian_apply_p32(const gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s) {
+    k_jacobian32<<<grid_for(m->n, 256), 256, 0, s>>>(m->n, m->K32.view(), m->kdiag32.get(), psi, phi, y);
+    GL_LAUNCH_CHECK();
+}
+void residual_p(const gl_mesh_s *m, const double2 *psi, double2 *r, cudaStream_t s) {
+    k_residual64<<<grid_for(m->n, 256), 256, 0, s>>>(m->n, m->K.view(), m->kdiag.get(), psi, r);
+    GL_LAUNCH_CHECK();
+}
+
+}  // namespace gl

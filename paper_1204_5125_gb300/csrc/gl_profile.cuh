@@ -1,0 +1,93 @@
+// gl_profile.cuh -- launch accounting and CUDA-event timing of one named kernel
+// class (instrumentation for measurement; not part of the method).
+//
+// Direct launches take an event pair from a pool and are summed at the next
+// harvest.  Launches captured into a CUDA graph keep their event pair for the
+// life of the graph; the graph's owner harvests those pairs after every replay.
+// Every gl_profile_begin/end bumps `generation`, so graphs captured under an
+// older generation (whose events may be gone) are captured again.
+#pragma once
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "gl_common.cuh"
+
+namespace gl {
+
+struct Profiler {
+    std::atomic<int64_t> launches{0};  // hot-path kernel launches since gl_profile_begin
+    int64_t generation = 0;
+    bool active = false;
+    std::string name;                  // kernel class timed with events ("" = none)
+    std::vector<cudaEvent_t> ev;       // 2 per slot
+    std::vector<double> slot_bytes;
+    std::vector<int> free_slots, pending;
+    std::vector<int> *capture = nullptr;  // slots of the graph being captured
+    double total_ms = 0, total_bytes = 0;
+    int64_t timed = 0, dropped = 0;
+
+    bool timing(const char *cls) const { return active && !name.empty() && name == cls; }
+    // sums the elapsed time of the given slots (their events have completed)
+    void harvest(const std::vector<int> &slots) {
+        for (int sl : slots) {
+            float t = 0;
+            if (cudaEventElapsedTime(&t, ev[2 * sl], ev[2 * sl + 1]) == cudaSuccess) {
+                total_ms += t;
+                total_bytes += slot_bytes[sl];
+                ++timed;
+            }
+        }
+    }
+    void harvest_direct() {
+        harvest(pending);
+        free_slots.insert(free_slots.end(), pending.begin(), pending.end());
+        pending.clear();
+    }
+};
+Profiler &profiler();
+
+inline void note_launch(int k = 1) { profiler().launches.fetch_add(k, std::memory_order_relaxed); }
+
+// Brackets one launch: records events around it when its class is being timed.
+class ProfScope {
+   public:
+    ProfScope(const char *cls, double alg_bytes, cudaStream_t s) : s_(s) {
+        Profiler &p = profiler();
+        note_launch();
+        if (!p.timing(cls)) return;
+        if (p.free_slots.empty()) {
+            ++p.dropped;
+            return;
+        }
+        slot_ = p.free_slots.back();
+        p.free_slots.pop_back();
+        p.slot_bytes[slot_] = alg_bytes;
+        graph_ = p.capture != nullptr;
+        if (graph_)
+            p.capture->push_back(slot_);
+        else
+            p.pending.push_back(slot_);
+        record(p.ev[2 * slot_]);
+    }
+    ~ProfScope() {
+        if (slot_ >= 0) record(profiler().ev[2 * slot_ + 1]);
+    }
+
+   private:
+    // inside stream capture an event record becomes a timing node of the graph
+    // only with cudaEventRecordExternal
+    void record(cudaEvent_t e) {
+        if (graph_)
+            cudaEventRecordWithFlags(e, s_, cudaEventRecordExternal);
+        else
+            cudaEventRecord(e, s_);
+    }
+
+    cudaStream_t s_;
+    int slot_ = -1;
+    bool graph_ = false;
+};
+
+}  // namespace gl

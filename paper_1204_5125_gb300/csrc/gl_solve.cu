@@ -1,0 +1,690 @@
+// gl_solve.cu -- preconditioned MINRES (Paige & Saunders 1975) for the Newton
+// system J(psi) x = b (Eq. Newton system) in the real inner product
+// <x, y>_R = Re sum_i |V_i| conj(x_i) y_i (Eq. disc inner2), in which J is
+// self-adjoint (Sec. 3) and R_k (Eq. prec2) is self-adjoint positive definite.
+//
+// The Lanczos/Givens scalars live on the device; every reduction writes one
+// partial per block of a fixed grid and is summed in index order, so results do
+// not depend on scheduling.  A device status word stops all kernels once the
+// solve has converged or failed; the host polls it every few iterations.
+//
+// GL_MIXED: FP64 defect correction x <- x + e around inner MINRES solves of
+// J e = r whose vectors, Jacobian applies and V-cycles are FP32 (dots and
+// scalars FP64, coarsest solve FP64); the FP64 true residual decides.
+#include <chrono>
+
+#include "gl_internal.cuh"
+#include "gl_kernels.cuh"
+#include "gl_profile.cuh"
+
+namespace gl {
+
+struct MinresDev {
+    double gamma, gamma_old, eta, eta0, c, c_old, s, s_old;
+    double delta, a1, a2, a3, c_new, eta_prev, gamma_cur;
+    double bnorm, tol, est, true_rel;
+    int it, maxit, check_true, status, lucky, use_true;
+};
+enum { ST_RUN = 0, ST_CONV = 1, ST_BREAK = 2, ST_NAN = 3, ST_MAXIT = 4 };
+
+template <typename T>
+struct SolveOps;
+template <>
+struct SolveOps<double> {
+    using C = double2;
+    static SellView<C> K(const gl_mesh_s *m) { return m->K.view(); }
+    static const double *kdiag(const gl_mesh_s *m) { return m->kdiag.get(); }
+    static const double *vol(const gl_mesh_s *m) { return m->volp.get(); }
+};
+template <>
+struct SolveOps<float> {
+    using C = float2;
+    static SellView<C> K(const gl_mesh_s *m) { return m->K32.view(); }
+    static const float *kdiag(const gl_mesh_s *m) { return m->kdiag32.get(); }
+    static const float *vol(const gl_mesh_s *m) { return m->volp32.get(); }
+};
+
+template <typename C>
+__device__ __forceinline__ double redot(C a, C b) {  // Re(conj(a) b)
+    return (double)a.x * (double)b.x + (double)a.y * (double)b.y;
+}
+
+// ------------------------------------------------------------------ vector kernels
+// v = b - J x ; partials of <b, b>_R and <v, v>_R
+template <typename C, typename R>
+__global__ void __launch_bounds__(RED_THREADS) k_init_resid(int64_t n, SellView<C> K, const R *kd, const R *vol,
+                                                            const C *psi, const C *b, const C *x, C *v,
+                                                            double *part) {
+    __shared__ double sh[32];
+    double ab = 0, av = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        C acc = sell_row<C, C>(K, p, x);
+        C jx = jacobian_epilogue(acc, kd[p], psi[p], x[p]);
+        C bb = b[p];
+        C vv = csub(bb, jx);
+        v[p] = vv;
+        ab += (double)vol[p] * redot(bb, bb);
+        av += (double)vol[p] * redot(vv, vv);
+    }
+    double t = block_sum(ab, sh);
+    double u = block_sum(av, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = t;
+        part[RED_BLOCKS + blockIdx.x] = u;
+    }
+}
+
+// partials of <x, y>_R
+template <typename C, typename R>
+__global__ void __launch_bounds__(RED_THREADS) k_dot(int64_t n, const R *vol, const C *x, const C *y, double *part,
+                                                     const int *stop) {
+    __shared__ double sh[32];
+    if (*stop) return;
+    double a = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        a += (double)vol[p] * redot(x[p], y[p]);
+    double t = block_sum(a, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// q = J z (z not yet normalised) ; partials of <J z, z>_R
+template <typename C, typename R>
+__global__ void __launch_bounds__(RED_THREADS) k_jz(int64_t n, SellView<C> K, const R *kd, const R *vol, const C *psi,
+                                                    const C *z, C *q, double *part, const int *stop) {
+    __shared__ double sh[32];
+    if (*stop) return;
+    double a = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        C acc = sell_row<C, C>(K, p, z);
+        C zz = z[p];
+        C jz = jacobian_epilogue(acc, kd[p], psi[p], zz);
+        q[p] = jz;
+        a += (double)vol[p] * redot(jz, zz);
+    }
+    double t = block_sum(a, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// v_new = q / gamma - (delta / gamma) v - (gamma / gamma_old) v_old
+template <typename C, typename R>
+__global__ void k_vnew(int64_t n, const MinresDev *S, const C *q, const C *v, const C *v_old, C *v_new) {
+    if (S->status) return;
+    R ig = (R)(1.0 / S->gamma), dg = (R)(S->delta / S->gamma), go = (R)(S->gamma / S->gamma_old);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        C a = q[p], b = v[p], c = v_old[p];
+        v_new[p] = mk(a.x * ig - dg * b.x - go * c.x, a.y * ig - dg * b.y - go * c.y);
+    }
+}
+
+// w_new = (z / gamma - a3 w_old - a2 w) / a1 ; x += c_new eta w_new
+template <typename C, typename R>
+__global__ void k_update(int64_t n, const MinresDev *S, const C *z, const C *w_old, const C *w, C *w_new, C *x) {
+    if (S->status) return;
+    R ig = (R)(1.0 / S->gamma_cur), a2 = (R)S->a2, a3 = (R)S->a3, ia1 = (R)(1.0 / S->a1);
+    R ce = (R)(S->c_new * S->eta_prev);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        C zz = z[p], wo = w_old[p], ww = w[p];
+        C wn = mk((zz.x * ig - a3 * wo.x - a2 * ww.x) * ia1, (zz.y * ig - a3 * wo.y - a2 * ww.y) * ia1);
+        w_new[p] = wn;
+        C xx = x[p];
+        x[p] = mk(xx.x + ce * wn.x, xx.y + ce * wn.y);
+    }
+}
+
+// partials of ||b - J x||_D^2, only when the scalar kernel asked for a check
+template <typename C, typename R>
+__global__ void __launch_bounds__(RED_THREADS) k_true_resid(int64_t n, SellView<C> K, const R *kd, const R *vol,
+                                                            const C *psi, const C *b, const C *x, double *part,
+                                                            const MinresDev *S, int force) {
+    __shared__ double sh[32];
+    if (!force && (S->status || !S->check_true)) return;
+    double a = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        C acc = sell_row<C, C>(K, p, x);
+        C jx = jacobian_epilogue(acc, kd[p], psi[p], x[p]);
+        C r = csub(b[p], jx);
+        a += (double)vol[p] * redot(r, r);
+    }
+    double t = block_sum(a, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// ------------------------------------------------------------------ scalar kernels (one block)
+__device__ double sum_parts(const double *part, double *sh) {
+    double a = 0;
+    for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) a += part[i];
+    return block_sum(a, sh);
+}
+
+__global__ void k_scal_init(MinresDev *S, const double *part) {
+    __shared__ double sh[32];
+    double bb = sum_parts(part, sh);
+    double vv = sum_parts(part + RED_BLOCKS, sh);
+    if (threadIdx.x) return;
+    double tol = S->tol;
+    int use_true = S->use_true;
+    S->it = 0;
+    S->status = ST_RUN;
+    S->check_true = 0;
+    S->lucky = 0;
+    S->bnorm = sqrt(bb);
+    S->true_rel = (S->bnorm > 0) ? sqrt(vv) / S->bnorm : 0.0;
+    S->est = 1.0;
+    if (!(S->bnorm > 0)) {
+        S->status = ST_CONV;
+        S->est = 0;
+    } else if (use_true && S->true_rel <= tol) {
+        S->status = ST_CONV;
+    } else if (!isfinite(S->true_rel)) {
+        S->status = ST_NAN;
+    } else if (S->maxit <= 0) {
+        S->status = ST_MAXIT;
+    }
+}
+
+// solve parameters, written before the captured init phase reads them
+__global__ void k_set_params(MinresDev *S, double tol, int maxit, int use_true) {
+    S->tol = tol;
+    S->maxit = maxit;
+    S->use_true = use_true;
+}
+
+__global__ void k_scal_gamma0(MinresDev *S, const double *part) {
+    __shared__ double sh[32];
+    double g2 = sum_parts(part, sh);
+    if (threadIdx.x || S->status) return;
+    if (!isfinite(g2)) {
+        S->status = ST_NAN;
+        return;
+    }
+    if (g2 < 0) {
+        S->status = ST_BREAK;
+        return;
+    }
+    double g = sqrt(g2);
+    S->gamma = g;
+    S->gamma_old = 1.0;
+    S->eta = S->eta0 = g;
+    S->c = S->c_old = 1.0;
+    S->s = S->s_old = 0.0;
+    if (g == 0) S->status = ST_CONV;
+}
+
+__global__ void k_scal_delta(MinresDev *S, const double *part) {
+    __shared__ double sh[32];
+    double d = sum_parts(part, sh);
+    if (threadIdx.x || S->status) return;
+    S->delta = d / (S->gamma * S->gamma);
+}
+
+__global__ void k_scal_givens(MinresDev *S, const double *part) {
+    __shared__ double sh[32];
+    double g2 = sum_parts(part, sh);
+    if (threadIdx.x || S->status) return;
+    if (!isfinite(g2) || !isfinite(S->delta)) {
+        S->status = ST_NAN;
+        return;
+    }
+    if (g2 < 0) {
+        S->status = ST_BREAK;
+        return;
+    }
+    double gn = sqrt(g2);
+    double g = S->gamma, d = S->delta;
+    double a0 = S->c * d - S->c_old * S->s * g;
+    double a1 = sqrt(a0 * a0 + gn * gn);
+    double a2 = S->s * d + S->c_old * S->c * g;
+    double a3 = S->s_old * g;
+    double cn = a0 / a1, sn = gn / a1;
+    S->a1 = a1;
+    S->a2 = a2;
+    S->a3 = a3;
+    S->c_new = cn;
+    S->eta_prev = S->eta;
+    S->gamma_cur = g;
+    S->eta = -sn * S->eta;
+    S->gamma_old = g;
+    S->gamma = gn;
+    S->c_old = S->c;
+    S->c = cn;
+    S->s_old = S->s;
+    S->s = sn;
+    S->it += 1;
+    S->est = fabs(S->eta) / S->eta0;
+    S->lucky = (gn == 0);
+    S->check_true = (S->est <= S->tol) || S->lucky;
+}
+
+__global__ void k_scal_true(MinresDev *S, const double *part) {
+    __shared__ double sh[32];
+    double r2 = sum_parts(part, sh);
+    if (threadIdx.x || S->status) return;
+    if (S->check_true) {
+        if (S->use_true) {
+            S->true_rel = sqrt(r2) / S->bnorm;
+            if (!isfinite(S->true_rel))
+                S->status = ST_NAN;
+            else if (S->true_rel <= S->tol)
+                S->status = ST_CONV;
+        } else {
+            S->status = ST_CONV;  // inner solves stop on the estimate alone
+        }
+        if (!S->status && S->lucky) S->status = ST_MAXIT;  // Krylov space exhausted above tol
+    }
+    if (!S->status && S->it >= S->maxit) S->status = ST_MAXIT;
+}
+
+__global__ void k_scal_final(MinresDev *S, const double *part) {
+    __shared__ double sh[32];
+    double r2 = sum_parts(part, sh);
+    if (threadIdx.x) return;
+    if (S->bnorm > 0) S->true_rel = sqrt(r2) / S->bnorm;
+}
+
+// ------------------------------------------------------------------ MINRES driver
+// The initial phase and a body of ITER_UNROLL iterations are captured once as
+// CUDA graphs and replayed; every kernel turns into a no-op once the status word
+// is set, so a replay past convergence costs only launch latency.  The three v,
+// two z and three w buffers rotate, so the body holds a multiple of 6 iterations
+// and starts every replay with the same buffer roles.
+constexpr int ITER_UNROLL = 6;
+
+struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> slots;  // profiler event slots recorded inside the graph
+    int64_t launches = 0;
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        slots.clear();
+        launches = 0;
+    }
+};
+
+struct GraphKey {
+    const void *m = nullptr, *psi = nullptr, *b = nullptr, *x = nullptr;
+    int64_t prec_uid = -1, generation = -1;
+    int vc32 = 0;
+    bool operator==(const GraphKey &o) const {
+        return m == o.m && psi == o.psi && b == o.b && x == o.x && prec_uid == o.prec_uid &&
+               generation == o.generation && vc32 == o.vc32;
+    }
+};
+
+template <typename T>
+struct MinresWork {
+    using C = cplx_t<T>;
+    DBuf<C> v[3], z[2], w[3], q;
+    DBuf<double> part;
+    DBuf<MinresDev> S;
+    int64_t n = 0;
+    cudaStream_t cap = nullptr;
+    GraphKey key;
+    Graph init, body;
+    void ensure(int64_t nn) {
+        if (!cap) GL_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        if (n == nn) return;
+        init.reset();
+        body.reset();
+        key = GraphKey{};
+        for (auto &b : v) b.alloc(nn);
+        for (auto &b : z) b.alloc(nn);
+        for (auto &b : w) b.alloc(nn);
+        q.alloc(nn);
+        part.alloc(2 * RED_BLOCKS);
+        S.alloc(1);
+        n = nn;
+    }
+};
+
+struct MinresResult {
+    int status, iters;
+    double est, true_rel;
+};
+
+// vc32: run the V-cycle in FP32 even when the Krylov vectors are FP64
+template <typename T>
+static void precond_apply_any(gl_prec_s *p, const cplx_t<T> *v, cplx_t<T> *z, const int *stop, bool vc32,
+                              cudaStream_t s);
+template <>
+void precond_apply_any<double>(gl_prec_s *p, const double2 *v, double2 *z, const int *stop, bool vc32,
+                               cudaStream_t s) {
+    if (vc32)
+        precond_apply_p64_via32(p, v, z, stop, s);
+    else
+        precond_apply_p(p, v, z, stop, s);
+}
+template <>
+void precond_apply_any<float>(gl_prec_s *p, const float2 *v, float2 *z, const int *stop, bool, cudaStream_t s) {
+    precond_apply_p32(p, v, z, stop, s);
+}
+
+// b = 0 has the solution x = 0 whatever the initial guess
+template <typename C>
+__global__ void k_zero_if_bzero(int64_t n, const MinresDev *S, C *x) {
+    if (S->bnorm > 0) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) x[i] = mk(decltype(x[0].x)(0), decltype(x[0].x)(0));
+}
+
+template <typename C>
+__global__ void k_copy_if(int64_t n, const C *a, C *b, const int *stop) {
+    if (*stop) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+// captures whatever `enqueue` launches on a private stream into g
+template <typename F>
+static void capture(Graph &g, cudaStream_t cs, F &&enqueue) {
+    g.reset();
+    Profiler &pr = profiler();
+    int64_t l0 = pr.launches.load();
+    pr.capture = &g.slots;
+    cudaGraph_t graph = nullptr;
+    GL_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    try {
+        enqueue(cs);
+    } catch (...) {
+        cudaStreamEndCapture(cs, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        pr.capture = nullptr;
+        throw;
+    }
+    GL_CUDA(cudaStreamEndCapture(cs, &graph));
+    pr.capture = nullptr;
+    g.launches = pr.launches.load() - l0;
+    pr.launches.fetch_sub(g.launches);
+    GL_CUDA(cudaGraphInstantiate(&g.exec, graph, 0));
+    GL_CUDA(cudaGraphDestroy(graph));
+}
+
+static void replay(Graph &g, cudaStream_t s) {
+    GL_CUDA(cudaGraphLaunch(g.exec, s));
+    note_launch((int)g.launches);
+}
+static void harvest(Graph &g) {
+    Profiler &pr = profiler();
+    if (pr.active) pr.harvest(g.slots);
+    pr.harvest_direct();
+}
+
+// Runs MINRES on J x = b with x as the initial guess (overwritten).  use_true:
+// stop on the FP64 true residual (FP64 path) or on the estimate alone (inner).
+template <typename T>
+static MinresResult minres(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const cplx_t<T> *b, cplx_t<T> *x,
+                           double tol, int maxit, bool use_true, bool vc32, MinresWork<T> &W, cudaStream_t s) {
+    using O = SolveOps<T>;
+    using C = cplx_t<T>;
+    int64_t n = m->n;
+    W.ensure(n);
+    MinresDev *S = W.S.get();
+    const int *stop = &S->status;
+    double *part = W.part.get();
+    auto K = O::K(m);
+    auto kd = O::kdiag(m);
+    auto vol = O::vol(m);
+    int G = grid_for(n, 256);
+    GraphKey key{m, psi, b, x, p ? p->uid : -1, profiler().generation, vc32 ? 1 : 0};
+    if (!(key == W.key) || !W.init.exec || !W.body.exec) {
+        W.key = key;
+        C *v0 = W.v[0].get(), *v1 = W.v[1].get(), *z0 = W.z[0].get();
+        C *w0 = W.w[0].get(), *w1 = W.w[1].get();
+        capture(W.init, W.cap, [&](cudaStream_t cs) {
+            GL_CUDA(cudaMemsetAsync(v0, 0, n * sizeof(C), cs));
+            GL_CUDA(cudaMemsetAsync(w0, 0, n * sizeof(C), cs));
+            GL_CUDA(cudaMemsetAsync(w1, 0, n * sizeof(C), cs));
+            note_launch(3);
+            k_init_resid<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, K, kd, vol, psi, b, x, v1, part);
+            k_scal_init<<<1, 1024, 0, cs>>>(S, part);
+            k_zero_if_bzero<C><<<G, 256, 0, cs>>>(n, S, x);
+            GL_LAUNCH_CHECK();
+            if (p) {
+                precond_apply_any<T>(p, v1, z0, stop, vc32, cs);
+            } else {
+                note_launch();
+                k_copy_if<C><<<G, 256, 0, cs>>>(n, v1, z0, stop);
+            }
+            note_launch(2);
+            k_dot<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, vol, v1, z0, part, stop);
+            k_scal_gamma0<<<1, 1024, 0, cs>>>(S, part);
+            GL_LAUNCH_CHECK();
+        });
+        capture(W.body, W.cap, [&](cudaStream_t cs) {
+            C *v_old = W.v[0].get(), *v = W.v[1].get(), *v_new = W.v[2].get();
+            C *z = W.z[0].get(), *z_new = W.z[1].get();
+            C *w_old = W.w[0].get(), *w = W.w[1].get(), *w_new = W.w[2].get();
+            for (int k = 0; k < ITER_UNROLL; ++k) {
+                {
+                    // algorithmic bytes of the fused Jacobian + dot: off-diagonals, K_ii,
+                    // |V|, psi, z (own row; neighbours cached) and the written q
+                    int64_t nnz = (sizeof(T) == 8) ? m->K.nnz_real : m->K32.nnz_real;
+                    double jb = (double)nnz * (sizeof(C) + 4) + (double)n * (2 * sizeof(T) + 3 * sizeof(C));
+                    ProfScope ps("jz", jb, cs);
+                    k_jz<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, K, kd, vol, psi, z, W.q.get(), part, stop);
+                }
+                note_launch(2);
+                k_scal_delta<<<1, 1024, 0, cs>>>(S, part);
+                k_vnew<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, S, W.q.get(), v, v_old, v_new);
+                if (p) {
+                    precond_apply_any<T>(p, v_new, z_new, stop, vc32, cs);
+                } else {
+                    note_launch();
+                    k_copy_if<C><<<G, 256, 0, cs>>>(n, v_new, z_new, stop);
+                }
+                note_launch(5);
+                k_dot<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, vol, v_new, z_new, part, stop);
+                k_scal_givens<<<1, 1024, 0, cs>>>(S, part);
+                k_update<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, S, z, w_old, w, w_new, x);
+                k_true_resid<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, K, kd, vol, psi, b, x, part, S, 0);
+                k_scal_true<<<1, 1024, 0, cs>>>(S, part);
+                GL_LAUNCH_CHECK();
+                C *t = v_old;
+                v_old = v;
+                v = v_new;
+                v_new = t;
+                t = z;
+                z = z_new;
+                z_new = t;
+                t = w_old;
+                w_old = w;
+                w = w_new;
+                w_new = t;
+            }
+        });
+    }
+    k_set_params<<<1, 1, 0, s>>>(S, tol, maxit, use_true ? 1 : 0);
+    GL_LAUNCH_CHECK();
+    replay(W.init, s);
+    MinresDev h;
+    int64_t polls = 0, max_polls = (int64_t)maxit / ITER_UNROLL + 3;
+    for (;;) {
+        GL_CUDA(cudaMemcpyAsync(&h, S, sizeof(MinresDev), cudaMemcpyDeviceToHost, s));
+        GL_CUDA(cudaStreamSynchronize(s));
+        harvest(W.init);
+        if (h.status != ST_RUN) break;
+        GL_REQUIRE(polls++ <= max_polls, GL_ERR_TIMEOUT, "MINRES status word was not updated");
+        replay(W.body, s);
+        GL_CUDA(cudaMemcpyAsync(&h, S, sizeof(MinresDev), cudaMemcpyDeviceToHost, s));
+        GL_CUDA(cudaStreamSynchronize(s));
+        harvest(W.body);
+        if (h.status != ST_RUN) break;
+    }
+    if (use_true) {
+        note_launch(2);
+        k_true_resid<C, T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, K, kd, vol, psi, b, x, part, S, 1);
+        k_scal_final<<<1, 1024, 0, s>>>(S, part);
+        GL_LAUNCH_CHECK();
+        GL_CUDA(cudaMemcpyAsync(&h, S, sizeof(MinresDev), cudaMemcpyDeviceToHost, s));
+        GL_CUDA(cudaStreamSynchronize(s));
+    }
+    return MinresResult{h.status, h.it, h.est, h.true_rel};
+}
+
+static gl_status status_of(int st) {
+    switch (st) {
+        case ST_CONV: return GL_OK;
+        case ST_BREAK: return GL_ERR_BREAKDOWN;
+        case ST_NAN: return GL_ERR_NAN;
+        default: return GL_ERR_NOT_CONVERGED;
+    }
+}
+
+// ------------------------------------------------------------------ mixed precision
+__global__ void k_resid64_scaled(int64_t n, SellView<double2> K, const double *kd, const double *vol,
+                                 const double2 *psi, const double2 *b, const double2 *x, double2 *r, double *part) {
+    __shared__ double sh[32];
+    double a = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        double2 acc = sell_row<double2, double2>(K, p, x);
+        double2 jx = jacobian_epilogue(acc, kd[p], psi[p], x[p]);
+        double2 rr = csub(b[p], jx);
+        r[p] = rr;
+        a += vol[p] * (rr.x * rr.x + rr.y * rr.y);
+    }
+    double t = block_sum(a, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+__global__ void k_sumsq_vol(int64_t n, const double *vol, const double2 *b, double *part) {
+    __shared__ double sh[32];
+    double a = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        a += vol[p] * (b[p].x * b[p].x + b[p].y * b[p].y);
+    double t = block_sum(a, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+__global__ void k_sum_to(const double *part, double *out) {
+    __shared__ double sh[32];
+    double a = 0;
+    for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) a += part[i];
+    double t = block_sum(a, sh);
+    if (threadIdx.x == 0) *out = t;
+}
+// r32 = r / scale
+__global__ void k_down(int64_t n, const double2 *r, double scale, float2 *r32, float2 *e32) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < n) {
+        r32[p] = make_float2((float)(r[p].x / scale), (float)(r[p].y / scale));
+        e32[p] = make_float2(0.f, 0.f);
+    }
+}
+// x += scale * e32
+__global__ void k_up(int64_t n, const float2 *e32, double scale, double2 *x) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < n) {
+        x[p].x += scale * (double)e32[p].x;
+        x[p].y += scale * (double)e32[p].y;
+    }
+}
+__global__ void k_psi32(int64_t n, const double2 *a, float2 *b) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < n) b[p] = to32(a[p]);
+}
+
+struct SolveWork {
+    MinresWork<double> w64;
+    MinresWork<float> w32;
+    DBuf<double2> r;
+    DBuf<float2> r32, e32, psi32;
+    DBuf<double> part, sc;
+};
+static SolveWork &solve_work() {
+    static thread_local SolveWork w;
+    return w;
+}
+
+gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, const double2 *b_p, double2 *x_p,
+                           const gl_options &o, gl_solve_info *info, cudaStream_t s) {
+    SolveWork &W = solve_work();
+    auto t0 = std::chrono::steady_clock::now();
+    gl_status st;
+    gl_solve_info inf{};
+    bool mixed = (o.precision == GL_MIXED) && p;
+    if (!mixed) {
+        bool vc32 = (o.precision == GL_MIXED_PRECOND) && p;
+        if (vc32) precond_ensure_fp32(p, s);
+        MinresResult r = minres<double>(m, p, psi_p, b_p, x_p, o.tol, o.maxit, true, vc32, W.w64, s);
+        inf.iters = r.iters;
+        inf.outer_iters = 1;
+        inf.true_relres = r.true_rel;
+        inf.est_relres = r.est;
+        inf.converged = (r.status == ST_CONV);
+        st = status_of(r.status);
+    } else {
+        precond_ensure_fp32(p, s);
+        int64_t n = m->n;
+        if (W.r.n != (size_t)n) {
+            W.r.alloc(n);
+            W.r32.alloc(n);
+            W.e32.alloc(n);
+            W.psi32.alloc(n);
+        }
+        W.part.alloc(RED_BLOCKS);
+        W.sc.alloc(2);
+        int G = grid_for(n, 256);
+        k_psi32<<<G, 256, 0, s>>>(n, psi_p, W.psi32.get());
+        k_sumsq_vol<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, m->volp.get(), b_p, W.part.get());
+        k_sum_to<<<1, 1024, 0, s>>>(W.part.get(), W.sc.get());
+        double bb = 0;
+        GL_CUDA(cudaMemcpyAsync(&bb, W.sc.get(), sizeof(double), cudaMemcpyDeviceToHost, s));
+        GL_CUDA(cudaStreamSynchronize(s));
+        double bnorm = std::sqrt(bb);
+        st = GL_ERR_NOT_CONVERGED;
+        int max_outer = o.max_outer > 0 ? o.max_outer : 20;
+        double inner_tol = o.inner_tol > 0 ? o.inner_tol : 1e-5;
+        double rel = 0;
+        int total = 0, outer = 0;
+        double est = 0;
+        if (bnorm == 0) {
+            GL_CUDA(cudaMemsetAsync(x_p, 0, n * sizeof(double2), s));
+            st = GL_OK;
+        }
+        for (; st != GL_OK && outer <= max_outer; ++outer) {
+            k_resid64_scaled<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, m->K.view(), m->kdiag.get(), m->volp.get(), psi_p,
+                                                                b_p, x_p, W.r.get(), W.part.get());
+            k_sum_to<<<1, 1024, 0, s>>>(W.part.get(), W.sc.get());
+            double rr = 0;
+            GL_CUDA(cudaMemcpyAsync(&rr, W.sc.get(), sizeof(double), cudaMemcpyDeviceToHost, s));
+            GL_CUDA(cudaStreamSynchronize(s));
+            rel = std::sqrt(rr) / bnorm;
+            if (!std::isfinite(rel)) {
+                st = GL_ERR_NAN;
+                break;
+            }
+            if (rel <= o.tol) {
+                st = GL_OK;
+                break;
+            }
+            if (outer == max_outer || total >= o.maxit) break;
+            double scale = std::sqrt(rr);
+            k_down<<<G, 256, 0, s>>>(n, W.r.get(), scale, W.r32.get(), W.e32.get());
+            GL_LAUNCH_CHECK();
+            MinresResult r = minres<float>(m, p, W.psi32.get(), W.r32.get(), W.e32.get(), inner_tol,
+                                           o.maxit - total, false, false, W.w32, s);
+            total += r.iters;
+            est = r.est;
+            if (r.status == ST_BREAK || r.status == ST_NAN) {
+                st = status_of(r.status);
+                break;
+            }
+            k_up<<<G, 256, 0, s>>>(n, W.e32.get(), scale, x_p);
+            GL_LAUNCH_CHECK();
+        }
+        inf.iters = total;
+        inf.outer_iters = outer;
+        inf.true_relres = rel;
+        inf.est_relres = est;
+        inf.converged = (st == GL_OK);
+    }
+    GL_CUDA(cudaStreamSynchronize(s));
+    auto t1 = std::chrono::steady_clock::now();
+    inf.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    if (info) {
+        double setup = info->setup_ms;
+        *info = inf;
+        info->setup_ms = setup;
+    }
+    return st;
+}
+
+}  // namespace gl

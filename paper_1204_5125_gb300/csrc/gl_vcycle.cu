@@ -1,0 +1,451 @@
+// gl_vcycle.cu -- the V-cycle that applies R_k = AMG_k(K-hat + 2 D|psi|^2, D .)
+// (Eq. prec2): on each level one symmetric Gauss-Seidel step before and after
+// the coarse correction (Sec. 4: one pre- and one post-smoothing step), the
+// Gauss-Seidel sweeps taken colour by colour (forward: colours ascending,
+// backward: descending), and a dense solve on the coarsest level.
+//
+// All vectors are in the solve ordering, where each colour is a contiguous
+// range of positions.  On level 0 the operator is used in its row-scaled form
+// K + 2|psi|^2 = D^-1 (K-hat + 2 D|psi|^2): Gauss-Seidel on D^-1 A with right-hand
+// side v is Gauss-Seidel on A with right-hand side D v, and the residual handed
+// to the restriction is multiplied by D.
+#include "gl_internal.cuh"
+#include "gl_kernels.cuh"
+#include "gl_profile.cuh"
+
+namespace gl {
+
+template <typename T>
+struct LevelOps;
+template <>
+struct LevelOps<double> {
+    using C = double2;
+    static const Sell<C> &A(const Level &L) { return *L.A; }
+    static const double *diag(const Level &L) { return L.diag.get(); }
+    static const Sell<C> &P(const Level &L) { return L.P; }
+    static const Sell<C> &PH(const Level &L) { return L.PH; }
+    static const CsrG<C> &Ag(const Level &L) { return L.Ag; }
+    static const CsrG<C> &PHg(const Level &L) { return L.PHg; }
+    static C *b(Level &L) { return L.b.get(); }
+    static C *x(Level &L) { return L.x.get(); }
+    static C *r(Level &L) { return L.r.get(); }
+};
+template <>
+struct LevelOps<float> {
+    using C = float2;
+    static const Sell<C> &A(const Level &L) { return *L.A32; }
+    static const float *diag(const Level &L) { return L.diag32.get(); }
+    static const Sell<C> &P(const Level &L) { return L.P32; }
+    static const Sell<C> &PH(const Level &L) { return L.PH32; }
+    static const CsrG<C> &Ag(const Level &L) { return L.Ag32; }
+    static const CsrG<C> &PHg(const Level &L) { return L.PHg32; }
+    static C *b(Level &L) { return L.b32.get(); }
+    static C *x(Level &L) { return L.x32.get(); }
+    static C *r(Level &L) { return L.r32.get(); }
+};
+
+// x_i <- (b_i - sum_{k != i} A_ik x_k) / A_ii for the rows of one colour [lo, hi).
+// `first`: first forward pass from x = 0, where only positions < lo hold values.
+template <typename C, typename R>
+__global__ void __launch_bounds__(256) k_gs(int64_t lo, int64_t hi, SellView<C> A, const R *__restrict__ diag,
+                                            const C *__restrict__ b, C *__restrict__ x, int first,
+                                            const int *__restrict__ stop) {
+    if (stop && *stop) return;
+    int64_t p = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= hi) return;
+    C acc;
+    if (first && lo == 0) {  // every neighbour of the first colour still holds zero
+        acc.x = 0;
+        acc.y = 0;
+    } else {
+        acc = first ? sell_row_before<C, C>(A, p, x, lo) : sell_row<C, C>(A, p, x);
+    }
+    C bb = b[p];
+    R d = (R)1 / diag[p];
+    x[p] = mk((bb.x - acc.x) * d, (bb.y - acc.y) * d);
+}
+
+// r = (b - A x) * scale (scale = |V| on level 0, none below)
+template <typename C, typename R>
+__global__ void __launch_bounds__(256) k_resid(int64_t n, SellView<C> A, const R *__restrict__ diag,
+                                               const C *__restrict__ b, const C *__restrict__ x,
+                                               const R *__restrict__ scale, C *__restrict__ r,
+                                               const int *__restrict__ stop) {
+    if (stop && *stop) return;
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    C acc = sell_row<C, C>(A, p, x);
+    C xx = x[p], bb = b[p];
+    R d = diag[p];
+    R sc = scale ? scale[p] : (R)1;
+    r[p] = mk((bb.x - acc.x - d * xx.x) * sc, (bb.y - acc.y - d * xx.y) * sc);
+}
+
+// y = S x (add = 0) or y += S x (add = 1) for a rectangular sliced-ELL S
+template <typename C>
+__global__ void __launch_bounds__(256) k_spmv(int64_t n, SellView<C> S, const C *__restrict__ x, C *__restrict__ y,
+                                              int add, const int *__restrict__ stop) {
+    if (stop && *stop) return;
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    C acc = sell_row<C, C>(S, p, x);
+    if (add) acc = cadd(acc, y[p]);
+    y[p] = acc;
+}
+
+// ---------------------------------------------------------------- grouped-CSR rows
+// sum over the stored entries of row `row` (columns below `lim` only) by the G
+// lanes of a group; every lane of the warp must call this (shuffles), rows past
+// the end pass row < 0.  The result is complete in the group's first lane.
+template <int G, typename C>
+__device__ __forceinline__ C group_row(const CsrGView<C> &A, int64_t row, int lane, const C *__restrict__ x,
+                                       int64_t lim) {
+    C acc;
+    acc.x = 0;
+    acc.y = 0;
+    if (row >= 0) {
+        int64_t q1 = A.rp[row + 1];
+        for (int64_t q = A.rp[row] + lane; q < q1; q += G) {
+            int32_t c = __ldg(A.col + q);
+            if (c < lim) cfma(acc, A.val[q], x[c]);
+        }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        acc.x += __shfl_down_sync(0xffffffffu, acc.x, o, G);
+        acc.y += __shfl_down_sync(0xffffffffu, acc.y, o, G);
+    }
+    return acc;
+}
+
+// y = S x (add = 0) or y += S x (add = 1), grouped CSR
+template <int G, typename C>
+__global__ void __launch_bounds__(256) k_spmv_g(CsrGView<C> S, const C *__restrict__ x, C *__restrict__ y, int add,
+                                                const int *__restrict__ stop) {
+    if (stop && *stop) return;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t row = t / G;
+    int lane = (int)(t % G);
+    bool ok = row < S.nrows;
+    C acc = group_row<G, C>(S, ok ? row : -1, lane, x, INT64_MAX);
+    if (ok && lane == 0) y[row] = add ? cadd(acc, y[row]) : acc;
+}
+
+// r = b - A x (coarse levels, no scaling), grouped CSR
+template <int G, typename C, typename R>
+__global__ void __launch_bounds__(256) k_resid_g(CsrGView<C> A, const R *__restrict__ diag, const C *__restrict__ b,
+                                                 const C *__restrict__ x, C *__restrict__ r,
+                                                 const int *__restrict__ stop) {
+    if (stop && *stop) return;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t row = t / G;
+    int lane = (int)(t % G);
+    bool ok = row < A.nrows;
+    C acc = group_row<G, C>(A, ok ? row : -1, lane, x, INT64_MAX);
+    if (ok && lane == 0) {
+        C xx = x[row], bb = b[row];
+        R d = diag[row];
+        r[row] = mk(bb.x - acc.x - d * xx.x, bb.y - acc.y - d * xx.y);
+    }
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The wait
+// is bounded: after ~2^26 polls the barrier records an error and lets the block
+// go on, so a broken launch ends instead of hanging.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned spins = 0;
+            while (*gen == g) {
+                if (++spins > (1u << 26)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int *)err == 0;
+}
+
+// One symmetric Gauss-Seidel step on a coarse level in a single cooperative
+// launch: colours 0..nc-1 forward then nc-2..0 backward, a grid barrier between
+// colours.  zero_start: the forward pass starts from x = 0 (only columns of
+// earlier colours are read).
+template <int G, typename C, typename R>
+__global__ void __launch_bounds__(512) k_sgs_coop(CsrGView<C> A, const R *__restrict__ diag,
+                                                  const int64_t *__restrict__ cstart, int ncolors,
+                                                  const C *__restrict__ b, C *__restrict__ x, int zero_start,
+                                                  unsigned *bar, int *err, const int *__restrict__ stop) {
+    if (stop && *stop) return;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t grp = t / G, ngroups = (int64_t)gridDim.x * blockDim.x / G;
+    int lane = (int)(t % G);
+    int nphase = 2 * ncolors - 1;
+    for (int ph = 0; ph < nphase; ++ph) {
+        int c = ph < ncolors ? ph : 2 * ncolors - 2 - ph;
+        bool first = zero_start && ph < ncolors;
+        int64_t lo = cstart[c], hi = cstart[c + 1];
+        int64_t rounds = (hi - lo + ngroups - 1) / ngroups;
+        for (int64_t k = 0; k < rounds; ++k) {
+            int64_t row = lo + k * ngroups + grp;
+            bool ok = row < hi;
+            C acc;
+            if (first && lo == 0) {
+                acc.x = 0;
+                acc.y = 0;
+            } else {
+                acc = group_row<G, C>(A, ok ? row : -1, lane, x, first ? lo : INT64_MAX);
+            }
+            if (ok && lane == 0) {
+                C bb = b[row];
+                R d = (R)1 / diag[row];
+                x[row] = mk((bb.x - acc.x) * d, (bb.y - acc.y) * d);
+            }
+        }
+        if (ph + 1 < nphase && !grid_barrier(bar, err)) return;
+    }
+}
+
+template <int G, typename C, typename R>
+static void launch_sgs_coop(const CsrG<C> &A, const R *diag, const int64_t *cstart, int nc, const C *b, C *x,
+                            int zero_start, unsigned *bar, int *err, const int *stop, int64_t max_colour,
+                            cudaStream_t s) {
+    static int per_sm = -1, nsm = 0;
+    const int threads = 512;
+    if (per_sm < 0) {
+        int dev = 0;
+        GL_CUDA(cudaGetDevice(&dev));
+        GL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        GL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sgs_coop<G, C, R>, threads, 0));
+        GL_REQUIRE(per_sm > 0, GL_ERR_CUDA, "cooperative sweep kernel cannot be resident");
+    }
+    int64_t want = (max_colour * G + threads - 1) / threads;
+    int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)per_sm * nsm);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    GL_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_coop<G, C, R>, A.view(), diag, cstart, nc, b, x, zero_start, bar, err,
+                               stop));
+}
+
+// dispatch on the group width
+#define GL_DISPATCH_G(G_, CALL)                       \
+    switch (G_) {                                     \
+        case 1: { constexpr int GG = 1; CALL; break; }   \
+        case 2: { constexpr int GG = 2; CALL; break; }   \
+        case 4: { constexpr int GG = 4; CALL; break; }   \
+        case 8: { constexpr int GG = 8; CALL; break; }   \
+        case 16: { constexpr int GG = 16; CALL; break; } \
+        default: { constexpr int GG = 32; CALL; break; } \
+    }
+
+template <typename C>
+static void spmv_g(const CsrG<C> &S, const C *x, C *y, int add, const int *stop, cudaStream_t s) {
+    GL_DISPATCH_G(S.G, (k_spmv_g<GG, C><<<grid_for(S.nrows * GG, 256), 256, 0, s>>>(S.view(), x, y, add, stop)));
+}
+
+// x = M b for the dense coarsest inverse (FP64), one warp per row
+__global__ void k_dense_mv(int64_t n, const double2 *__restrict__ M, const double2 *__restrict__ b,
+                           double2 *__restrict__ x, const int *__restrict__ stop) {
+    if (stop && *stop) return;
+    int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    double2 acc = make_double2(0, 0);
+    for (int64_t j = lane; j < n; j += 32) cfma(acc, M[row * n + j], b[j]);
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) x[row] = acc;
+}
+
+template <typename C>
+__global__ void k_axpy_t(int64_t n, const C *__restrict__ e, C *__restrict__ z, const int *__restrict__ stop) {
+    if (stop && *stop) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) z[i] = cadd(z[i], e[i]);
+}
+
+__global__ void k_f2d(int64_t n, const float2 *a, double2 *b, const int *stop) {
+    if (stop && *stop) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = to64(a[i]);
+}
+__global__ void k_d2f2(int64_t n, const double2 *a, float2 *b, const int *stop) {
+    if (stop && *stop) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = to32(a[i]);
+}
+
+template <typename T>
+static void coarse_solve(gl_prec_s *p, Level &L, const typename LevelOps<T>::C *b, typename LevelOps<T>::C *x,
+                         const int *stop, cudaStream_t s);
+template <>
+void coarse_solve<double>(gl_prec_s *, Level &L, const double2 *b, double2 *x, const int *stop, cudaStream_t s) {
+    note_launch();
+    k_dense_mv<<<grid_for(L.n * 32, 256), 256, 0, s>>>(L.n, L.Ainv.get(), b, x, stop);
+}
+template <>
+void coarse_solve<float>(gl_prec_s *p, Level &L, const float2 *b, float2 *x, const int *stop, cudaStream_t s) {
+    note_launch(3);
+    k_f2d<<<grid_for(L.n, 256), 256, 0, s>>>(L.n, b, p->coarse_b64.get(), stop);
+    k_dense_mv<<<grid_for(L.n * 32, 256), 256, 0, s>>>(L.n, L.Ainv.get(), p->coarse_b64.get(), p->coarse_x64.get(),
+                                                      stop);
+    k_d2f2<<<grid_for(L.n, 256), 256, 0, s>>>(L.n, p->coarse_x64.get(), x, stop);
+}
+
+template <typename T>
+static void gs_sweep(Level &L, int level, const typename LevelOps<T>::C *b, typename LevelOps<T>::C *x, int c,
+                     bool first, const int *stop, cudaStream_t s) {
+    using O = LevelOps<T>;
+    using C = typename O::C;
+    int64_t lo = L.cstart[c], hi = L.cstart[c + 1];
+    if (hi <= lo) return;
+    // algorithmic bytes: diagonal, b and the written x for each row; the stored
+    // off-diagonals (value + column) and each neighbour value once, unless the
+    // colour is relaxed from an all-zero guess
+    double rows = (double)(hi - lo);
+    double bytes = rows * (sizeof(T) + 2 * sizeof(C));
+    if (!(first && lo == 0))
+        bytes += (double)L.cnnz[c] * (sizeof(C) + 4) + (double)(first ? lo : L.n - (hi - lo)) * sizeof(C);
+    ProfScope ps(level == 0 ? "gs0" : "gs", bytes, s);
+    k_gs<C, T><<<grid_for(hi - lo, 256), 256, 0, s>>>(lo, hi, O::A(L).view(), O::diag(L), b, x, first ? 1 : 0, stop);
+}
+
+// symmetric Gauss-Seidel: forward over colours, then backward; the backward pass
+// starts one colour early because re-relaxing the last forward colour with
+// unchanged neighbours reproduces the same values
+template <typename T>
+static void sgs(Level &L, int level, const typename LevelOps<T>::C *b, typename LevelOps<T>::C *x, bool zero_start,
+                const int *stop, cudaStream_t s) {
+    int nc = L.ncolors;
+    for (int c = 0; c < nc; ++c) gs_sweep<T>(L, level, b, x, c, zero_start, stop, s);
+    for (int c = nc - 2; c >= 0; --c) gs_sweep<T>(L, level, b, x, c, false, stop, s);
+}
+
+// pre- or post-smoothing on level l: per-colour launches on the lattice level
+// (two colours, large sweeps), one cooperative launch on coarse levels
+template <typename T>
+static void smooth(gl_prec_s *p, int l, const typename LevelOps<T>::C *b, typename LevelOps<T>::C *x, bool zero_start,
+                   const int *stop, cudaStream_t s) {
+    using O = LevelOps<T>;
+    using C = typename O::C;
+    Level &L = p->L[l];
+    if (l == 0) {
+        sgs<T>(L, l, b, x, zero_start, stop, s);
+        return;
+    }
+    const CsrG<C> &A = O::Ag(L);
+    int64_t maxc = 0;
+    for (int c = 0; c < L.ncolors; ++c) maxc = std::max(maxc, L.cstart[c + 1] - L.cstart[c]);
+    ProfScope ps("gs", 0, s);
+    GL_DISPATCH_G(A.G, (launch_sgs_coop<GG, C, T>(A, O::diag(L), L.cstart_dev.get(), L.ncolors, b, x,
+                                                   zero_start ? 1 : 0, L.barrier.get(), p->err.get(), stop, maxc, s)));
+}
+
+template <typename T>
+static void vcycle(gl_prec_s *p, int l, const typename LevelOps<T>::C *b, typename LevelOps<T>::C *x,
+                   const int *stop, cudaStream_t s) {
+    using O = LevelOps<T>;
+    using C = typename O::C;
+    Level &L = p->L[l];
+    if (l == p->nlev - 1) {
+        coarse_solve<T>(p, L, b, x, stop, s);
+        return;
+    }
+    Level &Lc = p->L[l + 1];
+    smooth<T>(p, l, b, x, true, stop, s);
+    C *r = O::r(L);
+    if (l == 0) {
+        const T *scale;
+        if constexpr (sizeof(T) == 8)
+            scale = p->mesh->volp.get();
+        else
+            scale = p->mesh->volp32.get();
+        ProfScope ps("resid0", 0, s);
+        k_resid<C, T><<<grid_for(L.n, 256), 256, 0, s>>>(L.n, O::A(L).view(), O::diag(L), b, x, scale, r, stop);
+    } else {
+        const CsrG<C> &A = O::Ag(L);
+        ProfScope ps("resid", 0, s);
+        GL_DISPATCH_G(A.G, (k_resid_g<GG, C, T><<<grid_for(L.n * GG, 256), 256, 0, s>>>(A.view(), O::diag(L), b, x,
+                                                                                        r, stop)));
+    }
+    {
+        ProfScope ps("restrict", 0, s);
+        spmv_g<C>(O::PHg(L), r, O::b(Lc), 0, stop, s);
+    }
+    vcycle<T>(p, l + 1, O::b(Lc), O::x(Lc), stop, s);
+    {
+        ProfScope ps("prolong", 0, s);
+        k_spmv<C><<<grid_for(L.n, 256), 256, 0, s>>>(L.n, O::P(L).view(), O::x(Lc), x, 1, stop);
+    }
+    smooth<T>(p, l, b, x, false, stop, s);
+    GL_LAUNCH_CHECK();
+}
+
+template <typename T>
+static void precond_apply_t(gl_prec_s *p, const typename LevelOps<T>::C *v, typename LevelOps<T>::C *z,
+                            const int *stop, cudaStream_t s) {
+    using O = LevelOps<T>;
+    using C = typename O::C;
+    if (p->cycles <= 1) {
+        vcycle<T>(p, 0, v, z, stop, s);
+    } else {
+        // R_k: k steps of z <- z + V(v - (K + 2|psi|^2) z) from z = 0
+        Level &L = p->L[0];
+        C *r, *e;
+        if constexpr (sizeof(T) == 8) {
+            r = p->cyc_r.get();
+            e = p->cyc_e.get();
+        } else {
+            r = p->cyc_r32.get();
+            e = p->cyc_e32.get();
+        }
+        for (int k = 0; k < p->cycles; ++k) {
+            if (k == 0) {
+                vcycle<T>(p, 0, v, z, stop, s);
+                continue;
+            }
+            note_launch(2);
+            k_resid<C, T><<<grid_for(L.n, 256), 256, 0, s>>>(L.n, O::A(L).view(), O::diag(L), v, z, nullptr, r, stop);
+            vcycle<T>(p, 0, r, e, stop, s);
+            k_axpy_t<C><<<grid_for(L.n, 256), 256, 0, s>>>(L.n, e, z, stop);
+        }
+    }
+    GL_LAUNCH_CHECK();
+}
+
+void precond_apply_p(gl_prec_s *p, const double2 *v, double2 *z, const int *stop, cudaStream_t s) {
+    precond_apply_t<double>(p, v, z, stop, s);
+}
+void precond_apply_p32(gl_prec_s *p, const float2 *v, float2 *z, const int *stop, cudaStream_t s) {
+    precond_apply_t<float>(p, v, z, stop, s);
+}
+void precond_apply_p64_via32(gl_prec_s *p, const double2 *v, double2 *z, const int *stop, cudaStream_t s) {
+    int64_t n = p->mesh->n;
+    note_launch(2);
+    k_d2f2<<<grid_for(n, 256), 256, 0, s>>>(n, v, p->mp_in.get(), stop);
+    precond_apply_t<float>(p, p->mp_in.get(), p->mp_out.get(), stop, s);
+    k_f2d<<<grid_for(n, 256), 256, 0, s>>>(n, p->mp_out.get(), z, stop);
+    GL_LAUNCH_CHECK();
+}
+
+}  // namespace gl
