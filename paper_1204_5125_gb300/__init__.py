@@ -23,7 +23,8 @@ __all__ = [
     "gl_mesh_khat", "gl_residual", "gl_jacobian_apply", "gl_precond_setup", "gl_precond_apply",
     "gl_precond_destroy", "gl_precond_levels", "gl_precond_level_info", "gl_precond_level_aggregates",
     "gl_precond_level_colors", "gl_precond_level_matrix", "gl_precond_level_P", "gl_jacobian_solve",
-    "gl_newton_step", "gl_batch_solve", "gl_profile_begin", "gl_profile_end", "gl_last_error", "EXPORTED",
+    "gl_newton_step", "gl_batch_solve", "gl_profile_begin", "gl_profile_end", "gl_jacobian_apply_noalloc",
+    "gl_last_error", "EXPORTED",
 ]
 
 GL_FP64, GL_MIXED, GL_MIXED_PRECOND = 0, 1, 2
@@ -36,7 +37,7 @@ EXPORTED = [
     "gl_precond_setup", "gl_precond_apply", "gl_precond_destroy", "gl_precond_levels", "gl_precond_level_info",
     "gl_precond_level_aggregates", "gl_precond_level_colors", "gl_precond_level_matrix", "gl_precond_level_P",
     "gl_mesh_nedges", "gl_mesh_edges", "gl_mesh_khat", "gl_jacobian_solve", "gl_newton_step", "gl_batch_solve",
-    "gl_profile_begin", "gl_profile_end", "gl_last_error",
+    "gl_profile_begin", "gl_profile_end", "gl_jacobian_apply_noalloc", "gl_last_error",
 ]
 
 
@@ -105,6 +106,7 @@ def library(build_if_missing: bool = True):
             "gl_batch_solve": [C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                C.POINTER(Options), C.POINTER(SolveInfo), vp],
             "gl_profile_begin": [C.c_char_p, C.c_int],
+            "gl_jacobian_apply_noalloc": [vp, vp, vp, vp, vp],
             "gl_profile_end": [i64p, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         }
         for name, args in sig.items():
@@ -204,6 +206,11 @@ def gl_residual(mesh, psi, r, stream=None):
 
 def gl_jacobian_apply(mesh, psi, phi, y, precision=GL_FP64, stream=None):
     _check(library().gl_jacobian_apply(mesh, _ptr(psi), _ptr(phi), _ptr(y), int(precision), _stream(stream)))
+
+
+def gl_jacobian_apply_noalloc(mesh, psi, phi, y, stream=None):
+    """FP64 Jacobian apply that allocates no device memory (static scratch; see gl.h)."""
+    _check(library().gl_jacobian_apply_noalloc(mesh, _ptr(psi), _ptr(phi), _ptr(y), _stream(stream)))
 
 
 def gl_precond_setup(mesh, psi, opts: Options | None = None, stream=None):
