@@ -6,9 +6,12 @@ complex-normal right-hand side (seed 5).
 
 One step = one R_1-preconditioned MINRES solve of J(psi) x = b from x = 0 until
 the FP64 true residual ||b - J x||_D / ||b||_D <= 1e-10.  The preconditioner is
-set up once for psi before the timed region (setup-exclusive solves/s).  The
-headline form is GL_MIXED (FP32 applies and V-cycles inside FP64 defect
-correction); the FP64 form is timed beside it.
+set up once for psi before the timed region (setup-exclusive solves/s).  Two
+mixed-precision forms are measured (GL_MIXED: FP32 inner MINRES solves with FP32
+Jacobian applies and V-cycles inside FP64 defect correction; GL_MIXED_PRECOND:
+FP32 V-cycle inside FP64 MINRES) and the faster one is the headline; the FP64
+form is timed beside it.  The AMG hierarchy stops coarsening at 4096 nodes
+(--max-coarse), where the dense FP64 inverse takes over.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 Multi-GPU (one rank per GPU via torch.distributed.run): every rank solves its
@@ -46,7 +49,7 @@ def parse():
     ap.add_argument("--N", type=int, default=128, help="nodes per side of the cube")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--max-coarse", type=int, default=512, help="coarsest-level size bound of the AMG hierarchy")
+    ap.add_argument("--max-coarse", type=int, default=4096, help="coarsest-level size bound of the AMG hierarchy")
     return ap.parse_args()
 
 
@@ -109,13 +112,30 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def recorded_traffic():
+    """DRAM bytes per launch of the roofline kernel from the committed ncu capture,
+    or None when the kernel's sources changed since that capture."""
+    import hashlib
+
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    h = hashlib.sha256()
+    for s in rec["sources"]:
+        with open(os.path.join(ROOT, s), "rb") as f:
+            h.update(f.read())
+    return rec["dram_bytes_per_launch"] if h.hexdigest() == rec["sources_sha256"] else None
+
+
 def workload(N):
     dim, _, mu, bh = gi.WORKLOADS["cube128"]
     n = N ** 3
     return dim, mu, bh, n
 
 
-def cpu_baseline(N, b, x_gpu):
+def cpu_baseline(N, b, x_gpu, max_coarse):
     """The oracle's FP64 R_1-MINRES solve of the same system on the host (setup
     excluded, like the GPU number); also the GPU solution's error against it."""
     import oracle
@@ -124,7 +144,7 @@ def cpu_baseline(N, b, x_gpu):
     t0 = time.perf_counter()
     m = oracle.Mesh(dim, N, mu, bh)
     psi = np.ones(n, complex)
-    P = oracle.Precond(m, psi)
+    P = oracle.Precond(m, psi, max_coarse=max_coarse)
     t1 = time.perf_counter()
     x, info = P.minres(b)
     t2 = time.perf_counter()
@@ -152,7 +172,7 @@ def run_reference(args):
     m = oracle.Mesh(dim, N, mu, bh)
     psi = np.ones(n, complex)
     b = gi.complex_normal(n, 5)
-    P = oracle.Precond(m, psi)
+    P = oracle.Precond(m, psi, max_coarse=args.max_coarse)
     x, info = P.minres(b)
     full_iters = info.iters
     per_it = []
@@ -302,7 +322,7 @@ def main():
         "bound": "hbm", "kernel": "k_gs (Gauss-Seidel colour sweep, finest level, FP32)",
         "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": achieved / peak if achieved else None, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-        "traffic": None, "alg_bytes_per_launch": per_launch_bytes,
+        "traffic": recorded_traffic(), "alg_bytes_per_launch": per_launch_bytes,
         "launches_timed": prof["timed"] if prof else None,
         "avg_launch_us": 1e3 * prof["ms"] / prof["timed"] if prof and prof["timed"] else None,
     }
@@ -310,7 +330,7 @@ def main():
     cpu = None
     err_vs_oracle = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, err_vs_oracle = cpu_baseline(N, b_host, x_mixed.cpu().numpy())
+        cpu, err_vs_oracle = cpu_baseline(N, b_host, x_mixed.cpu().numpy(), args.max_coarse)
 
     if rank == 0:
         line = {
