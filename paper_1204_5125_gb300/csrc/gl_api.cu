@@ -330,33 +330,16 @@ gl_status gl_newton_step(gl_mesh m, void *psi, const gl_options *opt, gl_solve_i
         cudaStream_t s = as_stream(stream);
         int64_t n = m->n;
         DBuf<double2> r(n), d(n);
-        GL_REQUIRE(gl_residual(m, psi, r.get(), stream) == GL_OK, GL_ERR_CUDA, last_error());
-        // ||GL||_R and the right-hand side -GL(psi)
-        std::vector<double2> hr(n);
-        std::vector<double> hv(n);
-        GL_CUDA(cudaMemcpyAsync(hr.data(), r.get(), n * sizeof(double2), cudaMemcpyDeviceToHost, s));
-        GL_CUDA(cudaMemcpyAsync(hv.data(), m->vol.get(), n * sizeof(double), cudaMemcpyDeviceToHost, s));
-        GL_CUDA(cudaStreamSynchronize(s));
-        double g2 = 0;
-        for (int64_t i = 0; i < n; ++i) {
-            g2 += hv[i] * (hr[i].x * hr[i].x + hr[i].y * hr[i].y);
-            hr[i].x = -hr[i].x;
-            hr[i].y = -hr[i].y;
-        }
-        if (gl_norm_out) *gl_norm_out = std::sqrt(g2);
-        GL_CUDA(cudaMemcpyAsync(r.get(), hr.data(), n * sizeof(double2), cudaMemcpyHostToDevice, s));
+        DBuf<double> part(RED_BLOCKS), scal(1);
+        // r = -GL(psi) and ||GL(psi)||_R, on the device
+        gl_status st = gl_residual(m, psi, r.get(), stream);
+        GL_REQUIRE(st == GL_OK, st, last_error());
+        double g = newton_rhs(m, r.get(), part.get(), scal.get(), s);
+        if (gl_norm_out) *gl_norm_out = g;
         GL_CUDA(cudaMemsetAsync(d.get(), 0, n * sizeof(double2), s));
-        gl_status st = gl_jacobian_solve(m, psi, nullptr, r.get(), d.get(), opt, info, stream);
+        st = gl_jacobian_solve(m, psi, nullptr, r.get(), d.get(), opt, info, stream);
         if (st != GL_OK && st != GL_ERR_NOT_CONVERGED) return st;
-        std::vector<double2> hp(n), hd(n);
-        GL_CUDA(cudaMemcpyAsync(hp.data(), psi, n * sizeof(double2), cudaMemcpyDeviceToHost, s));
-        GL_CUDA(cudaMemcpyAsync(hd.data(), d.get(), n * sizeof(double2), cudaMemcpyDeviceToHost, s));
-        GL_CUDA(cudaStreamSynchronize(s));
-        for (int64_t i = 0; i < n; ++i) {
-            hp[i].x += hd[i].x;
-            hp[i].y += hd[i].y;
-        }
-        GL_CUDA(cudaMemcpyAsync(psi, hp.data(), n * sizeof(double2), cudaMemcpyHostToDevice, s));
+        newton_update(n, d.get(), static_cast<double2 *>(psi), s);
         GL_CUDA(cudaStreamSynchronize(s));
         return st;
     });

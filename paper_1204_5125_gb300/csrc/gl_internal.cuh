@@ -53,7 +53,7 @@ struct Level {
     Sell<double2> P, PH;            // permuted prolongator / its adjoint
     CsrG<double2> Ag, PHg;          // grouped-CSR forms: coarse-level A (ell >= 1) and P^H
     DBuf<int64_t> cstart_dev;       // cstart on the device (cooperative sweeps)
-    DBuf<unsigned> barrier;         // grid-barrier state of the cooperative sweeps
+    DBuf<unsigned> barrier;         // grid-barrier state of the cooperative coarse sweeps
     DBuf<double2> b, x, r;          // level vectors (solve ordering)
     DBuf<double2> Ainv;             // coarsest: dense inverse, row-major
     // FP32 copies (mixed precision)
@@ -106,6 +106,9 @@ void permute_out(int64_t n, const int32_t *perm, const double2 *sol, double2 *na
 void jacobian_apply_p(const gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s);
 void jacobian_apply_p32(const gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s);
 void residual_p(const gl_mesh_s *m, const double2 *psi, double2 *r, cudaStream_t s);
+// node order: r <- -r, returns ||r||_R (part: RED_BLOCKS doubles, scal: 1 double)
+double newton_rhs(const gl_mesh_s *m, double2 *r, double *part, double *scal, cudaStream_t s);
+void newton_update(int64_t n, const double2 *d, double2 *psi, cudaStream_t s);
 
 // gl_vcycle.cu: z = R_k v in solve ordering; `stop` (nullable) is a device flag
 // that turns every kernel into a no-op when nonzero.

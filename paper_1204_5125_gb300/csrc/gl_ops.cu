@@ -70,6 +70,46 @@ __global__ void k_residual64(int64_t n, SellView<double2> K, const double *__res
     r[p] = mk(acc.x + d * ps.x, acc.y + d * ps.y);
 }
 
+// Newton right-hand side (Eq. Newton system): r <- -r in place, with per-block
+// partials of ||r||_R^2 = sum |V_i| |r_i|^2
+__global__ void k_negate_norm(int64_t n, const double *__restrict__ vol, double2 *__restrict__ r, double *part) {
+    __shared__ double sh[32];
+    double a = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 v = r[i];
+        a += vol[i] * (v.x * v.x + v.y * v.y);
+        r[i] = make_double2(-v.x, -v.y);
+    }
+    double t = block_sum(a, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+__global__ void k_sum_parts_sqrt(const double *part, int np, double *out) {
+    __shared__ double sh[32];
+    double a = 0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) a += part[i];
+    double t = block_sum(a, sh);
+    if (threadIdx.x == 0) *out = sqrt(t);
+}
+// psi <- psi + d
+__global__ void k_axpy64(int64_t n, const double2 *__restrict__ d, double2 *__restrict__ psi) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) psi[i] = cadd(psi[i], d[i]);
+}
+
+double newton_rhs(const gl_mesh_s *m, double2 *r, double *part, double *scal, cudaStream_t s) {
+    k_negate_norm<<<RED_BLOCKS, RED_THREADS, 0, s>>>(m->n, m->vol.get(), r, part);
+    k_sum_parts_sqrt<<<1, 1024, 0, s>>>(part, RED_BLOCKS, scal);
+    GL_LAUNCH_CHECK();
+    double g = 0;
+    GL_CUDA(cudaMemcpyAsync(&g, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaStreamSynchronize(s));
+    return g;
+}
+void newton_update(int64_t n, const double2 *d, double2 *psi, cudaStream_t s) {
+    k_axpy64<<<grid_for(n, 256), 256, 0, s>>>(n, d, psi);
+    GL_LAUNCH_CHECK();
+}
+
 void jacobian_apply_p(const gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s) {
     k_jacobian64<<<grid_for(m->n, 256), 256, 0, s>>>(m->n, m->K.view(), m->kdiag.get(), psi, phi, y);
     GL_LAUNCH_CHECK();

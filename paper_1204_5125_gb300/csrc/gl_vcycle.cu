@@ -149,71 +149,148 @@ __global__ void __launch_bounds__(256) k_resid_g(CsrGView<C> A, const R *__restr
     }
 }
 
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The wait
-// is bounded: after ~2^26 polls the barrier records an error and lets the block
-// go on, so a broken launch ends instead of hanging.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
+// ---------------------------------------------------------------- coarse-level SGS
+// Grid-wide barrier for a cooperative launch (all blocks co-resident), split
+// into arrive and wait so that independent work can run in between.  The wait
+// is bounded: after ~2^24 polls it records an error and lets the block go on,
+// so a broken launch ends instead of hanging.
+__device__ __forceinline__ unsigned grid_arrive(unsigned *bar) {
     __syncthreads();
+    unsigned g = 0;
     if (threadIdx.x == 0) {
         volatile unsigned *gen = bar + 1;
-        unsigned g = *gen;
+        g = *gen;
         __threadfence();
         if (atomicAdd(bar, 1u) == gridDim.x - 1) {
             atomicExch(bar, 0u);
             __threadfence();
             atomicAdd(bar + 1, 1u);
-        } else {
-            unsigned spins = 0;
-            while (*gen == g) {
-                if (++spins > (1u << 26)) {
-                    atomicExch(err, 1);
-                    break;
-                }
-                __nanosleep(32);
+        }
+    }
+    return g;
+}
+__device__ __forceinline__ bool grid_wait(unsigned *bar, unsigned g, int *err) {
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        unsigned spins = 0;
+        int good = 1;
+        while (*gen == g) {
+            if (++spins > (1u << 24)) {
+                atomicExch(err, 1);
+                good = 0;
+                break;
             }
         }
         __threadfence();
+        ok = good;
     }
     __syncthreads();
-    return *(volatile int *)err == 0;
+    return ok;
 }
 
 // One symmetric Gauss-Seidel step on a coarse level in a single cooperative
 // launch: colours 0..nc-1 forward then nc-2..0 backward, a grid barrier between
 // colours.  zero_start: the forward pass starts from x = 0 (only columns of
-// earlier colours are read).
+// earlier colours are read).  Between arriving at and leaving a barrier each
+// group loads the structure, values, b and diagonal of its row in the next
+// colour (they do not depend on x), so after the barrier only the neighbour
+// gathers remain.  The gathers use L2 loads (__ldcg): the values were written
+// by other blocks.
+constexpr int PF = 8;  // prefetched entries per lane
+
+template <typename R>
+constexpr int coop_threads() {
+    return sizeof(R) == 8 ? 512 : 1024;  // FP64 rows need more registers per thread
+}
+
 template <int G, typename C, typename R>
-__global__ void __launch_bounds__(512) k_sgs_coop(CsrGView<C> A, const R *__restrict__ diag,
-                                                  const int64_t *__restrict__ cstart, int ncolors,
-                                                  const C *__restrict__ b, C *__restrict__ x, int zero_start,
-                                                  unsigned *bar, int *err, const int *__restrict__ stop) {
+__global__ void __launch_bounds__(coop_threads<R>()) k_sgs_coop(CsrGView<C> A, const R *__restrict__ diag,
+                                                                const int64_t *__restrict__ cstart, int ncolors,
+                                                                const C *__restrict__ b, C *x, int zero_start,
+                                                                unsigned *bar, int *err,
+                                                                const int *__restrict__ stop) {
     if (stop && *stop) return;
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t grp = t / G, ngroups = (int64_t)gridDim.x * blockDim.x / G;
     int lane = (int)(t % G);
     int nphase = 2 * ncolors - 1;
+    int32_t pcol[PF];
+    C pval[PF];
+    C pb;
+    R pd = 1;
+    int64_t pq0 = 0, pq1 = 0;
+    auto colour_of = [&](int ph) { return ph < ncolors ? ph : 2 * ncolors - 2 - ph; };
+    // loads the x-independent data of row `row` (first round of a phase)
+    auto prefetch = [&](int64_t row, bool ok) {
+        pq0 = pq1 = 0;
+        if (ok) {
+            pq0 = A.rp[row];
+            pq1 = A.rp[row + 1];
+            pb = b[row];
+            pd = diag[row];
+        }
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            int64_t q = pq0 + lane + (int64_t)k * G;
+            if (q < pq1) {
+                pcol[k] = __ldg(A.col + q);
+                pval[k] = A.val[q];
+            }
+        }
+    };
+    {
+        int c = colour_of(0);
+        prefetch(cstart[c] + grp, cstart[c] + grp < cstart[c + 1]);
+    }
     for (int ph = 0; ph < nphase; ++ph) {
-        int c = ph < ncolors ? ph : 2 * ncolors - 2 - ph;
+        int c = colour_of(ph);
         bool first = zero_start && ph < ncolors;
         int64_t lo = cstart[c], hi = cstart[c + 1];
+        int64_t lim = first ? lo : INT64_MAX;
         int64_t rounds = (hi - lo + ngroups - 1) / ngroups;
         for (int64_t k = 0; k < rounds; ++k) {
             int64_t row = lo + k * ngroups + grp;
             bool ok = row < hi;
             C acc;
-            if (first && lo == 0) {
-                acc.x = 0;
-                acc.y = 0;
-            } else {
-                acc = group_row<G, C>(A, ok ? row : -1, lane, x, first ? lo : INT64_MAX);
+            acc.x = 0;
+            acc.y = 0;
+            if (!(first && lo == 0)) {
+                if (k == 0) {
+#pragma unroll
+                    for (int e = 0; e < PF; ++e) {
+                        int64_t q = pq0 + lane + (int64_t)e * G;
+                        if (q < pq1 && pcol[e] < lim) cfma(acc, pval[e], __ldcg(x + pcol[e]));
+                    }
+                    for (int64_t q = pq0 + lane + (int64_t)PF * G; q < pq1; q += G) {
+                        int32_t cc = __ldg(A.col + q);
+                        if (cc < lim) cfma(acc, A.val[q], __ldcg(x + cc));
+                    }
+                } else if (ok) {
+                    for (int64_t q = A.rp[row] + lane; q < A.rp[row + 1]; q += G) {
+                        int32_t cc = __ldg(A.col + q);
+                        if (cc < lim) cfma(acc, A.val[q], __ldcg(x + cc));
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) {
+                acc.x += __shfl_down_sync(0xffffffffu, acc.x, o, G);
+                acc.y += __shfl_down_sync(0xffffffffu, acc.y, o, G);
             }
             if (ok && lane == 0) {
-                C bb = b[row];
-                R d = (R)1 / diag[row];
+                C bb = (k == 0) ? pb : b[row];
+                R d = (R)1 / ((k == 0) ? pd : diag[row]);
                 x[row] = mk((bb.x - acc.x) * d, (bb.y - acc.y) * d);
             }
         }
-        if (ph + 1 < nphase && !grid_barrier(bar, err)) return;
+        if (ph + 1 < nphase) {
+            // arrive, load the next colour's x-independent data, then wait
+            unsigned g = grid_arrive(bar);
+            int cn = colour_of(ph + 1);
+            prefetch(cstart[cn] + grp, cstart[cn] + grp < cstart[cn + 1]);
+            if (!grid_wait(bar, g, err)) return;
+        }
     }
 }
 
@@ -222,7 +299,7 @@ static void launch_sgs_coop(const CsrG<C> &A, const R *diag, const int64_t *csta
                             int zero_start, unsigned *bar, int *err, const int *stop, int64_t max_colour,
                             cudaStream_t s) {
     static int per_sm = -1, nsm = 0;
-    const int threads = 512;
+    const int threads = coop_threads<R>();
     if (per_sm < 0) {
         int dev = 0;
         GL_CUDA(cudaGetDevice(&dev));
@@ -261,20 +338,34 @@ static void spmv_g(const CsrG<C> &S, const C *x, C *y, int add, const int *stop,
     GL_DISPATCH_G(S.G, (k_spmv_g<GG, C><<<grid_for(S.nrows * GG, 256), 256, 0, s>>>(S.view(), x, y, add, stop)));
 }
 
-// x = M b for the dense coarsest inverse (FP64), one warp per row
-__global__ void k_dense_mv(int64_t n, const double2 *__restrict__ M, const double2 *__restrict__ b,
-                           double2 *__restrict__ x, const int *__restrict__ stop) {
+// x = M b for the dense coarsest inverse (FP64), one block of 256 threads per row
+__global__ void __launch_bounds__(256) k_dense_mv(int64_t n, const double2 *__restrict__ M,
+                                                  const double2 *__restrict__ b, double2 *__restrict__ x,
+                                                  const int *__restrict__ stop) {
+    __shared__ double shx[8], shy[8];
     if (stop && *stop) return;
-    int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (row >= n) return;
+    int64_t row = blockIdx.x;
     double2 acc = make_double2(0, 0);
-    for (int64_t j = lane; j < n; j += 32) cfma(acc, M[row * n + j], b[j]);
+    const double2 *mr = M + row * n;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) cfma(acc, mr[j], b[j]);
     for (int o = 16; o > 0; o >>= 1) {
         acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
         acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
     }
-    if (lane == 0) x[row] = acc;
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        shx[w] = acc.x;
+        shy[w] = acc.y;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sx = 0, sy = 0;
+        for (int k = 0; k < 8; ++k) {
+            sx += shx[k];
+            sy += shy[k];
+        }
+        x[row] = make_double2(sx, sy);
+    }
 }
 
 template <typename C>
@@ -301,13 +392,13 @@ static void coarse_solve(gl_prec_s *p, Level &L, const typename LevelOps<T>::C *
 template <>
 void coarse_solve<double>(gl_prec_s *, Level &L, const double2 *b, double2 *x, const int *stop, cudaStream_t s) {
     note_launch();
-    k_dense_mv<<<grid_for(L.n * 32, 256), 256, 0, s>>>(L.n, L.Ainv.get(), b, x, stop);
+    k_dense_mv<<<(unsigned)L.n, 256, 0, s>>>(L.n, L.Ainv.get(), b, x, stop);
 }
 template <>
 void coarse_solve<float>(gl_prec_s *p, Level &L, const float2 *b, float2 *x, const int *stop, cudaStream_t s) {
     note_launch(3);
     k_f2d<<<grid_for(L.n, 256), 256, 0, s>>>(L.n, b, p->coarse_b64.get(), stop);
-    k_dense_mv<<<grid_for(L.n * 32, 256), 256, 0, s>>>(L.n, L.Ainv.get(), p->coarse_b64.get(), p->coarse_x64.get(),
+    k_dense_mv<<<(unsigned)L.n, 256, 0, s>>>(L.n, L.Ainv.get(), p->coarse_b64.get(), p->coarse_x64.get(),
                                                       stop);
     k_d2f2<<<grid_for(L.n, 256), 256, 0, s>>>(L.n, p->coarse_x64.get(), x, stop);
 }
