@@ -42,6 +42,7 @@ extern "C" {
 
 typedef struct gl_mesh_s *gl_mesh;
 typedef struct gl_prec_s *gl_prec;
+typedef struct gl_batch_s *gl_batch;
 
 typedef enum {
     GL_OK = 0,
@@ -74,6 +75,8 @@ typedef struct {
     double inner_tol;    /* GL_MIXED: relative reduction asked of each FP32 inner solve (default 1e-5) */
     int max_outer;       /* GL_MIXED: cap on FP64 refinement steps (default 20) */
     int check_every;     /* host polls the device convergence flag every this many iterations (default 6) */
+    int autotune;        /* 1: at setup, time the SpMV variants of every coarse operator on this GPU and keep
+                            the fastest lanes-per-row width (default 1) */
 } gl_options;
 
 /* Per-solve report. */
@@ -191,11 +194,26 @@ GL_API gl_status gl_jacobian_solve(gl_mesh mesh, const void *psi_dev, gl_prec pr
 GL_API gl_status gl_newton_step(gl_mesh mesh, void *psi_dev, const gl_options *opt, gl_solve_info *info,
                          double *gl_norm_out, void *stream);
 
-/* Solves count independent systems J(psi_s) x_s = b_s on their own meshes with
- * their own R_1(psi_s), all on one stream.  infos: count entries (nullable).
- * Returns the first non-GL_OK status (all instances are still attempted). */
+/* Many independent Newton systems at once (the continuation setting of Sec. 4,
+ * where each step needs a Jacobian solve).  gl_batch_create sets up R_1(psi_s)
+ * for every instance (meshes of any sizes; psi_dev[s] has that mesh's n complex
+ * FP64 values).  gl_batch_run solves J(psi_s) x_s = b_s for all instances in ONE
+ * CUDA-graph launch: every instance is a branch of the graph and iterates inside
+ * a device-side WHILE conditional node until its own stopping test holds (same
+ * test as gl_jacobian_solve); x_dev[s] holds the initial guess on entry.  With
+ * precision GL_MIXED or GL_MIXED_PRECOND the V-cycles run in FP32 inside FP64
+ * MINRES.  The graph is built on the first run and rebuilt when the b/x pointers
+ * change.  infos (nullable): count entries.  Returns the first non-GL_OK status.
+ * Synchronises `stream`. */
+GL_API gl_status gl_batch_create(int count, const gl_mesh *meshes, const void *const *psi_dev, const gl_options *opt,
+                                 void *stream, gl_batch *out);
+GL_API gl_status gl_batch_run(gl_batch batch, const void *const *b_dev, void *const *x_dev, gl_solve_info *infos,
+                              void *stream);
+GL_API gl_status gl_batch_destroy(gl_batch batch);
+
+/* gl_batch_create + gl_batch_run + gl_batch_destroy in one call. */
 GL_API gl_status gl_batch_solve(int count, const gl_mesh *meshes, const void *const *psi_dev, const void *const *b_dev,
-                         void *const *x_dev, const gl_options *opt, gl_solve_info *infos, void *stream);
+                                void *const *x_dev, const gl_options *opt, gl_solve_info *infos, void *stream);
 
 /* Measurement instrumentation (no counterpart in the paper).
  * gl_profile_begin resets the count of hot-path kernel launches and, when

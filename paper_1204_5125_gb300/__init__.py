@@ -23,7 +23,8 @@ __all__ = [
     "gl_mesh_khat", "gl_residual", "gl_jacobian_apply", "gl_precond_setup", "gl_precond_apply",
     "gl_precond_destroy", "gl_precond_levels", "gl_precond_level_info", "gl_precond_level_aggregates",
     "gl_precond_level_colors", "gl_precond_level_matrix", "gl_precond_level_P", "gl_jacobian_solve",
-    "gl_newton_step", "gl_batch_solve", "gl_profile_begin", "gl_profile_end", "gl_jacobian_apply_noalloc",
+    "gl_newton_step", "gl_batch_solve", "gl_batch_create", "gl_batch_run", "gl_batch_destroy",
+    "gl_profile_begin", "gl_profile_end", "gl_jacobian_apply_noalloc",
     "gl_last_error", "EXPORTED",
 ]
 
@@ -37,7 +38,8 @@ EXPORTED = [
     "gl_precond_setup", "gl_precond_apply", "gl_precond_destroy", "gl_precond_levels", "gl_precond_level_info",
     "gl_precond_level_aggregates", "gl_precond_level_colors", "gl_precond_level_matrix", "gl_precond_level_P",
     "gl_mesh_nedges", "gl_mesh_edges", "gl_mesh_khat", "gl_jacobian_solve", "gl_newton_step", "gl_batch_solve",
-    "gl_profile_begin", "gl_profile_end", "gl_jacobian_apply_noalloc", "gl_last_error",
+    "gl_profile_begin", "gl_profile_end", "gl_jacobian_apply_noalloc", "gl_batch_create", "gl_batch_run",
+    "gl_batch_destroy", "gl_last_error",
 ]
 
 
@@ -51,7 +53,7 @@ class Options(C.Structure):
     _fields_ = [
         ("tol", C.c_double), ("maxit", C.c_int), ("cycles", C.c_int), ("max_coarse", C.c_int),
         ("max_levels", C.c_int), ("power_its", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double),
-        ("max_outer", C.c_int), ("check_every", C.c_int),
+        ("max_outer", C.c_int), ("check_every", C.c_int), ("autotune", C.c_int),
     ]
 
 
@@ -107,6 +109,9 @@ def library(build_if_missing: bool = True):
                                C.POINTER(Options), C.POINTER(SolveInfo), vp],
             "gl_profile_begin": [C.c_char_p, C.c_int],
             "gl_jacobian_apply_noalloc": [vp, vp, vp, vp, vp],
+            "gl_batch_create": [C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(Options), vp, C.POINTER(vp)],
+            "gl_batch_run": [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveInfo), vp],
+            "gl_batch_destroy": [vp],
             "gl_profile_end": [i64p, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         }
         for name, args in sig.items():
@@ -288,6 +293,30 @@ def gl_newton_step(mesh, psi, opts: Options | None = None, stream=None):
     if st not in (0, 4):
         _check(st)
     return st, info, gn.value
+
+
+def _vparr(xs_):
+    return (vp * len(xs_))(*[x.value if isinstance(x, C.c_void_p) else _ptr(x).value for x in xs_])
+
+
+def gl_batch_create(meshes, psis, opts: Options | None = None, stream=None):
+    o = opts if opts is not None else gl_options_default()
+    out = C.c_void_p()
+    _check(library().gl_batch_create(len(meshes), _vparr(meshes), _vparr(psis), C.byref(o), _stream(stream),
+                                     C.byref(out)))
+    return out
+
+
+def gl_batch_run(batch, bs, xs, stream=None):
+    infos = (SolveInfo * len(bs))()
+    st = library().gl_batch_run(batch, _vparr(bs), _vparr(xs), infos, _stream(stream))
+    if st not in (0, 4):
+        _check(st)
+    return st, list(infos)
+
+
+def gl_batch_destroy(batch):
+    _check(library().gl_batch_destroy(batch))
 
 
 def gl_batch_solve(meshes, psis, bs, xs, opts: Options | None = None, stream=None):

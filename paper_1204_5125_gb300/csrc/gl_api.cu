@@ -70,6 +70,7 @@ gl_status gl_options_default(gl_options *o) {
     o->inner_tol = 1e-5;
     o->max_outer = 20;
     o->check_every = 6;
+    o->autotune = 1;
     return GL_OK;
 }
 
@@ -345,20 +346,55 @@ gl_status gl_newton_step(gl_mesh m, void *psi, const gl_options *opt, gl_solve_i
     });
 }
 
+gl_status gl_batch_create(int count, const gl_mesh *meshes, const void *const *psi, const gl_options *opt, void *stream,
+                          gl_batch *out) {
+    return guard([&] {
+        GL_REQUIRE(out && count > 0 && meshes && psi, GL_ERR_ARG, "NULL argument or empty batch");
+        check_opts(opt);
+        for (int i = 0; i < count; ++i) GL_REQUIRE(meshes[i] && psi[i], GL_ERR_ARG, "NULL mesh or psi in batch");
+        GL_REQUIRE(opt->cycles >= 1, GL_ERR_ARG, "batched solves need a preconditioner (cycles >= 1)");
+        *out = nullptr;
+        gl_batch_s *B = batch_new();
+        try {
+            batch_create(B, count, meshes, reinterpret_cast<const double2 *const *>(psi), *opt, as_stream(stream));
+        } catch (...) {
+            batch_delete(B);
+            throw;
+        }
+        *out = B;
+        return GL_OK;
+    });
+}
+
+gl_status gl_batch_run(gl_batch B, const void *const *b, void *const *x, gl_solve_info *infos, void *stream) {
+    return guard([&] {
+        GL_REQUIRE(B && b && x, GL_ERR_ARG, "NULL argument");
+        for (size_t i = 0; i < batch_size(B); ++i) GL_REQUIRE(b[i] && x[i], GL_ERR_ARG, "NULL b or x in batch");
+        gl_status st = batch_run(B, reinterpret_cast<const double2 *const *>(b), reinterpret_cast<double2 *const *>(x),
+                                 infos, as_stream(stream));
+        if (st != GL_OK) set_error("at least one batched solve did not converge");
+        return st;
+    });
+}
+
+gl_status gl_batch_destroy(gl_batch B) {
+    return guard([&] {
+        if (B) batch_delete(B);
+        return GL_OK;
+    });
+}
+
 gl_status gl_batch_solve(int count, const gl_mesh *meshes, const void *const *psi, const void *const *b,
                          void *const *x, const gl_options *opt, gl_solve_info *infos, void *stream) {
-    return guard([&] {
-        GL_REQUIRE(count >= 0 && (count == 0 || (meshes && psi && b && x)), GL_ERR_ARG, "NULL argument");
-        check_opts(opt);
-        gl_status first = GL_OK;
-        for (int i = 0; i < count; ++i) {
-            gl_solve_info inf{};
-            gl_status st = gl_jacobian_solve(meshes[i], psi[i], nullptr, b[i], x[i], opt, &inf, stream);
-            if (infos) infos[i] = inf;
-            if (st != GL_OK && first == GL_OK) first = st;
-        }
-        return first;
-    });
+    if (count == 0) return GL_OK;
+    gl_batch B = nullptr;
+    gl_status st = gl_batch_create(count, meshes, psi, opt, stream, &B);
+    if (st != GL_OK) return st;
+    st = gl_batch_run(B, b, x, infos, stream);
+    std::string msg = last_error();
+    gl_batch_destroy(B);
+    if (st != GL_OK) set_error(msg);
+    return st;
 }
 
 gl_status gl_profile_begin(const char *kernel_class, int max_launches) {

@@ -75,6 +75,7 @@ struct gl_prec_s {
     int nlev = 0;
     int cycles = 1;
     bool has32 = false;
+    bool autotune = true;
     gl::Level L[gl::MAX_LEVELS];
     gl::DBuf<double2> psi_p;          // psi in solve ordering
     gl::DBuf<double2> cyc_r, cyc_e;   // work vectors for k > 1 cycles
@@ -114,10 +115,18 @@ void newton_update(int64_t n, const double2 *d, double2 *psi, cudaStream_t s);
 // that turns every kernel into a no-op when nonzero.
 void precond_apply_p(gl_prec_s *p, const double2 *v, double2 *z, const int *stop, cudaStream_t s);
 void precond_apply_p32(gl_prec_s *p, const float2 *v, float2 *z, const int *stop, cudaStream_t s);
+// autotuner: picks the lanes-per-row width of every grouped-CSR operator by timing
+void autotune_levels(gl_prec_s *p, bool fp32, cudaStream_t s);
 // z = R_k v with FP64 vectors and an FP32 V-cycle
 void precond_apply_p64_via32(gl_prec_s *p, const double2 *v, double2 *z, const int *stop, cudaStream_t s);
 
 // gl_solve.cu
+gl_batch_s *batch_new();
+void batch_delete(gl_batch_s *B);
+size_t batch_size(const gl_batch_s *B);
+void batch_create(gl_batch_s *B, int count, gl_mesh_s *const *meshes, const double2 *const *psi, const gl_options &o,
+                  cudaStream_t s);
+gl_status batch_run(gl_batch_s *B, const double2 *const *b, double2 *const *x, gl_solve_info *infos, cudaStream_t s);
 gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, const double2 *b_p, double2 *x_p,
                            const gl_options &o, gl_solve_info *info, cudaStream_t s);
 

@@ -979,6 +979,8 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
         p->cyc_e.alloc(n);
     }
     GL_CUDA(cudaStreamSynchronize(s));
+    p->autotune = o.autotune != 0;
+    if (p->autotune) autotune_levels(p, false, s);
     if (o.precision != GL_FP64) precond_ensure_fp32(p, s);
 }
 
@@ -1015,6 +1017,7 @@ void precond_ensure_fp32(gl_prec_s *p, cudaStream_t s) {
         p->cyc_r32.alloc(m->n);
         p->cyc_e32.alloc(m->n);
     }
+    if (p->autotune) autotune_levels(p, true, s);
     p->mp_in.alloc(m->n);
     p->mp_out.alloc(m->n);
     Level &Lb = p->L[p->nlev - 1];

@@ -12,6 +12,7 @@
 // J e = r whose vectors, Jacobian applies and V-cycles are FP32 (dots and
 // scalars FP64, coarsest solve FP64); the FP64 true residual decides.
 #include <chrono>
+#include <memory>
 
 #include "gl_internal.cuh"
 #include "gl_kernels.cuh"
@@ -23,7 +24,7 @@ struct MinresDev {
     double gamma, gamma_old, eta, eta0, c, c_old, s, s_old;
     double delta, a1, a2, a3, c_new, eta_prev, gamma_cur;
     double bnorm, tol, est, true_rel;
-    int it, maxit, check_true, status, lucky, use_true;
+    int it, maxit, check_true, status, lucky, use_true, replays;
 };
 enum { ST_RUN = 0, ST_CONV = 1, ST_BREAK = 2, ST_NAN = 3, ST_MAXIT = 4 };
 
@@ -164,6 +165,7 @@ __global__ void k_scal_init(MinresDev *S, const double *part) {
     double tol = S->tol;
     int use_true = S->use_true;
     S->it = 0;
+    S->replays = 0;
     S->status = ST_RUN;
     S->check_true = 0;
     S->lucky = 0;
@@ -409,6 +411,97 @@ static void harvest(Graph &g) {
     pr.harvest_direct();
 }
 
+// Enqueues the initial phase of MINRES (v_1 = b - J x_0, z_1 = R v_1,
+// gamma_1) on `cs`; the parameters tol/maxit/use_true are read from S.
+template <typename T>
+static void enqueue_init(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const cplx_t<T> *b, cplx_t<T> *x,
+                         bool vc32, MinresWork<T> &W, cudaStream_t cs) {
+    using O = SolveOps<T>;
+    using C = cplx_t<T>;
+    int64_t n = m->n;
+    MinresDev *S = W.S.get();
+    const int *stop = &S->status;
+    double *part = W.part.get();
+    int G = grid_for(n, 256);
+    C *v0 = W.v[0].get(), *v1 = W.v[1].get(), *z0 = W.z[0].get();
+    C *w0 = W.w[0].get(), *w1 = W.w[1].get();
+    GL_CUDA(cudaMemsetAsync(v0, 0, n * sizeof(C), cs));
+    GL_CUDA(cudaMemsetAsync(w0, 0, n * sizeof(C), cs));
+    GL_CUDA(cudaMemsetAsync(w1, 0, n * sizeof(C), cs));
+    note_launch(3);
+    k_init_resid<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, O::K(m), O::kdiag(m), O::vol(m), psi, b, x, v1, part);
+    k_scal_init<<<1, 1024, 0, cs>>>(S, part);
+    k_zero_if_bzero<C><<<G, 256, 0, cs>>>(n, S, x);
+    GL_LAUNCH_CHECK();
+    if (p) {
+        precond_apply_any<T>(p, v1, z0, stop, vc32, cs);
+    } else {
+        note_launch();
+        k_copy_if<C><<<G, 256, 0, cs>>>(n, v1, z0, stop);
+    }
+    note_launch(2);
+    k_dot<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, O::vol(m), v1, z0, part, stop);
+    k_scal_gamma0<<<1, 1024, 0, cs>>>(S, part);
+    GL_LAUNCH_CHECK();
+}
+
+// Enqueues ITER_UNROLL MINRES iterations on `cs` (buffer roles rotate inside
+// and return to the starting roles at the end).
+template <typename T>
+static void enqueue_body(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const cplx_t<T> *b, cplx_t<T> *x,
+                         bool vc32, MinresWork<T> &W, cudaStream_t cs) {
+    using O = SolveOps<T>;
+    using C = cplx_t<T>;
+    int64_t n = m->n;
+    MinresDev *S = W.S.get();
+    const int *stop = &S->status;
+    double *part = W.part.get();
+    auto K = O::K(m);
+    auto kd = O::kdiag(m);
+    auto vol = O::vol(m);
+    int G = grid_for(n, 256);
+    C *v_old = W.v[0].get(), *v = W.v[1].get(), *v_new = W.v[2].get();
+    C *z = W.z[0].get(), *z_new = W.z[1].get();
+    C *w_old = W.w[0].get(), *w = W.w[1].get(), *w_new = W.w[2].get();
+    for (int k = 0; k < ITER_UNROLL; ++k) {
+        {
+            // algorithmic bytes of the fused Jacobian + dot: off-diagonals, K_ii,
+            // |V|, psi, z (own row; neighbours cached) and the written q
+            int64_t nnz = (sizeof(T) == 8) ? m->K.nnz_real : m->K32.nnz_real;
+            double jb = (double)nnz * (sizeof(C) + 4) + (double)n * (2 * sizeof(T) + 3 * sizeof(C));
+            ProfScope ps("jz", jb, cs);
+            k_jz<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, K, kd, vol, psi, z, W.q.get(), part, stop);
+        }
+        note_launch(2);
+        k_scal_delta<<<1, 1024, 0, cs>>>(S, part);
+        k_vnew<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, S, W.q.get(), v, v_old, v_new);
+        if (p) {
+            precond_apply_any<T>(p, v_new, z_new, stop, vc32, cs);
+        } else {
+            note_launch();
+            k_copy_if<C><<<G, 256, 0, cs>>>(n, v_new, z_new, stop);
+        }
+        note_launch(5);
+        k_dot<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, vol, v_new, z_new, part, stop);
+        k_scal_givens<<<1, 1024, 0, cs>>>(S, part);
+        k_update<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, S, z, w_old, w, w_new, x);
+        k_true_resid<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, K, kd, vol, psi, b, x, part, S, 0);
+        k_scal_true<<<1, 1024, 0, cs>>>(S, part);
+        GL_LAUNCH_CHECK();
+        C *t = v_old;
+        v_old = v;
+        v = v_new;
+        v_new = t;
+        t = z;
+        z = z_new;
+        z_new = t;
+        t = w_old;
+        w_old = w;
+        w = w_new;
+        w_new = t;
+    }
+}
+
 // Runs MINRES on J x = b with x as the initial guess (overwritten).  use_true:
 // stop on the FP64 true residual (FP64 path) or on the estimate alone (inner).
 template <typename T>
@@ -419,79 +512,12 @@ static MinresResult minres(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, con
     int64_t n = m->n;
     W.ensure(n);
     MinresDev *S = W.S.get();
-    const int *stop = &S->status;
     double *part = W.part.get();
-    auto K = O::K(m);
-    auto kd = O::kdiag(m);
-    auto vol = O::vol(m);
-    int G = grid_for(n, 256);
     GraphKey key{m, psi, b, x, p ? p->uid : -1, profiler().generation, vc32 ? 1 : 0};
     if (!(key == W.key) || !W.init.exec || !W.body.exec) {
         W.key = key;
-        C *v0 = W.v[0].get(), *v1 = W.v[1].get(), *z0 = W.z[0].get();
-        C *w0 = W.w[0].get(), *w1 = W.w[1].get();
-        capture(W.init, W.cap, [&](cudaStream_t cs) {
-            GL_CUDA(cudaMemsetAsync(v0, 0, n * sizeof(C), cs));
-            GL_CUDA(cudaMemsetAsync(w0, 0, n * sizeof(C), cs));
-            GL_CUDA(cudaMemsetAsync(w1, 0, n * sizeof(C), cs));
-            note_launch(3);
-            k_init_resid<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, K, kd, vol, psi, b, x, v1, part);
-            k_scal_init<<<1, 1024, 0, cs>>>(S, part);
-            k_zero_if_bzero<C><<<G, 256, 0, cs>>>(n, S, x);
-            GL_LAUNCH_CHECK();
-            if (p) {
-                precond_apply_any<T>(p, v1, z0, stop, vc32, cs);
-            } else {
-                note_launch();
-                k_copy_if<C><<<G, 256, 0, cs>>>(n, v1, z0, stop);
-            }
-            note_launch(2);
-            k_dot<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, vol, v1, z0, part, stop);
-            k_scal_gamma0<<<1, 1024, 0, cs>>>(S, part);
-            GL_LAUNCH_CHECK();
-        });
-        capture(W.body, W.cap, [&](cudaStream_t cs) {
-            C *v_old = W.v[0].get(), *v = W.v[1].get(), *v_new = W.v[2].get();
-            C *z = W.z[0].get(), *z_new = W.z[1].get();
-            C *w_old = W.w[0].get(), *w = W.w[1].get(), *w_new = W.w[2].get();
-            for (int k = 0; k < ITER_UNROLL; ++k) {
-                {
-                    // algorithmic bytes of the fused Jacobian + dot: off-diagonals, K_ii,
-                    // |V|, psi, z (own row; neighbours cached) and the written q
-                    int64_t nnz = (sizeof(T) == 8) ? m->K.nnz_real : m->K32.nnz_real;
-                    double jb = (double)nnz * (sizeof(C) + 4) + (double)n * (2 * sizeof(T) + 3 * sizeof(C));
-                    ProfScope ps("jz", jb, cs);
-                    k_jz<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, K, kd, vol, psi, z, W.q.get(), part, stop);
-                }
-                note_launch(2);
-                k_scal_delta<<<1, 1024, 0, cs>>>(S, part);
-                k_vnew<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, S, W.q.get(), v, v_old, v_new);
-                if (p) {
-                    precond_apply_any<T>(p, v_new, z_new, stop, vc32, cs);
-                } else {
-                    note_launch();
-                    k_copy_if<C><<<G, 256, 0, cs>>>(n, v_new, z_new, stop);
-                }
-                note_launch(5);
-                k_dot<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, vol, v_new, z_new, part, stop);
-                k_scal_givens<<<1, 1024, 0, cs>>>(S, part);
-                k_update<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, S, z, w_old, w, w_new, x);
-                k_true_resid<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, K, kd, vol, psi, b, x, part, S, 0);
-                k_scal_true<<<1, 1024, 0, cs>>>(S, part);
-                GL_LAUNCH_CHECK();
-                C *t = v_old;
-                v_old = v;
-                v = v_new;
-                v_new = t;
-                t = z;
-                z = z_new;
-                z_new = t;
-                t = w_old;
-                w_old = w;
-                w = w_new;
-                w_new = t;
-            }
-        });
+        capture(W.init, W.cap, [&](cudaStream_t cs) { enqueue_init<T>(m, p, psi, b, x, vc32, W, cs); });
+        capture(W.body, W.cap, [&](cudaStream_t cs) { enqueue_body<T>(m, p, psi, b, x, vc32, W, cs); });
     }
     k_set_params<<<1, 1, 0, s>>>(S, tol, maxit, use_true ? 1 : 0);
     GL_LAUNCH_CHECK();
@@ -512,7 +538,8 @@ static MinresResult minres(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, con
     }
     if (use_true) {
         note_launch(2);
-        k_true_resid<C, T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, K, kd, vol, psi, b, x, part, S, 1);
+        k_true_resid<C, T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, O::K(m), O::kdiag(m), O::vol(m), psi, b, x, part, S,
+                                                              1);
         k_scal_final<<<1, 1024, 0, s>>>(S, part);
         GL_LAUNCH_CHECK();
         GL_CUDA(cudaMemcpyAsync(&h, S, sizeof(MinresDev), cudaMemcpyDeviceToHost, s));
@@ -591,6 +618,184 @@ struct SolveWork {
 static SolveWork &solve_work() {
     static thread_local SolveWork w;
     return w;
+}
+
+// ------------------------------------------------------------------ batched solves
+// Many independent systems J(psi_s) x_s = b_s in ONE CUDA-graph launch: each
+// instance is a branch of the graph (its own buffers and preconditioner), and
+// its MINRES iterations run inside a WHILE conditional node whose condition a
+// kernel sets from the instance's status word, so the whole batch runs on the
+// device without host round trips.  The loop is bounded by a replay count.
+__global__ void k_set_cond(cudaGraphConditionalHandle h, MinresDev *S, int max_replays) {
+    int go = (S->status == ST_RUN) && (S->replays < max_replays);
+    S->replays += 1;
+    if (!go && S->status == ST_RUN) S->status = ST_MAXIT;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+struct BatchInst {
+    gl_mesh_s *m = nullptr;
+    gl_prec_s *p = nullptr;
+    MinresWork<double> W;
+    DBuf<double2> b, x;  // solve ordering
+};
+
+}  // namespace gl
+
+struct gl_batch_s {
+    std::vector<std::unique_ptr<gl::BatchInst>> inst;
+    gl_options o{};
+    bool vc32 = false;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void *> b_ptr, x_ptr;  // user pointers the graph was built for
+    cudaStream_t s0 = nullptr, sb = nullptr;
+    std::vector<cudaStream_t> br;
+    std::vector<cudaEvent_t> ev;
+    int64_t launches = 0;
+    ~gl_batch_s() {
+        cudaDeviceSynchronize();
+        if (exec) cudaGraphExecDestroy(exec);
+        for (auto e : ev) cudaEventDestroy(e);
+        for (auto t : br) cudaStreamDestroy(t);
+        if (s0) cudaStreamDestroy(s0);
+        if (sb) cudaStreamDestroy(sb);
+        for (auto &i : inst) delete i->p;
+    }
+};
+
+namespace gl {
+
+gl_batch_s *batch_new() { return new gl_batch_s(); }
+void batch_delete(gl_batch_s *B) { delete B; }
+size_t batch_size(const gl_batch_s *B) { return B->inst.size(); }
+
+void batch_create(gl_batch_s *B, int count, gl_mesh_s *const *meshes, const double2 *const *psi, const gl_options &o,
+                  cudaStream_t s) {
+    B->o = o;
+    B->vc32 = (o.precision != GL_FP64);
+    gl_options so = o;
+    so.precision = B->vc32 ? GL_MIXED_PRECOND : GL_FP64;
+    for (int i = 0; i < count; ++i) {
+        auto I = std::make_unique<BatchInst>();
+        I->m = meshes[i];
+        I->p = new gl_prec_s();
+        precond_setup(I->p, I->m, psi[i], so, s);
+        I->W.ensure(I->m->n);
+        I->b.alloc(I->m->n);
+        I->x.alloc(I->m->n);
+        B->inst.push_back(std::move(I));
+    }
+    GL_CUDA(cudaStreamCreateWithFlags(&B->s0, cudaStreamNonBlocking));
+    GL_CUDA(cudaStreamCreateWithFlags(&B->sb, cudaStreamNonBlocking));
+    B->br.resize(count);
+    for (auto &t : B->br) GL_CUDA(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking));
+    B->ev.resize(count + 1);
+    for (auto &e : B->ev) GL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+}
+
+static void batch_build(gl_batch_s *B, const double2 *const *b, double2 *const *x) {
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+    Profiler &pr = profiler();
+    bool was_active = pr.active;
+    pr.active = false;  // no event nodes inside conditional bodies
+    int64_t l0 = pr.launches.load();
+    cudaStream_t s0 = B->s0;
+    cudaGraph_t graph = nullptr;
+    GL_CUDA(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+    try {
+        GL_CUDA(cudaEventRecord(B->ev[0], s0));
+        for (size_t i = 0; i < B->inst.size(); ++i) {
+            BatchInst &I = *B->inst[i];
+            cudaStream_t si = B->br[i];
+            int64_t n = I.m->n;
+            MinresDev *S = I.W.S.get();
+            GL_CUDA(cudaStreamWaitEvent(si, B->ev[0], 0));
+            permute_in(n, I.m->perm.get(), b[i], I.b.get(), si);
+            permute_in(n, I.m->perm.get(), x[i], I.x.get(), si);
+            k_set_params<<<1, 1, 0, si>>>(S, B->o.tol, B->o.maxit, 1);
+            enqueue_init<double>(I.m, I.p, I.p->psi_p.get(), I.b.get(), I.x.get(), B->vc32, I.W, si);
+            // the WHILE node: its handle lives in the graph being captured
+            cudaStreamCaptureStatus cst;
+            cudaGraph_t cg = nullptr;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t ndeps = 0;
+            GL_CUDA(cudaStreamGetCaptureInfo(si, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
+            cudaGraphConditionalHandle h;
+            GL_CUDA(cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault));
+            int max_replays = B->o.maxit / ITER_UNROLL + 2;
+            k_set_cond<<<1, 1, 0, si>>>(h, S, max_replays);
+            GL_LAUNCH_CHECK();
+            GL_CUDA(cudaStreamGetCaptureInfo(si, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t wnode;
+            GL_CUDA(cudaGraphAddNode(&wnode, cg, deps, nullptr, ndeps, &cp));
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            GL_CUDA(cudaStreamUpdateCaptureDependencies(si, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+            GL_CUDA(cudaStreamBeginCaptureToGraph(B->sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            enqueue_body<double>(I.m, I.p, I.p->psi_p.get(), I.b.get(), I.x.get(), B->vc32, I.W, B->sb);
+            k_set_cond<<<1, 1, 0, B->sb>>>(h, S, max_replays);
+            GL_LAUNCH_CHECK();
+            GL_CUDA(cudaStreamEndCapture(B->sb, &body));
+            // final FP64 true residual, back to node order
+            k_true_resid<double2, double><<<RED_BLOCKS, RED_THREADS, 0, si>>>(
+                n, I.m->K.view(), I.m->kdiag.get(), I.m->volp.get(), I.p->psi_p.get(), I.b.get(), I.x.get(),
+                I.W.part.get(), S, 1);
+            k_scal_final<<<1, 1024, 0, si>>>(S, I.W.part.get());
+            GL_LAUNCH_CHECK();
+            permute_out(n, I.m->perm.get(), I.x.get(), x[i], si);
+            GL_CUDA(cudaEventRecord(B->ev[i + 1], si));
+            GL_CUDA(cudaStreamWaitEvent(s0, B->ev[i + 1], 0));
+        }
+    } catch (...) {
+        cudaStreamEndCapture(s0, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        pr.active = was_active;
+        throw;
+    }
+    GL_CUDA(cudaStreamEndCapture(s0, &graph));
+    pr.active = was_active;
+    B->launches = pr.launches.load() - l0;
+    pr.launches.fetch_sub(B->launches);
+    GL_CUDA(cudaGraphInstantiate(&B->exec, graph, 0));
+    GL_CUDA(cudaGraphDestroy(graph));
+    B->b_ptr.assign(b, b + B->inst.size());
+    B->x_ptr.assign(x, x + B->inst.size());
+}
+
+gl_status batch_run(gl_batch_s *B, const double2 *const *b, double2 *const *x, gl_solve_info *infos, cudaStream_t s) {
+    size_t k = B->inst.size();
+    bool same = B->exec && B->b_ptr.size() == k;
+    for (size_t i = 0; same && i < k; ++i) same = (B->b_ptr[i] == b[i] && B->x_ptr[i] == x[i]);
+    if (!same) batch_build(B, b, x);
+    auto t0 = std::chrono::steady_clock::now();
+    GL_CUDA(cudaGraphLaunch(B->exec, s));
+    note_launch((int)B->launches);  // captured launches; loop bodies replay on the device
+    GL_CUDA(cudaStreamSynchronize(s));
+    double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    gl_status first = GL_OK;
+    for (size_t i = 0; i < k; ++i) {
+        MinresDev h;
+        GL_CUDA(cudaMemcpy(&h, B->inst[i]->W.S.get(), sizeof(MinresDev), cudaMemcpyDeviceToHost));
+        if (infos) {
+            gl_solve_info inf{};
+            inf.iters = h.it;
+            inf.outer_iters = 1;
+            inf.converged = (h.status == ST_CONV && h.true_rel <= B->o.tol);
+            inf.true_relres = h.true_rel;
+            inf.est_relres = h.est;
+            inf.solve_ms = ms;
+            infos[i] = inf;
+        }
+        gl_status st = (h.status == ST_CONV) ? (h.true_rel <= B->o.tol ? GL_OK : GL_ERR_NOT_CONVERGED)
+                                             : status_of(h.status);
+        if (st != GL_OK && first == GL_OK) first = st;
+    }
+    return first;
 }
 
 gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, const double2 *b_p, double2 *x_p,

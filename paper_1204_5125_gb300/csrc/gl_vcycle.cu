@@ -338,6 +338,50 @@ static void spmv_g(const CsrG<C> &S, const C *x, C *y, int add, const int *stop,
     GL_DISPATCH_G(S.G, (k_spmv_g<GG, C><<<grid_for(S.nrows * GG, 256), 256, 0, s>>>(S.view(), x, y, add, stop)));
 }
 
+// Autotuner: times the grouped-CSR SpMV of one operator for every group width
+// (lanes per row) on this GPU and keeps the fastest.  x must hold the
+// operator's column count, y its row count (contents irrelevant).
+template <typename C>
+static void tune_groups(CsrG<C> &S, const C *x, C *y, cudaStream_t s) {
+    if (S.nrows <= 0 || S.nnz <= 0) return;
+    cudaEvent_t e0, e1;
+    GL_CUDA(cudaEventCreate(&e0));
+    GL_CUDA(cudaEventCreate(&e1));
+    int best = S.G;
+    float best_ms = 1e30f;
+    for (int g = 1; g <= 32; g *= 2) {
+        S.G = g;
+        spmv_g<C>(S, x, y, 0, nullptr, s);  // warm
+        GL_CUDA(cudaEventRecord(e0, s));
+        for (int r = 0; r < 5; ++r) spmv_g<C>(S, x, y, 0, nullptr, s);
+        GL_CUDA(cudaEventRecord(e1, s));
+        GL_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        GL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = g;
+        }
+    }
+    S.G = best;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
+
+void autotune_levels(gl_prec_s *p, bool fp32, cudaStream_t s) {
+    for (int l = 0; l + 1 < p->nlev; ++l) {
+        Level &L = p->L[l], &Lc = p->L[l + 1];
+        if (fp32) {
+            if (l > 0) tune_groups<float2>(L.Ag32, L.x32.get(), L.r32.get(), s);
+            tune_groups<float2>(L.PHg32, L.r32.get(), Lc.b32.get(), s);
+        } else {
+            if (l > 0) tune_groups<double2>(L.Ag, L.x.get(), L.r.get(), s);
+            tune_groups<double2>(L.PHg, L.r.get(), Lc.b.get(), s);
+        }
+    }
+    GL_LAUNCH_CHECK();
+}
+
 // x = M b for the dense coarsest inverse (FP64), one block of 256 threads per row
 __global__ void __launch_bounds__(256) k_dense_mv(int64_t n, const double2 *__restrict__ M,
                                                   const double2 *__restrict__ b, double2 *__restrict__ x,

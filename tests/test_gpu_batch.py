@@ -1,0 +1,106 @@
+"""Batched Jacobian solves: many independent instances of uneven sizes in one
+CUDA-graph launch (each iterating in a device-side loop).  Every instance must
+reach the true residual 1e-10 measured with the oracle's Jacobian, and match
+the single-instance solve of the same system."""
+import numpy as np
+import pytest
+
+import gl_inputs as gi
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_1204_5125_gb300 as gl  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def true_relres(om, psi, b, x):
+    vol = om.volumes()
+    r = b - om.jacobian(psi, x)
+    return np.sqrt(np.sum(vol * np.abs(r) ** 2) / np.sum(vol * np.abs(b) ** 2))
+
+
+def instances(sizes, seed0=7):
+    """The batched-continuation workload: 2D squares, mu_s = 2 (s + 1) / count,
+    psi_s = 1 + 0.1 x (disk noise, seed 7 + s), b_s complex normal (seed 100 + s).
+    mu = 0 is left out: psi = 1 solves the zero-field problem, J is singular along
+    i psi next to it (Sec. 3), and a random right-hand side then stalls above
+    1e-10 (the oracle stalls at 2e-10 on the 17^2 instance, kappa ~ 3e7)."""
+    out = []
+    k = len(sizes)
+    for s, N in enumerate(sizes):
+        mu = 2.0 * (s + 1) / k
+        n = N * N
+        out.append((N, mu, gi.psi_noisy_one(n, seed0 + s), gi.complex_normal(n, 100 + s)))
+    return out
+
+
+@pytest.mark.parametrize("precision", [gl.GL_FP64, gl.GL_MIXED_PRECOND])
+def test_batch_matches_single_solves(oracle_mod, precision):
+    sizes = [17, 33, 45, 24, 60, 31]
+    inst = instances(sizes)
+    meshes = [gl.gl_mesh_create(2, N, mu) for N, mu, _, _ in inst]
+    try:
+        psis = [torch.from_numpy(p).to(DEV) for _, _, p, _ in inst]
+        bs = [torch.from_numpy(b).to(DEV) for _, _, _, b in inst]
+        xs = [torch.zeros_like(b) for b in bs]
+        opts = gl.options(precision=precision, max_coarse=64)
+        st, infos = gl.gl_batch_solve(meshes, psis, bs, xs, opts)
+        assert st == 0, [(N, i.iters, i.converged, i.true_relres) for (N, _, _, _), i in zip(inst, infos)]
+        for k, (N, mu, psi, b) in enumerate(inst):
+            om = oracle_mod.Mesh(2, N, mu)
+            assert infos[k].converged
+            assert true_relres(om, psi, b, xs[k].cpu().numpy()) <= 1.01e-10
+            x1 = torch.zeros_like(bs[k])
+            st1, info1 = gl.gl_jacobian_solve(meshes[k], psis[k], None, bs[k], x1, opts)
+            assert st1 == 0 and abs(info1.iters - infos[k].iters) <= 1
+            assert torch.linalg.norm(x1 - xs[k]) <= 1e-8 * torch.linalg.norm(x1)
+    finally:
+        for m in meshes:
+            gl.gl_mesh_destroy(m)
+
+
+@pytest.mark.parametrize("precision", [gl.GL_FP64, gl.GL_MIXED_PRECOND])
+def test_batch64_full_size(oracle_mod, precision):
+    """All 64 instances of the batched-continuation workload (N_s log-uniform in
+    [32, 512], seed 6) in one launch, run twice through the same graph."""
+    sizes = gi.batch_sizes(64, seed=6)
+    inst = instances(sizes)
+    meshes = [gl.gl_mesh_create(2, N, mu) for N, mu, _, _ in inst]
+    B = None
+    try:
+        psis = [torch.from_numpy(p).to(DEV) for _, _, p, _ in inst]
+        bs = [torch.from_numpy(b).to(DEV) for _, _, _, b in inst]
+        xs = [torch.zeros_like(b) for b in bs]
+        B = gl.gl_batch_create(meshes, psis, gl.options(precision=precision))
+        for rep in range(2):
+            for x in xs:
+                x.zero_()
+            if rep == 1:  # new right-hand sides through the cached graph
+                for k, b in enumerate(bs):
+                    b.copy_(torch.from_numpy(gi.complex_normal(b.numel(), 500 + k)))
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record()
+            st, infos = gl.gl_batch_run(B, bs, xs)
+            t1.record()
+            torch.cuda.synchronize()
+            assert st == 0, [(N, i.iters, i.converged, i.true_relres) for N, i in zip(sizes, infos) if not i.converged]
+            iters = [i.iters for i in infos]
+            print(f"batch64 precision={precision} rep={rep}: {64e3 / t0.elapsed_time(t1):.1f} solves/s, "
+                  f"iterations {min(iters)}..{max(iters)}, total n = {sum(N * N for N in sizes)}")
+            for k, (N, mu, psi, _) in enumerate(inst):
+                om = oracle_mod.Mesh(2, N, mu)
+                bh = bs[k].cpu().numpy()
+                assert infos[k].converged
+                assert true_relres(om, psi, bh, xs[k].cpu().numpy()) <= 1.01e-10
+    finally:
+        if B is not None:
+            gl.gl_batch_destroy(B)
+        for m in meshes:
+            gl.gl_mesh_destroy(m)
