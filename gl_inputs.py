@@ -35,6 +35,7 @@ __all__ = [
     "complex_normal",
     "psi_noisy_one",
     "batch_sizes",
+    "warmstart_init",
     "WORKLOADS",
 ]
 
@@ -83,3 +84,15 @@ WORKLOADS = {
     "cube128": (3, 128, 1.0, (INV_SQRT3, INV_SQRT3, INV_SQRT3)),
     "cube256": (3, 256, 1.5, (0.0, 0.0, 1.0)),
 }
+
+
+def warmstart_init(seed: int = 11, layers: int = 4, channels: int = 64) -> np.ndarray:
+    """Random initial parameters of the warm-start network, one flat float32
+    vector: layers matrices of channels x (2 channels) drawn N(0, 2 / fan_in)
+    (He initialisation, fan_in = 2 channels), then a 2 x channels head drawn
+    N(0, 1 / channels) scaled by 0.1."""
+    g = rng(seed)
+    cin = 2 * channels
+    ws = [g.standard_normal(channels * cin) * math.sqrt(2.0 / cin) for _ in range(layers)]
+    head = g.standard_normal(2 * channels) * (0.1 / math.sqrt(channels))
+    return np.concatenate(ws + [head]).astype(np.float32)
