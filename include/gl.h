@@ -43,6 +43,11 @@ extern "C" {
 typedef struct gl_mesh_s *gl_mesh;
 typedef struct gl_prec_s *gl_prec;
 typedef struct gl_batch_s *gl_batch;
+typedef struct gl_warmstart_s *gl_warmstart;
+
+/* Size of the warm-start network's flat parameter vector: four 64 x 128 layer
+ * matrices W^0..W^3 (row-major, outputs x inputs), then the 2 x 64 head U. */
+#define GL_WS_NPARAM (4 * 64 * 128 + 2 * 64)
 
 typedef enum {
     GL_OK = 0,
@@ -77,6 +82,9 @@ typedef struct {
     int check_every;     /* host polls the device convergence flag every this many iterations (default 6) */
     int autotune;        /* 1: at setup, time the SpMV variants of every coarse operator on this GPU and keep
                             the fastest lanes-per-row width (default 1) */
+    gl_warmstart warmstart; /* learned initial guess: when set, gl_jacobian_solve and gl_newton_step ignore the
+                            x passed in, start from the network's x0, and fall back to x0 = 0 when
+                            ||b - J x0||_D >= ||b||_D (default NULL: start from x as given) */
 } gl_options;
 
 /* Per-solve report. */
@@ -88,7 +96,8 @@ typedef struct {
     double est_relres;   /* last MINRES recurrence estimate (preconditioned norm) */
     double setup_ms;     /* preconditioner setup time inside this call (0 if a gl_prec was given) */
     double solve_ms;     /* wall time of the Krylov part */
-    int warmstart_used;  /* reserved: 1 if x was taken from a learned initial guess */
+    int warmstart_used;  /* 1 if the solve started from the learned guess, 0 if from x as given or after
+                            the zero-guess fallback */
 } gl_solve_info;
 
 /* Default options (values listed in gl_options).  Returns GL_ERR_ARG on NULL. */
@@ -230,6 +239,46 @@ GL_API gl_status gl_batch_solve(int count, const gl_mesh *meshes, const void *co
  * summed algorithmic bytes.  Not thread-safe; one profile at a time. */
 GL_API gl_status gl_profile_begin(const char *kernel_class, int max_launches);
 GL_API gl_status gl_profile_end(int64_t *launches, int64_t *timed, double *total_ms, double *alg_bytes);
+
+/* ---------------------------------------------------------------------------
+ * Learned warm start.  The paper has no counterpart: its Newton-Krylov solves
+ * start from x0 = 0 (Sec. 4).  The network predicts the initial guess of the
+ * solve of J(psi) x = b (Eq. (16)) as
+ *     x0 = ||b||_D * y(psi, b / ||b||_D) / K_ii,    ||b||_D^2 = sum_i |V_i| |b_i|^2,
+ * with y a 4-layer, 64-channel graph network whose aggregation is the magnetic
+ * Jacobi operator S = I - diag(K)^-1 K of Eq. (10) (edge weights and phases,
+ * normalised per row), relu activations, channel 63 held at 1 (biases), and a
+ * 2 x 64 linear head.  Its dense layers run as BF16 tensor-core MMAs with FP32
+ * accumulation; activations are BF16.  Training minimises the squared relative
+ * true-Jacobian residual ||b - J x0||_D^2 / ||b||_D^2 with Adam (beta1 0.9,
+ * beta2 0.999, eps 1e-8).  All vectors are n complex FP64 in node order on the
+ * device; every call runs on `stream` and synchronises it.
+ * ------------------------------------------------------------------------- */
+
+/* New network with the given parameters (host, GL_WS_NPARAM floats; NULL =
+ * zeros).  The handle owns its parameters, Adam moments and work buffers
+ * (about 900 bytes per mesh node of the largest mesh it has seen). */
+GL_API gl_status gl_warmstart_create(const float *params_host, gl_warmstart *out);
+GL_API gl_status gl_warmstart_destroy(gl_warmstart ws);
+/* Copy the FP32 parameters out / in (set also resets the Adam state). */
+GL_API gl_status gl_warmstart_get_params(gl_warmstart ws, float *params_host);
+GL_API gl_status gl_warmstart_set_params(gl_warmstart ws, const float *params_host);
+/* x0 = network guess for (psi, b); x0_dev must not alias psi or b. */
+GL_API gl_status gl_warmstart_predict(gl_warmstart ws, gl_mesh mesh, const void *psi_dev, const void *b_dev,
+                                      void *x0_dev, void *stream);
+/* Loss ||b^ - J x^||_D^2 of one sample and its gradient (host, GL_WS_NPARAM
+ * floats, nullable) with respect to the parameters. */
+GL_API gl_status gl_warmstart_grad(gl_warmstart ws, gl_mesh mesh, const void *psi_dev, const void *b_dev,
+                                   float *grad_host, double *loss_out, void *stream);
+/* `steps` Adam steps with learning rate lr; step t averages the losses and
+ * gradients of samples (t * batch + j) mod count, j < batch.  Sample k is
+ * (meshes[k], psi_dev[k], b_dev[k]); meshes may differ between samples.
+ * loss_out (host, nullable) receives the mean loss of every step. */
+GL_API gl_status gl_warmstart_train(gl_warmstart ws, int count, const gl_mesh *meshes, const void *const *psi_dev,
+                                    const void *const *b_dev, int steps, int batch, float lr, double *loss_out,
+                                    void *stream);
+/* One Adam step with the given gradient (host, GL_WS_NPARAM floats). */
+GL_API gl_status gl_warmstart_adam_step(gl_warmstart ws, const float *grad_host, float lr);
 
 /* Message describing the last failure on this host thread ("" if none). */
 GL_API const char *gl_last_error(void);

@@ -25,6 +25,8 @@ __all__ = [
     "gl_precond_level_colors", "gl_precond_level_matrix", "gl_precond_level_P", "gl_jacobian_solve",
     "gl_newton_step", "gl_batch_solve", "gl_batch_create", "gl_batch_run", "gl_batch_destroy",
     "gl_profile_begin", "gl_profile_end", "gl_jacobian_apply_noalloc",
+    "gl_warmstart_create", "gl_warmstart_destroy", "gl_warmstart_get_params", "gl_warmstart_set_params",
+    "gl_warmstart_predict", "gl_warmstart_grad", "gl_warmstart_train", "gl_warmstart_adam_step", "GL_WS_NPARAM",
     "gl_last_error", "EXPORTED",
 ]
 
@@ -39,8 +41,12 @@ EXPORTED = [
     "gl_precond_level_aggregates", "gl_precond_level_colors", "gl_precond_level_matrix", "gl_precond_level_P",
     "gl_mesh_nedges", "gl_mesh_edges", "gl_mesh_khat", "gl_jacobian_solve", "gl_newton_step", "gl_batch_solve",
     "gl_profile_begin", "gl_profile_end", "gl_jacobian_apply_noalloc", "gl_batch_create", "gl_batch_run",
-    "gl_batch_destroy", "gl_last_error",
+    "gl_batch_destroy", "gl_warmstart_create", "gl_warmstart_destroy", "gl_warmstart_get_params",
+    "gl_warmstart_set_params", "gl_warmstart_predict", "gl_warmstart_grad", "gl_warmstart_train",
+    "gl_warmstart_adam_step", "gl_last_error",
 ]
+
+GL_WS_NPARAM = 4 * 64 * 128 + 2 * 64
 
 
 class GLError(RuntimeError):
@@ -53,7 +59,7 @@ class Options(C.Structure):
     _fields_ = [
         ("tol", C.c_double), ("maxit", C.c_int), ("cycles", C.c_int), ("max_coarse", C.c_int),
         ("max_levels", C.c_int), ("power_its", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double),
-        ("max_outer", C.c_int), ("check_every", C.c_int), ("autotune", C.c_int),
+        ("max_outer", C.c_int), ("check_every", C.c_int), ("autotune", C.c_int), ("warmstart", C.c_void_p),
     ]
 
 
@@ -113,6 +119,15 @@ def library(build_if_missing: bool = True):
             "gl_batch_run": [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveInfo), vp],
             "gl_batch_destroy": [vp],
             "gl_profile_end": [i64p, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+            "gl_warmstart_create": [vp, C.POINTER(vp)],
+            "gl_warmstart_destroy": [vp],
+            "gl_warmstart_get_params": [vp, vp],
+            "gl_warmstart_set_params": [vp, vp],
+            "gl_warmstart_predict": [vp, vp, vp, vp, vp, vp],
+            "gl_warmstart_grad": [vp, vp, vp, vp, vp, C.POINTER(C.c_double), vp],
+            "gl_warmstart_train": [vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.c_int, C.c_int,
+                                   C.c_float, vp, vp],
+            "gl_warmstart_adam_step": [vp, vp, C.c_float],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -339,3 +354,59 @@ def gl_profile_end() -> dict:
     ms, by = C.c_double(), C.c_double()
     _check(library().gl_profile_end(C.byref(la), C.byref(ti), C.byref(ms), C.byref(by)))
     return dict(launches=la.value, timed=ti.value, ms=ms.value, bytes=by.value)
+
+
+def _f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.size != GL_WS_NPARAM:
+        raise ValueError(f"expected {GL_WS_NPARAM} parameters, got {a.size}")
+    return a
+
+
+def gl_warmstart_create(params=None):
+    """New warm-start network (params: GL_WS_NPARAM floats, None = zeros)."""
+    out = C.c_void_p()
+    p = None if params is None else _f32(params)
+    _check(library().gl_warmstart_create(None if p is None else p.ctypes.data_as(vp), C.byref(out)))
+    return out
+
+
+def gl_warmstart_destroy(ws):
+    _check(library().gl_warmstart_destroy(ws))
+
+
+def gl_warmstart_get_params(ws) -> np.ndarray:
+    out = np.zeros(GL_WS_NPARAM, np.float32)
+    _check(library().gl_warmstart_get_params(ws, out.ctypes.data_as(vp)))
+    return out
+
+
+def gl_warmstart_set_params(ws, params):
+    p = _f32(params)
+    _check(library().gl_warmstart_set_params(ws, p.ctypes.data_as(vp)))
+
+
+def gl_warmstart_predict(ws, mesh, psi, b, x0, stream=None):
+    _check(library().gl_warmstart_predict(ws, mesh, _ptr(psi), _ptr(b), _ptr(x0), _stream(stream)))
+
+
+def gl_warmstart_grad(ws, mesh, psi, b, stream=None):
+    """(loss, gradient as GL_WS_NPARAM float32) of one sample."""
+    g = np.zeros(GL_WS_NPARAM, np.float32)
+    L = C.c_double()
+    _check(library().gl_warmstart_grad(ws, mesh, _ptr(psi), _ptr(b), g.ctypes.data_as(vp), C.byref(L),
+                                       _stream(stream)))
+    return L.value, g
+
+
+def gl_warmstart_train(ws, meshes, psis, bs, steps: int, batch: int = 1, lr: float = 1e-3, stream=None):
+    """Adam training on samples (meshes[k], psis[k], bs[k]); returns the mean loss of every step."""
+    losses = np.zeros(max(steps, 1), np.float64)
+    _check(library().gl_warmstart_train(ws, len(meshes), _vparr(meshes), _vparr(psis), _vparr(bs), int(steps),
+                                        int(batch), float(lr), losses.ctypes.data_as(vp), _stream(stream)))
+    return losses[:steps]
+
+
+def gl_warmstart_adam_step(ws, grad, lr: float):
+    g = _f32(grad)
+    _check(library().gl_warmstart_adam_step(ws, g.ctypes.data_as(vp), float(lr)))

@@ -804,6 +804,7 @@ gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, con
     auto t0 = std::chrono::steady_clock::now();
     gl_status st;
     gl_solve_info inf{};
+    if (o.warmstart) warmstart_apply_p(o.warmstart, m, psi_p, b_p, x_p, s);
     bool mixed = (o.precision == GL_MIXED) && p;
     if (!mixed) {
         bool vc32 = (o.precision == GL_MIXED_PRECOND) && p;
@@ -884,6 +885,7 @@ gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, con
     GL_CUDA(cudaStreamSynchronize(s));
     auto t1 = std::chrono::steady_clock::now();
     inf.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    inf.warmstart_used = o.warmstart ? warmstart_used(o.warmstart, s) : 0;
     if (info) {
         double setup = info->setup_ms;
         *info = inf;

@@ -1,0 +1,159 @@
+"""Learned warm start on the GPU: forward pass, gradients and Adam against the
+FP64 oracle (``oracle/warmstart.py``), training, the zero-guess fallback, and
+what the trained network gains over the zero initial guess.
+
+BF16 tolerances: the GPU rounds every activation, the aggregated features, the
+backpropagated dz and the weights to BF16 (relative rounding 2^-9), over four
+layers; per-tensor relative errors of 2e-2 with cosine similarity >= 0.999 are
+the bar, the loss within 1e-2.
+"""
+import numpy as np
+import pytest
+
+import gl_inputs as gi
+from oracle import warmstart as ows
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_1204_5125_gb300 as gl  # noqa: E402
+
+DEV = torch.device("cuda:0")
+INV_SQRT3 = 1.0 / np.sqrt(3.0)
+# (dim, N, mu, field): n = 2025 and 2197 nodes = 16 and 18 tiles of 128 with ragged tails
+CASES = [(2, 45, 1.0, (0.0, 0.0, 1.0)), (3, 13, 1.0, (INV_SQRT3, INV_SQRT3, INV_SQRT3))]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cosine(a, b):
+    return float(np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+@pytest.mark.parametrize("dim,N,mu,field", CASES)
+def test_forward_matches_oracle(oracle_mod, dim, N, mu, field):
+    om = oracle_mod.Mesh(dim, N, mu, field)
+    g = ows.Graph(om)
+    psi = gi.disk(om.n, 21)
+    b = gi.complex_normal(om.n, 22)
+    theta = gi.warmstart_init(3)
+    m = gl.gl_mesh_create(dim, N, mu, field)
+    ws = gl.gl_warmstart_create(theta)
+    try:
+        x0 = torch.zeros(om.n, dtype=torch.complex128, device=DEV)
+        gl.gl_warmstart_predict(ws, m, dev(psi), dev(b), x0)
+        torch.cuda.synchronize()
+        expect = ows.predict(theta.astype(np.float64), g, psi, b)
+        got = x0.cpu().numpy()
+        assert rel(got, expect) <= 2e-2, rel(got, expect)
+        # scale equivariance holds exactly up to the FP64 scaling of the output
+        x1 = torch.zeros_like(x0)
+        gl.gl_warmstart_predict(ws, m, dev(psi), dev(4.0 * b), x1)
+        np.testing.assert_allclose(x1.cpu().numpy(), 4.0 * got, rtol=1e-6, atol=1e-6 * np.abs(got).max())
+    finally:
+        gl.gl_warmstart_destroy(ws)
+        gl.gl_mesh_destroy(m)
+
+
+@pytest.mark.parametrize("dim,N,mu,field", CASES)
+def test_gradient_matches_oracle(oracle_mod, dim, N, mu, field):
+    om = oracle_mod.Mesh(dim, N, mu, field)
+    g = ows.Graph(om)
+    psi = gi.disk(om.n, 31)
+    b = gi.complex_normal(om.n, 32)
+    theta = gi.warmstart_init(4)
+    m = gl.gl_mesh_create(dim, N, mu, field)
+    ws = gl.gl_warmstart_create(theta)
+    try:
+        L, grad = gl.gl_warmstart_grad(ws, m, dev(psi), dev(b))
+        Lo, go = ows.loss_and_grad(theta.astype(np.float64), g, psi, b)
+        assert abs(L - Lo) <= 1e-2 * Lo, (L, Lo)
+        Ws, U = ows.split(np.arange(ows.NPARAM))
+        for name, idx in [("W0", Ws[0]), ("W1", Ws[1]), ("W2", Ws[2]), ("W3", Ws[3]), ("U", U)]:
+            a, e = grad[idx.ravel()].astype(np.float64), go[idx.ravel()]
+            assert rel(a, e) <= 2e-2 and cosine(a, e) >= 0.999, (name, rel(a, e), cosine(a, e))
+            assert np.all(grad[Ws[0][ows.C - 1]] == 0.0)
+    finally:
+        gl.gl_warmstart_destroy(ws)
+        gl.gl_mesh_destroy(m)
+
+
+def test_adam_matches_oracle():
+    theta = gi.warmstart_init(5)
+    ws = gl.gl_warmstart_create(theta)
+    try:
+        th = theta.astype(np.float64)
+        mm = np.zeros_like(th)
+        vv = np.zeros_like(th)
+        rng = gi.rng(8)
+        for t in range(1, 4):
+            grad = (rng.standard_normal(th.size) * 1e-2).astype(np.float32)
+            gl.gl_warmstart_adam_step(ws, grad, 1e-3)
+            th, mm, vv = ows.adam_step(th, grad.astype(np.float64), mm, vv, t, 1e-3)
+        np.testing.assert_allclose(gl.gl_warmstart_get_params(ws), th, rtol=1e-5, atol=1e-7)
+    finally:
+        gl.gl_warmstart_destroy(ws)
+
+
+def true_relres(om, psi, b, x):
+    vol = om.volumes()
+    r = b - om.jacobian(psi, x)
+    return np.sqrt(np.sum(vol * np.abs(r) ** 2) / np.sum(vol * np.abs(b) ** 2))
+
+
+def test_training_fallback_and_solve(oracle_mod):
+    """Train on 8 right-hand sides, solve a ninth from the network's guess; a
+    zero network and a wildly scaled one must both fall back to x0 = 0."""
+    N, mu = 64, 1.0
+    om = oracle_mod.Mesh(2, N, mu)
+    n = om.n
+    psi = gi.disk(n, 1)
+    m = gl.gl_mesh_create(2, N, mu)
+    ws = gl.gl_warmstart_create(gi.warmstart_init(6))
+    try:
+        psis = [dev(psi)] * 8
+        bs = [dev(gi.complex_normal(n, 300 + j)) for j in range(8)]
+        losses = gl.gl_warmstart_train(ws, [m] * 8, psis, bs, steps=300, batch=2, lr=2e-3)
+        first, last = float(np.mean(losses[:10])), float(np.mean(losses[-10:]))
+        print(f"training loss {first:.3f} -> {last:.3f}")
+        assert np.all(np.isfinite(losses))
+        assert last < 0.5 * first and last < 0.5
+        b = gi.complex_normal(n, 1)
+        opts = gl.options(max_coarse=64)
+        x = torch.zeros(n, dtype=torch.complex128, device=DEV)
+        st0, inf0 = gl.gl_jacobian_solve(m, dev(psi), None, dev(b), x, opts)
+        assert st0 == 0 and inf0.warmstart_used == 0
+        x0 = torch.zeros_like(x)
+        gl.gl_warmstart_predict(ws, m, dev(psi), dev(b), x0)
+        r0 = true_relres(om, psi, b, x0.cpu().numpy())
+        assert r0 < 1.0
+        opts.warmstart = ws.value
+        x.fill_(123.0)  # ignored: the network supplies the initial guess
+        st1, inf1 = gl.gl_jacobian_solve(m, dev(psi), None, dev(b), x, opts)
+        print(f"guess residual {r0:.3f}; iterations {inf0.iters} (zero guess) vs {inf1.iters} (warm start)")
+        assert st1 == 0 and inf1.warmstart_used == 1
+        assert true_relres(om, psi, b, x.cpu().numpy()) <= 1.01e-10
+        assert inf1.iters <= inf0.iters + 1
+        # fallbacks: the zero network gives x0 = 0 (not better than zero)...
+        gl.gl_warmstart_set_params(ws, np.zeros(gl.GL_WS_NPARAM, np.float32))
+        x.zero_()
+        st2, inf2 = gl.gl_jacobian_solve(m, dev(psi), None, dev(b), x, opts)
+        assert st2 == 0 and inf2.warmstart_used == 0 and inf2.iters == inf0.iters
+        # ... and a network whose guess is far too large is rejected
+        big = gi.warmstart_init(6) * 40.0
+        gl.gl_warmstart_set_params(ws, big)
+        st3, inf3 = gl.gl_jacobian_solve(m, dev(psi), None, dev(b), x, opts)
+        assert st3 == 0 and inf3.warmstart_used == 0 and inf3.iters == inf0.iters
+        assert true_relres(om, psi, b, x.cpu().numpy()) <= 1.01e-10
+    finally:
+        gl.gl_warmstart_destroy(ws)
+        gl.gl_mesh_destroy(m)
