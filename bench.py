@@ -9,8 +9,11 @@ the FP64 true residual ||b - J x||_D / ||b||_D <= 1e-10.  The preconditioner is
 set up once for psi before the timed region (setup-exclusive solves/s).  Two
 mixed-precision forms are measured (GL_MIXED: FP32 inner MINRES solves with FP32
 Jacobian applies and V-cycles inside FP64 defect correction; GL_MIXED_PRECOND:
-FP32 V-cycle inside FP64 MINRES) and the faster one is the headline; the FP64
-form is timed beside it.  The AMG hierarchy stops coarsening at 4096 nodes
+FP32 V-cycle inside FP64 MINRES); the faster one is then measured again with
+the learned warm start (a 4-layer, 64-channel graph network trained on the GPU
+on eight other right-hand sides of the same state; every solve pays its
+inference and the zero-guess fallback check), and the faster of the two is the
+headline.  The FP64 form is timed beside it.  The AMG hierarchy stops coarsening at 4096 nodes
 (--max-coarse), where the dense FP64 inverse takes over.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
@@ -50,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--max-coarse", type=int, default=4096, help="coarsest-level size bound of the AMG hierarchy")
+    ap.add_argument("--no-learned", action="store_true", help="skip training and timing the learned warm start")
+    ap.add_argument("--ws-steps", type=int, default=200, help="Adam steps of warm-start training")
     return ap.parse_args()
 
 
@@ -281,9 +286,51 @@ def main():
                        "outer": [i.outer_iters for i in q_inf], "true_relres": max(i.true_relres for i in q_inf)}
     head = max(quick, key=lambda k: quick[k]["solves_per_s"])
     opts_head = forms[head]
-    # headline: the chosen mixed form, with the dominant kernel timed live by CUDA events
+
+    # learned warm start: trained on the GPU on eight other right-hand sides
+    # (seeds 1000..1007) of the same state; the timed right-hand side is not among them
+    learned = None
+    wsh = None
+    if not args.no_learned:
+        wsh = gl.gl_warmstart_create(gi.warmstart_init(11))
+        train_b = [torch.from_numpy(gi.complex_normal(n, 1000 + j)).to(dev) for j in range(8)]
+        torch.cuda.synchronize()
+        tt0 = time.perf_counter()
+        losses = gl.gl_warmstart_train(wsh, [mesh] * 8, [psi] * 8, train_b, steps=args.ws_steps, batch=2, lr=2e-3)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - tt0
+        del train_b
+        # relative true residual of the guess for the timed right-hand side
+        x0 = torch.zeros_like(b)
+        gl.gl_warmstart_predict(wsh, mesh, psi, b, x0)
+        vol = torch.zeros(n, dtype=torch.float64, device=dev)
+        gl.gl_mesh_info(mesh, vol)
+        jx = torch.zeros_like(b)
+        gl.gl_jacobian_apply(mesh, psi, x0, jx)
+        guess_rel = float(torch.sqrt(torch.sum(vol * torch.abs(b - jx) ** 2) / torch.sum(vol * torch.abs(b) ** 2)))
+        del x0, jx, vol
+        opts_learned = gl.options(precision=opts_head.precision, max_coarse=args.max_coarse)
+        opts_learned.warmstart = wsh.value
+        q_ms, q_inf, _ = timed(opts_learned, 2, 1)
+        wsf_ms, _, wsf_prof = timed(opts_learned, 2, 0, profile_class="wsf")
+        learned = {
+            "train_steps": args.ws_steps, "train_batch": 2, "train_s": train_s,
+            "train_loss_first": float(np.mean(losses[:10])), "train_loss_last": float(np.mean(losses[-10:])),
+            "guess_relres": guess_rel, "warmstart_used": [i.warmstart_used for i in q_inf],
+            "solves_per_s": 2e3 / q_ms, "iters": [i.iters for i in q_inf],
+            "true_relres": max(i.true_relres for i in q_inf),
+            "forward_layer_us": 1e3 * wsf_prof["ms"] / wsf_prof["timed"] if wsf_prof["timed"] else None,
+            "forward_layer_gbs": (wsf_prof["bytes"] / (wsf_prof["ms"] / 1e3) / 1e9) if wsf_prof["ms"] > 0 else None,
+        }
+    use_learned = learned is not None and learned["solves_per_s"] > quick[head]["solves_per_s"]
+    opts_final = opts_learned if use_learned else opts_head
+    form = head + ("+learned" if use_learned else "")
+    if learned is not None:
+        learned["headline"] = use_learned
+
+    # headline: the chosen form, with the dominant kernel timed live by CUDA events
     with Clocks(dev.index if world == 1 else local) as clk:
-        ms, infos, prof = timed(opts_head, args.steps, args.warmup, profile_class="gs0")
+        ms, infos, prof = timed(opts_final, args.steps, args.warmup, profile_class="gs0")
     x_mixed = x.clone()
     err_mixed_vs_fp64 = float(torch.linalg.norm(x_mixed - x64) / torch.linalg.norm(x64))
 
@@ -294,7 +341,7 @@ def main():
         x_pin = torch.empty_like(b_pin).pin_memory()
         for _ in range(1):
             b.copy_(b_pin, non_blocking=True)
-            solve(opts_head)
+            solve(opts_final)
             x_pin.copy_(x, non_blocking=True)
         torch.cuda.synchronize()
         if dist:
@@ -302,7 +349,7 @@ def main():
         te0 = time.perf_counter()
         for _ in range(args.steps):
             b.copy_(b_pin, non_blocking=True)
-            solve(opts_head)
+            solve(opts_final)
             x_pin.copy_(x, non_blocking=True)
         torch.cuda.synchronize()
         te = time.perf_counter() - te0
@@ -338,11 +385,11 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64/f64", "data": "synthetic",
             "config": {"workload": f"cube{N}^3 mu=1 bhat=(1,1,1)/sqrt3 psi=1 b=CN(0,1) seed 5",
-                       "n": n, "tol": 1e-10, "form": head, "max_coarse": args.max_coarse,
+                       "n": n, "tol": 1e-10, "form": form, "max_coarse": args.max_coarse,
                        "l2": "inputs larger than L2 (operators ~0.5 GB)", "levels": [lv["n"] for lv in levels],
                        "colors": [lv["ncolors"] for lv in levels], "parallelism": f"replicas x{world}"},
             "iters_mixed": [i.iters for i in infos], "outer_mixed": [i.outer_iters for i in infos],
-            "mixed_forms": quick,
+            "mixed_forms": quick, "learned": learned, "warmstart_used": [i.warmstart_used for i in infos],
             "true_relres_mixed": max(i.true_relres for i in infos),
             "fp64_value": value64, "iters_fp64": [i.iters for i in infos64],
             "true_relres_fp64": max(i.true_relres for i in infos64),
@@ -353,6 +400,8 @@ def main():
             "gpu_launches": prof["launches"] if prof else None, "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
+    if wsh is not None:
+        gl.gl_warmstart_destroy(wsh)
     gl.gl_precond_destroy(prec)
     gl.gl_mesh_destroy(mesh)
     if dist:

@@ -39,6 +39,7 @@
 #include <cstring>
 
 #include "gl_internal.cuh"
+#include "gl_profile.cuh"
 
 namespace gl {
 namespace ws {
@@ -842,9 +843,16 @@ void ws_forward(gl_warmstart_s *w, gl_mesh_s *m, const double2 *psi_p, const dou
     k_bnorm_final<<<1, 1024, 0, s>>>(w->part.get(), RED_BLOCKS, w->bn.get());
     k_features<<<grid_for(n, 256), 256, 0, s>>>(n, b_p, psi_p, w->bn.get(), reinterpret_cast<uint4 *>(Hbuf(w, 0)));
     GL_LAUNCH_CHECK();
+    note_launch(3);
     const int64_t ntiles = (n + TILE - 1) / TILE;
     const int grid = (int)std::min<int64_t>(ntiles, w->fwd_grid);
+    // algorithmic bytes of one layer: each node's h row read once (neighbour rows
+    // are re-reads of the same array), its K row (value + column) and K_ii, and
+    // the written h row (the last layer of a prediction writes x0 instead)
+    const double k_bytes = (double)m->K32.nnz_stored * (sizeof(float2) + 4) + (double)n * 4;
     for (int l = 0; l < NL; ++l) {
+        const bool last_pred = (l == NL - 1) && !train;
+        ProfScope ps("wsf", (double)n * (CH * 2 + (last_pred ? 16 : CH * 2)) + k_bytes, s);
         FwdArgs a{};
         a.n = n;
         a.ntiles = ntiles;
@@ -875,6 +883,7 @@ void ws_forward(gl_warmstart_s *w, gl_mesh_s *m, const double2 *psi_p, const dou
 void ws_backward(gl_warmstart_s *w, gl_mesh_s *m, const double2 *psi_p, const double2 *b_p, double scale,
                  double *loss, int slot, cudaStream_t s) {
     const int64_t n = m->n;
+    note_launch(5);
     k_resid<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, m->K32.view(), m->kdiag32.get(), m->volp32.get(), psi_p, b_p,
                                                w->bn.get(), w->xh.get(), w->r.get(), w->part.get());
     k_loss_acc<<<1, 1024, 0, s>>>(w->part.get(), RED_BLOCKS, scale, loss, slot);
@@ -886,7 +895,10 @@ void ws_backward(gl_warmstart_s *w, gl_mesh_s *m, const double2 *psi_p, const do
     GL_LAUNCH_CHECK();
     const int64_t ntiles = (n + TILE - 1) / TILE;
     const int grid = (int)std::min<int64_t>(ntiles, w->bwd_grid);
+    const double k_bytes = (double)m->K32.nnz_stored * (sizeof(float2) + 4) + (double)n * 8;
     for (int l = NL - 1; l >= 0; --l) {
+        // algorithmic bytes: h^l and dz rows read, K row, dA rows written
+        note_launch(l > 0 ? 2 : 1);
         BwdArgs a{};
         a.n = n;
         a.ntiles = ntiles;
@@ -902,12 +914,16 @@ void ws_backward(gl_warmstart_s *w, gl_mesh_s *m, const double2 *psi_p, const do
         a.dA = w->dA.get();
         a.dWpart = w->dWpart.get();
         a.err = w->err.get();
-        if (l == NL - 1)
-            k_bwd<true, true><<<grid, THREADS, BWD_SMEM, s>>>(a);
-        else if (l > 0)
-            k_bwd<false, true><<<grid, THREADS, BWD_SMEM, s>>>(a);
-        else
-            k_bwd<false, false><<<grid, THREADS, BWD_SMEM, s>>>(a);
+        {
+            // algorithmic bytes: h^l and dz rows read, K row, dA rows written
+            ProfScope ps("wsb", (double)n * (CH * 2 + CH * 2 + (l > 0 ? CIN * 4 : 0)) + k_bytes, s);
+            if (l == NL - 1)
+                k_bwd<true, true><<<grid, THREADS, BWD_SMEM, s>>>(a);
+            else if (l > 0)
+                k_bwd<false, true><<<grid, THREADS, BWD_SMEM, s>>>(a);
+            else
+                k_bwd<false, false><<<grid, THREADS, BWD_SMEM, s>>>(a);
+        }
         GL_LAUNCH_CHECK();
         k_dw_final<<<grid_for(WSZ, 256), 256, 0, s>>>(w->dWpart.get(), grid, w->grad.get() + (size_t)l * WSZ);
         GL_LAUNCH_CHECK();
@@ -954,6 +970,7 @@ void warmstart_predict_p(gl_warmstart_s *w, gl_mesh_s *m, const double2 *psi_p, 
 void warmstart_apply_p(gl_warmstart_s *w, gl_mesh_s *m, const double2 *psi_p, const double2 *b_p, double2 *x_p,
                        cudaStream_t s) {
     warmstart_predict_p(w, m, psi_p, b_p, x_p, s);
+    note_launch(3);
     k_fallback_part<<<RED_BLOCKS, RED_THREADS, 0, s>>>(m->n, m->K.view(), m->kdiag.get(), m->volp.get(), psi_p, b_p,
                                                        x_p, w->fpart.get());
     k_fallback_decide<<<1, 1024, 0, s>>>(w->fpart.get(), RED_BLOCKS, w->used.get());
