@@ -184,6 +184,59 @@ __device__ __forceinline__ void aggregate_row(const SellView<float2> &K, const f
     for (int c = 0; c < CH; ++c) acc[c] *= sc;
 }
 
+// (S h)_p restricted to channels 8 j .. 8 j + 7 (four complex pairs), packed to
+// BF16.  Eight threads share a node, one 16-byte chunk each, so the neighbour
+// rows are read as whole 128-byte lines; four neighbours are loaded at a time.
+__device__ __forceinline__ uint4 aggregate_chunk(const SellView<float2> &K, const float *__restrict__ kdiag,
+                                                 const uint4 *__restrict__ H, int64_t p, int j) {
+    float acc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+    const int64_t s = p >> 5;
+    const int lane = (int)(p & 31);
+    const int64_t beg = K.sptr[s];
+    const int w = (int)((K.sptr[s + 1] - beg) >> 5);
+    int k = 0;
+    for (; k + 4 <= w; k += 4) {
+        int32_t c[4];
+        float2 v[4];
+        uint4 r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t e = beg + (int64_t)(k + u) * SELL_C + lane;
+            c[u] = K.col[e];
+            v[u] = K.val[e];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) r[u] = __ldg(H + (int64_t)c[u] * 8 + j);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float f[8];
+            unpack8(r[u], f);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                acc[2 * t] += v[u].x * f[2 * t] - v[u].y * f[2 * t + 1];
+                acc[2 * t + 1] += v[u].x * f[2 * t + 1] + v[u].y * f[2 * t];
+            }
+        }
+    }
+    for (; k < w; ++k) {
+        const int64_t e = beg + (int64_t)k * SELL_C + lane;
+        const float2 v = K.val[e];
+        float f[8];
+        unpack8(__ldg(H + (int64_t)K.col[e] * 8 + j), f);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            acc[2 * t] += v.x * f[2 * t] - v.y * f[2 * t + 1];
+            acc[2 * t + 1] += v.x * f[2 * t + 1] + v.y * f[2 * t];
+        }
+    }
+    const float sc = -1.f / kdiag[p];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] *= sc;
+    return pack8(acc);
+}
+
 // ------------------------------------------------------------------ small kernels
 // partials of sum |V_i| |b_i|^2
 __global__ void k_bnorm_part(int64_t n, const double *__restrict__ vol, const double2 *__restrict__ b,
@@ -271,20 +324,22 @@ __global__ void __launch_bounds__(THREADS) k_fwd(FwdArgs a) {
     }
     for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int64_t p = t * TILE + tid;
-        // ---- operand row tid: [h_p, (S h)_p] in BF16
+        // ---- operand rows [h, S h] in BF16: eight threads per node, one chunk each
         uint4 *rowA = reinterpret_cast<uint4 *>(sA);
-        if (p < a.n) {
-            const uint4 *hp = a.Hin + p * 8;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) rowA[cm_off(tid, 8 * j, CIN) >> 3] = hp[j];
-            float acc[CH];
-            aggregate_row(a.K, a.kdiag, a.Hin, p, acc);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) rowA[cm_off(tid, CH + 8 * j, CIN) >> 3] = pack8(acc + 8 * j);
-        } else {
-            uint4 z = make_uint4(0, 0, 0, 0);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) rowA[cm_off(tid, 8 * j, CIN) >> 3] = z;
+        {
+            const int j = tid & 7;
+#pragma unroll 1
+            for (int pass = 0; pass < TILE / 16; ++pass) {
+                const int r = pass * 16 + (tid >> 3);
+                const int64_t node = t * TILE + r;
+                uint4 hv = make_uint4(0, 0, 0, 0), sv = make_uint4(0, 0, 0, 0);
+                if (node < a.n) {
+                    hv = __ldg(a.Hin + node * 8 + j);
+                    sv = aggregate_chunk(a.K, a.kdiag, a.Hin, node, j);
+                }
+                rowA[cm_off(r, 8 * j, CIN) >> 3] = hv;
+                rowA[cm_off(r, CH + 8 * j, CIN) >> 3] = sv;
+            }
         }
         proxy_fence();
         __syncthreads();
@@ -318,9 +373,10 @@ __global__ void __launch_bounds__(THREADS) k_fwd(FwdArgs a) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) packed[j] = pack8(h + 8 * j);
             if (MODE != FWD_LAST_PREDICT) {
-                uint4 *hq = a.Hout + p * 8;
+                // stage the row in shared memory (chunks XOR-swizzled by row) for coalesced stores
+                uint4 *stage = reinterpret_cast<uint4 *>(sA);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) hq[j] = packed[j];
+                for (int j = 0; j < 8; ++j) stage[tid * 8 + (j ^ (tid & 7))] = packed[j];
             }
             if (MODE != FWD_HIDDEN) {
                 // head on the stored (BF16-rounded) h^4
@@ -344,6 +400,17 @@ __global__ void __launch_bounds__(THREADS) k_fwd(FwdArgs a) {
                 }
             }
         }
+        if (MODE != FWD_LAST_PREDICT) {
+            __syncthreads();
+            const uint4 *stage = reinterpret_cast<const uint4 *>(sA);
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+                const int idx = it * THREADS + tid, r = idx >> 3, c = idx & 7;
+                const int64_t node = t * TILE + r;
+                if (node < a.n) a.Hout[node * 8 + c] = stage[r * 8 + (c ^ (r & 7))];
+            }
+        }
+        __syncthreads();
     }
     __syncthreads();
     if (warp == 0) tmem_free(tmem, CH);
