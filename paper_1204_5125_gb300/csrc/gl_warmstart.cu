@@ -184,57 +184,65 @@ __device__ __forceinline__ void aggregate_row(const SellView<float2> &K, const f
     for (int c = 0; c < CH; ++c) acc[c] *= sc;
 }
 
-// (S h)_p restricted to channels 8 j .. 8 j + 7 (four complex pairs), packed to
-// BF16.  Eight threads share a node, one 16-byte chunk each, so the neighbour
-// rows are read as whole 128-byte lines; four neighbours are loaded at a time.
-__device__ __forceinline__ uint4 aggregate_chunk(const SellView<float2> &K, const float *__restrict__ kdiag,
-                                                 const uint4 *__restrict__ H, int64_t p, int j) {
-    float acc[8];
+constexpr int WMAX = 8;   // sliced-ELL entries per row staged in shared memory
+
+// accumulate K_pq h_q over one 16-byte chunk (four complex pairs) of h_q
+__device__ __forceinline__ void cacc4(float *acc, float2 v, uint4 r) {
+    float f[8];
+    unpack8(r, f);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i] = 0.f;
-    const int64_t s = p >> 5;
-    const int lane = (int)(p & 31);
-    const int64_t beg = K.sptr[s];
-    const int w = (int)((K.sptr[s + 1] - beg) >> 5);
-    int k = 0;
-    for (; k + 4 <= w; k += 4) {
-        int32_t c[4];
-        float2 v[4];
-        uint4 r[4];
+    for (int t = 0; t < 4; ++t) {
+        acc[2 * t] += v.x * f[2 * t] - v.y * f[2 * t + 1];
+        acc[2 * t + 1] += v.x * f[2 * t + 1] + v.y * f[2 * t];
+    }
+}
+
+// (S h) for channels 8 j .. 8 j + 7 of two nodes rA, rB of the tile, with their
+// sliced-ELL entries staged in shared memory (entries beyond WMAX, which the
+// lattice meshes do not have, are read from global memory).  All neighbour
+// chunks of both nodes are requested before any is used.
+__device__ __forceinline__ void aggregate_pair(const SellView<float2> &K, const float *__restrict__ kdiag,
+                                               const uint4 *__restrict__ H, const int32_t *sCol,
+                                               const float2 *sVal, const int *sWid, int64_t base, int rA, int rB,
+                                               int j, int64_t n, uint4 &outA, uint4 &outB) {
+    float accA[8], accB[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t e = beg + (int64_t)(k + u) * SELL_C + lane;
-            c[u] = K.col[e];
-            v[u] = K.val[e];
-        }
+    for (int i = 0; i < 8; ++i) accA[i] = accB[i] = 0.f;
+    const int wA = (base + rA < n) ? sWid[rA >> 5] : 0, wB = (base + rB < n) ? sWid[rB >> 5] : 0;
+    uint4 ra[WMAX], rb[WMAX];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) r[u] = __ldg(H + (int64_t)c[u] * 8 + j);
+    for (int k = 0; k < WMAX; ++k) {
+        if (k < wA) ra[k] = __ldg(H + (int64_t)sCol[k * TILE + rA] * 8 + j);
+        if (k < wB) rb[k] = __ldg(H + (int64_t)sCol[k * TILE + rB] * 8 + j);
+    }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            float f[8];
-            unpack8(r[u], f);
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                acc[2 * t] += v[u].x * f[2 * t] - v[u].y * f[2 * t + 1];
-                acc[2 * t + 1] += v[u].x * f[2 * t + 1] + v[u].y * f[2 * t];
-            }
+    for (int k = 0; k < WMAX; ++k) {
+        if (k < wA) cacc4(accA, sVal[k * TILE + rA], ra[k]);
+        if (k < wB) cacc4(accB, sVal[k * TILE + rB], rb[k]);
+    }
+    // rows wider than WMAX (not produced by the lattice meshes)
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        const int r = h ? rB : rA;
+        const int64_t p = base + r;
+        if (p >= n) continue;
+        const int64_t sl = p >> 5;
+        const int64_t beg = K.sptr[sl];
+        const int w = (int)((K.sptr[sl + 1] - beg) >> 5);
+        for (int k = WMAX; k < w; ++k) {
+            const int64_t e = beg + (int64_t)k * SELL_C + (p & 31);
+            cacc4(h ? accB : accA, K.val[e], __ldg(H + (int64_t)K.col[e] * 8 + j));
         }
     }
-    for (; k < w; ++k) {
-        const int64_t e = beg + (int64_t)k * SELL_C + lane;
-        const float2 v = K.val[e];
-        float f[8];
-        unpack8(__ldg(H + (int64_t)K.col[e] * 8 + j), f);
+    const float sa = base + rA < n ? -1.f / kdiag[base + rA] : 0.f;
+    const float sb = base + rB < n ? -1.f / kdiag[base + rB] : 0.f;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            acc[2 * t] += v.x * f[2 * t] - v.y * f[2 * t + 1];
-            acc[2 * t + 1] += v.x * f[2 * t + 1] + v.y * f[2 * t];
-        }
+    for (int i = 0; i < 8; ++i) {
+        accA[i] *= sa;
+        accB[i] *= sb;
     }
-    const float sc = -1.f / kdiag[p];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i] *= sc;
-    return pack8(acc);
+    outA = pack8(accA);
+    outB = pack8(accB);
 }
 
 // ------------------------------------------------------------------ small kernels
@@ -304,6 +312,9 @@ __global__ void __launch_bounds__(THREADS) k_fwd(FwdArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(smem);          // 128 x 128
     uint4 *sW = reinterpret_cast<uint4 *>(smem + TILE * CIN * 2);          // 64 x 128 image
+    __shared__ int32_t sCol[WMAX * TILE];
+    __shared__ float2 sVal[WMAX * TILE];
+    __shared__ int sWid[TILE / SELL_C];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -324,21 +335,42 @@ __global__ void __launch_bounds__(THREADS) k_fwd(FwdArgs a) {
     }
     for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int64_t p = t * TILE + tid;
-        // ---- operand rows [h, S h] in BF16: eight threads per node, one chunk each
+        // ---- stage the tile's sliced-ELL rows (thread tid: node tid of the tile)
+        const int64_t base = t * TILE;
+        {
+            const int64_t sl = (base >> 5) + (tid >> 5);
+            int w = 0;
+            int64_t beg = 0;
+            if (sl * SELL_C < a.n) {
+                beg = a.K.sptr[sl];
+                w = (int)((a.K.sptr[sl + 1] - beg) >> 5);
+            }
+            if ((tid & 31) == 0) sWid[tid >> 5] = w;
+#pragma unroll
+            for (int k = 0; k < WMAX; ++k) {
+                if (k < w) {
+                    const int64_t e = beg + (int64_t)k * SELL_C + (tid & 31);
+                    sCol[k * TILE + tid] = a.K.col[e];
+                    sVal[k * TILE + tid] = a.K.val[e];
+                }
+            }
+        }
+        __syncthreads();
+        // ---- operand rows [h, S h] in BF16: eight threads per node, one 16-byte chunk each
         uint4 *rowA = reinterpret_cast<uint4 *>(sA);
         {
             const int j = tid & 7;
 #pragma unroll 1
-            for (int pass = 0; pass < TILE / 16; ++pass) {
-                const int r = pass * 16 + (tid >> 3);
-                const int64_t node = t * TILE + r;
-                uint4 hv = make_uint4(0, 0, 0, 0), sv = make_uint4(0, 0, 0, 0);
-                if (node < a.n) {
-                    hv = __ldg(a.Hin + node * 8 + j);
-                    sv = aggregate_chunk(a.K, a.kdiag, a.Hin, node, j);
-                }
-                rowA[cm_off(r, 8 * j, CIN) >> 3] = hv;
-                rowA[cm_off(r, CH + 8 * j, CIN) >> 3] = sv;
+            for (int pass = 0; pass < TILE / 32; ++pass) {
+                const int rA = pass * 32 + (tid >> 3), rB = rA + 16;
+                uint4 hA = make_uint4(0, 0, 0, 0), hB = make_uint4(0, 0, 0, 0), sA4, sB4;
+                if (base + rA < a.n) hA = __ldg(a.Hin + (base + rA) * 8 + j);
+                if (base + rB < a.n) hB = __ldg(a.Hin + (base + rB) * 8 + j);
+                aggregate_pair(a.K, a.kdiag, a.Hin, sCol, sVal, sWid, base, rA, rB, j, a.n, sA4, sB4);
+                rowA[cm_off(rA, 8 * j, CIN) >> 3] = hA;
+                rowA[cm_off(rA, CH + 8 * j, CIN) >> 3] = sA4;
+                rowA[cm_off(rB, 8 * j, CIN) >> 3] = hB;
+                rowA[cm_off(rB, CH + 8 * j, CIN) >> 3] = sB4;
             }
         }
         proxy_fence();
@@ -875,19 +907,36 @@ void ws_setup_kernels(gl_warmstart_s *w) {
     GL_CUDA(cudaFuncSetAttribute(k_bwd<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, BWD_SMEM));
     GL_CUDA(cudaFuncSetAttribute(k_bwd<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, BWD_SMEM));
     GL_CUDA(cudaFuncSetAttribute(k_bwd<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, BWD_SMEM));
-    int dev = 0, nsm = 0;
+    // ask for the largest shared-memory carveout, or only one CTA fits an SM
+    GL_CUDA(cudaFuncSetAttribute(k_fwd<FWD_HIDDEN>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    GL_CUDA(cudaFuncSetAttribute(k_fwd<FWD_LAST_TRAIN>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    GL_CUDA(cudaFuncSetAttribute(k_fwd<FWD_LAST_PREDICT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    GL_CUDA(cudaFuncSetAttribute(k_bwd<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    GL_CUDA(cudaFuncSetAttribute(k_bwd<false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    GL_CUDA(cudaFuncSetAttribute(k_bwd<false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    int dev = 0, nsm = 0, smem_sm = 0;
     GL_CUDA(cudaGetDevice(&dev));
     GL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    // residency: tensor memory holds 512 columns per SM; the forward kernel takes
-    // 64 and the backward 256, so at most 8 and 2 CTAs of them fit an SM
-    int f = 0, b = 0, b2 = 0, b3 = 0;
-    GL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f, k_fwd<FWD_LAST_TRAIN>, THREADS, FWD_SMEM));
-    GL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bwd<true, true>, THREADS, BWD_SMEM));
-    GL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_bwd<false, true>, THREADS, BWD_SMEM));
-    GL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b3, k_bwd<false, false>, THREADS, BWD_SMEM));
-    b = std::min(b, std::min(b2, b3));
-    f = std::max(1, std::min(f, 8));
-    b = std::max(1, std::min(b, 2));
+    GL_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    // CTAs per SM from the kernels' own register and shared-memory use (the
+    // occupancy query reports 0 for these kernels); tensor memory holds 512
+    // columns per SM: the forward kernel takes 64 and the backward 256.  The
+    // CTAs of one launch never wait on each other, so an estimate that is too
+    // high only queues CTAs.
+    auto per_sm = [&](const void *fn, int dyn, int cap) {
+        cudaFuncAttributes fa;
+        GL_CUDA(cudaFuncGetAttributes(&fa, fn));
+        int regs = ((fa.numRegs + 7) / 8) * 8 * THREADS;
+        int by_regs = regs > 0 ? 65536 / regs : cap;
+        int by_smem = smem_sm / (dyn + (int)fa.sharedSizeBytes + 1024);
+        return std::max(1, std::min(cap, std::min(by_regs, by_smem)));
+    };
+    int f = std::min(per_sm((const void *)k_fwd<FWD_HIDDEN>, FWD_SMEM, 8),
+                     std::min(per_sm((const void *)k_fwd<FWD_LAST_TRAIN>, FWD_SMEM, 8),
+                              per_sm((const void *)k_fwd<FWD_LAST_PREDICT>, FWD_SMEM, 8)));
+    int b = std::min(per_sm((const void *)k_bwd<true, true>, BWD_SMEM, 2),
+                     std::min(per_sm((const void *)k_bwd<false, true>, BWD_SMEM, 2),
+                              per_sm((const void *)k_bwd<false, false>, BWD_SMEM, 2)));
     w->fwd_grid = f * nsm;
     w->bwd_grid = b * nsm;
     w->part.alloc(RED_BLOCKS);
