@@ -82,6 +82,10 @@ typedef struct {
     int check_every;     /* host polls the device convergence flag every this many iterations (default 6) */
     int autotune;        /* 1: at setup, time the SpMV variants of every coarse operator on this GPU and keep
                             the fastest lanes-per-row width (default 1) */
+    int lattice;         /* 1: on a mesh with an even number of nodes per side, the FP32 finest-level
+                            sweeps and residuals of the V-cycle use the closed-form lattice stencil (checked
+                            entry by entry against the assembled K at setup) instead of the stored one;
+                            0: always the stored stencil (default 1) */
     gl_warmstart warmstart; /* learned initial guess: when set, gl_jacobian_solve and gl_newton_step ignore the
                             x passed in, start from the network's x0, and fall back to x0 = 0 when
                             ||b - J x0||_D >= ||b||_D (default NULL: start from x as given) */
@@ -98,6 +102,7 @@ typedef struct {
     double solve_ms;     /* wall time of the Krylov part */
     int warmstart_used;  /* 1 if the solve started from the learned guess, 0 if from x as given or after
                             the zero-guess fallback */
+    int lattice_stencil; /* 1 if the FP32 finest-level V-cycle kernels used the closed-form stencil */
 } gl_solve_info;
 
 /* Default options (values listed in gl_options).  Returns GL_ERR_ARG on NULL. */

@@ -59,7 +59,8 @@ class Options(C.Structure):
     _fields_ = [
         ("tol", C.c_double), ("maxit", C.c_int), ("cycles", C.c_int), ("max_coarse", C.c_int),
         ("max_levels", C.c_int), ("power_its", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double),
-        ("max_outer", C.c_int), ("check_every", C.c_int), ("autotune", C.c_int), ("warmstart", C.c_void_p),
+        ("max_outer", C.c_int), ("check_every", C.c_int), ("autotune", C.c_int), ("lattice", C.c_int),
+        ("warmstart", C.c_void_p),
     ]
 
 
@@ -67,7 +68,7 @@ class SolveInfo(C.Structure):
     _fields_ = [
         ("iters", C.c_int), ("outer_iters", C.c_int), ("converged", C.c_int), ("true_relres", C.c_double),
         ("est_relres", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
-        ("warmstart_used", C.c_int),
+        ("warmstart_used", C.c_int), ("lattice_stencil", C.c_int),
     ]
 
     def as_dict(self):

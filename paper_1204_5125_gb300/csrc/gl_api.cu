@@ -71,6 +71,7 @@ gl_status gl_options_default(gl_options *o) {
     o->max_outer = 20;
     o->check_every = 6;
     o->autotune = 1;
+    o->lattice = 1;
     o->warmstart = nullptr;
     return GL_OK;
 }

@@ -23,6 +23,10 @@ struct gl_mesh_s {
     bool has32 = false;
     gl::Sell<float2> K32;
     gl::DBuf<float> kdiag32, volp32;
+    // closed-form finest-level stencil (gl_lattice.cu): phase tables per axis
+    bool lat_checked = false, lat_ok = false;
+    int64_t lat_per_axis = 0;
+    gl::DBuf<float2> lat_tab;
     // scratch for the node-order public calls
     gl::DBuf<double2> t0, t1, t2;
 };
@@ -76,6 +80,7 @@ struct gl_prec_s {
     int cycles = 1;
     bool has32 = false;
     bool autotune = true;
+    bool lattice = true;              // closed-form finest-level stencil in the FP32 V-cycle when available
     gl::Level L[gl::MAX_LEVELS];
     gl::DBuf<double2> psi_p;          // psi in solve ordering
     gl::DBuf<double2> cyc_r, cyc_e;   // work vectors for k > 1 cycles
@@ -96,6 +101,17 @@ void to_float(const double *in, float *out, int64_t n, cudaStream_t s);
 template <typename C>
 void build_csrg(int64_t nrows, const int32_t *perm, const int32_t *icol, const CsrDev &A, bool drop_diag,
                 CsrG<C> &out, double *diag_out, cudaStream_t s);
+
+// gl_lattice.cu: validates the closed-form finest-level stencil against the
+// assembled K and builds its phase tables (sets lat_ok)
+struct LatticeView {
+    int dim, N;
+    int64_t nred;
+    const float *vol;              // |V| in the solve ordering
+    const float2 *tx, *ty, *tz;    // K-hat of the +x, +y, +z edges by perpendicular position
+};
+void mesh_ensure_lattice(gl_mesh_s *m, cudaStream_t s);
+LatticeView lattice_view(const gl_mesh_s *m);
 
 // gl_setup.cu
 void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_options &o, cudaStream_t s);

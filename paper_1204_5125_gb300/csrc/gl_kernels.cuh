@@ -2,7 +2,7 @@
 // Krylov kernels.
 #pragma once
 
-#include "gl_common.cuh"
+#include "gl_internal.cuh"
 
 namespace gl {
 
@@ -71,6 +71,49 @@ __device__ __forceinline__ C jacobian_epilogue(C acc, R kd, C ps, C ph) {
     r.x = acc.x + d * ph.x + (p2.x * ph.x + p2.y * ph.y);  // psi^2 conj(phi): (a+ib)(c-id)
     r.y = acc.y + d * ph.y + (p2.y * ph.x - p2.x * ph.y);
     return r;
+}
+
+// sum_{k != p} K_pk x_k with the tabulated finest-level stencil (FP32) at solve
+// position p of an even-N lattice: red nodes ((i + j + k) even) first, node v of
+// either colour at position v / 2 within its colour, neighbours of the other
+// colour; K-hat of a +e edge from the per-axis table at the perpendicular
+// position, its conjugate for the -e edge; the row scaled by 1 / |V_p|.
+__device__ __forceinline__ float2 lattice_row(const LatticeView &L, int64_t p, const float2 *__restrict__ x) {
+    const uint32_t c = p >= L.nred ? 1u : 0u;
+    const uint32_t N = (uint32_t)L.N;
+    uint32_t v = 2u * (uint32_t)(p - (c ? L.nred : 0));
+    uint32_t i = v % N;
+    const uint32_t r = v / N, j = r % N, k = r / N;
+    if (((i + j + k) & 1u) != c) {
+        ++v;
+        ++i;
+    }
+    const int64_t other = c ? 0 : L.nred;
+    float2 acc = make_float2(0.f, 0.f);
+    // acc += t x_u (plus) or conj(t) x_u (minus)
+    auto edge = [&](float2 t, uint32_t u, bool plus) {
+        const float2 xv = x[(u >> 1) + other];
+        const float ty = plus ? t.y : -t.y;
+        acc.x += t.x * xv.x - ty * xv.y;
+        acc.y += t.x * xv.y + ty * xv.x;
+    };
+    {
+        const float2 t = __ldg(L.tx + (j + N * k));
+        if (i + 1 < N) edge(t, v + 1, true);
+        if (i > 0) edge(t, v - 1, false);
+    }
+    {
+        const float2 t = __ldg(L.ty + (i + N * k));
+        if (j + 1 < N) edge(t, v + N, true);
+        if (j > 0) edge(t, v - N, false);
+    }
+    if (L.dim == 3) {
+        const float2 t = __ldg(L.tz + (i + N * j));
+        if (k + 1 < N) edge(t, v + N * N, true);
+        if (k > 0) edge(t, v - N * N, false);
+    }
+    const float iv = 1.f / L.vol[p];
+    return make_float2(acc.x * iv, acc.y * iv);
 }
 
 }  // namespace gl

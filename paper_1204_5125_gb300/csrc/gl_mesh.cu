@@ -621,6 +621,7 @@ void mesh_ensure_fp32(gl_mesh_s *m, cudaStream_t s) {
     to_float(m->kdiag.get(), m->kdiag32.get(), m->n, s);
     to_float(m->volp.get(), m->volp32.get(), m->n, s);
     GL_CUDA(cudaStreamSynchronize(s));
+    mesh_ensure_lattice(m, s);
     m->has32 = true;
 }
 

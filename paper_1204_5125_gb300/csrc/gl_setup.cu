@@ -980,6 +980,7 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
     }
     GL_CUDA(cudaStreamSynchronize(s));
     p->autotune = o.autotune != 0;
+    p->lattice = o.lattice != 0;
     if (p->autotune) autotune_levels(p, false, s);
     if (o.precision != GL_FP64) precond_ensure_fp32(p, s);
 }

@@ -81,6 +81,35 @@ __global__ void __launch_bounds__(256) k_resid(int64_t n, SellView<C> A, const R
     r[p] = mk((bb.x - acc.x - d * xx.x) * sc, (bb.y - acc.y - d * xx.y) * sc);
 }
 
+// the two kernels above on the finest level of an even-N lattice, with the
+// closed-form stencil instead of the stored one (FP32)
+__global__ void __launch_bounds__(256) k_gs_lat(int64_t lo, int64_t hi, LatticeView L, const float *__restrict__ diag,
+                                                const float2 *__restrict__ b, float2 *__restrict__ x, int first,
+                                                const int *__restrict__ stop) {
+    if (stop && *stop) return;
+    int64_t p = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= hi) return;
+    // from x = 0 the first colour has no nonzero neighbour and the second sees
+    // only the first (two colours, each node's neighbours of the other colour)
+    float2 acc = (first && lo == 0) ? make_float2(0.f, 0.f) : lattice_row(L, p, x);
+    float2 bb = b[p];
+    float d = 1.f / diag[p];
+    x[p] = make_float2((bb.x - acc.x) * d, (bb.y - acc.y) * d);
+}
+__global__ void __launch_bounds__(256) k_resid_lat(int64_t n, LatticeView L, const float *__restrict__ diag,
+                                                   const float2 *__restrict__ b, const float2 *__restrict__ x,
+                                                   const float *__restrict__ scale, float2 *__restrict__ r,
+                                                   const int *__restrict__ stop) {
+    if (stop && *stop) return;
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    float2 acc = lattice_row(L, p, x);
+    float2 xx = x[p], bb = b[p];
+    float d = diag[p];
+    float sc = scale ? scale[p] : 1.f;
+    r[p] = make_float2((bb.x - acc.x - d * xx.x) * sc, (bb.y - acc.y - d * xx.y) * sc);
+}
+
 // y = S x (add = 0) or y += S x (add = 1) for a rectangular sliced-ELL S
 template <typename C>
 __global__ void __launch_bounds__(256) k_spmv(int64_t n, SellView<C> S, const C *__restrict__ x, C *__restrict__ y,
@@ -449,11 +478,23 @@ void coarse_solve<float>(gl_prec_s *p, Level &L, const float2 *b, float2 *x, con
 
 template <typename T>
 static void gs_sweep(Level &L, int level, const typename LevelOps<T>::C *b, typename LevelOps<T>::C *x, int c,
-                     bool first, const int *stop, cudaStream_t s) {
+                     bool first, const int *stop, cudaStream_t s, const LatticeView *lat = nullptr) {
     using O = LevelOps<T>;
     using C = typename O::C;
     int64_t lo = L.cstart[c], hi = L.cstart[c + 1];
     if (hi <= lo) return;
+    if constexpr (sizeof(T) == 4) {
+        if (lat) {
+            // diagonal, b and the written x per row; the other colour's x once and
+            // the phase tables, unless the colour is relaxed from a zero guess
+            double bytes = (double)(hi - lo) * (sizeof(T) + 2 * sizeof(C));
+            if (!(first && lo == 0))
+                bytes += (double)(L.n - (hi - lo)) * sizeof(C) + (double)lat->N * lat->N * lat->dim * 8.0;
+            ProfScope ps("gs0", bytes, s);
+            k_gs_lat<<<grid_for(hi - lo, 256), 256, 0, s>>>(lo, hi, *lat, O::diag(L), b, x, first ? 1 : 0, stop);
+            return;
+        }
+    }
     // algorithmic bytes: diagonal, b and the written x for each row; the stored
     // off-diagonals (value + column) and each neighbour value once, unless the
     // colour is relaxed from an all-zero guess
@@ -470,10 +511,22 @@ static void gs_sweep(Level &L, int level, const typename LevelOps<T>::C *b, type
 // unchanged neighbours reproduces the same values
 template <typename T>
 static void sgs(Level &L, int level, const typename LevelOps<T>::C *b, typename LevelOps<T>::C *x, bool zero_start,
-                const int *stop, cudaStream_t s) {
+                const int *stop, cudaStream_t s, const LatticeView *lat = nullptr) {
     int nc = L.ncolors;
-    for (int c = 0; c < nc; ++c) gs_sweep<T>(L, level, b, x, c, zero_start, stop, s);
-    for (int c = nc - 2; c >= 0; --c) gs_sweep<T>(L, level, b, x, c, false, stop, s);
+    for (int c = 0; c < nc; ++c) gs_sweep<T>(L, level, b, x, c, zero_start, stop, s, lat);
+    for (int c = nc - 2; c >= 0; --c) gs_sweep<T>(L, level, b, x, c, false, stop, s, lat);
+}
+
+// closed-form finest-level stencil for the FP32 V-cycle, when the mesh has one
+template <typename T>
+static bool lattice_for(const gl_prec_s *p, LatticeView &v) {
+    if constexpr (sizeof(T) == 4) {
+        if (p->lattice && p->mesh->lat_ok && p->L[0].ncolors == 2) {
+            v = lattice_view(p->mesh);
+            return true;
+        }
+    }
+    return false;
 }
 
 // pre- or post-smoothing on level l: per-colour launches on the lattice level
@@ -485,7 +538,9 @@ static void smooth(gl_prec_s *p, int l, const typename LevelOps<T>::C *b, typena
     using C = typename O::C;
     Level &L = p->L[l];
     if (l == 0) {
-        sgs<T>(L, l, b, x, zero_start, stop, s);
+        LatticeView lv;
+        bool lat = lattice_for<T>(p, lv);
+        sgs<T>(L, l, b, x, zero_start, stop, s, lat ? &lv : nullptr);
         return;
     }
     const CsrG<C> &A = O::Ag(L);
@@ -516,7 +571,14 @@ static void vcycle(gl_prec_s *p, int l, const typename LevelOps<T>::C *b, typena
         else
             scale = p->mesh->volp32.get();
         ProfScope ps("resid0", 0, s);
-        k_resid<C, T><<<grid_for(L.n, 256), 256, 0, s>>>(L.n, O::A(L).view(), O::diag(L), b, x, scale, r, stop);
+        LatticeView lv;
+        bool lat = lattice_for<T>(p, lv);
+        if constexpr (sizeof(T) == 4) {
+            if (lat)
+                k_resid_lat<<<grid_for(L.n, 256), 256, 0, s>>>(L.n, lv, O::diag(L), b, x, scale, r, stop);
+        }
+        if (!lat)
+            k_resid<C, T><<<grid_for(L.n, 256), 256, 0, s>>>(L.n, O::A(L).view(), O::diag(L), b, x, scale, r, stop);
     } else {
         const CsrG<C> &A = O::Ag(L);
         ProfScope ps("resid", 0, s);
