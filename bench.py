@@ -117,16 +117,19 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the roofline kernel from the committed ncu capture,
-    or None when the kernel's sources changed since that capture."""
+def recorded_traffic(cls):
+    """DRAM bytes per launch of kernel class `cls` from the committed ncu capture,
+    or None when there is none or the kernel's sources changed since it."""
     import hashlib
 
     p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
-        rec = json.load(f)
+        recs = json.load(f)
+    rec = recs.get(cls)
+    if not rec:
+        return None
     h = hashlib.sha256()
     for s in rec["sources"]:
         with open(os.path.join(ROOT, s), "rb") as f:
@@ -251,20 +254,27 @@ def main():
             raise RuntimeError(f"solve failed: status {st} {info.as_dict()}")
         return info
 
-    def timed(opts, steps, warm, profile_class=None):
+    def timed(opts, steps, warm, profile_class=None, count=False):
+        """Times `steps` solves after `warm` untimed ones.  profile_class: time every
+        launch of that kernel class with CUDA events; count: only count launches."""
+        profiling = bool(profile_class) or count
+        if profiling:
+            # before the warm-up, so graphs it makes the solver re-capture are captured there
+            gl.gl_profile_begin(profile_class, 1 << 16 if profile_class else 0)
         for _ in range(warm):
             solve(opts)
+        if profiling:
+            gl.gl_profile_end()
+            gl.gl_profile_begin(profile_class, 1 << 16 if profile_class else 0)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        if profile_class:
-            gl.gl_profile_begin(profile_class, 1 << 16)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         infos = [solve(opts) for _ in range(steps)]
         ev1.record(stream)
         torch.cuda.synchronize()
-        prof = gl.gl_profile_end() if profile_class else None
+        prof = gl.gl_profile_end() if profiling else None
         ms = ev0.elapsed_time(ev1)
         if dist:
             t = torch.tensor([ms], device=dev)
@@ -312,7 +322,7 @@ def main():
         opts_learned = gl.options(precision=opts_head.precision, max_coarse=args.max_coarse)
         opts_learned.warmstart = wsh.value
         q_ms, q_inf, _ = timed(opts_learned, 2, 1)
-        wsf_ms, _, wsf_prof = timed(opts_learned, 2, 0, profile_class="wsf")
+        wsf_ms, _, wsf_prof = timed(opts_learned, 2, 1, profile_class="wsf")
         learned = {
             "train_steps": args.ws_steps, "train_batch": 2, "train_s": train_s,
             "train_loss_first": float(np.mean(losses[:10])), "train_loss_last": float(np.mean(losses[-10:])),
@@ -329,8 +339,9 @@ def main():
         learned["headline"] = use_learned
 
     # headline: the chosen form, with the dominant kernel timed live by CUDA events
+    # launches are counted during the timed solves; nothing is timed per kernel
     with Clocks(dev.index if world == 1 else local) as clk:
-        ms, infos, prof = timed(opts_final, args.steps, args.warmup, profile_class="gs0")
+        ms, infos, count = timed(opts_final, args.steps, args.warmup, count=True)
     x_mixed = x.clone()
     err_mixed_vs_fp64 = float(torch.linalg.norm(x_mixed - x64) / torch.linalg.norm(x64))
 
@@ -363,16 +374,37 @@ def main():
     value = world * args.steps / (ms / 1e3)
     value64 = world * len(infos64) / (ms64 / 1e3)
     peak, peak_kind = peaks()
-    achieved = prof["bytes"] / (prof["ms"] / 1e3) / 1e9 if prof and prof["ms"] > 0 else None
-    per_launch_bytes = prof["bytes"] / prof["timed"] if prof and prof["timed"] else None
-    roofline = {
-        "bound": "hbm", "kernel": "k_gs (Gauss-Seidel colour sweep, finest level, FP32)",
-        "achieved": achieved, "peak": peak, "unit": "GB/s",
-        "frac": achieved / peak if achieved else None, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-        "traffic": recorded_traffic(), "alg_bytes_per_launch": per_launch_bytes,
-        "launches_timed": prof["timed"] if prof else None,
-        "avg_launch_us": 1e3 * prof["ms"] / prof["timed"] if prof and prof["timed"] else None,
+
+    # live per-class timing (CUDA events around every launch of the class, on the
+    # launching stream): the finest-level sweep from the headline run, then the
+    # coarse-level sweeps and the Jacobian in two short runs of the same form
+    KERNELS = {
+        "gs0": ("k_gs_lat (Gauss-Seidel colour sweep, finest level, FP32, tabulated lattice stencil)"
+                if infos[-1].lattice_stencil else "k_gs (Gauss-Seidel colour sweep, finest level, FP32)"),
+        "gs": "k_sgs_cluster / k_sgs_coop (symmetric Gauss-Seidel step, coarse levels, FP32)",
+        "jz": "k_jz (Jacobian apply fused with the Lanczos dot, FP64)",
     }
+    profs = {}
+    for cls in ("gs0", "gs", "jz"):
+        _, _, pr = timed(opts_final, 2, 1, profile_class=cls)
+        profs[cls] = (pr, 2)
+    prof = profs["gs0"][0]
+    rooflines = {}
+    for cls, (pr, nsolves) in profs.items():
+        if not pr or not pr["timed"] or pr["ms"] <= 0:
+            continue
+        rooflines[cls] = {
+            "bound": "hbm", "kernel": KERNELS[cls], "unit": "GB/s", "peak": peak,
+            "achieved": pr["bytes"] / (pr["ms"] / 1e3) / 1e9,
+            "frac": pr["bytes"] / (pr["ms"] / 1e3) / 1e9 / peak,
+            "traffic": recorded_traffic(cls), "alg_bytes_per_launch": pr["bytes"] / pr["timed"],
+            "launches_timed": pr["timed"], "avg_launch_us": 1e3 * pr["ms"] / pr["timed"],
+            "ms_per_solve": pr["ms"] / nsolves, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+        }
+    dominant = max(rooflines, key=lambda k: rooflines[k]["ms_per_solve"]) if rooflines else None
+    roofline = dict(rooflines[dominant]) if dominant else None
+    if roofline:
+        roofline["class"] = dominant
 
     cpu = None
     err_vs_oracle = None
@@ -396,8 +428,8 @@ def main():
             "mixed_over_fp64": value / value64, "err_mixed_vs_fp64_gpu": err_mixed_vs_fp64,
             "err_mixed_vs_fp64_oracle": err_vs_oracle,
             "setup_s": {"mesh": t1 - t0, "precond": t2 - t1},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": prof["launches"] if prof else None, "clocks": clk.summary(),
+            "roofline": roofline, "rooflines": rooflines, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": count["launches"] if count else None, "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
     if wsh is not None:

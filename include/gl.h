@@ -86,6 +86,10 @@ typedef struct {
                             sweeps and residuals of the V-cycle use the closed-form lattice stencil (checked
                             entry by entry against the assembled K at setup) instead of the stored one;
                             0: always the stored stencil (default 1) */
+    int cluster_sweeps;  /* 1: FP32 coarse-level Gauss-Seidel steps whose level vector fits the shared memory
+                            of one thread-block cluster may run in that cluster (hardware barrier between
+                            colours) instead of a cooperative grid: with autotune, where the setup timing
+                            finds it faster; without, wherever it fits; 0: always the grid (default 1) */
     gl_warmstart warmstart; /* learned initial guess: when set, gl_jacobian_solve and gl_newton_step ignore the
                             x passed in, start from the network's x0, and fall back to x0 = 0 when
                             ||b - J x0||_D >= ||b||_D (default NULL: start from x as given) */

@@ -72,6 +72,7 @@ gl_status gl_options_default(gl_options *o) {
     o->check_every = 6;
     o->autotune = 1;
     o->lattice = 1;
+    o->cluster_sweeps = 1;
     o->warmstart = nullptr;
     return GL_OK;
 }
@@ -418,7 +419,7 @@ gl_status gl_profile_begin(const char *kernel_class, int max_launches) {
         p.total_ms = p.total_bytes = 0;
         p.timed = p.dropped = 0;
         p.launches.store(0);
-        p.generation += 1;
+        p.retarget(p.name);
         p.active = true;
         return GL_OK;
     });
@@ -439,7 +440,7 @@ gl_status gl_profile_end(int64_t *launches, int64_t *timed, double *total_ms, do
         p.free_slots.clear();
         p.active = false;
         p.name.clear();
-        p.generation += 1;
+        p.retarget("");
         return GL_OK;
     });
 }

@@ -68,6 +68,7 @@ struct Level {
     CsrG<float2> Ag32, PHg32;
     DBuf<float2> b32, x32, r32;
     DBuf<float2> Ainv32;            // unused: the coarsest solve stays FP64
+    int cl_size = 0, cl_chunk = 0;  // FP32 sweeps by one thread-block cluster (0: cooperative grid)
 };
 
 }  // namespace gl
@@ -81,6 +82,7 @@ struct gl_prec_s {
     bool has32 = false;
     bool autotune = true;
     bool lattice = true;              // closed-form finest-level stencil in the FP32 V-cycle when available
+    bool cluster_sweeps = true;       // FP32 coarse sweeps by one thread-block cluster when the level fits
     gl::Level L[gl::MAX_LEVELS];
     gl::DBuf<double2> psi_p;          // psi in solve ordering
     gl::DBuf<double2> cyc_r, cyc_e;   // work vectors for k > 1 cycles
@@ -133,6 +135,9 @@ void precond_apply_p(gl_prec_s *p, const double2 *v, double2 *z, const int *stop
 void precond_apply_p32(gl_prec_s *p, const float2 *v, float2 *z, const int *stop, cudaStream_t s);
 // autotuner: picks the lanes-per-row width of every grouped-CSR operator by timing
 void autotune_levels(gl_prec_s *p, bool fp32, cudaStream_t s);
+// picks the thread-block-cluster or the cooperative-grid sweep for every coarse
+// FP32 level (timed on the GPU when autotuning)
+void plan_cluster_sweeps(gl_prec_s *p, cudaStream_t s);
 // z = R_k v with FP64 vectors and an FP32 V-cycle
 void precond_apply_p64_via32(gl_prec_s *p, const double2 *v, double2 *z, const int *stop, cudaStream_t s);
 

@@ -4,8 +4,9 @@
 // Direct launches take an event pair from a pool and are summed at the next
 // harvest.  Launches captured into a CUDA graph keep their event pair for the
 // life of the graph; the graph's owner harvests those pairs after every replay.
-// Every gl_profile_begin/end bumps `generation`, so graphs captured under an
-// older generation (whose events may be gone) are captured again.
+// gl_profile_begin/end bump `generation` whenever graphs may hold event nodes
+// of the old event pool or must gain some, so those graphs are captured again;
+// counting launches only (no class) leaves graphs without event nodes alone.
 #pragma once
 
 #include <atomic>
@@ -19,6 +20,14 @@ namespace gl {
 struct Profiler {
     std::atomic<int64_t> launches{0};  // hot-path kernel launches since gl_profile_begin
     int64_t generation = 0;
+    // timed class under which the graphs of the current generation are captured
+    // ("" = none: such graphs hold no event nodes and survive a change to "" )
+    std::string graph_state;
+    // a new generation unless both the graphs' state and the new one time nothing
+    void retarget(const std::string &state) {
+        if (!(graph_state.empty() && state.empty())) generation += 1;
+        graph_state = state;
+    }
     bool active = false;
     std::string name;                  // kernel class timed with events ("" = none)
     std::vector<cudaEvent_t> ev;       // 2 per slot

@@ -981,6 +981,7 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
     GL_CUDA(cudaStreamSynchronize(s));
     p->autotune = o.autotune != 0;
     p->lattice = o.lattice != 0;
+    p->cluster_sweeps = o.cluster_sweeps != 0;
     if (p->autotune) autotune_levels(p, false, s);
     if (o.precision != GL_FP64) precond_ensure_fp32(p, s);
 }
@@ -1019,6 +1020,7 @@ void precond_ensure_fp32(gl_prec_s *p, cudaStream_t s) {
         p->cyc_e32.alloc(m->n);
     }
     if (p->autotune) autotune_levels(p, true, s);
+    plan_cluster_sweeps(p, s);
     p->mp_in.alloc(m->n);
     p->mp_out.alloc(m->n);
     Level &Lb = p->L[p->nlev - 1];

@@ -9,6 +9,8 @@
 // K + 2|psi|^2 = D^-1 (K-hat + 2 D|psi|^2): Gauss-Seidel on D^-1 A with right-hand
 // side v is Gauss-Seidel on A with right-hand side D v, and the residual handed
 // to the restriction is multiplied by D.
+#include <cooperative_groups.h>
+
 #include "gl_internal.cuh"
 #include "gl_kernels.cuh"
 #include "gl_profile.cuh"
@@ -82,32 +84,57 @@ __global__ void __launch_bounds__(256) k_resid(int64_t n, SellView<C> A, const R
 }
 
 // the two kernels above on the finest level of an even-N lattice, with the
-// closed-form stencil instead of the stored one (FP32)
+// tabulated stencil instead of the stored one (FP32).  Each thread takes
+// LAT_RPT rows, blockDim.x apart, and issues the neighbour reads of all of them
+// before any write: a colour's rows read only the other colour's x.
+constexpr int LAT_RPT = 1;
+
 __global__ void __launch_bounds__(256) k_gs_lat(int64_t lo, int64_t hi, LatticeView L, const float *__restrict__ diag,
                                                 const float2 *__restrict__ b, float2 *__restrict__ x, int first,
                                                 const int *__restrict__ stop) {
     if (stop && *stop) return;
-    int64_t p = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= hi) return;
+    const int64_t p0 = lo + (int64_t)blockIdx.x * blockDim.x * LAT_RPT + threadIdx.x;
     // from x = 0 the first colour has no nonzero neighbour and the second sees
     // only the first (two colours, each node's neighbours of the other colour)
-    float2 acc = (first && lo == 0) ? make_float2(0.f, 0.f) : lattice_row(L, p, x);
-    float2 bb = b[p];
-    float d = 1.f / diag[p];
-    x[p] = make_float2((bb.x - acc.x) * d, (bb.y - acc.y) * d);
+    const bool none = first && lo == 0;
+    float2 acc[LAT_RPT];
+#pragma unroll
+    for (int u = 0; u < LAT_RPT; ++u) {
+        const int64_t p = p0 + (int64_t)u * blockDim.x;
+        acc[u] = (p < hi && !none) ? lattice_row(L, p, x) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < LAT_RPT; ++u) {
+        const int64_t p = p0 + (int64_t)u * blockDim.x;
+        if (p < hi) {
+            const float2 bb = b[p];
+            const float d = 1.f / diag[p];
+            x[p] = make_float2((bb.x - acc[u].x) * d, (bb.y - acc[u].y) * d);
+        }
+    }
 }
 __global__ void __launch_bounds__(256) k_resid_lat(int64_t n, LatticeView L, const float *__restrict__ diag,
                                                    const float2 *__restrict__ b, const float2 *__restrict__ x,
                                                    const float *__restrict__ scale, float2 *__restrict__ r,
                                                    const int *__restrict__ stop) {
     if (stop && *stop) return;
-    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    float2 acc = lattice_row(L, p, x);
-    float2 xx = x[p], bb = b[p];
-    float d = diag[p];
-    float sc = scale ? scale[p] : 1.f;
-    r[p] = make_float2((bb.x - acc.x - d * xx.x) * sc, (bb.y - acc.y - d * xx.y) * sc);
+    const int64_t p0 = (int64_t)blockIdx.x * blockDim.x * LAT_RPT + threadIdx.x;
+    float2 acc[LAT_RPT];
+#pragma unroll
+    for (int u = 0; u < LAT_RPT; ++u) {
+        const int64_t p = p0 + (int64_t)u * blockDim.x;
+        acc[u] = p < n ? lattice_row(L, p, x) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < LAT_RPT; ++u) {
+        const int64_t p = p0 + (int64_t)u * blockDim.x;
+        if (p < n) {
+            const float2 xx = x[p], bb = b[p];
+            const float d = diag[p];
+            const float sc = scale ? scale[p] : 1.f;
+            r[p] = make_float2((bb.x - acc[u].x - d * xx.x) * sc, (bb.y - acc[u].y - d * xx.y) * sc);
+        }
+    }
 }
 
 // y = S x (add = 0) or y += S x (add = 1) for a rectangular sliced-ELL S
@@ -351,6 +378,187 @@ static void launch_sgs_coop(const CsrG<C> &A, const R *diag, const int64_t *csta
                                stop));
 }
 
+// ---------------------------------------------------------------- cluster sweeps
+// One thread-block cluster runs a whole symmetric Gauss-Seidel step of a coarse
+// level in FP32.  The level's x lives in the distributed shared memory of the
+// cluster: CTA r holds positions [r chunk, (r + 1) chunk).  Rows of a colour are
+// spread over all the cluster's threads (G lanes per row); neighbour values are
+// read from the owning CTA's shared memory and new values written there, and
+// consecutive colours are separated by the cluster's hardware barrier, split
+// into arrive and wait so that the next colour's x-independent data (row
+// bounds, columns, values, b, diagonal) is loaded in between.  The same colour
+// order and the same first-sweep rule (from x = 0, later colours are still 0) as
+// the cooperative kernel.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+constexpr int CLUSTER_THREADS = 1024;
+
+template <int G>
+__global__ void __launch_bounds__(CLUSTER_THREADS) k_sgs_cluster(CsrGView<float2> A, const float *__restrict__ diag,
+                                                                 const int64_t *__restrict__ cstart, int ncolors,
+                                                                 const float2 *__restrict__ b, float2 *x,
+                                                                 int zero_start, int chunk, float inv_chunk,
+                                                                 const int *__restrict__ stop) {
+    extern __shared__ float2 xs[];
+    if (stop && *stop) return;
+    namespace cgs = cooperative_groups;
+    cgs::cluster_group cl = cgs::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int nblk = (int)cl.num_blocks();
+    const int64_t n = A.nrows;
+    const int64_t base = (int64_t)rank * chunk;
+    const int64_t mine = std::max<int64_t>(0, std::min<int64_t>(chunk, n - base));
+    for (int64_t i = threadIdx.x; i < mine; i += blockDim.x) xs[i] = zero_start ? make_float2(0.f, 0.f) : x[base + i];
+    // owning CTA and offset of position c
+    auto owner_of = [&](int32_t c) {
+        int o = (int)((float)c * inv_chunk);
+        if ((int64_t)o * chunk > c) --o;
+        else if ((int64_t)(o + 1) * chunk <= c) ++o;
+        return o;
+    };
+    auto xget = [&](int32_t c) {
+        const int o = owner_of(c);
+        return cl.map_shared_rank(xs, o)[c - (int64_t)o * chunk];
+    };
+    const int64_t t = (int64_t)rank * blockDim.x + threadIdx.x;
+    const int64_t grp = t / G, ngroups = (int64_t)nblk * blockDim.x / G;
+    const int lane = (int)(t % G);
+    const int nphase = 2 * ncolors - 1;
+    int32_t pcol[PF];
+    float2 pval[PF];
+    float2 pb = make_float2(0.f, 0.f);
+    float pd = 1.f;
+    int64_t pq0 = 0, pq1 = 0;
+    auto colour_of = [&](int ph) { return ph < ncolors ? ph : 2 * ncolors - 2 - ph; };
+    auto prefetch = [&](int64_t row, bool ok) {
+        pq0 = pq1 = 0;
+        if (ok) {
+            pq0 = A.rp[row];
+            pq1 = A.rp[row + 1];
+            pb = b[row];
+            pd = diag[row];
+        }
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            int64_t q = pq0 + lane + (int64_t)k * G;
+            if (q < pq1) {
+                pcol[k] = __ldg(A.col + q);
+                pval[k] = A.val[q];
+            }
+        }
+    };
+    cluster_arrive();
+    {
+        int c = colour_of(0);
+        prefetch(cstart[c] + grp, cstart[c] + grp < cstart[c + 1]);
+    }
+    cluster_wait();
+    for (int ph = 0; ph < nphase; ++ph) {
+        const int c = colour_of(ph);
+        const bool first = zero_start && ph < ncolors;
+        const int64_t lo = cstart[c], hi = cstart[c + 1];
+        const int64_t rounds = (hi - lo + ngroups - 1) / ngroups;
+        for (int64_t k = 0; k < rounds; ++k) {
+            const int64_t row = lo + k * ngroups + grp;
+            const bool ok = row < hi;
+            float2 acc = make_float2(0.f, 0.f);
+            if (!(first && lo == 0)) {
+                if (k == 0) {
+#pragma unroll
+                    for (int e = 0; e < PF; ++e) {
+                        int64_t q = pq0 + lane + (int64_t)e * G;
+                        if (q < pq1) cfma(acc, pval[e], xget(pcol[e]));
+                    }
+                    for (int64_t q = pq0 + lane + (int64_t)PF * G; q < pq1; q += G)
+                        cfma(acc, A.val[q], xget(__ldg(A.col + q)));
+                } else if (ok) {
+                    for (int64_t q = A.rp[row] + lane; q < A.rp[row + 1]; q += G)
+                        cfma(acc, A.val[q], xget(__ldg(A.col + q)));
+                }
+            }
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) {
+                acc.x += __shfl_down_sync(0xffffffffu, acc.x, o, G);
+                acc.y += __shfl_down_sync(0xffffffffu, acc.y, o, G);
+            }
+            if (ok && lane == 0) {
+                const float2 bb = (k == 0) ? pb : b[row];
+                const float d = 1.f / ((k == 0) ? pd : diag[row]);
+                const int o = owner_of((int32_t)row);
+                cl.map_shared_rank(xs, o)[row - (int64_t)o * chunk] =
+                    make_float2((bb.x - acc.x) * d, (bb.y - acc.y) * d);
+            }
+        }
+        cluster_arrive();
+        if (ph + 1 < nphase) {
+            const int cn = colour_of(ph + 1);
+            prefetch(cstart[cn] + grp, cstart[cn] + grp < cstart[cn + 1]);
+        }
+        cluster_wait();
+    }
+    for (int64_t i = threadIdx.x; i < mine; i += blockDim.x) x[base + i] = xs[i];
+}
+
+// cluster size (16 with the non-portable opt-in, else 8) and chunk for a level
+// of n rows whose x fits the cluster's shared memory; size 0 if none fits
+template <int G>
+static void plan_sgs_cluster(int64_t n, int &size, int &chunk) {
+    size = 0;
+    chunk = 0;
+    if (n <= 0) return;
+    GL_CUDA(cudaFuncSetAttribute(k_sgs_cluster<G>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    for (int cs : {16, 8}) {
+        int64_t ch = (n + cs - 1) / cs;
+        int64_t smem = ch * (int64_t)sizeof(float2);
+        if (smem > 200 * 1024) continue;
+        GL_CUDA(cudaFuncSetAttribute(k_sgs_cluster<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(CLUSTER_THREADS);
+        cfg.dynamicSmemBytes = (size_t)smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_sgs_cluster<G>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (nclusters >= 1) {
+            size = cs;
+            chunk = (int)ch;
+            return;
+        }
+    }
+}
+
+template <int G>
+static void launch_sgs_cluster(const CsrG<float2> &A, const float *diag, const int64_t *cstart, int nc,
+                               const float2 *b, float2 *x, int zero_start, int size, int chunk, const int *stop,
+                               cudaStream_t s) {
+    const size_t smem = (size_t)chunk * sizeof(float2);
+    GL_CUDA(cudaFuncSetAttribute(k_sgs_cluster<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(size);
+    cfg.blockDim = dim3(CLUSTER_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = size;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    GL_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_cluster<G>, A.view(), diag, cstart, nc, b, x, zero_start, chunk,
+                               1.0f / (float)chunk, stop));
+}
+
 // dispatch on the group width
 #define GL_DISPATCH_G(G_, CALL)                       \
     switch (G_) {                                     \
@@ -491,7 +699,8 @@ static void gs_sweep(Level &L, int level, const typename LevelOps<T>::C *b, type
             if (!(first && lo == 0))
                 bytes += (double)(L.n - (hi - lo)) * sizeof(C) + (double)lat->N * lat->N * lat->dim * 8.0;
             ProfScope ps("gs0", bytes, s);
-            k_gs_lat<<<grid_for(hi - lo, 256), 256, 0, s>>>(lo, hi, *lat, O::diag(L), b, x, first ? 1 : 0, stop);
+            k_gs_lat<<<grid_for(hi - lo, 256 * LAT_RPT), 256, 0, s>>>(lo, hi, *lat, O::diag(L), b, x, first ? 1 : 0,
+                                                                     stop);
             return;
         }
     }
@@ -546,7 +755,24 @@ static void smooth(gl_prec_s *p, int l, const typename LevelOps<T>::C *b, typena
     const CsrG<C> &A = O::Ag(L);
     int64_t maxc = 0;
     for (int c = 0; c < L.ncolors; ++c) maxc = std::max(maxc, L.cstart[c + 1] - L.cstart[c]);
-    ProfScope ps("gs", 0, s);
+    // algorithmic bytes of one symmetric step: every visit of a colour reads its
+    // rows' stored entries (value + column) and b, diagonal and writes x; the
+    // first colour from a zero guess reads no entries
+    double bytes = 0;
+    for (int ph = 0; ph < 2 * L.ncolors - 1; ++ph) {
+        int c = ph < L.ncolors ? ph : 2 * L.ncolors - 2 - ph;
+        double rows = (double)(L.cstart[c + 1] - L.cstart[c]);
+        bytes += rows * (2 * sizeof(C) + sizeof(T));
+        if (!(zero_start && ph == 0)) bytes += (double)L.cnnz[c] * (sizeof(C) + 4);
+    }
+    ProfScope ps("gs", bytes, s);
+    if constexpr (sizeof(T) == 4) {
+        if (L.cl_size > 0 && p->cluster_sweeps) {
+            GL_DISPATCH_G(A.G, (launch_sgs_cluster<GG>(A, O::diag(L), L.cstart_dev.get(), L.ncolors, b, x,
+                                                        zero_start ? 1 : 0, L.cl_size, L.cl_chunk, stop, s)));
+            return;
+        }
+    }
     GL_DISPATCH_G(A.G, (launch_sgs_coop<GG, C, T>(A, O::diag(L), L.cstart_dev.get(), L.ncolors, b, x,
                                                    zero_start ? 1 : 0, L.barrier.get(), p->err.get(), stop, maxc, s)));
 }
@@ -575,7 +801,8 @@ static void vcycle(gl_prec_s *p, int l, const typename LevelOps<T>::C *b, typena
         bool lat = lattice_for<T>(p, lv);
         if constexpr (sizeof(T) == 4) {
             if (lat)
-                k_resid_lat<<<grid_for(L.n, 256), 256, 0, s>>>(L.n, lv, O::diag(L), b, x, scale, r, stop);
+                k_resid_lat<<<grid_for(L.n, 256 * LAT_RPT), 256, 0, s>>>(L.n, lv, O::diag(L), b, x, scale, r,
+                                                                         stop);
         }
         if (!lat)
             k_resid<C, T><<<grid_for(L.n, 256), 256, 0, s>>>(L.n, O::A(L).view(), O::diag(L), b, x, scale, r, stop);
@@ -643,6 +870,59 @@ void precond_apply_p64_via32(gl_prec_s *p, const double2 *v, double2 *z, const i
     precond_apply_t<float>(p, p->mp_in.get(), p->mp_out.get(), stop, s);
     k_f2d<<<grid_for(n, 256), 256, 0, s>>>(n, p->mp_out.get(), z, stop);
     GL_LAUNCH_CHECK();
+}
+
+// chooses, for every coarse FP32 level, between the cooperative-grid sweep and
+// the thread-block-cluster sweep (levels whose vector fits a cluster's shared
+// memory): with autotuning the faster of the two timed on this GPU, without it
+// the cluster sweep wherever it fits
+void plan_cluster_sweeps(gl_prec_s *p, cudaStream_t s) {
+    cudaEvent_t e0, e1;
+    GL_CUDA(cudaEventCreate(&e0));
+    GL_CUDA(cudaEventCreate(&e1));
+    for (int l = 1; l < p->nlev - 1; ++l) {
+        Level &L = p->L[l];
+        L.cl_size = 0;
+        L.cl_chunk = 0;
+        if (!p->cluster_sweeps || L.n > INT32_MAX) continue;
+        int size = 0, chunk = 0;
+        GL_DISPATCH_G(L.Ag32.G, (plan_sgs_cluster<GG>(L.n, size, chunk)));
+        if (size == 0) continue;
+        if (p->autotune) {
+            const CsrG<float2> &A = L.Ag32;
+            int64_t maxc = 0;
+            for (int c = 0; c < L.ncolors; ++c) maxc = std::max(maxc, L.cstart[c + 1] - L.cstart[c]);
+            GL_CUDA(cudaMemsetAsync(L.b32.get(), 0, L.n * sizeof(float2), s));
+            GL_CUDA(cudaMemsetAsync(L.x32.get(), 0, L.n * sizeof(float2), s));
+            float best[2] = {0, 0};
+            for (int v = 0; v < 2; ++v) {
+                float bestv = 1e30f;
+                for (int rep = 0; rep < 4; ++rep) {
+                    GL_CUDA(cudaEventRecord(e0, s));
+                    if (v == 0) {
+                        GL_DISPATCH_G(A.G, (launch_sgs_coop<GG, float2, float>(
+                                               A, L.diag32.get(), L.cstart_dev.get(), L.ncolors, L.b32.get(),
+                                               L.x32.get(), 0, L.barrier.get(), p->err.get(), nullptr, maxc, s)));
+                    } else {
+                        GL_DISPATCH_G(A.G, (launch_sgs_cluster<GG>(A, L.diag32.get(), L.cstart_dev.get(), L.ncolors,
+                                                                    L.b32.get(), L.x32.get(), 0, size, chunk,
+                                                                    nullptr, s)));
+                    }
+                    GL_CUDA(cudaEventRecord(e1, s));
+                    GL_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0;
+                    GL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (rep > 0) bestv = std::min(bestv, ms);  // the first launch warms up
+                }
+                best[v] = bestv;
+            }
+            if (best[1] >= best[0]) continue;
+        }
+        L.cl_size = size;
+        L.cl_chunk = chunk;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
 }
 
 }  // namespace gl
