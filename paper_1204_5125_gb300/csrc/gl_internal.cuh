@@ -34,6 +34,8 @@ struct gl_mesh_s {
 namespace gl {
 
 constexpr int MAX_LEVELS = 16;
+// grid-barrier state of a cooperative sweep: arrivals and completed rounds
+constexpr int GRID_BARRIER_WORDS = 2;
 constexpr int MAX_COARSE_DENSE = 4096;
 
 struct Level {
@@ -69,6 +71,7 @@ struct Level {
     DBuf<float2> b32, x32, r32;
     DBuf<float2> Ainv32;            // unused: the coarsest solve stays FP64
     int cl_size = 0, cl_chunk = 0;  // FP32 sweeps by one thread-block cluster (0: cooperative grid)
+    int sgs_G32 = 1, sgs_G64 = 1;   // lanes per row of the coarse Gauss-Seidel sweeps
 };
 
 }  // namespace gl
@@ -135,9 +138,9 @@ void precond_apply_p(gl_prec_s *p, const double2 *v, double2 *z, const int *stop
 void precond_apply_p32(gl_prec_s *p, const float2 *v, float2 *z, const int *stop, cudaStream_t s);
 // autotuner: picks the lanes-per-row width of every grouped-CSR operator by timing
 void autotune_levels(gl_prec_s *p, bool fp32, cudaStream_t s);
-// picks the thread-block-cluster or the cooperative-grid sweep for every coarse
-// FP32 level (timed on the GPU when autotuning)
-void plan_cluster_sweeps(gl_prec_s *p, cudaStream_t s);
+// picks, per coarse level, the lanes per row of the Gauss-Seidel sweep and (FP32)
+// the thread-block-cluster or the cooperative-grid form (timed when autotuning)
+void plan_sweeps(gl_prec_s *p, bool fp32, cudaStream_t s);
 // z = R_k v with FP64 vectors and an FP32 V-cycle
 void precond_apply_p64_via32(gl_prec_s *p, const double2 *v, double2 *z, const int *stop, cudaStream_t s);
 

@@ -948,8 +948,8 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
             L.cstart_dev.alloc(L.ncolors + 1);
             GL_CUDA(cudaMemcpyAsync(L.cstart_dev.get(), L.cstart.data(), (L.ncolors + 1) * sizeof(int64_t),
                                     cudaMemcpyHostToDevice, s));
-            L.barrier.alloc(2);
-            GL_CUDA(cudaMemsetAsync(L.barrier.get(), 0, 2 * sizeof(unsigned), s));
+            L.barrier.alloc(GRID_BARRIER_WORDS);
+            GL_CUDA(cudaMemsetAsync(L.barrier.get(), 0, GRID_BARRIER_WORDS * sizeof(unsigned), s));
         }
         if (!coarsest) {
             Level &Lc = p->L[k + 1];
@@ -983,6 +983,7 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
     p->lattice = o.lattice != 0;
     p->cluster_sweeps = o.cluster_sweeps != 0;
     if (p->autotune) autotune_levels(p, false, s);
+    plan_sweeps(p, false, s);
     if (o.precision != GL_FP64) precond_ensure_fp32(p, s);
 }
 
@@ -1020,7 +1021,7 @@ void precond_ensure_fp32(gl_prec_s *p, cudaStream_t s) {
         p->cyc_e32.alloc(m->n);
     }
     if (p->autotune) autotune_levels(p, true, s);
-    plan_cluster_sweeps(p, s);
+    plan_sweeps(p, true, s);
     p->mp_in.alloc(m->n);
     p->mp_out.alloc(m->n);
     Level &Lb = p->L[p->nlev - 1];

@@ -210,35 +210,51 @@ __global__ void __launch_bounds__(256) k_resid_g(CsrGView<C> A, const R *__restr
 // into arrive and wait so that independent work can run in between.  The wait
 // is bounded: after ~2^24 polls it records an error and lets the block go on,
 // so a broken launch ends instead of hanging.
-__device__ __forceinline__ unsigned grid_arrive(unsigned *bar) {
+// Grid barrier of the cooperative sweeps.  bar[0] counts the CTAs that arrived
+// in the current round, bar[1] counts completed rounds.  The last CTA to arrive
+// resets bar[0] and releases bar[1]; the others acquire bar[1].  A CTA reads
+// bar[1] once at kernel start (no round can complete before every CTA has
+// started) and waits for round k to complete at its k-th barrier, so nothing
+// but the arrival atomic, the release and the acquiring load sits between the
+// last CTA's work and everybody's next phase.  The release/acquire pair, after
+// the CTA-wide __syncthreads on both sides, orders every thread's x writes
+// before the other CTAs' reads.  (A flag per CTA polled by one warp, which
+// avoids the atomic, measured slower on these grids.)
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned grid_round0(unsigned *bar) {
+    __shared__ unsigned g0;
+    if (threadIdx.x == 0) g0 = ld_acquire_u32(bar + 1);
     __syncthreads();
-    unsigned g = 0;
+    return g0;
+}
+__device__ __forceinline__ void grid_arrive(unsigned *bar) {
+    __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *gen = bar + 1;
-        g = *gen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+        unsigned old;
+        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
+        if (old == gridDim.x - 1) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
         }
     }
-    return g;
 }
-__device__ __forceinline__ bool grid_wait(unsigned *bar, unsigned g, int *err) {
+// waits for round `k` (counted from g0) to complete; false if the wait ran out
+__device__ __forceinline__ bool grid_wait(unsigned *bar, unsigned g0, unsigned k, int *err) {
     __shared__ int ok;
     if (threadIdx.x == 0) {
-        volatile unsigned *gen = bar + 1;
         unsigned spins = 0;
         int good = 1;
-        while (*gen == g) {
+        while (ld_acquire_u32(bar + 1) - g0 <= k) {
             if (++spins > (1u << 24)) {
                 atomicExch(err, 1);
                 good = 0;
                 break;
             }
         }
-        __threadfence();
         ok = good;
     }
     __syncthreads();
@@ -267,6 +283,7 @@ __global__ void __launch_bounds__(coop_threads<R>()) k_sgs_coop(CsrGView<C> A, c
                                                                 unsigned *bar, int *err,
                                                                 const int *__restrict__ stop) {
     if (stop && *stop) return;
+    const unsigned g0 = grid_round0(bar);
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t grp = t / G, ngroups = (int64_t)gridDim.x * blockDim.x / G;
     int lane = (int)(t % G);
@@ -342,10 +359,10 @@ __global__ void __launch_bounds__(coop_threads<R>()) k_sgs_coop(CsrGView<C> A, c
         }
         if (ph + 1 < nphase) {
             // arrive, load the next colour's x-independent data, then wait
-            unsigned g = grid_arrive(bar);
+            grid_arrive(bar);
             int cn = colour_of(ph + 1);
             prefetch(cstart[cn] + grp, cstart[cn] + grp < cstart[cn + 1]);
-            if (!grid_wait(bar, g, err)) return;
+            if (!grid_wait(bar, g0, (unsigned)ph, err)) return;
         }
     }
 }
@@ -542,6 +559,7 @@ static void launch_sgs_cluster(const CsrG<float2> &A, const float *diag, const i
                                const float2 *b, float2 *x, int zero_start, int size, int chunk, const int *stop,
                                cudaStream_t s) {
     const size_t smem = (size_t)chunk * sizeof(float2);
+    GL_CUDA(cudaFuncSetAttribute(k_sgs_cluster<G>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     GL_CUDA(cudaFuncSetAttribute(k_sgs_cluster<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(size);
@@ -766,15 +784,16 @@ static void smooth(gl_prec_s *p, int l, const typename LevelOps<T>::C *b, typena
         if (!(zero_start && ph == 0)) bytes += (double)L.cnnz[c] * (sizeof(C) + 4);
     }
     ProfScope ps("gs", bytes, s);
+    const int sG = sizeof(T) == 4 ? L.sgs_G32 : L.sgs_G64;
     if constexpr (sizeof(T) == 4) {
         if (L.cl_size > 0 && p->cluster_sweeps) {
-            GL_DISPATCH_G(A.G, (launch_sgs_cluster<GG>(A, O::diag(L), L.cstart_dev.get(), L.ncolors, b, x,
-                                                        zero_start ? 1 : 0, L.cl_size, L.cl_chunk, stop, s)));
+            GL_DISPATCH_G(sG, (launch_sgs_cluster<GG>(A, O::diag(L), L.cstart_dev.get(), L.ncolors, b, x,
+                                                       zero_start ? 1 : 0, L.cl_size, L.cl_chunk, stop, s)));
             return;
         }
     }
-    GL_DISPATCH_G(A.G, (launch_sgs_coop<GG, C, T>(A, O::diag(L), L.cstart_dev.get(), L.ncolors, b, x,
-                                                   zero_start ? 1 : 0, L.barrier.get(), p->err.get(), stop, maxc, s)));
+    GL_DISPATCH_G(sG, (launch_sgs_coop<GG, C, T>(A, O::diag(L), L.cstart_dev.get(), L.ncolors, b, x,
+                                                  zero_start ? 1 : 0, L.barrier.get(), p->err.get(), stop, maxc, s)));
 }
 
 template <typename T>
@@ -872,57 +891,94 @@ void precond_apply_p64_via32(gl_prec_s *p, const double2 *v, double2 *z, const i
     GL_LAUNCH_CHECK();
 }
 
-// chooses, for every coarse FP32 level, between the cooperative-grid sweep and
-// the thread-block-cluster sweep (levels whose vector fits a cluster's shared
-// memory): with autotuning the faster of the two timed on this GPU, without it
-// the cluster sweep wherever it fits
-void plan_cluster_sweeps(gl_prec_s *p, cudaStream_t s) {
+// chooses how every coarse level runs its symmetric Gauss-Seidel steps: the
+// lanes-per-row width G of the cooperative-grid sweep (a latency-bound kernel
+// wants more lanes per row than the throughput-bound SpMV that set the operator's
+// own G) and, in FP32, the thread-block-cluster sweep for levels whose vector
+// fits a cluster.  With autotuning every candidate (G = 2, 4, 8, 16) is timed on
+// this GPU (best of two after a warm-up launch, on zero vectors) and the fastest
+// kept; without it the operator's G, and the cluster sweep wherever it fits.
+template <typename T>
+static void plan_sweeps_t(gl_prec_s *p, cudaStream_t s) {
+    using O = LevelOps<T>;
+    using C = typename O::C;
     cudaEvent_t e0, e1;
     GL_CUDA(cudaEventCreate(&e0));
     GL_CUDA(cudaEventCreate(&e1));
     for (int l = 1; l < p->nlev - 1; ++l) {
         Level &L = p->L[l];
-        L.cl_size = 0;
-        L.cl_chunk = 0;
-        if (!p->cluster_sweeps || L.n > INT32_MAX) continue;
-        int size = 0, chunk = 0;
-        GL_DISPATCH_G(L.Ag32.G, (plan_sgs_cluster<GG>(L.n, size, chunk)));
-        if (size == 0) continue;
-        if (p->autotune) {
-            const CsrG<float2> &A = L.Ag32;
-            int64_t maxc = 0;
-            for (int c = 0; c < L.ncolors; ++c) maxc = std::max(maxc, L.cstart[c + 1] - L.cstart[c]);
-            GL_CUDA(cudaMemsetAsync(L.b32.get(), 0, L.n * sizeof(float2), s));
-            GL_CUDA(cudaMemsetAsync(L.x32.get(), 0, L.n * sizeof(float2), s));
-            float best[2] = {0, 0};
-            for (int v = 0; v < 2; ++v) {
-                float bestv = 1e30f;
-                for (int rep = 0; rep < 4; ++rep) {
-                    GL_CUDA(cudaEventRecord(e0, s));
-                    if (v == 0) {
-                        GL_DISPATCH_G(A.G, (launch_sgs_coop<GG, float2, float>(
-                                               A, L.diag32.get(), L.cstart_dev.get(), L.ncolors, L.b32.get(),
-                                               L.x32.get(), 0, L.barrier.get(), p->err.get(), nullptr, maxc, s)));
-                    } else {
-                        GL_DISPATCH_G(A.G, (launch_sgs_cluster<GG>(A, L.diag32.get(), L.cstart_dev.get(), L.ncolors,
-                                                                    L.b32.get(), L.x32.get(), 0, size, chunk,
-                                                                    nullptr, s)));
-                    }
-                    GL_CUDA(cudaEventRecord(e1, s));
-                    GL_CUDA(cudaEventSynchronize(e1));
-                    float ms = 0;
-                    GL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                    if (rep > 0) bestv = std::min(bestv, ms);  // the first launch warms up
-                }
-                best[v] = bestv;
-            }
-            if (best[1] >= best[0]) continue;
+        const CsrG<C> &A = O::Ag(L);
+        int &sG = sizeof(T) == 4 ? L.sgs_G32 : L.sgs_G64;
+        sG = A.G;
+        if constexpr (sizeof(T) == 4) {
+            L.cl_size = 0;
+            L.cl_chunk = 0;
         }
-        L.cl_size = size;
-        L.cl_chunk = chunk;
+        int size = 0, chunk = 0;
+        if constexpr (sizeof(T) == 4) {
+            if (p->cluster_sweeps && L.n <= INT32_MAX) GL_DISPATCH_G(A.G, (plan_sgs_cluster<GG>(L.n, size, chunk)));
+        }
+        if (!p->autotune) {
+            if constexpr (sizeof(T) == 4) {
+                L.cl_size = size;
+                L.cl_chunk = chunk;
+            }
+            continue;
+        }
+        int64_t maxc = 0;
+        for (int c = 0; c < L.ncolors; ++c) maxc = std::max(maxc, L.cstart[c + 1] - L.cstart[c]);
+        C *b = O::b(L), *x = O::x(L);
+        GL_CUDA(cudaMemsetAsync(b, 0, L.n * sizeof(C), s));
+        GL_CUDA(cudaMemsetAsync(x, 0, L.n * sizeof(C), s));
+        auto time_it = [&](auto &&launch) {
+            float best = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                GL_CUDA(cudaEventRecord(e0, s));
+                launch();
+                GL_CUDA(cudaEventRecord(e1, s));
+                GL_CUDA(cudaEventSynchronize(e1));
+                float ms = 0;
+                GL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep > 0) best = std::min(best, ms);
+            }
+            return best;
+        };
+        float best = 1e30f;
+        int bestG = A.G;
+        bool best_cluster = false;
+        for (int g : {2, 4, 8, 16}) {
+            float t = time_it([&] {
+                GL_DISPATCH_G(g, (launch_sgs_coop<GG, C, T>(A, O::diag(L), L.cstart_dev.get(), L.ncolors, b, x, 0,
+                                                             L.barrier.get(), p->err.get(), nullptr, maxc, s)));
+            });
+            if (t < best) best = t, bestG = g;
+            if constexpr (sizeof(T) == 4) {
+                if (size > 0) {
+                    float tc = time_it([&] {
+                        GL_DISPATCH_G(g, (launch_sgs_cluster<GG>(A, O::diag(L), L.cstart_dev.get(), L.ncolors, b, x, 0,
+                                                                  size, chunk, nullptr, s)));
+                    });
+                    if (tc < best) best = tc, bestG = g, best_cluster = true;
+                }
+            }
+        }
+        sG = bestG;
+        if constexpr (sizeof(T) == 4) {
+            if (best_cluster) {
+                L.cl_size = size;
+                L.cl_chunk = chunk;
+            }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+}
+
+void plan_sweeps(gl_prec_s *p, bool fp32, cudaStream_t s) {
+    if (fp32)
+        plan_sweeps_t<float>(p, s);
+    else
+        plan_sweeps_t<double>(p, s);
 }
 
 }  // namespace gl
