@@ -107,6 +107,9 @@ typedef struct {
     int warmstart_used;  /* 1 if the solve started from the learned guess, 0 if from x as given or after
                             the zero-guess fallback */
     int lattice_stencil; /* 1 if the FP32 finest-level V-cycle kernels used the closed-form stencil */
+    int df_jacobian;     /* 1 if MINRES applied the Jacobian in double-FP32 arithmetic (GL_MIXED_PRECOND on
+                            an even-N lattice with options.lattice = 1) */
+    int stall_restarts;  /* 1 if that run stalled above tol and MINRES finished with the FP64 Jacobian */
 } gl_solve_info;
 
 /* Default options (values listed in gl_options).  Returns GL_ERR_ARG on NULL. */

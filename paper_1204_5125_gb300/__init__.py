@@ -69,7 +69,8 @@ class SolveInfo(C.Structure):
     _fields_ = [
         ("iters", C.c_int), ("outer_iters", C.c_int), ("converged", C.c_int), ("true_relres", C.c_double),
         ("est_relres", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
-        ("warmstart_used", C.c_int), ("lattice_stencil", C.c_int),
+        ("warmstart_used", C.c_int), ("lattice_stencil", C.c_int), ("df_jacobian", C.c_int),
+        ("stall_restarts", C.c_int),
     ]
 
     def as_dict(self):

@@ -27,6 +27,12 @@ struct gl_mesh_s {
     bool lat_checked = false, lat_ok = false;
     int64_t lat_per_axis = 0;
     gl::DBuf<float2> lat_tab;
+    // the same tables as double-float magnitude a = |K-hat| / h^d and unit phase,
+    // the FP64 remainders K_ii - sum_k |K_ik| (solve ordering) and h^d
+    gl::DBuf<float2> lat_a;
+    gl::DBuf<float4> lat_u;
+    gl::DBuf<double> lat_krem;
+    double lat_hd = 0;
     // scratch for the node-order public calls
     gl::DBuf<double2> t0, t1, t2;
 };
@@ -117,6 +123,15 @@ struct LatticeView {
 };
 void mesh_ensure_lattice(gl_mesh_s *m, cudaStream_t s);
 LatticeView lattice_view(const gl_mesh_s *m);
+// double-float view of the same stencil (row scaled by 2^b / h^d, b = boundary coordinates)
+struct LatticeDfView {
+    int dim, N;
+    int64_t nred;
+    int64_t per_axis;
+    const float2 *a;   // |K-hat| / h^d as (hi, lo), axis-major tables
+    const float4 *u;   // exp(-i theta) of the +e edge as (re_hi, re_lo, im_hi, im_lo)
+};
+LatticeDfView lattice_df_view(const gl_mesh_s *m);
 
 // gl_setup.cu
 void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_options &o, cudaStream_t s);

@@ -129,6 +129,39 @@ __global__ void k_lat_round(int64_t m, const double2 *__restrict__ a, float2 *__
     if (i < m) b[i] = make_float2((float)a[i].x, (float)a[i].y);
 }
 
+__device__ __forceinline__ float2 split2(double x) {
+    float hi = __double2float_rn(x);
+    return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+// double-float magnitude a = |K-hat| / h^d and unit phase u = -K-hat / |K-hat| of
+// every table entry
+__global__ void k_lat_df(int64_t m, const double2 *__restrict__ t, double hd, float2 *__restrict__ a,
+                         float4 *__restrict__ u) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double2 k = make_double2(t[i].x / hd, t[i].y / hd);
+    double mag = sqrt(k.x * k.x + k.y * k.y);
+    double ur = mag > 0 ? -k.x / mag : 0.0, ui = mag > 0 ? -k.y / mag : 0.0;
+    a[i] = split2(mag);
+    float2 re = split2(ur), im = split2(ui);
+    u[i] = make_float4(re.x, re.y, im.x, im.y);
+}
+// K_ii - sum_k |K_ik| over the stored row (solve ordering, FP64)
+__global__ void k_lat_krem(int64_t n, SellView<double2> K, const double *__restrict__ kd, double *__restrict__ rem) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int64_t s = p >> 5;
+    int lane = (int)(p & 31);
+    int64_t beg = K.sptr[s];
+    int w = (int)((K.sptr[s + 1] - beg) >> 5);
+    double sum = 0;
+    for (int q = 0; q < w; ++q) {
+        double2 v = K.val[beg + (int64_t)q * SELL_C + lane];
+        sum += sqrt(v.x * v.x + v.y * v.y);
+    }
+    rem[p] = kd[p] - sum;
+}
+
 }  // namespace
 
 void mesh_ensure_lattice(gl_mesh_s *m, cudaStream_t s) {
@@ -162,9 +195,30 @@ void mesh_ensure_lattice(gl_mesh_s *m, cudaStream_t s) {
     m->lat_tab.alloc((size_t)per_axis * m->dim);
     k_lat_round<<<grid_for(per_axis * m->dim, 256), 256, 0, s>>>(per_axis * m->dim, tab64.get(), m->lat_tab.get());
     GL_LAUNCH_CHECK();
+    // double-float tables: the control volumes are h^d 2^-b exactly (b boundary
+    // coordinates), so K_ik = 2^b (K-hat_ik / h^d) with an exact power-of-2 factor
+    m->lat_hd = m->dim == 2 ? m->h * m->h : m->h * m->h * m->h;
+    m->lat_a.alloc((size_t)per_axis * m->dim);
+    m->lat_u.alloc((size_t)per_axis * m->dim);
+    m->lat_krem.alloc(m->n);
+    k_lat_df<<<grid_for(per_axis * m->dim, 256), 256, 0, s>>>(per_axis * m->dim, tab64.get(), m->lat_hd,
+                                                               m->lat_a.get(), m->lat_u.get());
+    k_lat_krem<<<grid_for(m->n, 256), 256, 0, s>>>(m->n, m->K.view(), m->kdiag.get(), m->lat_krem.get());
+    GL_LAUNCH_CHECK();
     GL_CUDA(cudaStreamSynchronize(s));
     m->lat_per_axis = per_axis;
     m->lat_ok = true;
+}
+
+LatticeDfView lattice_df_view(const gl_mesh_s *m) {
+    LatticeDfView v{};
+    v.dim = m->dim;
+    v.N = m->N;
+    v.nred = m->nred;
+    v.per_axis = m->lat_per_axis;
+    v.a = m->lat_a.get();
+    v.u = m->lat_u.get();
+    return v;
 }
 
 LatticeView lattice_view(const gl_mesh_s *m) {

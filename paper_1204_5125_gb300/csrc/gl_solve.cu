@@ -25,8 +25,9 @@ struct MinresDev {
     double delta, a1, a2, a3, c_new, eta_prev, gamma_cur;
     double bnorm, tol, est, true_rel;
     int it, maxit, check_true, status, lucky, use_true, replays;
+    int stall_check;  // 1: stop with ST_STALL when the estimate is far below tol but the true residual is not
 };
-enum { ST_RUN = 0, ST_CONV = 1, ST_BREAK = 2, ST_NAN = 3, ST_MAXIT = 4 };
+enum { ST_RUN = 0, ST_CONV = 1, ST_BREAK = 2, ST_NAN = 3, ST_MAXIT = 4, ST_STALL = 5 };
 
 template <typename T>
 struct SolveOps;
@@ -103,6 +104,141 @@ __global__ void __launch_bounds__(RED_THREADS) k_jz(int64_t n, SellView<C> K, co
         a += (double)vol[p] * redot(jz, zz);
     }
     double t = block_sum(a, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// ------------------------------------------------------------------ double-float Jacobian apply
+// In the mixed-precision solve (FP64 MINRES, FP32 V-cycle) every z that meets
+// the Jacobian is the FP64 image of the V-cycle's FP32 output, so its FP32 copy
+// is exact.  On even-N lattices J z is then formed with FP32 arithmetic only
+// (far faster than FP64 on this GPU) from double-float data (hi + lo):
+//   (J z)_i = 2^b_i sum_k a_ik (z_i - u_ik z_k) + (r_i - 1 + 2|psi_i|^2) z_i + psi_i^2 conj(z_i)
+// with a = |K-hat| / h^d and the unit phase u = exp(-i theta) tabulated per axis
+// (gl_lattice.cu), K_ik = -2^b_i a_ik u_ik (|V_i| = h^d 2^-b_i, b_i boundary
+// coordinates: an exact power-of-2 factor) and r_i = K_ii - sum_k |K_ik|.  The
+// differences z_i - u z_k are formed with Knuth's error-free TwoSum after an
+// FMA-based TwoProd, so a smooth z cancels without error, and products and sums
+// accumulate in the compensated form of Ogita, Rump and Oishi's Dot2 (an FP32
+// running sum and an FP32 compensation collecting the exact rounding errors):
+// about 48 significant bits, against 53 in FP64.  The solve watches for the
+// consequence (see k_scal_true) and finishes with the FP64 apply if it stalls.
+__device__ __forceinline__ float2 split_df(double x) {
+    float hi = __double2float_rn(x);
+    return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+// (s, c) += p exactly: s + p = t + e (TwoSum), the error e joins the compensation c
+__device__ __forceinline__ void dot2_add(float &s, float &c, float p) {
+    float t = __fadd_rn(s, p);
+    float bp = __fadd_rn(t, -s);
+    float e = __fadd_rn(__fadd_rn(s, -__fadd_rn(t, -bp)), __fadd_rn(p, -bp));
+    s = t;
+    c = __fadd_rn(c, e);
+}
+// (s, c) += a b, a = a.x + a.y: the exact product of the high part (TwoProd) and
+// the low part's product into the compensation
+__device__ __forceinline__ void dot2_df(float &s, float &c, float2 a, float b) {
+    float p = __fmul_rn(a.x, b);
+    float e = __fmaf_rn(a.x, b, -p);
+    dot2_add(s, c, p);
+    c = __fadd_rn(c, e);
+    c = __fmaf_rn(a.y, b, c);
+}
+
+// per-solve coefficients of the local part: d = r - 1 + 2|psi|^2 and psi^2
+__global__ void k_jz_coef(int64_t n, const double *__restrict__ rem, const double2 *__restrict__ psi,
+                          float2 *__restrict__ d, float4 *__restrict__ p2) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 ps = psi[i];
+    d[i] = split_df(rem[i] - 1.0 + 2.0 * (ps.x * ps.x + ps.y * ps.y));
+    float2 re = split_df(ps.x * ps.x - ps.y * ps.y), im = split_df(2.0 * ps.x * ps.y);
+    p2[i] = make_float4(re.x, re.y, im.x, im.y);
+}
+
+// q = J z from the exact FP32 copy z of the V-cycle output; partials of <J z, z>_R
+__global__ void __launch_bounds__(RED_THREADS) k_jz_latdf(int64_t n, LatticeDfView L, double hd,
+                                                          const float2 *__restrict__ d, const float4 *__restrict__ p2,
+                                                          const float2 *__restrict__ z, double2 *__restrict__ q,
+                                                          double *part, const int *stop) {
+    __shared__ double sh[32];
+    if (*stop) return;
+    float as = 0.f, ac = 0.f;
+    const uint32_t N = (uint32_t)L.N;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = p >= L.nred ? 1u : 0u;
+        uint32_t v = 2u * (uint32_t)(p - (c ? L.nred : 0));
+        uint32_t i = v % N;
+        const uint32_t r = v / N, j = r % N, k = r / N;
+        if (((i + j + k) & 1u) != c) {
+            ++v;
+            ++i;
+        }
+        const int64_t other = c ? 0 : L.nred;
+        const int b = (i == 0 || i == N - 1) + (j == 0 || j == N - 1) + (L.dim == 3 && (k == 0 || k == N - 1));
+        const float2 zp = z[p];
+        float rs = 0.f, rc = 0.f, is = 0.f, ic = 0.f;
+        // + a (z_p - u z_u) for the edge to node u; conj: the -e edge
+        auto edge = [&](int64_t idx, uint32_t u, bool conj) {
+            const float2 a = L.a[idx];
+            const float4 t = L.u[idx];
+            const float2 ur = make_float2(t.x, t.y);
+            const float2 ui = conj ? make_float2(-t.z, -t.w) : make_float2(t.z, t.w);
+            const float2 zu = z[(int64_t)(u >> 1) + other];
+            float ws = 0.f, wc = 0.f, vs = 0.f, vc = 0.f;
+            dot2_df(ws, wc, ur, zu.x);
+            dot2_df(ws, wc, ui, -zu.y);
+            dot2_df(vs, vc, ur, zu.y);
+            dot2_df(vs, vc, ui, zu.x);
+            float tr = zp.x, er = 0.f, ti = zp.y, ei = 0.f;
+            dot2_add(tr, er, -ws);
+            er = __fadd_rn(er, -wc);
+            dot2_add(ti, ei, -vs);
+            ei = __fadd_rn(ei, -vc);
+            dot2_df(rs, rc, a, tr);
+            rc = __fmaf_rn(a.x, er, rc);
+            dot2_df(is, ic, a, ti);
+            ic = __fmaf_rn(a.x, ei, ic);
+        };
+        {
+            const int64_t idx = j + (int64_t)N * k;
+            if (i + 1 < N) edge(idx, v + 1, false);
+            if (i > 0) edge(idx, v - 1, true);
+        }
+        {
+            const int64_t idx = L.per_axis + i + (int64_t)N * k;
+            if (j + 1 < N) edge(idx, v + N, false);
+            if (j > 0) edge(idx, v - N, true);
+        }
+        if (L.dim == 3) {
+            const int64_t idx = 2 * L.per_axis + i + (int64_t)N * j;
+            if (k + 1 < N) edge(idx, v + N * N, false);
+            if (k > 0) edge(idx, v - N * N, true);
+        }
+        // row scale 2^b (exact), then + d z + psi^2 conj(z)
+        const float sb = (float)(1 << b);
+        rs *= sb;
+        rc *= sb;
+        is *= sb;
+        ic *= sb;
+        const float2 dd = d[p];
+        const float4 pp = p2[p];
+        const float2 pr = make_float2(pp.x, pp.y), pi = make_float2(pp.z, pp.w);
+        dot2_df(rs, rc, dd, zp.x);
+        dot2_df(rs, rc, pr, zp.x);
+        dot2_df(rs, rc, pi, zp.y);
+        dot2_df(is, ic, dd, zp.y);
+        dot2_df(is, ic, pi, zp.x);
+        dot2_df(is, ic, pr, -zp.y);
+        q[p] = make_double2((double)rs + (double)rc, (double)is + (double)ic);
+        // |V_p| Re(conj(q_p) z_p) / h^d = 2^-b Re(conj(q_p) z_p)
+        float ts = 0.f, tc = 0.f;
+        dot2_df(ts, tc, make_float2(rs, rc), zp.x);
+        dot2_df(ts, tc, make_float2(is, ic), zp.y);
+        const float isb = 1.f / sb;
+        dot2_add(as, ac, ts * isb);
+        ac = __fadd_rn(ac, tc * isb);
+    }
+    double t = block_sum(((double)as + (double)ac) * hd, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -185,10 +321,11 @@ __global__ void k_scal_init(MinresDev *S, const double *part) {
 }
 
 // solve parameters, written before the captured init phase reads them
-__global__ void k_set_params(MinresDev *S, double tol, int maxit, int use_true) {
+__global__ void k_set_params(MinresDev *S, double tol, int maxit, int use_true, int stall_check) {
     S->tol = tol;
     S->maxit = maxit;
     S->use_true = use_true;
+    S->stall_check = stall_check;
 }
 
 __global__ void k_scal_gamma0(MinresDev *S, const double *part) {
@@ -268,6 +405,8 @@ __global__ void k_scal_true(MinresDev *S, const double *part) {
                 S->status = ST_NAN;
             else if (S->true_rel <= S->tol)
                 S->status = ST_CONV;
+            else if (S->stall_check && S->est <= 1e-3 * S->tol)
+                S->status = ST_STALL;  // the recurrence has run far past what the true residual shows
         } else {
             S->status = ST_CONV;  // inner solves stop on the estimate alone
         }
@@ -306,10 +445,10 @@ struct Graph {
 struct GraphKey {
     const void *m = nullptr, *psi = nullptr, *b = nullptr, *x = nullptr;
     int64_t prec_uid = -1, generation = -1;
-    int vc32 = 0;
+    int vc32 = 0, df = 0;
     bool operator==(const GraphKey &o) const {
         return m == o.m && psi == o.psi && b == o.b && x == o.x && prec_uid == o.prec_uid &&
-               generation == o.generation && vc32 == o.vc32;
+               generation == o.generation && vc32 == o.vc32 && df == o.df;
     }
 };
 
@@ -317,6 +456,8 @@ template <typename T>
 struct MinresWork {
     using C = cplx_t<T>;
     DBuf<C> v[3], z[2], w[3], q;
+    DBuf<float2> jd;      // double-float Jacobian coefficients (mixed-precision solve)
+    DBuf<float4> jp2;
     DBuf<double> part;
     DBuf<MinresDev> S;
     int64_t n = 0;
@@ -335,7 +476,15 @@ struct MinresWork {
         q.alloc(nn);
         part.alloc(2 * RED_BLOCKS);
         S.alloc(1);
+        jd.release();
+        jp2.release();
         n = nn;
+    }
+    void ensure_df() {
+        if (jd.n != (size_t)n) {
+            jd.alloc(n);
+            jp2.alloc(n);
+        }
     }
 };
 
@@ -415,7 +564,7 @@ static void harvest(Graph &g) {
 // gamma_1) on `cs`; the parameters tol/maxit/use_true are read from S.
 template <typename T>
 static void enqueue_init(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const cplx_t<T> *b, cplx_t<T> *x,
-                         bool vc32, MinresWork<T> &W, cudaStream_t cs) {
+                         bool vc32, bool df, MinresWork<T> &W, cudaStream_t cs) {
     using O = SolveOps<T>;
     using C = cplx_t<T>;
     int64_t n = m->n;
@@ -428,6 +577,12 @@ static void enqueue_init(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const
     GL_CUDA(cudaMemsetAsync(v0, 0, n * sizeof(C), cs));
     GL_CUDA(cudaMemsetAsync(w0, 0, n * sizeof(C), cs));
     GL_CUDA(cudaMemsetAsync(w1, 0, n * sizeof(C), cs));
+    if constexpr (std::is_same<T, double>::value) {
+        if (df) {
+            note_launch();
+            k_jz_coef<<<G, 256, 0, cs>>>(n, m->lat_krem.get(), psi, W.jd.get(), W.jp2.get());
+        }
+    }
     note_launch(3);
     k_init_resid<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, O::K(m), O::kdiag(m), O::vol(m), psi, b, x, v1, part);
     k_scal_init<<<1, 1024, 0, cs>>>(S, part);
@@ -449,7 +604,7 @@ static void enqueue_init(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const
 // and return to the starting roles at the end).
 template <typename T>
 static void enqueue_body(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const cplx_t<T> *b, cplx_t<T> *x,
-                         bool vc32, MinresWork<T> &W, cudaStream_t cs) {
+                         bool vc32, bool df, MinresWork<T> &W, cudaStream_t cs) {
     using O = SolveOps<T>;
     using C = cplx_t<T>;
     int64_t n = m->n;
@@ -468,9 +623,20 @@ static void enqueue_body(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const
             // algorithmic bytes of the fused Jacobian + dot: off-diagonals, K_ii,
             // |V|, psi, z (own row; neighbours cached) and the written q
             int64_t nnz = (sizeof(T) == 8) ? m->K.nnz_real : m->K32.nnz_real;
-            double jb = (double)nnz * (sizeof(C) + 4) + (double)n * (2 * sizeof(T) + 3 * sizeof(C));
-            ProfScope ps("jz", jb, cs);
-            k_jz<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, K, kd, vol, psi, z, W.q.get(), part, stop);
+            bool use_df = false;
+            if constexpr (std::is_same<T, double>::value) use_df = df;
+            if (use_df) {
+                // z32 (8 B), d and psi^2 (24 B) and the written q (16 B) per row; the
+                // neighbours' z and the tables from cache
+                ProfScope ps("jz", (double)n * (8 + 24 + 16), cs);
+                k_jz_latdf<<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, lattice_df_view(m), m->lat_hd, W.jd.get(),
+                                                               W.jp2.get(), p->mp_out.get(), (double2 *)W.q.get(),
+                                                               part, stop);
+            } else {
+                double jb = (double)nnz * (sizeof(C) + 4) + (double)n * (2 * sizeof(T) + 3 * sizeof(C));
+                ProfScope ps("jz", jb, cs);
+                k_jz<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, K, kd, vol, psi, z, W.q.get(), part, stop);
+            }
         }
         note_launch(2);
         k_scal_delta<<<1, 1024, 0, cs>>>(S, part);
@@ -506,20 +672,22 @@ static void enqueue_body(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const
 // stop on the FP64 true residual (FP64 path) or on the estimate alone (inner).
 template <typename T>
 static MinresResult minres(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const cplx_t<T> *b, cplx_t<T> *x,
-                           double tol, int maxit, bool use_true, bool vc32, MinresWork<T> &W, cudaStream_t s) {
+                           double tol, int maxit, bool use_true, bool vc32, MinresWork<T> &W, cudaStream_t s,
+                           bool df = false) {
     using O = SolveOps<T>;
     using C = cplx_t<T>;
     int64_t n = m->n;
     W.ensure(n);
+    if (df) W.ensure_df();
     MinresDev *S = W.S.get();
     double *part = W.part.get();
-    GraphKey key{m, psi, b, x, p ? p->uid : -1, profiler().generation, vc32 ? 1 : 0};
+    GraphKey key{m, psi, b, x, p ? p->uid : -1, profiler().generation, vc32 ? 1 : 0, df ? 1 : 0};
     if (!(key == W.key) || !W.init.exec || !W.body.exec) {
         W.key = key;
-        capture(W.init, W.cap, [&](cudaStream_t cs) { enqueue_init<T>(m, p, psi, b, x, vc32, W, cs); });
-        capture(W.body, W.cap, [&](cudaStream_t cs) { enqueue_body<T>(m, p, psi, b, x, vc32, W, cs); });
+        capture(W.init, W.cap, [&](cudaStream_t cs) { enqueue_init<T>(m, p, psi, b, x, vc32, df, W, cs); });
+        capture(W.body, W.cap, [&](cudaStream_t cs) { enqueue_body<T>(m, p, psi, b, x, vc32, df, W, cs); });
     }
-    k_set_params<<<1, 1, 0, s>>>(S, tol, maxit, use_true ? 1 : 0);
+    k_set_params<<<1, 1, 0, s>>>(S, tol, maxit, use_true ? 1 : 0, df ? 1 : 0);
     GL_LAUNCH_CHECK();
     replay(W.init, s);
     MinresDev h;
@@ -713,8 +881,8 @@ static void batch_build(gl_batch_s *B, const double2 *const *b, double2 *const *
             GL_CUDA(cudaStreamWaitEvent(si, B->ev[0], 0));
             permute_in(n, I.m->perm.get(), b[i], I.b.get(), si);
             permute_in(n, I.m->perm.get(), x[i], I.x.get(), si);
-            k_set_params<<<1, 1, 0, si>>>(S, B->o.tol, B->o.maxit, 1);
-            enqueue_init<double>(I.m, I.p, I.p->psi_p.get(), I.b.get(), I.x.get(), B->vc32, I.W, si);
+            k_set_params<<<1, 1, 0, si>>>(S, B->o.tol, B->o.maxit, 1, 0);
+            enqueue_init<double>(I.m, I.p, I.p->psi_p.get(), I.b.get(), I.x.get(), B->vc32, false, I.W, si);
             // the WHILE node: its handle lives in the graph being captured
             cudaStreamCaptureStatus cst;
             cudaGraph_t cg = nullptr;
@@ -737,7 +905,7 @@ static void batch_build(gl_batch_s *B, const double2 *const *b, double2 *const *
             cudaGraph_t body = cp.conditional.phGraph_out[0];
             GL_CUDA(cudaStreamUpdateCaptureDependencies(si, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
             GL_CUDA(cudaStreamBeginCaptureToGraph(B->sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-            enqueue_body<double>(I.m, I.p, I.p->psi_p.get(), I.b.get(), I.x.get(), B->vc32, I.W, B->sb);
+            enqueue_body<double>(I.m, I.p, I.p->psi_p.get(), I.b.get(), I.x.get(), B->vc32, false, I.W, B->sb);
             k_set_cond<<<1, 1, 0, B->sb>>>(h, S, max_replays);
             GL_LAUNCH_CHECK();
             GL_CUDA(cudaStreamEndCapture(B->sb, &body));
@@ -809,7 +977,18 @@ gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, con
     if (!mixed) {
         bool vc32 = (o.precision == GL_MIXED_PRECOND) && p;
         if (vc32) precond_ensure_fp32(p, s);
-        MinresResult r = minres<double>(m, p, psi_p, b_p, x_p, o.tol, o.maxit, true, vc32, W.w64, s);
+        // the double-float Jacobian on lattices; if its ~48-bit arithmetic stalls
+        // the FP64 true residual above tol, MINRES restarts from the current x
+        // with the FP64 Jacobian
+        const bool df = vc32 && p->lattice && m->lat_ok;
+        MinresResult r = minres<double>(m, p, psi_p, b_p, x_p, o.tol, o.maxit, true, vc32, W.w64, s, df);
+        inf.df_jacobian = df ? 1 : 0;
+        if (df && r.status == ST_STALL) {
+            int used = r.iters;
+            r = minres<double>(m, p, psi_p, b_p, x_p, o.tol, std::max(o.maxit - used, 1), true, vc32, W.w64, s, false);
+            r.iters += used;
+            inf.stall_restarts = 1;
+        }
         inf.iters = r.iters;
         inf.outer_iters = 1;
         inf.true_relres = r.true_rel;

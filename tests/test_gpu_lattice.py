@@ -43,6 +43,7 @@ def test_lattice_stencil_matches_stored(oracle_mod, dim, N, mu, field, precision
                                                        autotune=0))
             assert st == 0 and info.converged
             assert info.lattice_stencil == (1 if (lat and N % 2 == 0) else 0)
+            assert info.df_jacobian == (1 if (lat and N % 2 == 0 and precision == gl.GL_MIXED_PRECOND) else 0)
             xh = x.cpu().numpy()
             r = b - om.jacobian(psi, xh)
             assert np.sqrt(np.sum(vol * np.abs(r) ** 2) / np.sum(vol * np.abs(b) ** 2)) <= 1.01e-10
@@ -83,5 +84,32 @@ def test_cluster_sweeps_match_cooperative(oracle_mod, dim, N, mu, field):
             res[cs] = (xh, info.iters)
         assert res[0][1] == res[1][1]
         np.testing.assert_array_equal(res[0][0], res[1][0])
+    finally:
+        gl.gl_mesh_destroy(m)
+
+
+@pytest.mark.parametrize("dim,N,mu", [(2, 64, 0.5), (2, 128, 1.0)])
+def test_double_float_jacobian_stall_restart(oracle_mod, dim, N, mu):
+    """The double-FP32 Jacobian carries about 48 bits, so at a tolerance near
+    what FP64 attains (1e-11 on these squares; no stall occurs at 1e-10) MINRES
+    stalls above it; the solve must detect that on the device, finish with the
+    FP64 Jacobian from the current iterate, and reach the FP64 true residual."""
+    om = oracle_mod.Mesh(dim, N, mu)
+    n = om.n
+    psi, b = gi.psi_noisy_one(n, 61), gi.complex_normal(n, 62)
+    vol = om.volumes()
+    m = gl.gl_mesh_create(dim, N, mu)
+    try:
+        x = torch.zeros(n, dtype=torch.complex128, device=DEV)
+        tol = 1e-11
+        st, info = gl.gl_jacobian_solve(m, dev(psi), None, dev(b), x,
+                                        gl.options(max_coarse=64, precision=gl.GL_MIXED_PRECOND, tol=tol,
+                                                   autotune=0))
+        print(f"{dim}D N={N} mu={mu}: iterations {info.iters}, restarts {info.stall_restarts}, "
+              f"true relres {info.true_relres:.2e}")
+        assert info.df_jacobian == 1 and info.stall_restarts == 1
+        assert st == 0 and info.converged
+        r = b - om.jacobian(psi, x.cpu().numpy())
+        assert np.sqrt(np.sum(vol * np.abs(r) ** 2) / np.sum(vol * np.abs(b) ** 2)) <= 1.01 * tol
     finally:
         gl.gl_mesh_destroy(m)
