@@ -40,8 +40,9 @@ struct gl_mesh_s {
 namespace gl {
 
 constexpr int MAX_LEVELS = 16;
-// grid-barrier state of a cooperative sweep: arrivals and completed rounds
-constexpr int GRID_BARRIER_WORDS = 2;
+// grid-barrier state of a level's cooperative sweeps: one 64-bit arrival
+// counter for the FP32 and one for the FP64 sweep
+constexpr int GRID_BARRIER_WORDS = 4;
 constexpr int MAX_COARSE_DENSE = 4096;
 
 struct Level {

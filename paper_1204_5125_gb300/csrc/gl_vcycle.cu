@@ -210,45 +210,46 @@ __global__ void __launch_bounds__(256) k_resid_g(CsrGView<C> A, const R *__restr
 // into arrive and wait so that independent work can run in between.  The wait
 // is bounded: after ~2^24 polls it records an error and lets the block go on,
 // so a broken launch ends instead of hanging.
-// Grid barrier of the cooperative sweeps.  bar[0] counts the CTAs that arrived
-// in the current round, bar[1] counts completed rounds.  The last CTA to arrive
-// resets bar[0] and releases bar[1]; the others acquire bar[1].  A CTA reads
-// bar[1] once at kernel start (no round can complete before every CTA has
-// started) and waits for round k to complete at its k-th barrier, so nothing
-// but the arrival atomic, the release and the acquiring load sits between the
-// last CTA's work and everybody's next phase.  The release/acquire pair, after
-// the CTA-wide __syncthreads on both sides, orders every thread's x writes
-// before the other CTAs' reads.  (A flag per CTA polled by one warp, which
-// avoids the atomic, measured slower on these grids.)
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+// Grid barrier of the cooperative sweeps: one 64-bit arrival counter per
+// (level, precision) that only grows.  Every launch on a counter uses the same
+// number of CTAs nb, so the counter is a multiple of nb between launches.  At
+// its first barrier a CTA takes a ticket with an atomic add (the round trip
+// tells it the launch's base: the ticket rounded down to a multiple of nb); at
+// every later barrier it only adds one with a release reduction that it does
+// not wait for.  Barrier k is passed when the counter reaches base + (k+1) nb,
+// which one thread per CTA observes with acquiring loads.  So the critical path
+// from the last CTA's work to everybody's next phase is one release reduction
+// and the loads that see it.  The release/acquire pair, after a CTA-wide
+// __syncthreads on both sides, orders every thread's x writes before the other
+// CTAs' reads.  (A flag per CTA polled by one warp, and a counter reset by the
+// last arriver, measured slower.)
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ unsigned grid_round0(unsigned *bar) {
-    __shared__ unsigned g0;
-    if (threadIdx.x == 0) g0 = ld_acquire_u32(bar + 1);
-    __syncthreads();
-    return g0;
-}
-__device__ __forceinline__ void grid_arrive(unsigned *bar) {
+// arrival at barrier k; thread 0's base is set at k = 0
+__device__ __forceinline__ void grid_arrive(unsigned long long *cnt, unsigned k, unsigned long long &base) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned old;
-        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
-        if (old == gridDim.x - 1) {
-            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
-            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
+        if (k == 0) {
+            unsigned long long t;
+            asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], 1;" : "=l"(t) : "l"(cnt) : "memory");
+            base = t - t % gridDim.x;
+        } else {
+            asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(cnt) : "memory");
         }
     }
 }
-// waits for round `k` (counted from g0) to complete; false if the wait ran out
-__device__ __forceinline__ bool grid_wait(unsigned *bar, unsigned g0, unsigned k, int *err) {
+// waits for barrier k; false if the wait ran out (thread 0 holds base)
+__device__ __forceinline__ bool grid_wait(const unsigned long long *cnt, unsigned k, unsigned long long base,
+                                          int *err) {
     __shared__ int ok;
     if (threadIdx.x == 0) {
+        const unsigned long long want = base + (unsigned long long)(k + 1) * gridDim.x;
         unsigned spins = 0;
         int good = 1;
-        while (ld_acquire_u32(bar + 1) - g0 <= k) {
+        while (ld_acquire_u64(cnt) < want) {
             if (++spins > (1u << 24)) {
                 atomicExch(err, 1);
                 good = 0;
@@ -283,7 +284,8 @@ __global__ void __launch_bounds__(coop_threads<R>()) k_sgs_coop(CsrGView<C> A, c
                                                                 unsigned *bar, int *err,
                                                                 const int *__restrict__ stop) {
     if (stop && *stop) return;
-    const unsigned g0 = grid_round0(bar);
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(bar) + (sizeof(R) == 4 ? 0 : 1);
+    unsigned long long base = 0;
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t grp = t / G, ngroups = (int64_t)gridDim.x * blockDim.x / G;
     int lane = (int)(t % G);
@@ -359,10 +361,10 @@ __global__ void __launch_bounds__(coop_threads<R>()) k_sgs_coop(CsrGView<C> A, c
         }
         if (ph + 1 < nphase) {
             // arrive, load the next colour's x-independent data, then wait
-            grid_arrive(bar);
+            grid_arrive(cnt, (unsigned)ph, base);
             int cn = colour_of(ph + 1);
             prefetch(cstart[cn] + grp, cstart[cn] + grp < cstart[cn + 1]);
-            if (!grid_wait(bar, g0, (unsigned)ph, err)) return;
+            if (!grid_wait(cnt, (unsigned)ph, base, err)) return;
         }
     }
 }
@@ -947,6 +949,8 @@ static void plan_sweeps_t(gl_prec_s *p, cudaStream_t s) {
         int bestG = A.G;
         bool best_cluster = false;
         for (int g : {2, 4, 8, 16}) {
+            // a new grid size on this level's barrier counter: start it from zero
+            GL_CUDA(cudaMemsetAsync(L.barrier.get(), 0, GRID_BARRIER_WORDS * sizeof(unsigned), s));
             float t = time_it([&] {
                 GL_DISPATCH_G(g, (launch_sgs_coop<GG, C, T>(A, O::diag(L), L.cstart_dev.get(), L.ncolors, b, x, 0,
                                                              L.barrier.get(), p->err.get(), nullptr, maxc, s)));
@@ -963,6 +967,9 @@ static void plan_sweeps_t(gl_prec_s *p, cudaStream_t s) {
             }
         }
         sG = bestG;
+        // the timing ran other grid sizes on this level's barrier counters
+        GL_CUDA(cudaMemsetAsync(L.barrier.get(), 0, GRID_BARRIER_WORDS * sizeof(unsigned), s));
+        GL_CUDA(cudaMemsetAsync(p->err.get(), 0, sizeof(int), s));
         if constexpr (sizeof(T) == 4) {
             if (best_cluster) {
                 L.cl_size = size;
