@@ -78,7 +78,16 @@ __device__ __forceinline__ C jacobian_epilogue(C acc, R kd, C ps, C ph) {
 // either colour at position v / 2 within its colour, neighbours of the other
 // colour; K-hat of a +e edge from the per-axis table at the perpendicular
 // position, its conjugate for the -e edge; the row scaled by 1 / |V_p|.
+template <typename F>
+__device__ __forceinline__ float2 lattice_row_f(const LatticeView &L, int64_t p, F xval);
+
 __device__ __forceinline__ float2 lattice_row(const LatticeView &L, int64_t p, const float2 *__restrict__ x) {
+    return lattice_row_f(L, p, [x](int64_t q) { return x[q]; });
+}
+
+// the same with the neighbour values supplied by xval(position)
+template <typename F>
+__device__ __forceinline__ float2 lattice_row_f(const LatticeView &L, int64_t p, F xval) {
     const uint32_t c = p >= L.nred ? 1u : 0u;
     const uint32_t N = (uint32_t)L.N;
     uint32_t v = 2u * (uint32_t)(p - (c ? L.nred : 0));
@@ -92,7 +101,7 @@ __device__ __forceinline__ float2 lattice_row(const LatticeView &L, int64_t p, c
     float2 acc = make_float2(0.f, 0.f);
     // acc += t x_u (plus) or conj(t) x_u (minus)
     auto edge = [&](float2 t, uint32_t u, bool plus) {
-        const float2 xv = x[(u >> 1) + other];
+        const float2 xv = xval((int64_t)(u >> 1) + other);
         const float ty = plus ? t.y : -t.y;
         acc.x += t.x * xv.x - ty * xv.y;
         acc.y += t.x * xv.y + ty * xv.x;

@@ -253,6 +253,35 @@ __global__ void k_vnew(int64_t n, const MinresDev *S, const C *q, const C *v, co
     }
 }
 
+// the mixed-precision form's two passes around the FP32 V-cycle, each fused
+// with its neighbour: v_new of k_vnew also written as the V-cycle's FP32 input,
+// and the V-cycle's FP32 output widened to z_new inside the <v_new, z_new>_R dot
+__global__ void k_vnew_mp(int64_t n, const MinresDev *S, const double2 *q, const double2 *v, const double2 *v_old,
+                          double2 *v_new, float2 *v32) {
+    if (S->status) return;
+    double ig = 1.0 / S->gamma, dg = S->delta / S->gamma, go = S->gamma / S->gamma_old;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        double2 a = q[p], b = v[p], c = v_old[p];
+        double2 r = make_double2(a.x * ig - dg * b.x - go * c.x, a.y * ig - dg * b.y - go * c.y);
+        v_new[p] = r;
+        v32[p] = to32(r);
+    }
+}
+__global__ void __launch_bounds__(RED_THREADS) k_widen_dot(int64_t n, const double *vol, const double2 *v,
+                                                           const float2 *z32, double2 *z, double *part,
+                                                           const int *stop) {
+    __shared__ double sh[32];
+    if (*stop) return;
+    double a = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        double2 zz = to64(z32[p]);
+        z[p] = zz;
+        a += vol[p] * redot(v[p], zz);
+    }
+    double t = block_sum(a, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
 // w_new = (z / gamma - a3 w_old - a2 w) / a1 ; x += c_new eta w_new
 template <typename C, typename R>
 __global__ void k_update(int64_t n, const MinresDev *S, const C *z, const C *w_old, const C *w, C *w_new, C *x) {
@@ -640,15 +669,28 @@ static void enqueue_body(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const
         }
         note_launch(2);
         k_scal_delta<<<1, 1024, 0, cs>>>(S, part);
-        k_vnew<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, S, W.q.get(), v, v_old, v_new);
-        if (p) {
-            precond_apply_any<T>(p, v_new, z_new, stop, vc32, cs);
+        bool fused = false;
+        if constexpr (std::is_same<T, double>::value) fused = vc32 && p;
+        if (fused) {
+            // FP32 V-cycle between the two fused passes
+            k_vnew_mp<<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, S, (const double2 *)W.q.get(), (const double2 *)v,
+                                                          (const double2 *)v_old, (double2 *)v_new,
+                                                          p->mp_in.get());
+            precond_apply_p32(p, p->mp_in.get(), p->mp_out.get(), stop, cs);
+            note_launch(5);
+            k_widen_dot<<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, m->volp.get(), (const double2 *)v_new,
+                                                            p->mp_out.get(), (double2 *)z_new, part, stop);
         } else {
-            note_launch();
-            k_copy_if<C><<<G, 256, 0, cs>>>(n, v_new, z_new, stop);
+            k_vnew<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, S, W.q.get(), v, v_old, v_new);
+            if (p) {
+                precond_apply_any<T>(p, v_new, z_new, stop, vc32, cs);
+            } else {
+                note_launch();
+                k_copy_if<C><<<G, 256, 0, cs>>>(n, v_new, z_new, stop);
+            }
+            note_launch(5);
+            k_dot<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, vol, v_new, z_new, part, stop);
         }
-        note_launch(5);
-        k_dot<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, vol, v_new, z_new, part, stop);
         k_scal_givens<<<1, 1024, 0, cs>>>(S, part);
         k_update<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, S, z, w_old, w, w_new, x);
         k_true_resid<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, K, kd, vol, psi, b, x, part, S, 0);

@@ -113,6 +113,27 @@ __global__ void __launch_bounds__(256) k_gs_lat(int64_t lo, int64_t hi, LatticeV
         }
     }
 }
+// the first two half-sweeps from x = 0 in one launch: red rows x = b / diag,
+// black rows relaxed against their red neighbours' b / diag (the values those
+// rows get in the same launch)
+__global__ void __launch_bounds__(256) k_gs_lat_first2(int64_t n, LatticeView L, const float *__restrict__ diag,
+                                                       const float2 *__restrict__ b, float2 *__restrict__ x,
+                                                       const int *__restrict__ stop) {
+    if (stop && *stop) return;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    float2 acc = make_float2(0.f, 0.f);
+    if (p >= L.nred)
+        acc = lattice_row_f(L, p, [&](int64_t q) {
+            const float2 bq = b[q];
+            const float dq = 1.f / diag[q];
+            return make_float2(bq.x * dq, bq.y * dq);
+        });
+    const float2 bb = b[p];
+    const float d = 1.f / diag[p];
+    x[p] = make_float2((bb.x - acc.x) * d, (bb.y - acc.y) * d);
+}
+
 __global__ void __launch_bounds__(256) k_resid_lat(int64_t n, LatticeView L, const float *__restrict__ diag,
                                                    const float2 *__restrict__ b, const float2 *__restrict__ x,
                                                    const float *__restrict__ scale, float2 *__restrict__ r,
@@ -639,34 +660,34 @@ void autotune_levels(gl_prec_s *p, bool fp32, cudaStream_t s) {
     GL_LAUNCH_CHECK();
 }
 
-// x = M b for the dense coarsest inverse (FP64), one block of 256 threads per row
-__global__ void __launch_bounds__(256) k_dense_mv(int64_t n, const double2 *__restrict__ M,
-                                                  const double2 *__restrict__ b, double2 *__restrict__ x,
-                                                  const int *__restrict__ stop) {
-    __shared__ double shx[8], shy[8];
+// x = M b for the dense coarsest inverse (FP64).  The product is bound by the
+// FP64 pipe (four FMAs per complex entry), so one warp takes one row and every
+// lane keeps four independent accumulators to keep FMAs in flight; b comes
+// through L1 (the same 16 n bytes for every row).
+constexpr int DMV_WARPS = 8;
+__global__ void __launch_bounds__(32 * DMV_WARPS) k_dense_mv(int64_t n, const double2 *__restrict__ M,
+                                                             const double2 *__restrict__ b, double2 *__restrict__ x,
+                                                             const int *__restrict__ stop) {
     if (stop && *stop) return;
-    int64_t row = blockIdx.x;
-    double2 acc = make_double2(0, 0);
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * DMV_WARPS + (threadIdx.x >> 5);
+    if (row >= n) return;
     const double2 *mr = M + row * n;
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) cfma(acc, mr[j], b[j]);
+    double2 a0 = make_double2(0, 0), a1 = a0, a2 = a0, a3 = a0;
+    int64_t j = lane;
+    for (; j + 96 < n; j += 128) {
+        cfma(a0, mr[j], __ldg(b + j));
+        cfma(a1, mr[j + 32], __ldg(b + j + 32));
+        cfma(a2, mr[j + 64], __ldg(b + j + 64));
+        cfma(a3, mr[j + 96], __ldg(b + j + 96));
+    }
+    for (; j < n; j += 32) cfma(a0, mr[j], __ldg(b + j));
+    double sx = (a0.x + a1.x) + (a2.x + a3.x), sy = (a0.y + a1.y) + (a2.y + a3.y);
     for (int o = 16; o > 0; o >>= 1) {
-        acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+        sx += __shfl_down_sync(0xffffffffu, sx, o);
+        sy += __shfl_down_sync(0xffffffffu, sy, o);
     }
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        shx[w] = acc.x;
-        shy[w] = acc.y;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double sx = 0, sy = 0;
-        for (int k = 0; k < 8; ++k) {
-            sx += shx[k];
-            sy += shy[k];
-        }
-        x[row] = make_double2(sx, sy);
-    }
+    if (lane == 0) x[row] = make_double2(sx, sy);
 }
 
 template <typename C>
@@ -692,15 +713,19 @@ static void coarse_solve(gl_prec_s *p, Level &L, const typename LevelOps<T>::C *
                          const int *stop, cudaStream_t s);
 template <>
 void coarse_solve<double>(gl_prec_s *, Level &L, const double2 *b, double2 *x, const int *stop, cudaStream_t s) {
-    note_launch();
-    k_dense_mv<<<(unsigned)L.n, 256, 0, s>>>(L.n, L.Ainv.get(), b, x, stop);
+    ProfScope ps("coarse", (double)L.n * L.n * sizeof(double2), s);
+    k_dense_mv<<<grid_for(L.n, DMV_WARPS), 32 * DMV_WARPS, 0, s>>>(L.n, L.Ainv.get(), b, x, stop);
 }
 template <>
 void coarse_solve<float>(gl_prec_s *p, Level &L, const float2 *b, float2 *x, const int *stop, cudaStream_t s) {
-    note_launch(3);
+    // the FP32 right-hand side widened once, the FP64 solve, the result narrowed
+    note_launch(2);
     k_f2d<<<grid_for(L.n, 256), 256, 0, s>>>(L.n, b, p->coarse_b64.get(), stop);
-    k_dense_mv<<<(unsigned)L.n, 256, 0, s>>>(L.n, L.Ainv.get(), p->coarse_b64.get(), p->coarse_x64.get(),
-                                                      stop);
+    {
+        ProfScope ps("coarse", (double)L.n * L.n * sizeof(double2), s);
+        k_dense_mv<<<grid_for(L.n, DMV_WARPS), 32 * DMV_WARPS, 0, s>>>(L.n, L.Ainv.get(), p->coarse_b64.get(),
+                                                                       p->coarse_x64.get(), stop);
+    }
     k_d2f2<<<grid_for(L.n, 256), 256, 0, s>>>(L.n, p->coarse_x64.get(), x, stop);
 }
 
@@ -742,6 +767,21 @@ template <typename T>
 static void sgs(Level &L, int level, const typename LevelOps<T>::C *b, typename LevelOps<T>::C *x, bool zero_start,
                 const int *stop, cudaStream_t s, const LatticeView *lat = nullptr) {
     int nc = L.ncolors;
+    if constexpr (sizeof(T) == 4) {
+        if (lat && zero_start && nc == 2) {
+            // both forward colours in one launch; per row b, diagonal and the written
+            // x, the red rows' b and diagonal once more for the black rows, the tables
+            double bytes = (double)L.n * (sizeof(T) + 2 * sizeof(typename LevelOps<T>::C)) +
+                           (double)L.cstart[1] * (sizeof(T) + sizeof(typename LevelOps<T>::C)) +
+                           (double)lat->N * lat->N * lat->dim * 8.0;
+            {
+                ProfScope ps("gs0", bytes, s);
+                k_gs_lat_first2<<<grid_for(L.n, 256), 256, 0, s>>>(L.n, *lat, LevelOps<T>::diag(L), b, x, stop);
+            }
+            gs_sweep<T>(L, level, b, x, 0, false, stop, s, lat);
+            return;
+        }
+    }
     for (int c = 0; c < nc; ++c) gs_sweep<T>(L, level, b, x, c, zero_start, stop, s, lat);
     for (int c = nc - 2; c >= 0; --c) gs_sweep<T>(L, level, b, x, c, false, stop, s, lat);
 }
