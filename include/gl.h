@@ -110,6 +110,8 @@ typedef struct {
     int df_jacobian;     /* 1 if MINRES applied the Jacobian in double-FP32 arithmetic (GL_MIXED_PRECOND on
                             an even-N lattice with options.lattice = 1) */
     int stall_restarts;  /* 1 if that run stalled above tol and MINRES finished with the FP64 Jacobian */
+    double matvec_equiv; /* cost in matrix-vector-product equivalents (Fig. 1): (iters + outer_iters) x
+                            (1 + cost of R_k from gl_precond_cost) */
 } gl_solve_info;
 
 /* Default options (values listed in gl_options).  Returns GL_ERR_ARG on NULL. */
@@ -173,6 +175,16 @@ GL_API gl_status gl_precond_setup(gl_mesh mesh, const void *psi_dev, const gl_op
  * x_dev, z_dev: n complex FP64, may not alias.  FP64 arithmetic. */
 GL_API gl_status gl_precond_apply(gl_prec prec, const void *x_dev, void *z_dev, void *stream);
 GL_API gl_status gl_precond_destroy(gl_prec prec);
+
+/* Cost of applying R_k (k = cycles >= 1) in matrix-vector-product equivalents,
+ * the measure of Fig. 1: matrix entries visited by k V-cycles and the k - 1
+ * finest-level residuals between them, divided by the entries of K-hat.  A
+ * V-cycle visits, per level, both symmetric Gauss-Seidel steps (a colour visit
+ * reads its rows' off-diagonals and diagonals; from the zero guess the first
+ * colour reads only diagonals; the backward pass skips the repeated last
+ * colour), the residual, the restriction and the prolongation (nnz(P) each), and
+ * n_c^2 entries of the dense coarsest inverse.  Host result; no GPU work. */
+GL_API gl_status gl_precond_cost(gl_prec prec, int cycles, double *matvecs);
 
 /* Hierarchy introspection (for parity checks).  Level 0 is the finest.
  * Node numbering is the canonical one: the mesh's node ids on level 0 and the

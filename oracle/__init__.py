@@ -307,6 +307,43 @@ class Precond:
         self._lib.glref_vcycle(self.ptr, l, _c128(b), x)
         return x
 
+    def vcycle_cost(self) -> tuple[float, float]:
+        """(entries visited by one V-cycle, entries of the finest operator K-hat).
+
+        Per level above the coarsest: the pre-smoothing symmetric Gauss-Seidel
+        step from x = 0 (the first colour reads only its diagonals), the
+        post-smoothing step (every colour), where a colour visit reads its rows'
+        off-diagonals and diagonals and the backward pass starts one colour before
+        the last; the residual (every entry); restriction and prolongation
+        (nnz(P) each).  The coarsest level: n_c^2 entries of the dense inverse.
+        This counts the GPU's sweep order (the backward pass skips the repeated
+        last colour); the oracle's own sweeps repeat it."""
+        E = 0.0
+        L = self.nlevels
+        for lvl in range(L - 1):
+            info = self.level_info(lvl)
+            rp, _, _ = self.level_matrix(lvl)
+            col = self.colors(lvl)
+            rowlen = np.diff(rp)  # off-diagonals + diagonal
+            nc = info["ncolors"]
+            visit = np.array([rowlen[col == c].sum() for c in range(nc)], dtype=float)
+            rows0 = float(np.sum(col == 0))
+            allv = visit.sum()
+            back = allv - visit[nc - 1]
+            E += (allv - visit[0] + rows0) + back
+            E += allv + back
+            E += allv
+            E += 2.0 * info["p_nnz"]
+        nc_rows = self.level_info(L - 1)["n"]
+        E += float(nc_rows) ** 2
+        return E, float(self.mesh.nnz)
+
+    def cost(self, k: int) -> float:
+        """R_k in matrix-vector-product equivalents (Fig. 1): k V-cycles and k - 1
+        finest residuals, over the entries of K-hat."""
+        E, fine = self.vcycle_cost()
+        return (k * E + (k - 1) * fine) / fine
+
     def minres(self, b, x0=None):
         x = np.zeros(self.mesh.n, np.complex128) if x0 is None else _c128(x0).copy()
         info = Info()

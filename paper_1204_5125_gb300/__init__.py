@@ -24,7 +24,7 @@ __all__ = [
     "gl_precond_destroy", "gl_precond_levels", "gl_precond_level_info", "gl_precond_level_aggregates",
     "gl_precond_level_colors", "gl_precond_level_matrix", "gl_precond_level_P", "gl_jacobian_solve",
     "gl_newton_step", "gl_batch_solve", "gl_batch_create", "gl_batch_run", "gl_batch_destroy",
-    "gl_profile_begin", "gl_profile_end", "gl_jacobian_apply_noalloc",
+    "gl_profile_begin", "gl_profile_end", "gl_jacobian_apply_noalloc", "gl_precond_cost",
     "gl_warmstart_create", "gl_warmstart_destroy", "gl_warmstart_get_params", "gl_warmstart_set_params",
     "gl_warmstart_predict", "gl_warmstart_grad", "gl_warmstart_train", "gl_warmstart_adam_step", "GL_WS_NPARAM",
     "gl_last_error", "EXPORTED",
@@ -41,7 +41,7 @@ EXPORTED = [
     "gl_precond_level_aggregates", "gl_precond_level_colors", "gl_precond_level_matrix", "gl_precond_level_P",
     "gl_mesh_nedges", "gl_mesh_edges", "gl_mesh_khat", "gl_jacobian_solve", "gl_newton_step", "gl_batch_solve",
     "gl_profile_begin", "gl_profile_end", "gl_jacobian_apply_noalloc", "gl_batch_create", "gl_batch_run",
-    "gl_batch_destroy", "gl_warmstart_create", "gl_warmstart_destroy", "gl_warmstart_get_params",
+    "gl_batch_destroy", "gl_precond_cost", "gl_warmstart_create", "gl_warmstart_destroy", "gl_warmstart_get_params",
     "gl_warmstart_set_params", "gl_warmstart_predict", "gl_warmstart_grad", "gl_warmstart_train",
     "gl_warmstart_adam_step", "gl_last_error",
 ]
@@ -70,7 +70,7 @@ class SolveInfo(C.Structure):
         ("iters", C.c_int), ("outer_iters", C.c_int), ("converged", C.c_int), ("true_relres", C.c_double),
         ("est_relres", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
         ("warmstart_used", C.c_int), ("lattice_stencil", C.c_int), ("df_jacobian", C.c_int),
-        ("stall_restarts", C.c_int),
+        ("stall_restarts", C.c_int), ("matvec_equiv", C.c_double),
     ]
 
     def as_dict(self):
@@ -122,6 +122,7 @@ def library(build_if_missing: bool = True):
             "gl_batch_run": [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveInfo), vp],
             "gl_batch_destroy": [vp],
             "gl_profile_end": [i64p, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+            "gl_precond_cost": [vp, C.c_int, C.POINTER(C.c_double)],
             "gl_warmstart_create": [vp, C.POINTER(vp)],
             "gl_warmstart_destroy": [vp],
             "gl_warmstart_get_params": [vp, vp],
@@ -413,3 +414,10 @@ def gl_warmstart_train(ws, meshes, psis, bs, steps: int, batch: int = 1, lr: flo
 def gl_warmstart_adam_step(ws, grad, lr: float):
     g = _f32(grad)
     _check(library().gl_warmstart_adam_step(ws, g.ctypes.data_as(vp), float(lr)))
+
+
+def gl_precond_cost(prec, cycles: int = 1) -> float:
+    """Cost of R_k in matrix-vector-product equivalents (Fig. 1)."""
+    c = C.c_double()
+    _check(library().gl_precond_cost(prec, int(cycles), C.byref(c)))
+    return c.value

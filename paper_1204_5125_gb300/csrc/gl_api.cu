@@ -209,6 +209,15 @@ gl_status gl_precond_apply(gl_prec p, const void *x, void *z, void *stream) {
     });
 }
 
+gl_status gl_precond_cost(gl_prec p, int cycles, double *matvecs) {
+    return guard([&] {
+        GL_REQUIRE(p && matvecs, GL_ERR_ARG, "NULL argument");
+        GL_REQUIRE(cycles >= 1 && cycles <= 64, GL_ERR_ARG, "cycles must be in [1, 64]");
+        *matvecs = precond_cost(p, cycles);
+        return GL_OK;
+    });
+}
+
 gl_status gl_precond_destroy(gl_prec p) {
     return guard([&] {
         if (p) {

@@ -99,6 +99,8 @@ struct gl_prec_s {
     gl::DBuf<float2> cyc_r32, cyc_e32;
     gl::DBuf<float2> mp_in, mp_out;   // FP32 V-cycle input/output inside FP64 MINRES
     gl::DBuf<double2> coarse_b64, coarse_x64;  // FP64 coarsest solve in mixed mode
+    // cost model (matrix entries visited): one V-cycle, and the finest operator K-hat
+    double cost_vcycle = 0, cost_fine = 0;
 };
 
 namespace gl {
@@ -136,6 +138,8 @@ LatticeDfView lattice_df_view(const gl_mesh_s *m);
 
 // gl_setup.cu
 void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_options &o, cudaStream_t s);
+// cost of R_k in matrix-vector-product equivalents (entries visited / entries of K-hat)
+double precond_cost(const gl_prec_s *p, int k);
 void precond_ensure_fp32(gl_prec_s *p, cudaStream_t s);
 
 // gl_ops.cu (solve ordering)

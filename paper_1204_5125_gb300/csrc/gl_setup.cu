@@ -974,6 +974,40 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
         L.cnnz.assign(L.ncolors, 0);
         for (int64_t i = 0; i < L.n; ++i) L.cnnz[hc[i]] += hrp[i + 1] - hrp[i] - 1;
     }
+    // cost of one V-cycle in matrix entries visited: per level the two symmetric
+    // Gauss-Seidel steps (a colour visit reads its rows' off-diagonals and
+    // diagonals; from the zero guess the first colour reads only diagonals; the
+    // backward pass skips the repeated last colour), the residual (all entries),
+    // restriction and prolongation (nnz(P) each); the dense coarsest product
+    // (n_c^2).  The finest operator K-hat has nnz_0 off-diagonals + n_0 diagonals.
+    {
+        double E = 0;
+        for (int k = 0; k < p->nlev - 1; ++k) {
+            const Level &L = p->L[k];
+            double all = 0;
+            std::vector<double> visit(L.ncolors);
+            for (int c = 0; c < L.ncolors; ++c) {
+                visit[c] = (double)L.cnnz[c] + (double)(L.cstart[c + 1] - L.cstart[c]);
+                all += visit[c];
+            }
+            const double rows0 = (double)(L.cstart[1] - L.cstart[0]);
+            const double back = all - visit[L.ncolors - 1];
+            E += (all - visit[0] + rows0) + back;  // pre-smoothing from zero
+            E += all + back;                       // post-smoothing
+            E += all;                              // residual
+            E += 2.0 * (double)L.P_can.nnz;        // restriction and prolongation
+        }
+        const Level &Lc = p->L[p->nlev - 1];
+        E += (double)Lc.n * (double)Lc.n;
+        p->cost_vcycle = E;
+        // (the per-colour counts exist on the smoothed levels only)
+        double fine = (double)m->khat.nnz;
+        if (p->nlev > 1) {
+            fine = (double)p->L[0].n;
+            for (int c = 0; c < p->L[0].ncolors; ++c) fine += (double)p->L[0].cnnz[c];
+        }
+        p->cost_fine = fine;
+    }
     if (p->cycles > 1) {
         p->cyc_r.alloc(n);
         p->cyc_e.alloc(n);
@@ -1029,6 +1063,12 @@ void precond_ensure_fp32(gl_prec_s *p, cudaStream_t s) {
     p->coarse_x64.alloc(Lb.n);
     GL_CUDA(cudaStreamSynchronize(s));
     p->has32 = true;
+}
+
+double precond_cost(const gl_prec_s *p, int k) {
+    if (k <= 0 || p->cost_fine <= 0) return 0.0;
+    // R_k: k V-cycles and, between them, k - 1 finest-level residuals
+    return ((double)k * p->cost_vcycle + (double)(k - 1) * p->cost_fine) / p->cost_fine;
 }
 
 }  // namespace gl

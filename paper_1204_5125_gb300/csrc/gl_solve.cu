@@ -1108,6 +1108,7 @@ gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, con
     inf.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     inf.warmstart_used = o.warmstart ? warmstart_used(o.warmstart, s) : 0;
     inf.lattice_stencil = (p && p->has32 && o.precision != GL_FP64 && p->lattice && m->lat_ok) ? 1 : 0;
+    inf.matvec_equiv = (double)(inf.iters + inf.outer_iters) * (1.0 + (p ? precond_cost(p, p->cycles) : 0.0));
     if (info) {
         double setup = info->setup_ms;
         *info = inf;

