@@ -16,6 +16,10 @@ from dataclasses import dataclass
 
 import numpy as np
 
+CYCLES_INF = -1        # options(cycles=CYCLES_INF): R_inf, the V-cycle repeated to high accuracy
+RINF_TOL = 1e-12       # ... until ||D^-1 (D v - P-hat z)||_D <= RINF_TOL ||v||_D
+RINF_MAXCYC = 200      # ... or this many cycles
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "glref.c")
 _BUILD = os.path.join(_HERE, "_build")
@@ -107,6 +111,8 @@ def lib():
             L.glref_prec_level_aggregates.argtypes = [vp, C.c_int, _i32p]
             L.glref_prec_level_colors.argtypes = [vp, C.c_int, _i32p]
             L.glref_precond_apply.argtypes = [vp, _c128p, _c128p]
+            L.glref_precond_apply_count.restype = C.c_int
+            L.glref_precond_apply_count.argtypes = [vp, _c128p, _c128p]
             L.glref_vcycle.argtypes = [vp, C.c_int, _c128p, _c128p]
             L.glref_minres.restype = C.c_int
             L.glref_minres.argtypes = [vp, _c128p, vp, _c128p, _c128p, C.POINTER(Options), C.POINTER(Info)]
@@ -302,6 +308,12 @@ class Precond:
         self._lib.glref_precond_apply(self.ptr, _c128(v), z)
         return z
 
+    def apply_count(self, v):
+        """(R v, number of V-cycles applied); with cycles=CYCLES_INF, R_inf."""
+        z = np.zeros(self.mesh.n, np.complex128)
+        k = self._lib.glref_precond_apply_count(self.ptr, _c128(v), z)
+        return z, k
+
     def vcycle(self, l: int, b):
         x = np.zeros(self.level_info(l)["n"], np.complex128)
         self._lib.glref_vcycle(self.ptr, l, _c128(b), x)
@@ -343,6 +355,12 @@ class Precond:
         finest residuals, over the entries of K-hat."""
         E, fine = self.vcycle_cost()
         return (k * E + (k - 1) * fine) / fine
+
+    def cost_inf(self, k: int) -> float:
+        """One R_inf apply that took k cycles, in matvec equivalents: k V-cycles
+        and the k residuals that decide whether to stop."""
+        E, fine = self.vcycle_cost()
+        return k * (E + fine) / fine
 
     def minres(self, b, x0=None):
         x = np.zeros(self.mesh.n, np.complex128) if x0 is None else _c128(x0).copy()

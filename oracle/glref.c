@@ -614,10 +614,15 @@ double glref_inner_r(const glref_mesh *m, const cplx *x, const cplx *y) {
 /* 5. smoothed-aggregation AMG for P-hat = K-hat + 2 D |psi|^2          */
 /* ------------------------------------------------------------------ */
 
+#define GLREF_CYCLES_INF (-1)
+#define GLREF_RINF_TOL 1e-12
+#define GLREF_RINF_MAXCYC 200
+
 typedef struct {
     double tol;        /* relative residual target */
     int maxit;         /* MINRES iteration cap */
-    int cycles;        /* k in R_k (Eq. prec2); 0 = no preconditioner */
+    int cycles;        /* k in R_k (Eq. prec2); 0 = no preconditioner;
+                          GLREF_CYCLES_INF = R_inf, cycled to high accuracy (Eq. prec1) */
     int max_coarse;    /* stop coarsening at or below this size */
     int max_levels;
     int power_its;     /* power iterations for the spectral radius of D^-1 A */
@@ -864,7 +869,7 @@ void glref_precond_destroy(glref_prec *p) {
 glref_prec *glref_precond_setup(const glref_mesh *m, const cplx *psi, const glref_options *o) {
     glref_prec *p = xcalloc(1, sizeof *p);
     p->mesh = m;
-    p->cycles = o->cycles > 0 ? o->cycles : 1;
+    p->cycles = o->cycles == GLREF_CYCLES_INF ? GLREF_CYCLES_INF : (o->cycles > 0 ? o->cycles : 1);
     int maxlev = o->max_levels > 0 ? o->max_levels : 10;
     if (maxlev > GLREF_MAXLEV) maxlev = GLREF_MAXLEV;
     int64_t max_coarse = o->max_coarse > 0 ? o->max_coarse : 512;
@@ -1061,26 +1066,46 @@ static void vcycle(const glref_prec *p, int l, const cplx *b, cplx *x) {
     sgs(L, b, x);
 }
 
-/* z = R_k v = AMG_k(P-hat, D v) (Eq. prec2): k V-cycles for P-hat z = D v from z = 0 */
-void glref_precond_apply(const glref_prec *p, const cplx *v, cplx *z) {
+/* z = R_k v = AMG_k(P-hat, D v) (Eq. prec2): k V-cycles for P-hat z = D v from
+ * z = 0.  R_inf (Eq. prec1, P^-1 D v) is the same iteration cycled until the
+ * scaled residual D^-1 (D v - P-hat z) is at most GLREF_RINF_TOL of v in the
+ * norm ||x||_D^2 = sum_i |V_i| |x_i|^2, checked after every cycle, with at most
+ * GLREF_RINF_MAXCYC cycles.  Returns the number of V-cycles applied. */
+int glref_precond_apply_count(const glref_prec *p, const cplx *v, cplx *z) {
     const glref_mesh *m = p->mesh;
     int64_t n = m->n;
     cplx *b = xcalloc((size_t)n, sizeof(cplx)), *e = xcalloc((size_t)n, sizeof(cplx));
     cplx *r = xcalloc((size_t)n, sizeof(cplx));
+    double v2 = 0;
     for (int64_t i = 0; i < n; ++i) {
         b[i] = m->vol[i] * v[i];
         z[i] = 0;
+        v2 += m->vol[i] * (creal(v[i]) * creal(v[i]) + cimag(v[i]) * cimag(v[i]));
     }
-    for (int k = 0; k < p->cycles; ++k) {
+    const int inf = p->cycles == GLREF_CYCLES_INF;
+    const int kmax = inf ? GLREF_RINF_MAXCYC : p->cycles;
+    int k = 0;
+    for (;;) {
         csr_matvec(&p->L[0].A, z, r);
         for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+        if (inf && k > 0) {
+            /* ||D^-1 r||_D^2 = sum |r_i|^2 / |V_i| */
+            double r2 = 0;
+            for (int64_t i = 0; i < n; ++i) r2 += (creal(r[i]) * creal(r[i]) + cimag(r[i]) * cimag(r[i])) / m->vol[i];
+            if (!(r2 > GLREF_RINF_TOL * GLREF_RINF_TOL * v2)) break;
+        }
+        if (k == kmax) break;
         vcycle(p, 0, r, e);
         for (int64_t i = 0; i < n; ++i) z[i] += e[i];
+        ++k;
     }
     free(b);
     free(e);
     free(r);
+    return k;
 }
+
+void glref_precond_apply(const glref_prec *p, const cplx *v, cplx *z) { (void)glref_precond_apply_count(p, v, z); }
 
 /* one V-cycle on level l for A_l x = b (exposed for the tests) */
 void glref_vcycle(const glref_prec *p, int l, const cplx *b, cplx *x) { vcycle(p, l, b, x); }
@@ -1218,7 +1243,7 @@ done:
 int glref_jacobian_solve(const glref_mesh *m, const cplx *psi, const cplx *b, cplx *x, const glref_options *o,
                          glref_info *info) {
     glref_prec *p = NULL;
-    if (o->cycles > 0) {
+    if (o->cycles != 0) {
         p = glref_precond_setup(m, psi, o);
         if (!p) return 3;
     }
