@@ -68,11 +68,18 @@ typedef enum {
     GL_MIXED_PRECOND = 2  /* FP64 MINRES and Jacobian applies; the V-cycle of R_k runs in FP32 */
 } gl_precision;
 
+/* options.cycles value selecting R_inf = P^-1 D (Eq. prec1), realised as the
+ * V-cycle repeated until ||D^-1 (D x - P-hat z)||_D <= 1e-12 ||x||_D (checked
+ * after every cycle on the device, at most 200 cycles).  FP64 only: a setup or
+ * solve with another precision returns GL_ERR_ARG, and so does gl_batch_create. */
+#define GL_CYCLES_INF (-1)
+
 /* Solver options.  Fill with gl_options_default() and override fields. */
 typedef struct {
     double tol;          /* target ||b - J x||_D / ||b||_D (default 1e-10) */
     int maxit;           /* MINRES iteration cap (inner cap in GL_MIXED) (default 500) */
-    int cycles;          /* k in R_k = AMG_k(...) (Eq. prec2); 0 = no preconditioner (default 1) */
+    int cycles;          /* k in R_k = AMG_k(...) (Eq. prec2); 0 = no preconditioner; GL_CYCLES_INF = R_inf
+                            (Eq. prec1), see gl_precond_apply (default 1) */
     int max_coarse;      /* stop coarsening at or below this many nodes (default 512, max 4096) */
     int max_levels;      /* hierarchy depth cap (default 10, max 16) */
     int power_its;       /* power iterations for rho(D^-1 A) in prolongator smoothing (default 20) */
@@ -111,7 +118,10 @@ typedef struct {
                             an even-N lattice with options.lattice = 1) */
     int stall_restarts;  /* 1 if that run stalled above tol and MINRES finished with the FP64 Jacobian */
     double matvec_equiv; /* cost in matrix-vector-product equivalents (Fig. 1): (iters + outer_iters) x
-                            (1 + cost of R_k from gl_precond_cost) */
+                            (1 + cost of R_k from gl_precond_cost); with R_inf, iters + outer_iters plus
+                            (cycles applied) x (one V-cycle + one finest residual) */
+    double cycles_per_apply; /* V-cycles per preconditioner application: k for R_k, the average for R_inf,
+                            0 without a preconditioner */
 } gl_solve_info;
 
 /* Default options (values listed in gl_options).  Returns GL_ERR_ARG on NULL. */
@@ -171,7 +181,9 @@ GL_API gl_status gl_jacobian_apply_noalloc(gl_mesh mesh, const void *psi_dev, co
 GL_API gl_status gl_precond_setup(gl_mesh mesh, const void *psi_dev, const gl_options *opt, void *stream,
                            gl_prec *out);
 
-/* z = R_k x: k V-cycles for (K-hat + 2 D|psi|^2) z = D x from z = 0 (Eq. prec2).
+/* z = R_k x: k V-cycles for (K-hat + 2 D|psi|^2) z = D x from z = 0 (Eq. prec2);
+ * with cycles = GL_CYCLES_INF, R_inf: cycles until the residual test of
+ * GL_CYCLES_INF holds (a device-side loop; no host round trip per cycle).
  * x_dev, z_dev: n complex FP64, may not alias.  FP64 arithmetic. */
 GL_API gl_status gl_precond_apply(gl_prec prec, const void *x_dev, void *z_dev, void *stream);
 GL_API gl_status gl_precond_destroy(gl_prec prec);

@@ -31,6 +31,7 @@ __all__ = [
 ]
 
 GL_FP64, GL_MIXED, GL_MIXED_PRECOND = 0, 1, 2
+GL_CYCLES_INF = -1  # options.cycles: R_inf, the V-cycle repeated until the 1e-12 residual test
 STATUS = {0: "GL_OK", 1: "GL_ERR_ARG", 2: "GL_ERR_CUDA", 3: "GL_ERR_OOM", 4: "GL_ERR_NOT_CONVERGED",
           5: "GL_ERR_BREAKDOWN", 6: "GL_ERR_NAN", 7: "GL_ERR_TIMEOUT", 8: "GL_ERR_CAPACITY"}
 
@@ -70,7 +71,7 @@ class SolveInfo(C.Structure):
         ("iters", C.c_int), ("outer_iters", C.c_int), ("converged", C.c_int), ("true_relres", C.c_double),
         ("est_relres", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
         ("warmstart_used", C.c_int), ("lattice_stencil", C.c_int), ("df_jacobian", C.c_int),
-        ("stall_restarts", C.c_int), ("matvec_equiv", C.c_double),
+        ("stall_restarts", C.c_int), ("matvec_equiv", C.c_double), ("cycles_per_apply", C.c_double),
     ]
 
     def as_dict(self):

@@ -33,7 +33,10 @@ void check_opts(const gl_options *o) {
     GL_REQUIRE(o, GL_ERR_ARG, "options must not be NULL");
     GL_REQUIRE(o->tol >= 0, GL_ERR_ARG, "tol must be >= 0");
     GL_REQUIRE(o->maxit >= 0, GL_ERR_ARG, "maxit must be >= 0");
-    GL_REQUIRE(o->cycles >= 0 && o->cycles <= 64, GL_ERR_ARG, "cycles must be in [0, 64]");
+    GL_REQUIRE((o->cycles >= 0 && o->cycles <= 64) || o->cycles == GL_CYCLES_INF, GL_ERR_ARG,
+               "cycles must be in [0, 64] or GL_CYCLES_INF");
+    GL_REQUIRE(o->cycles != GL_CYCLES_INF || o->precision == GL_FP64, GL_ERR_ARG,
+               "R_inf (cycles = GL_CYCLES_INF) needs precision GL_FP64");
     GL_REQUIRE(o->precision == GL_FP64 || o->precision == GL_MIXED || o->precision == GL_MIXED_PRECOND, GL_ERR_ARG,
                "unknown precision");
     GL_REQUIRE(o->max_coarse <= MAX_COARSE_DENSE, GL_ERR_ARG, "max_coarse must be <= 4096");
@@ -293,7 +296,7 @@ gl_status gl_jacobian_solve(gl_mesh m, const void *psi, gl_prec prec, const void
         gl_solve_info inf{};
         gl_prec_s *p = prec;
         gl_prec_s *own = nullptr;
-        if (!p && opt->cycles > 0) {
+        if (!p && opt->cycles != 0) {
             auto t0 = std::chrono::steady_clock::now();
             own = new gl_prec_s();
             try {

@@ -81,9 +81,22 @@ struct Level {
     int sgs_G32 = 1, sgs_G64 = 1;   // lanes per row of the coarse Gauss-Seidel sweeps
 };
 
+// R_inf (Eq. prec1): V-cycles until the scaled residual is RINF_TOL of the input
+constexpr int CYCLES_INF = -1;
+constexpr double RINF_TOL = 1e-12;
+constexpr int RINF_MAXCYC = 200;
+struct RinfDev {
+    double v2;                     // ||v||_D^2 of the current application
+    unsigned long long cycles;     // V-cycles applied since the last reset
+    unsigned long long applies;    // applications since the last reset
+    int k;                         // cycles of the current application
+    int hit_max;                   // an application stopped at RINF_MAXCYC above the tolerance
+};
+
 }  // namespace gl
 
 struct gl_prec_s {
+    ~gl_prec_s();
     int64_t uid = 0;                  // unique per handle (keys cached CUDA graphs)
     gl_mesh_s *mesh = nullptr;
     gl::DBuf<int> err;                // set by a device-side wait that ran out
@@ -101,6 +114,13 @@ struct gl_prec_s {
     gl::DBuf<double2> coarse_b64, coarse_x64;  // FP64 coarsest solve in mixed mode
     // cost model (matrix entries visited): one V-cycle, and the finest operator K-hat
     double cost_vcycle = 0, cost_fine = 0;
+    // R_inf: device loop state, the stream its loop body is captured on, and the
+    // stream and events of an application outside stream capture
+    bool rinf = false;
+    gl::DBuf<double> rinf_part;
+    gl::DBuf<gl::RinfDev> rinf_dev;
+    cudaStream_t rinf_body = nullptr, rinf_eager = nullptr;
+    cudaEvent_t rinf_ev[2] = {nullptr, nullptr};
 };
 
 namespace gl {
@@ -140,6 +160,9 @@ LatticeDfView lattice_df_view(const gl_mesh_s *m);
 void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_options &o, cudaStream_t s);
 // cost of R_k in matrix-vector-product equivalents (entries visited / entries of K-hat)
 double precond_cost(const gl_prec_s *p, int k);
+// R_inf counters: zeroed before a solve, read after it (synchronises s)
+void rinf_reset(gl_prec_s *p, cudaStream_t s);
+RinfDev rinf_read(gl_prec_s *p, cudaStream_t s);
 void precond_ensure_fp32(gl_prec_s *p, cudaStream_t s);
 
 // gl_ops.cu (solve ordering)

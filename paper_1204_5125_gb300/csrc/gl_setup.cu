@@ -811,6 +811,8 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
     static std::atomic<int64_t> next_uid{1};
     p->uid = next_uid.fetch_add(1);
     p->mesh = m;
+    p->rinf = (o.cycles == CYCLES_INF);
+    GL_REQUIRE(!p->rinf || o.precision == GL_FP64, GL_ERR_ARG, "R_inf (cycles = -1) needs precision GL_FP64");
     p->cycles = o.cycles > 0 ? o.cycles : 1;
     int maxlev = o.max_levels > 0 ? std::min(o.max_levels, MAX_LEVELS) : 10;
     int64_t max_coarse = o.max_coarse > 0 ? o.max_coarse : 512;
@@ -1008,7 +1010,15 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
         }
         p->cost_fine = fine;
     }
-    if (p->cycles > 1) {
+    if (p->rinf) {
+        p->rinf_part.alloc(RED_BLOCKS);
+        p->rinf_dev.alloc(1);
+        GL_CUDA(cudaMemsetAsync(p->rinf_dev.get(), 0, sizeof(RinfDev), s));
+        GL_CUDA(cudaStreamCreateWithFlags(&p->rinf_body, cudaStreamNonBlocking));
+        GL_CUDA(cudaStreamCreateWithFlags(&p->rinf_eager, cudaStreamNonBlocking));
+        for (auto &e : p->rinf_ev) GL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    if (p->cycles > 1 || p->rinf) {
         p->cyc_r.alloc(n);
         p->cyc_e.alloc(n);
     }
@@ -1065,6 +1075,19 @@ void precond_ensure_fp32(gl_prec_s *p, cudaStream_t s) {
     p->has32 = true;
 }
 
+void rinf_reset(gl_prec_s *p, cudaStream_t s) {
+    if (p && p->rinf) GL_CUDA(cudaMemsetAsync(p->rinf_dev.get(), 0, sizeof(RinfDev), s));
+}
+
+RinfDev rinf_read(gl_prec_s *p, cudaStream_t s) {
+    RinfDev r{};
+    if (p && p->rinf) {
+        GL_CUDA(cudaMemcpyAsync(&r, p->rinf_dev.get(), sizeof(RinfDev), cudaMemcpyDeviceToHost, s));
+        GL_CUDA(cudaStreamSynchronize(s));
+    }
+    return r;
+}
+
 double precond_cost(const gl_prec_s *p, int k) {
     if (k <= 0 || p->cost_fine <= 0) return 0.0;
     // R_k: k V-cycles and, between them, k - 1 finest-level residuals
@@ -1072,3 +1095,10 @@ double precond_cost(const gl_prec_s *p, int k) {
 }
 
 }  // namespace gl
+
+gl_prec_s::~gl_prec_s() {
+    if (rinf_body) cudaStreamDestroy(rinf_body);
+    if (rinf_eager) cudaStreamDestroy(rinf_eager);
+    for (auto e : rinf_ev)
+        if (e) cudaEventDestroy(e);
+}

@@ -1014,6 +1014,8 @@ gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, con
     auto t0 = std::chrono::steady_clock::now();
     gl_status st;
     gl_solve_info inf{};
+    GL_REQUIRE(!(p && p->rinf) || o.precision == GL_FP64, GL_ERR_ARG, "R_inf needs precision GL_FP64");
+    rinf_reset(p, s);
     if (o.warmstart) warmstart_apply_p(o.warmstart, m, psi_p, b_p, x_p, s);
     bool mixed = (o.precision == GL_MIXED) && p;
     if (!mixed) {
@@ -1108,7 +1110,16 @@ gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, con
     inf.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     inf.warmstart_used = o.warmstart ? warmstart_used(o.warmstart, s) : 0;
     inf.lattice_stencil = (p && p->has32 && o.precision != GL_FP64 && p->lattice && m->lat_ok) ? 1 : 0;
-    inf.matvec_equiv = (double)(inf.iters + inf.outer_iters) * (1.0 + (p ? precond_cost(p, p->cycles) : 0.0));
+    if (p && p->rinf) {
+        // measured: every application ran its own number of cycles, each followed by a residual
+        const RinfDev R = rinf_read(p, s);
+        const double per = p->cost_fine > 0 ? (p->cost_vcycle + p->cost_fine) / p->cost_fine : 0.0;
+        inf.matvec_equiv = (double)(inf.iters + inf.outer_iters) + (double)R.cycles * per;
+        inf.cycles_per_apply = R.applies ? (double)R.cycles / (double)R.applies : 0.0;
+    } else {
+        inf.matvec_equiv = (double)(inf.iters + inf.outer_iters) * (1.0 + (p ? precond_cost(p, p->cycles) : 0.0));
+        inf.cycles_per_apply = p ? (double)p->cycles : 0.0;
+    }
     if (info) {
         double setup = info->setup_ms;
         *info = inf;

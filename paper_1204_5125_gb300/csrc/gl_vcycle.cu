@@ -886,11 +886,188 @@ static void vcycle(gl_prec_s *p, int l, const typename LevelOps<T>::C *b, typena
     GL_LAUNCH_CHECK();
 }
 
+// ------------------------------------------------------------------ R_inf
+// partial sums of ||x||_D^2 = sum_i |V_i| |x_i|^2 (fixed grid RED_BLOCKS x RED_THREADS)
+__global__ void __launch_bounds__(RED_THREADS) k_dnorm2_part(int64_t n, const double2 *__restrict__ x,
+                                                             const double *__restrict__ vol,
+                                                             double *__restrict__ part, const int *stop) {
+    if (stop && *stop) return;
+    __shared__ double sh[RED_THREADS];
+    double acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 a = x[i];
+        acc += vol[i] * (a.x * a.x + a.y * a.y);
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// sum of the RED_BLOCKS partial sums by one block of RED_THREADS (every thread gets it)
+__device__ double sum_parts(const double *__restrict__ part) {
+    __shared__ double sh[RED_THREADS];
+    double acc = 0;
+    for (int i = threadIdx.x; i < RED_BLOCKS; i += RED_THREADS) acc += part[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    return sh[0];
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_rinf_begin(RinfDev *R, const double *__restrict__ part,
+                                                            const int *stop) {
+    if (stop && *stop) return;
+    double v2 = sum_parts(part);
+    if (threadIdx.x == 0) {
+        R->v2 = v2;
+        R->k = 0;
+    }
+}
+
+// after a cycle: continue while ||r||_D^2 > tol^2 ||v||_D^2 and fewer than kmax
+// cycles ran (a NaN stops the loop; MINRES reports it).  Always sets the
+// condition, so the loop ends whatever the state.
+__global__ void __launch_bounds__(RED_THREADS) k_rinf_decide(cudaGraphConditionalHandle h, RinfDev *R,
+                                                             const double *__restrict__ part, const int *stop,
+                                                             double tol2, int kmax) {
+    const bool halted = stop && *stop;
+    double r2 = 0;
+    if (!halted) r2 = sum_parts(part);
+    if (threadIdx.x == 0) {
+        unsigned go = 0;
+        if (!halted) {
+            int k = R->k + 1;
+            R->k = k;
+            bool above = r2 > tol2 * R->v2;
+            go = (above && k < kmax) ? 1u : 0u;
+            if (!go) {
+                R->cycles += (unsigned long long)k;
+                R->applies += 1ull;
+                if (above) R->hit_max = 1;
+            }
+        }
+        cudaGraphSetConditional(h, go);
+    }
+}
+
+// z = R_inf v on a capturing stream: the first cycle from z = 0, its residual
+// and the decision, then a WHILE node whose body runs one more cycle, the
+// correction, the residual and the decision.
+static void rinf_enqueue(gl_prec_s *p, const double2 *v, double2 *z, const int *stop, cudaStream_t s) {
+    using O = LevelOps<double>;
+    Level &L = p->L[0];
+    const int64_t n = L.n;
+    double2 *r = p->cyc_r.get(), *e = p->cyc_e.get();
+    RinfDev *R = p->rinf_dev.get();
+    double *part = p->rinf_part.get();
+    const double *vol = p->mesh->volp.get();
+    const double tol2 = RINF_TOL * RINF_TOL;
+    note_launch(5);
+    k_dnorm2_part<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, v, vol, part, stop);
+    k_rinf_begin<<<1, RED_THREADS, 0, s>>>(R, part, stop);
+    vcycle<double>(p, 0, v, z, stop, s);
+    k_resid<double2, double><<<grid_for(n, 256), 256, 0, s>>>(n, O::A(L).view(), O::diag(L), v, z, nullptr, r, stop);
+    k_dnorm2_part<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, r, vol, part, stop);
+    GL_LAUNCH_CHECK();
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    GL_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
+    cudaGraphConditionalHandle h;
+    GL_CUDA(cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault));
+    k_rinf_decide<<<1, RED_THREADS, 0, s>>>(h, R, part, stop, tol2, RINF_MAXCYC);
+    GL_LAUNCH_CHECK();
+    GL_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    GL_CUDA(cudaGraphAddNode(&wnode, cg, deps, nullptr, ndeps, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    GL_CUDA(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaStream_t sb = p->rinf_body;
+    GL_CUDA(cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+        vcycle<double>(p, 0, r, e, stop, sb);
+        note_launch(4);
+        k_axpy_t<double2><<<grid_for(n, 256), 256, 0, sb>>>(n, e, z, stop);
+        k_resid<double2, double><<<grid_for(n, 256), 256, 0, sb>>>(n, O::A(L).view(), O::diag(L), v, z, nullptr,
+                                                                    r, stop);
+        k_dnorm2_part<<<RED_BLOCKS, RED_THREADS, 0, sb>>>(n, r, vol, part, stop);
+        k_rinf_decide<<<1, RED_THREADS, 0, sb>>>(h, R, part, stop, tol2, RINF_MAXCYC);
+        GL_LAUNCH_CHECK();
+    } catch (...) {
+        cudaStreamEndCapture(sb, &body);
+        throw;
+    }
+    GL_CUDA(cudaStreamEndCapture(sb, &body));
+}
+
+// R_inf on any stream: inserted into the graph being captured, or (outside
+// capture) captured into a graph of its own and launched once.  No event nodes
+// of the profiler go into the loop body.
+static void rinf_apply(gl_prec_s *p, const double2 *v, double2 *z, const int *stop, cudaStream_t s) {
+    Profiler &pr = profiler();
+    const bool was_active = pr.active;
+    pr.active = false;
+    struct Restore {
+        Profiler &pr;
+        bool a;
+        ~Restore() { pr.active = a; }
+    } restore{pr, was_active};
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    GL_CUDA(cudaStreamIsCapturing(s, &st));
+    if (st == cudaStreamCaptureStatusActive) {
+        rinf_enqueue(p, v, z, stop, s);
+        return;
+    }
+    cudaStream_t se = p->rinf_eager;
+    GL_CUDA(cudaEventRecord(p->rinf_ev[0], s));
+    GL_CUDA(cudaStreamWaitEvent(se, p->rinf_ev[0], 0));
+    cudaGraph_t g = nullptr;
+    GL_CUDA(cudaStreamBeginCapture(se, cudaStreamCaptureModeThreadLocal));
+    try {
+        rinf_enqueue(p, v, z, stop, se);
+    } catch (...) {
+        cudaStreamEndCapture(se, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    GL_CUDA(cudaStreamEndCapture(se, &g));
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    GL_CUDA(ie);
+    cudaError_t le = cudaGraphLaunch(ex, se);
+    cudaGraphExecDestroy(ex);  // released when the launch completes
+    GL_CUDA(le);
+    GL_CUDA(cudaEventRecord(p->rinf_ev[1], se));
+    GL_CUDA(cudaStreamWaitEvent(s, p->rinf_ev[1], 0));
+}
+
 template <typename T>
 static void precond_apply_t(gl_prec_s *p, const typename LevelOps<T>::C *v, typename LevelOps<T>::C *z,
                             const int *stop, cudaStream_t s) {
     using O = LevelOps<T>;
     using C = typename O::C;
+    if (p->rinf) {
+        if constexpr (sizeof(T) == 8) {
+            rinf_apply(p, v, z, stop, s);
+            return;
+        } else {
+            GL_REQUIRE(false, GL_ERR_ARG, "R_inf runs in FP64 only");
+        }
+    }
     if (p->cycles <= 1) {
         vcycle<T>(p, 0, v, z, stop, s);
     } else {

@@ -117,3 +117,92 @@ def test_rk_residual_matches_oracle(oracle_mod):
         assert prev < 1e-3
     finally:
         gl.gl_mesh_destroy(m)
+
+
+@pytest.mark.parametrize("dim,N,mc", [(2, 65, 64), (3, 17, 64)])
+def test_rinf_apply(oracle_mod, dim, N, mc):
+    """R_inf = P^-1 D (Eq. prec1): the GPU's cycled V-cycle against a sparse
+    direct solve of K-hat + 2 D|psi|^2 and against the oracle's R_inf; the
+    device loop runs the same number of cycles as the oracle (within one, the
+    stopping test sits at 1e-12 where rounding may move it)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+
+    field = (0.0, 0.0, 1.0) if dim == 2 else gi.WORKLOADS["cube128"][3]
+    om = oracle_mod.Mesh(dim, N, 1.0, field)
+    n = om.n
+    psi = gi.psi_noisy_one(n, 5)
+    v = gi.complex_normal(n, 6)
+    vol = om.volumes()
+    rp, ci, kv = om.khat_csr()
+    Ph = sp.csr_matrix((kv, ci, rp), shape=(n, n)) + sp.diags(2.0 * vol * np.abs(psi) ** 2)
+    exact = spl.spsolve(sp.csc_matrix(Ph), vol * v)
+    zo, ko = oracle_mod.Precond(om, psi, cycles=oracle_mod.CYCLES_INF, max_coarse=mc).apply_count(v)
+    dn = lambda x: np.sqrt(np.sum(vol * np.abs(x) ** 2))  # noqa: E731
+    m = gl.gl_mesh_create(dim, N, 1.0, field)
+    G = gl.gl_precond_setup(m, dev(psi), gl.options(cycles=gl.GL_CYCLES_INF, max_coarse=mc))
+    try:
+        z = torch.zeros(n, dtype=torch.complex128, device=DEV)
+        gl.gl_precond_apply(G, dev(v), z)
+        zg = z.cpu().numpy()
+        print(f"R_inf: oracle {ko} cycles; error vs direct solve GPU {dn(zg - exact) / dn(exact):.2e}, "
+              f"oracle {dn(zo - exact) / dn(exact):.2e}")
+        assert dn(zg - exact) <= 1e-10 * dn(exact)
+        assert dn(zg - zo) <= 1e-10 * dn(zo)
+        # the same input gives the same output; a zero input gives zero
+        z2 = torch.zeros_like(z)
+        gl.gl_precond_apply(G, dev(v), z2)
+        assert torch.equal(z, z2)
+        gl.gl_precond_apply(G, torch.zeros_like(z), z2)
+        assert not bool(torch.any(z2 != 0))
+    finally:
+        gl.gl_precond_destroy(G)
+        gl.gl_mesh_destroy(m)
+
+
+def test_rinf_solve(oracle_mod):
+    """MINRES with R_inf on the Fig. 1 setting (psi = b = 1): iterations equal the
+    oracle's within one and are at most those of R_10; the cycles per
+    application and the matvec equivalents come from the device counters, and
+    R_1 stays the cheapest (Fig. 1's conclusion)."""
+    N, mu = 129, 1.0
+    om = oracle_mod.Mesh(2, N, mu)
+    n = om.n
+    psi = np.ones(n, np.complex128)
+    b = np.ones(n, np.complex128)
+    m = gl.gl_mesh_create(2, N, mu)
+    res = {}
+    try:
+        for k in (1, 10, gl.GL_CYCLES_INF):
+            opts = gl.options(cycles=k, max_coarse=512)
+            x = torch.zeros(n, dtype=torch.complex128, device=DEV)
+            st, info = gl.gl_jacobian_solve(m, dev(psi), None, dev(b), x, opts)
+            assert st == 0 and info.converged
+            res[k] = info
+        _, oinfo = om.solve(psi, b, cycles=oracle_mod.CYCLES_INF, max_coarse=512, tol=1e-10)
+        inf = res[gl.GL_CYCLES_INF]
+        print(f"R_inf: {inf.iters} iterations (oracle {oinfo.iters}), {inf.cycles_per_apply:.1f} cycles per "
+              f"application, {inf.matvec_equiv:.0f} matvec equivalents; R_10 {res[10].iters} iterations, "
+              f"{res[10].matvec_equiv:.0f}; R_1 {res[1].iters}, {res[1].matvec_equiv:.0f}")
+        assert abs(inf.iters - oinfo.iters) <= 1
+        assert inf.iters <= res[10].iters
+        assert 10 < inf.cycles_per_apply < 200
+        assert res[1].cycles_per_apply == 1 and res[10].cycles_per_apply == 10
+        # the counters: matvec_equiv = (iters + 1) + (cycles applied) x (V-cycle + residual),
+        # cycles applied = applications x cycles_per_apply, one application per
+        # iteration plus the initial one (a whole number within [iters, iters + 2])
+        G = gl.gl_precond_setup(m, dev(psi), gl.options(max_coarse=512))
+        try:
+            per = gl.gl_precond_cost(G, 1) + 1.0
+        finally:
+            gl.gl_precond_destroy(G)
+        applies = (inf.matvec_equiv - (inf.iters + 1)) / (inf.cycles_per_apply * per)
+        assert abs(applies - round(applies)) < 1e-6 and inf.iters <= round(applies) <= inf.iters + 2, applies
+        assert res[1].matvec_equiv < res[10].matvec_equiv < inf.matvec_equiv
+        # FP32 forms reject R_inf
+        with pytest.raises(gl.GLError):
+            x = torch.zeros(n, dtype=torch.complex128, device=DEV)
+            gl.gl_jacobian_solve(m, dev(psi), None, dev(b), x,
+                                 gl.options(cycles=gl.GL_CYCLES_INF, precision=gl.GL_MIXED_PRECOND))
+    finally:
+        gl.gl_mesh_destroy(m)
