@@ -140,7 +140,23 @@ GL_API gl_status gl_options_default(gl_options *opt);
  * synchronises it.  *out receives a new handle. */
 GL_API gl_status gl_mesh_create(int dim, int n_per_side, double mu, const double *bhat_host, void *stream,
                          gl_mesh *out);
+/* The same on the square / cube of side `edge` > 0 centred at the origin (nodes
+ * -edge/2 + i h, h = edge / (N - 1)); gl_mesh_create is edge = 1.  The paper's
+ * domains have edges of order 10 (Sec. 4; the continuation of Fig. 4 uses a
+ * square of edge 10). */
+GL_API gl_status gl_mesh_create_edge(int dim, int n_per_side, double edge, double mu, const double *bhat_host,
+                                     void *stream, gl_mesh *out);
 GL_API gl_status gl_mesh_destroy(gl_mesh mesh);
+
+/* Changes the field strength of A = (mu/2) bhat x x in place: only the link
+ * phases depend on mu (theta_jk = mu theta1_jk, Eq. link variable), so every
+ * stored K-hat entry becomes -alpha_jk exp(-i mu theta1_jk), and K, its FP32
+ * copy and the lattice tables are rewritten into the same buffers.  The sparsity,
+ * ordering, volumes and the diagonal stay.  A preconditioner set up before the
+ * call no longer matches the operator: using it afterwards returns GL_ERR_ARG.
+ * (Entries may differ from a mesh created at that mu in the last bit: the phase
+ * is formed as mu * theta1.)  Synchronises `stream`. */
+GL_API gl_status gl_mesh_set_mu(gl_mesh mesh, double mu, void *stream);
 
 /* n = number of nodes; nnz = stored entries of K-hat (diagonal included);
  * volumes_dev (nullable): receives |V_j| as n doubles.  Synchronises `stream`
@@ -150,6 +166,19 @@ GL_API gl_status gl_mesh_info(gl_mesh mesh, int64_t *n, int64_t *nnz, double *vo
 /* Discrete GL residual (Eq. discr ginla): r_i = (K psi)_i - psi_i (1 - |psi_i|^2),
  * K = D^-1 K-hat.  psi_dev, r_dev: n complex (FP64); may not alias. */
 GL_API gl_status gl_residual(gl_mesh mesh, const void *psi_dev, void *r_dev, void *stream);
+
+/* d GL / d mu at fixed psi (the parameter derivative that pseudo-arclength
+ * continuation in mu needs, Sec. 4): only K depends on mu, through the phases,
+ * so out = D^-1 (d K-hat / d mu) psi with (d K-hat / d mu)_jk =
+ * -i theta1_jk K-hat_jk off the diagonal and 0 on it.  psi_dev, out_dev: n
+ * complex FP64, may not alias. */
+GL_API gl_status gl_residual_dmu(gl_mesh mesh, const void *psi_dev, void *out_dev, void *stream);
+
+/* Discrete energy (Eq. discr energy): F = F_1 + F_2 with
+ * F_1 = sum_edges alpha_jk |psi_j - exp(-i theta_jk) psi_k|^2 = Re psi^H K-hat psi
+ * and F_2 = sum_i |V_i| (-|psi_i|^2 + |psi_i|^4 / 2) (Eq. mass lumping).
+ * *energy_host = F (FP64 sums).  Synchronises `stream`. */
+GL_API gl_status gl_energy(gl_mesh mesh, const void *psi_dev, double *energy_host, void *stream);
 
 /* Discrete Jacobian (Sec. 3):
  *   y_i = (K phi)_i + (-1 + 2|psi_i|^2) phi_i + psi_i^2 conj(phi_i).
@@ -315,6 +344,58 @@ GL_API gl_status gl_warmstart_train(gl_warmstart ws, int count, const gl_mesh *m
                                     void *stream);
 /* One Adam step with the given gradient (host, GL_WS_NPARAM floats). */
 GL_API gl_status gl_warmstart_adam_step(gl_warmstart ws, const float *grad_host, float lr);
+
+/* ---------------------------------------------------------------------------
+ * Pseudo-arclength parameter continuation in mu (Sec. 4, "Numerical parameter
+ * continuation"): a predictor-corrector in (psi, mu) whose corrector is the
+ * Newton-Krylov process of this library.
+ *   metric:     ||(phi, nu)||^2 = <phi, phi>_R / |Omega| + nu^2 (Eq. disc inner2);
+ *   start:      Newton at the mesh's mu; first tangent (c, 1) / norm with
+ *               J c = -dGL/dmu (increasing mu); later tangents are secants;
+ *   predictor:  (psi, mu) + ds t;
+ *   corrector:  Newton on GL(psi, mu) = 0 and <t_psi, psi - psi_s>_R / |Omega|
+ *               + t_mu (mu - mu_s) = ds, each step solving J a = -GL and
+ *               J c = -dGL/dmu with one R_k(psi) and eliminating the border:
+ *               dmu = (-n - <t_psi, a>) / (t_mu + <t_psi, c>), dpsi = a + dmu c;
+ *               converged when ||GL||_R / sqrt|Omega| <= newton_tol;
+ *   step size:  halved (same point) when Newton fails; after a step that took
+ *               <= 2 Newton steps ds grows 1.5x (<= ds_max), >= 5 shrinks 0.7x.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double ds, ds_min, ds_max; /* arclength step: start, bounds (defaults 0.05, 1e-4, 0.2) */
+    double mu_max;             /* stop once mu >= mu_max (default 1) */
+    int max_steps;             /* accepted steps at most (default 100) */
+    double newton_tol;         /* ||GL||_R / sqrt|Omega| target (default 1e-9) */
+    int newton_maxit;          /* Newton steps per point before ds is halved (default 8) */
+    gl_options solver;         /* the Jacobian solves (default: gl_options_default with tol 1e-8, the
+                                  paper's continuation tolerance); cycles >= 1 */
+} gl_cont_options;
+
+typedef struct {
+    double mu;           /* field strength of the point */
+    double energy;       /* F / |Omega| (Eq. discr energy per unit volume; -1/2 for psi = 1, mu = 0) */
+    double gl_norm;      /* ||GL(psi)||_R / sqrt|Omega| at acceptance */
+    double ds;           /* arclength step that produced the point (0 for the start) */
+    int newton_steps;    /* Newton steps of the point */
+    int iters_last;      /* MINRES iterations of the last Newton step's J a = -GL solve (Fig. 4, right) */
+    int iters_total;     /* all MINRES iterations of the point (both solves, retries included) */
+    int retries;         /* step halvings before the point was accepted */
+    double setup_ms;     /* preconditioner setups of the point */
+    double solve_ms;     /* Jacobian solves of the point */
+} gl_cont_point;
+
+GL_API gl_status gl_cont_options_default(gl_cont_options *opt);
+
+/* Runs the continuation from (psi_dev, the mesh's mu).  psi_dev: n complex FP64
+ * in node order, in: the start state, out: the last accepted state; the mesh is
+ * left at that state's mu (gl_mesh_set_mu).  points_host: room for max_points
+ * entries; *npoints_out = points written (the start is the first).
+ * states_dev (nullable): max_points device pointers, each n complex FP64,
+ * receiving psi of every point.  Stops at mu >= mu_max, max_steps, a full
+ * points array, or ds < ds_min (then GL_ERR_NOT_CONVERGED with the points so
+ * far).  Synchronises `stream`. */
+GL_API gl_status gl_continuation(gl_mesh mesh, void *psi_dev, const gl_cont_options *opt, gl_cont_point *points_host,
+                                 int max_points, int *npoints_out, void *const *states_dev, void *stream);
 
 /* Message describing the last failure on this host thread ("" if none). */
 GL_API const char *gl_last_error(void);

@@ -72,6 +72,9 @@ def lib():
             vp = C.c_void_p
             L.glref_mesh_create.restype = vp
             L.glref_mesh_create.argtypes = [C.c_int, C.c_int, C.c_double, _f64p, _f64p]
+            L.glref_mesh_create_edge.restype = vp
+            L.glref_mesh_create_edge.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _f64p, _f64p]
+            L.glref_residual_dmu.argtypes = [vp, _c128p, _c128p]
             L.glref_mesh_destroy.argtypes = [vp]
             for f in ("glref_mesh_n", "glref_mesh_nedges", "glref_mesh_nnz"):
                 getattr(L, f).restype = C.c_int64
@@ -149,16 +152,17 @@ class SolveInfo:
 
 class Mesh:
     """Structured square (dim=2) or cube (dim=3) mesh of N nodes per side on the
-    unit square/cube centred at the origin, with A(x) = (mu/2) bhat x x + a0."""
+    square/cube of side `edge` centred at the origin, with A(x) = (mu/2) bhat x x + a0."""
 
-    def __init__(self, dim: int, N: int, mu: float, bhat=(0.0, 0.0, 1.0), a0=(0.0, 0.0, 0.0)):
+    def __init__(self, dim: int, N: int, mu: float, bhat=(0.0, 0.0, 1.0), a0=(0.0, 0.0, 0.0), edge: float = 1.0):
         self._lib = lib()
         b = np.ascontiguousarray(bhat, dtype=np.float64)
         a = np.ascontiguousarray(a0, dtype=np.float64)
-        self.ptr = self._lib.glref_mesh_create(dim, N, float(mu), b, a)
+        self.ptr = self._lib.glref_mesh_create_edge(dim, N, float(edge), float(mu), b, a)
         if not self.ptr:
             raise ValueError("glref_mesh_create failed")
-        self.dim, self.N, self.mu = dim, N, float(mu)
+        self.dim, self.N, self.mu, self.edge = dim, N, float(mu), float(edge)
+        self.bhat, self.a0 = tuple(float(c) for c in bhat), tuple(float(c) for c in a0)
         self.n = self._lib.glref_mesh_n(self.ptr)
         self.nedges = self._lib.glref_mesh_nedges(self.ptr)
         self.nnz = self._lib.glref_mesh_nnz(self.ptr)
@@ -214,6 +218,12 @@ class Mesh:
         y = np.zeros(self.n, np.complex128)
         self._lib.glref_jacobian_apply(self.ptr, _c128(psi), _c128(phi), y)
         return y
+
+    def residual_dmu(self, psi):
+        """d GL / d mu at fixed psi."""
+        out = np.zeros(self.n, np.complex128)
+        self._lib.glref_residual_dmu(self.ptr, _c128(psi), out)
+        return out
 
     def energy(self, psi) -> float:
         return self._lib.glref_energy(self.ptr, _c128(psi))

@@ -274,7 +274,7 @@ int glref_simplex_alpha_cot(const double *p, double *alpha) {
 typedef struct glref_mesh {
     int dim, N;
     int64_t n;
-    double h, mu, bhat[3], a0[3];
+    double h, mu, bhat[3], a0[3], edge;
     double *x;     /* n x 3 node coordinates (z = 0 in 2D) */
     double *vol;   /* |V_j| */
     int64_t ne;    /* kept edges, (j < k) lexicographic */
@@ -364,13 +364,16 @@ static int cell_simplices(const glref_mesh *m, int i, int j, int k, int64_t vid[
     return 6;
 }
 
-glref_mesh *glref_mesh_create(int dim, int N, double mu, const double *bhat, const double *a0) {
-    if ((dim != 2 && dim != 3) || N < 2) return NULL;
+/* The square/cube of side `edge` centred at the origin (the paper's domains have
+ * edge lengths of order 10; the unit domain is glref_mesh_create). */
+glref_mesh *glref_mesh_create_edge(int dim, int N, double edge, double mu, const double *bhat, const double *a0) {
+    if ((dim != 2 && dim != 3) || N < 2 || !(edge > 0)) return NULL;
     glref_mesh *m = xcalloc(1, sizeof *m);
     m->dim = dim;
     m->N = N;
     m->n = (dim == 2) ? (int64_t)N * N : (int64_t)N * N * N;
-    m->h = 1.0 / (N - 1);
+    m->h = edge / (N - 1);
+    m->edge = edge;
     m->mu = mu;
     for (int c = 0; c < 3; ++c) {
         m->bhat[c] = bhat ? bhat[c] : (c == 2 ? 1.0 : 0.0);
@@ -379,15 +382,16 @@ glref_mesh *glref_mesh_create(int dim, int N, double mu, const double *bhat, con
     int64_t n = m->n;
     int nz = (dim == 2) ? 1 : N;
 
-    /* nodes of the unit square/cube centred at the origin */
+    /* nodes of the square/cube centred at the origin */
+    const double x0 = -0.5 * edge;
     m->x = xcalloc((size_t)n * 3, sizeof(double));
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < N; ++j)
             for (int i = 0; i < N; ++i) {
                 int64_t id = node_id(m, i, j, k);
-                m->x[3 * id + 0] = -0.5 + i * m->h;
-                m->x[3 * id + 1] = -0.5 + j * m->h;
-                m->x[3 * id + 2] = (dim == 3) ? -0.5 + k * m->h : 0.0;
+                m->x[3 * id + 0] = x0 + i * m->h;
+                m->x[3 * id + 1] = x0 + j * m->h;
+                m->x[3 * id + 2] = (dim == 3) ? x0 + k * m->h : 0.0;
             }
 
     /* control volumes: the Voronoi cell of a lattice node is the cube of side h
@@ -530,6 +534,10 @@ glref_mesh *glref_mesh_create(int dim, int N, double mu, const double *bhat, con
     return m;
 }
 
+glref_mesh *glref_mesh_create(int dim, int N, double mu, const double *bhat, const double *a0) {
+    return glref_mesh_create_edge(dim, N, 1.0, mu, bhat, a0);
+}
+
 void glref_mesh_destroy(glref_mesh *m) {
     if (!m) return;
     free(m->x);
@@ -601,6 +609,34 @@ double glref_energy(const glref_mesh *m, const cplx *psi) {
         f2 += m->vol[i] * (-a2 + 0.5 * a2 * a2);
     }
     return f1 + f2;
+}
+
+/* d GL / d mu at fixed psi for A = mu A_1 + a0 (A_1 = (1/2) bhat x x): only the
+ * link phases depend on mu, theta_jk = mu theta1_jk + (a0 part), so
+ * d K-hat_jk / d mu = i theta1_jk alpha_jk exp(-i theta_jk) on the stored edge
+ * j < k and its conjugate on (k, j); the diagonal sum of alpha does not move.
+ * out = D^-1 (d K-hat / d mu) psi.  (The tangent of the continuation curve in
+ * Sec. 4's parameter continuation needs this derivative.) */
+void glref_residual_dmu(const glref_mesh *m, const cplx *psi, cplx *out) {
+    for (int64_t i = 0; i < m->n; ++i) out[i] = 0;
+    for (int64_t e = 0; e < m->ne; ++e) {
+        const int64_t j = m->ej[e], k = m->ek[e];
+        const double *xa = m->x + 3 * j, *xb = m->x + 3 * k;
+        double mid[3], d[3], A1[3];
+        for (int c = 0; c < 3; ++c) {
+            mid[c] = 0.5 * (xa[c] + xb[c]);
+            d[c] = xb[c] - xa[c];
+        }
+        const double *b = m->bhat;
+        A1[0] = 0.5 * (b[1] * mid[2] - b[2] * mid[1]);
+        A1[1] = 0.5 * (b[2] * mid[0] - b[0] * mid[2]);
+        A1[2] = 0.5 * (b[0] * mid[1] - b[1] * mid[0]);
+        const double th1 = dot3(A1, d);
+        const cplx djk = I * th1 * m->alpha[e] * cexp(-I * m->theta[e]);
+        out[j] += djk * psi[k];
+        out[k] += conj(djk) * psi[j];
+    }
+    for (int64_t i = 0; i < m->n; ++i) out[i] /= m->vol[i];
 }
 
 /* Eq. disc inner2: <x, y>_R = Re sum_i |V_i| conj(x_i) y_i */

@@ -27,7 +27,8 @@ __all__ = [
     "gl_profile_begin", "gl_profile_end", "gl_jacobian_apply_noalloc", "gl_precond_cost",
     "gl_warmstart_create", "gl_warmstart_destroy", "gl_warmstart_get_params", "gl_warmstart_set_params",
     "gl_warmstart_predict", "gl_warmstart_grad", "gl_warmstart_train", "gl_warmstart_adam_step", "GL_WS_NPARAM",
-    "gl_last_error", "EXPORTED",
+    "gl_last_error", "EXPORTED", "GL_CYCLES_INF", "ContOptions", "ContPoint", "gl_mesh_create_edge",
+    "gl_mesh_set_mu", "gl_residual_dmu", "gl_energy", "cont_options", "gl_continuation",
 ]
 
 GL_FP64, GL_MIXED, GL_MIXED_PRECOND = 0, 1, 2
@@ -44,7 +45,8 @@ EXPORTED = [
     "gl_profile_begin", "gl_profile_end", "gl_jacobian_apply_noalloc", "gl_batch_create", "gl_batch_run",
     "gl_batch_destroy", "gl_precond_cost", "gl_warmstart_create", "gl_warmstart_destroy", "gl_warmstart_get_params",
     "gl_warmstart_set_params", "gl_warmstart_predict", "gl_warmstart_grad", "gl_warmstart_train",
-    "gl_warmstart_adam_step", "gl_last_error",
+    "gl_warmstart_adam_step", "gl_last_error", "gl_mesh_create_edge", "gl_mesh_set_mu", "gl_residual_dmu",
+    "gl_energy", "gl_cont_options_default", "gl_continuation",
 ]
 
 GL_WS_NPARAM = 4 * 64 * 128 + 2 * 64
@@ -72,6 +74,24 @@ class SolveInfo(C.Structure):
         ("est_relres", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
         ("warmstart_used", C.c_int), ("lattice_stencil", C.c_int), ("df_jacobian", C.c_int),
         ("stall_restarts", C.c_int), ("matvec_equiv", C.c_double), ("cycles_per_apply", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ContOptions(C.Structure):
+    _fields_ = [
+        ("ds", C.c_double), ("ds_min", C.c_double), ("ds_max", C.c_double), ("mu_max", C.c_double),
+        ("max_steps", C.c_int), ("newton_tol", C.c_double), ("newton_maxit", C.c_int), ("solver", Options),
+    ]
+
+
+class ContPoint(C.Structure):
+    _fields_ = [
+        ("mu", C.c_double), ("energy", C.c_double), ("gl_norm", C.c_double), ("ds", C.c_double),
+        ("newton_steps", C.c_int), ("iters_last", C.c_int), ("iters_total", C.c_int), ("retries", C.c_int),
+        ("setup_ms", C.c_double), ("solve_ms", C.c_double),
     ]
 
     def as_dict(self):
@@ -133,6 +153,14 @@ def library(build_if_missing: bool = True):
             "gl_warmstart_train": [vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.c_int, C.c_int,
                                    C.c_float, vp, vp],
             "gl_warmstart_adam_step": [vp, vp, C.c_float],
+            "gl_mesh_create_edge": [C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_double), vp,
+                                    C.POINTER(vp)],
+            "gl_mesh_set_mu": [vp, C.c_double, vp],
+            "gl_residual_dmu": [vp, vp, vp, vp],
+            "gl_energy": [vp, vp, C.POINTER(C.c_double), vp],
+            "gl_cont_options_default": [C.POINTER(ContOptions)],
+            "gl_continuation": [vp, vp, C.POINTER(ContOptions), C.POINTER(ContPoint), C.c_int, C.POINTER(C.c_int),
+                                C.POINTER(vp), vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -187,11 +215,66 @@ def options(**kw) -> Options:
     return o
 
 
-def gl_mesh_create(dim: int, n_per_side: int, mu: float, bhat=(0.0, 0.0, 1.0), stream=None):
+def gl_mesh_create(dim: int, n_per_side: int, mu: float, bhat=(0.0, 0.0, 1.0), stream=None, edge: float = 1.0):
     b = (C.c_double * 3)(*bhat)
     out = C.c_void_p()
-    _check(library().gl_mesh_create(dim, n_per_side, float(mu), b, _stream(stream), C.byref(out)))
+    if edge == 1.0:
+        _check(library().gl_mesh_create(dim, n_per_side, float(mu), b, _stream(stream), C.byref(out)))
+    else:
+        _check(library().gl_mesh_create_edge(dim, n_per_side, float(edge), float(mu), b, _stream(stream),
+                                             C.byref(out)))
     return out
+
+
+def gl_mesh_create_edge(dim: int, n_per_side: int, edge: float, mu: float, bhat=(0.0, 0.0, 1.0), stream=None):
+    b = (C.c_double * 3)(*bhat)
+    out = C.c_void_p()
+    _check(library().gl_mesh_create_edge(dim, n_per_side, float(edge), float(mu), b, _stream(stream), C.byref(out)))
+    return out
+
+
+def gl_mesh_set_mu(mesh, mu: float, stream=None):
+    _check(library().gl_mesh_set_mu(mesh, float(mu), _stream(stream)))
+
+
+def gl_residual_dmu(mesh, psi, out, stream=None):
+    _check(library().gl_residual_dmu(mesh, _ptr(psi), _ptr(out), _stream(stream)))
+
+
+def gl_energy(mesh, psi, stream=None) -> float:
+    F = C.c_double()
+    _check(library().gl_energy(mesh, _ptr(psi), C.byref(F), _stream(stream)))
+    return F.value
+
+
+def cont_options(**kw) -> ContOptions:
+    """gl_cont_options_default() with fields overridden; solver=dict(...) overrides solver fields."""
+    o = ContOptions()
+    _check(library().gl_cont_options_default(C.byref(o)))
+    for k, v in kw.items():
+        if k == "solver":
+            for sk, sv in v.items():
+                setattr(o.solver, sk, sv)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def gl_continuation(mesh, psi, opts: ContOptions | None = None, max_points: int = 256, states=None, stream=None,
+                    raise_on_fail: bool = True):
+    """Runs the pseudo-arclength continuation; returns (status, list of point dicts)."""
+    if opts is None:
+        opts = cont_options()
+    pts = (ContPoint * max_points)()
+    npts = C.c_int()
+    st_arr = None
+    if states is not None:
+        st_arr = (vp * max_points)(*[_ptr(t).value for t in states] + [None] * (max_points - len(states)))
+    st = library().gl_continuation(mesh, _ptr(psi), C.byref(opts), pts, int(max_points), C.byref(npts), st_arr,
+                                   _stream(stream))
+    if st != 0 and (raise_on_fail or st != 4):
+        _check(st)
+    return st, [pts[i].as_dict() for i in range(npts.value)]
 
 
 def gl_mesh_destroy(mesh):

@@ -83,12 +83,25 @@ gl_status gl_options_default(gl_options *o) {
 const char *gl_last_error(void) { return last_error(); }
 
 gl_status gl_mesh_create(int dim, int n_per_side, double mu, const double *bhat, void *stream, gl_mesh *out) {
+    return gl_mesh_create_edge(dim, n_per_side, 1.0, mu, bhat, stream, out);
+}
+
+gl_status gl_mesh_set_mu(gl_mesh m, double mu, void *stream) {
+    return guard([&] {
+        GL_REQUIRE(m, GL_ERR_ARG, "NULL mesh");
+        mesh_set_mu(m, mu, as_stream(stream));
+        return GL_OK;
+    });
+}
+
+gl_status gl_mesh_create_edge(int dim, int n_per_side, double edge, double mu, const double *bhat, void *stream,
+                              gl_mesh *out) {
     return guard([&] {
         GL_REQUIRE(out, GL_ERR_ARG, "out must not be NULL");
         *out = nullptr;
         auto *m = new gl_mesh_s();
         try {
-            mesh_create(m, dim, n_per_side, mu, bhat, as_stream(stream));
+            mesh_create(m, dim, n_per_side, edge, mu, bhat, as_stream(stream));
         } catch (...) {
             delete m;
             throw;
@@ -203,6 +216,7 @@ gl_status gl_precond_apply(gl_prec p, const void *x, void *z, void *stream) {
         GL_REQUIRE(p && x && z, GL_ERR_ARG, "NULL argument");
         GL_REQUIRE(x != z, GL_ERR_ARG, "x and z must not alias");
         gl_mesh_s *m = p->mesh;
+        GL_REQUIRE(p->mesh_version == m->version, GL_ERR_ARG, "preconditioner set up before the mesh's mu changed");
         cudaStream_t s = as_stream(stream);
         ensure_tmp(m);
         permute_in(m->n, m->perm.get(), (const double2 *)x, m->t0.get(), s);
@@ -292,6 +306,8 @@ gl_status gl_jacobian_solve(gl_mesh m, const void *psi, gl_prec prec, const void
         GL_REQUIRE(m && psi && b && x, GL_ERR_ARG, "NULL argument");
         check_opts(opt);
         GL_REQUIRE(!prec || prec->mesh == m, GL_ERR_ARG, "preconditioner belongs to another mesh");
+        GL_REQUIRE(!prec || prec->mesh_version == m->version, GL_ERR_ARG,
+                   "preconditioner set up before the mesh's mu changed");
         cudaStream_t s = as_stream(stream);
         gl_solve_info inf{};
         gl_prec_s *p = prec;

@@ -8,12 +8,15 @@ struct gl_mesh_s {
     int dim = 0, N = 0;
     int64_t n = 0;
     double h = 0, mu = 0, bhat[3] = {0, 0, 1};
+    double edge = 1;                      // side of the square / cube
+    int64_t version = 0;                  // bumped by every change of mu (gl_mesh_set_mu)
     // canonical (node-order) data
     gl::CsrDev khat;                      // K-hat, columns ascending
     gl::DBuf<double> vol;                 // |V_j|
     int64_t nedges = 0;
     gl::DBuf<int32_t> ej, ek;             // edges j < k, lexicographic
-    gl::DBuf<double> ealpha, etheta;
+    gl::DBuf<double> ealpha, etheta, etheta1;  // etheta1: phase per unit mu
+    gl::DBuf<double> kal, kth1;           // per stored K-hat entry: alpha and phase per unit mu (0 on the diagonal)
     gl::DBuf<int32_t> color0;             // red-black colour of each node
     // solve ordering: position p holds node perm[p]; red nodes occupy [0, nred)
     int64_t nred = 0;
@@ -99,6 +102,7 @@ struct gl_prec_s {
     ~gl_prec_s();
     int64_t uid = 0;                  // unique per handle (keys cached CUDA graphs)
     gl_mesh_s *mesh = nullptr;
+    int64_t mesh_version = 0;         // the mesh's version (mu) the operator was built for
     gl::DBuf<int> err;                // set by a device-side wait that ran out
     int nlev = 0;
     int cycles = 1;
@@ -126,7 +130,10 @@ struct gl_prec_s {
 namespace gl {
 
 // gl_mesh.cu
-void mesh_create(gl_mesh_s *m, int dim, int N, double mu, const double *bhat, cudaStream_t s);
+void mesh_create(gl_mesh_s *m, int dim, int N, double edge, double mu, const double *bhat, cudaStream_t s);
+// new field strength: rewrites every phase-dependent value in place (K-hat, K, the
+// FP32 copy and the lattice tables); bumps m->version
+void mesh_set_mu(gl_mesh_s *m, double mu, cudaStream_t s);
 void mesh_ensure_fp32(gl_mesh_s *m, cudaStream_t s);
 template <typename C>
 void build_sell(int64_t nrows, int64_t ncols, const int32_t *perm, const int32_t *icol, const CsrDev &A,
@@ -145,6 +152,9 @@ struct LatticeView {
     const float2 *tx, *ty, *tz;    // K-hat of the +x, +y, +z edges by perpendicular position
 };
 void mesh_ensure_lattice(gl_mesh_s *m, cudaStream_t s);
+// after a change of mu: the tables again, into the same buffers (checked again;
+// a failed check turns the stencil off)
+void mesh_refresh_lattice(gl_mesh_s *m, cudaStream_t s);
 LatticeView lattice_view(const gl_mesh_s *m);
 // double-float view of the same stencil (row scaled by 2^b / h^d, b = boundary coordinates)
 struct LatticeDfView {

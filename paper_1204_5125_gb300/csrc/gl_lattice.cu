@@ -164,11 +164,10 @@ __global__ void k_lat_krem(int64_t n, SellView<double2> K, const double *__restr
 
 }  // namespace
 
-void mesh_ensure_lattice(gl_mesh_s *m, cudaStream_t s) {
-    if (m->lat_checked) return;
-    m->lat_checked = true;
-    m->lat_ok = false;
-    if (m->N % 2 != 0 || m->N < 4 || m->nred * 2 != m->n) return;
+// fills the tables from the assembled K-hat and checks them against K; with
+// `reuse` the buffers of an earlier call are rewritten in place.  Returns
+// whether the check passed (the tables are left unused otherwise).
+static bool lattice_tables(gl_mesh_s *m, bool reuse, cudaStream_t s) {
     LatDev L{m->dim, m->N, m->n};
     const int64_t per_axis = m->dim == 3 ? (int64_t)m->N * m->N : m->N;
     DBuf<double2> tab64((size_t)per_axis * m->dim);
@@ -191,23 +190,38 @@ void mesh_ensure_lattice(gl_mesh_s *m, cudaStream_t s) {
     unsigned nb = 0;
     GL_CUDA(cudaMemcpyAsync(&nb, bad.get(), sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     GL_CUDA(cudaStreamSynchronize(s));
-    if (nb != 0) return;
-    m->lat_tab.alloc((size_t)per_axis * m->dim);
+    if (nb != 0) return false;
+    if (!reuse) {
+        m->lat_tab.alloc((size_t)per_axis * m->dim);
+        m->lat_a.alloc((size_t)per_axis * m->dim);
+        m->lat_u.alloc((size_t)per_axis * m->dim);
+        m->lat_krem.alloc(m->n);
+    }
     k_lat_round<<<grid_for(per_axis * m->dim, 256), 256, 0, s>>>(per_axis * m->dim, tab64.get(), m->lat_tab.get());
     GL_LAUNCH_CHECK();
     // double-float tables: the control volumes are h^d 2^-b exactly (b boundary
     // coordinates), so K_ik = 2^b (K-hat_ik / h^d) with an exact power-of-2 factor
     m->lat_hd = m->dim == 2 ? m->h * m->h : m->h * m->h * m->h;
-    m->lat_a.alloc((size_t)per_axis * m->dim);
-    m->lat_u.alloc((size_t)per_axis * m->dim);
-    m->lat_krem.alloc(m->n);
     k_lat_df<<<grid_for(per_axis * m->dim, 256), 256, 0, s>>>(per_axis * m->dim, tab64.get(), m->lat_hd,
                                                                m->lat_a.get(), m->lat_u.get());
     k_lat_krem<<<grid_for(m->n, 256), 256, 0, s>>>(m->n, m->K.view(), m->kdiag.get(), m->lat_krem.get());
     GL_LAUNCH_CHECK();
     GL_CUDA(cudaStreamSynchronize(s));
     m->lat_per_axis = per_axis;
-    m->lat_ok = true;
+    return true;
+}
+
+void mesh_ensure_lattice(gl_mesh_s *m, cudaStream_t s) {
+    if (m->lat_checked) return;
+    m->lat_checked = true;
+    m->lat_ok = false;
+    if (m->N % 2 != 0 || m->N < 4 || m->nred * 2 != m->n) return;
+    m->lat_ok = lattice_tables(m, false, s);
+}
+
+void mesh_refresh_lattice(gl_mesh_s *m, cudaStream_t s) {
+    if (!m->lat_checked || !m->lat_ok) return;
+    m->lat_ok = lattice_tables(m, true, s);
 }
 
 LatticeDfView lattice_df_view(const gl_mesh_s *m) {

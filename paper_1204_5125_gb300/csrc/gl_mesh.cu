@@ -17,6 +17,7 @@ namespace gl {
 struct Lattice {
     int dim, N;
     double h, mu, b[3];
+    double x0;  // coordinate of the first node on every axis (-edge / 2)
     __device__ __host__ int64_t id(int i, int j, int k) const { return (int64_t)i + (int64_t)N * ((int64_t)j + (int64_t)N * k); }
     __device__ __host__ void coords(int64_t v, int &i, int &j, int &k) const {
         i = (int)(v % N);
@@ -25,9 +26,9 @@ struct Lattice {
         k = (int)(r / N);
     }
     __device__ void pos(int i, int j, int k, double *x) const {
-        x[0] = -0.5 + i * h;
-        x[1] = -0.5 + j * h;
-        x[2] = (dim == 3) ? -0.5 + k * h : 0.0;
+        x[0] = x0 + i * h;
+        x[1] = x0 + j * h;
+        x[2] = (dim == 3) ? x0 + k * h : 0.0;
     }
 };
 
@@ -264,10 +265,25 @@ __device__ double edge_phase(const Lattice &L, const double *xa, const double *x
     return A0 * d[0] + A1 * d[1] + A2 * d[2];
 }
 
-// CSR row of K-hat: K-hat_vv = sum alpha, K-hat_vk = -alpha exp(-i theta_vk)
+// the same integral per unit mu (A_1 = (1/2) bhat x x): theta = mu theta1
+__device__ double edge_phase1(const Lattice &L, const double *xa, const double *xb) {
+    double m[3], d[3];
+    for (int c = 0; c < 3; ++c) {
+        m[c] = 0.5 * (xa[c] + xb[c]);
+        d[c] = xb[c] - xa[c];
+    }
+    double A0 = 0.5 * (L.b[1] * m[2] - L.b[2] * m[1]);
+    double A1 = 0.5 * (L.b[2] * m[0] - L.b[0] * m[2]);
+    double A2 = 0.5 * (L.b[0] * m[1] - L.b[1] * m[0]);
+    return A0 * d[0] + A1 * d[1] + A2 * d[2];
+}
+
+// CSR row of K-hat: K-hat_vv = sum alpha, K-hat_vk = -alpha exp(-i theta_vk); per
+// stored entry also alpha and the phase per unit mu (0 on the diagonal), per edge
+// the phase per unit mu
 __global__ void k_fill_khat(Lattice L, int64_t n, int ndir, const double *ealpha, double cut, const int64_t *rp,
                             int32_t *ci, double2 *val, const int64_t *erp, int32_t *ej, int32_t *ek, double *eal,
-                            double *eth) {
+                            double *eth, double *kal, double *kth1, double *eth1) {
     int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (v >= n) return;
     Nbr nb[16];
@@ -283,6 +299,8 @@ __global__ void k_fill_khat(Lattice L, int64_t n, int ndir, const double *ealpha
     for (int s = 0; s < c; ++s) {
         if (!diag_done && nb[s].col > v) {
             ci[q] = (int32_t)v;
+            kal[q] = 0.0;
+            kth1[q] = 0.0;
             val[q++] = make_double2(diag, 0.0);
             diag_done = true;
         }
@@ -291,22 +309,46 @@ __global__ void k_fill_khat(Lattice L, int64_t n, int ndir, const double *ealpha
         double xk[3];
         L.pos(a, b, cc, xk);
         double th = edge_phase(L, xv, xk);
+        double th1 = edge_phase1(L, xv, xk);
         double sn, cs;
         sincos(th, &sn, &cs);
         ci[q] = (int32_t)nb[s].col;
+        kal[q] = nb[s].alpha;
+        kth1[q] = th1;
         val[q++] = make_double2(-nb[s].alpha * cs, nb[s].alpha * sn);
         if (nb[s].col > v) {
             ej[e] = (int32_t)v;
             ek[e] = (int32_t)nb[s].col;
             eal[e] = nb[s].alpha;
             eth[e] = th;
+            eth1[e] = th1;
             ++e;
         }
     }
     if (!diag_done) {
         ci[q] = (int32_t)v;
+        kal[q] = 0.0;
+        kth1[q] = 0.0;
         val[q] = make_double2(diag, 0.0);
     }
+}
+
+// the phase-dependent values at a new mu: K-hat_vk = -alpha exp(-i mu theta1)
+// (stored entries and edge list); the diagonal sums of alpha do not change
+__global__ void k_khat_set_mu(int64_t n, double mu, const int64_t *rp, const int32_t *ci, const double *kal,
+                              const double *kth1, double2 *val) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    for (int64_t q = rp[v]; q < rp[v + 1]; ++q) {
+        if (ci[q] == v) continue;
+        double sn, cs;
+        sincos(mu * kth1[q], &sn, &cs);
+        val[q] = make_double2(-kal[q] * cs, kal[q] * sn);
+    }
+}
+__global__ void k_edges_set_mu(int64_t ne, double mu, const double *eth1, double *eth) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < ne) eth[e] = mu * eth1[e];
 }
 
 __global__ void k_volumes(Lattice L, int64_t n, double *vol) {
@@ -519,15 +561,17 @@ void to_float(const double *in, float *out, int64_t n, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- mesh creation
-void mesh_create(gl_mesh_s *m, int dim, int N, double mu, const double *bhat, cudaStream_t s) {
+void mesh_create(gl_mesh_s *m, int dim, int N, double edge, double mu, const double *bhat, cudaStream_t s) {
     GL_REQUIRE(dim == 2 || dim == 3, GL_ERR_ARG, "dim must be 2 or 3");
     GL_REQUIRE(N >= 2, GL_ERR_ARG, "n_per_side must be >= 2");
+    GL_REQUIRE(edge > 0 && std::isfinite(edge), GL_ERR_ARG, "edge length must be positive");
     double nd = (dim == 2) ? (double)N * N : (double)N * N * N;
     GL_REQUIRE(nd < 2147483647.0, GL_ERR_ARG, "too many nodes for int32 indices");
     Lattice L;
     L.dim = dim;
     L.N = N;
-    L.h = 1.0 / (N - 1);
+    L.h = edge / (N - 1);
+    L.x0 = -0.5 * edge;
     L.mu = mu;
     double b[3] = {0, 0, 1};
     if (bhat) {
@@ -539,6 +583,7 @@ void mesh_create(gl_mesh_s *m, int dim, int N, double mu, const double *bhat, cu
     m->dim = dim;
     m->N = N;
     m->h = L.h;
+    m->edge = edge;
     m->mu = mu;
     int64_t n = (int64_t)nd;
     m->n = n;
@@ -576,14 +621,17 @@ void mesh_create(gl_mesh_s *m, int dim, int N, double mu, const double *bhat, cu
     GL_CUDA(cudaStreamSynchronize(s));
     K.ci.alloc(K.nnz);
     K.v.alloc(K.nnz);
+    m->kal.alloc(K.nnz);
+    m->kth1.alloc(K.nnz);
     int64_t nem = m->nedges > 0 ? m->nedges : 1;
     m->ej.alloc(nem);
     m->ek.alloc(nem);
     m->ealpha.alloc(nem);
     m->etheta.alloc(nem);
+    m->etheta1.alloc(nem);
     k_fill_khat<<<grid_for(n, 128), 128, 0, s>>>(L, n, ndir, ealpha.get(), cut, K.rp.get(), K.ci.get(), K.v.get(),
                                                   erp.get(), m->ej.get(), m->ek.get(), m->ealpha.get(),
-                                                  m->etheta.get());
+                                                  m->etheta.get(), m->kal.get(), m->kth1.get(), m->etheta1.get());
     GL_LAUNCH_CHECK();
     m->vol.alloc(n);
     k_volumes<<<grid_for(n, 256), 256, 0, s>>>(L, n, m->vol.get());
@@ -610,6 +658,36 @@ void mesh_create(gl_mesh_s *m, int dim, int N, double mu, const double *bhat, cu
     k_permute_real<<<grid_for(n, 256), 256, 0, s>>>(n, m->perm.get(), m->vol.get(), m->volp.get());
     GL_LAUNCH_CHECK();
     GL_CUDA(cudaStreamSynchronize(s));
+}
+
+// rewrites the values of a sliced ELL built by build_sell from a CSR of the same
+// sparsity (same slices, widths and columns; buffers kept, so captured graphs
+// that read them stay valid)
+template <typename C>
+static void refill_sell(int64_t nrows, int64_t ncols, const int32_t *perm, const int32_t *icol, const CsrDev &A,
+                        const double *row_scale, bool drop_diag, Sell<C> &out, double *diag_out, cudaStream_t s) {
+    k_sell_fill<C><<<grid_for(nrows, 256), 256, 0, s>>>(nrows, ncols, perm, icol, A.rp.get(), A.ci.get(), A.v.get(),
+                                                        row_scale, drop_diag, out.sptr.get(), out.col.get(),
+                                                        out.val.get(), diag_out);
+    GL_LAUNCH_CHECK();
+}
+
+void mesh_set_mu(gl_mesh_s *m, double mu, cudaStream_t s) {
+    GL_REQUIRE(std::isfinite(mu), GL_ERR_ARG, "mu must be finite");
+    const int64_t n = m->n;
+    k_khat_set_mu<<<grid_for(n, 256), 256, 0, s>>>(n, mu, m->khat.rp.get(), m->khat.ci.get(), m->kal.get(),
+                                                   m->kth1.get(), m->khat.v.get());
+    if (m->nedges > 0)
+        k_edges_set_mu<<<grid_for(m->nedges, 256), 256, 0, s>>>(m->nedges, mu, m->etheta1.get(), m->etheta.get());
+    GL_LAUNCH_CHECK();
+    refill_sell<double2>(n, n, m->perm.get(), m->iperm.get(), m->khat, m->vol.get(), true, m->K, m->kdiag.get(), s);
+    if (m->has32) {
+        refill_sell<float2>(n, n, m->perm.get(), m->iperm.get(), m->khat, m->vol.get(), true, m->K32, nullptr, s);
+        mesh_refresh_lattice(m, s);
+    }
+    GL_CUDA(cudaStreamSynchronize(s));
+    m->mu = mu;
+    m->version += 1;
 }
 
 // FP32 copies of the fine operator for the mixed-precision path (built on demand)

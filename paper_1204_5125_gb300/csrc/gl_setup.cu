@@ -811,6 +811,7 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
     static std::atomic<int64_t> next_uid{1};
     p->uid = next_uid.fetch_add(1);
     p->mesh = m;
+    p->mesh_version = m->version;
     p->rinf = (o.cycles == CYCLES_INF);
     GL_REQUIRE(!p->rinf || o.precision == GL_FP64, GL_ERR_ARG, "R_inf (cycles = -1) needs precision GL_FP64");
     p->cycles = o.cycles > 0 ? o.cycles : 1;

@@ -473,11 +473,11 @@ struct Graph {
 
 struct GraphKey {
     const void *m = nullptr, *psi = nullptr, *b = nullptr, *x = nullptr;
-    int64_t prec_uid = -1, generation = -1;
+    int64_t prec_uid = -1, generation = -1, mesh_version = -1;
     int vc32 = 0, df = 0;
     bool operator==(const GraphKey &o) const {
         return m == o.m && psi == o.psi && b == o.b && x == o.x && prec_uid == o.prec_uid &&
-               generation == o.generation && vc32 == o.vc32 && df == o.df;
+               generation == o.generation && mesh_version == o.mesh_version && vc32 == o.vc32 && df == o.df;
     }
 };
 
@@ -723,7 +723,7 @@ static MinresResult minres(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, con
     if (df) W.ensure_df();
     MinresDev *S = W.S.get();
     double *part = W.part.get();
-    GraphKey key{m, psi, b, x, p ? p->uid : -1, profiler().generation, vc32 ? 1 : 0, df ? 1 : 0};
+    GraphKey key{m, psi, b, x, p ? p->uid : -1, profiler().generation, m->version, vc32 ? 1 : 0, df ? 1 : 0};
     if (!(key == W.key) || !W.init.exec || !W.body.exec) {
         W.key = key;
         capture(W.init, W.cap, [&](cudaStream_t cs) { enqueue_init<T>(m, p, psi, b, x, vc32, df, W, cs); });
@@ -979,6 +979,8 @@ static void batch_build(gl_batch_s *B, const double2 *const *b, double2 *const *
 
 gl_status batch_run(gl_batch_s *B, const double2 *const *b, double2 *const *x, gl_solve_info *infos, cudaStream_t s) {
     size_t k = B->inst.size();
+    for (auto &I : B->inst)
+        GL_REQUIRE(I->p->mesh_version == I->m->version, GL_ERR_ARG, "a batch mesh's mu changed after gl_batch_create");
     bool same = B->exec && B->b_ptr.size() == k;
     for (size_t i = 0; same && i < k; ++i) same = (B->b_ptr[i] == b[i] && B->x_ptr[i] == x[i]);
     if (!same) batch_build(B, b, x);

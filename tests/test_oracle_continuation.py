@@ -1,0 +1,71 @@
+"""Pins of the oracle pieces that the parameter continuation of Sec. 4 needs:
+domains of any edge length, d GL / d mu, and the energy (Eq. discr energy)."""
+import numpy as np
+import pytest
+
+import gl_inputs as gi
+
+BH3 = gi.WORKLOADS["cube128"][3]
+
+
+@pytest.mark.parametrize("dim,N,field", [(2, 17, (0.0, 0.0, 1.0)), (3, 7, BH3)])
+def test_edge_length_scaling(oracle_mod, dim, N, field):
+    """Scaling the domain by L: the link phases of A = (mu/2) bhat x x grow by L^2
+    (theta_L(mu) = theta_1(mu L^2)), alpha by L^(d-2) (cotangents are scale-free,
+    Kuhn tetrahedra scale with length) and |V| by L^d, so K-hat_L(mu) =
+    L^(d-2) K-hat_1(mu L^2) and K_L(mu) = K_1(mu L^2) / L^2."""
+    L, mu = 10.0, 0.37
+    mL = oracle_mod.Mesh(dim, N, mu, field, edge=L)
+    m1 = oracle_mod.Mesh(dim, N, mu * L * L, field)
+    rpL, ciL, vL = mL.khat_csr()
+    rp1, ci1, v1 = m1.khat_csr()
+    np.testing.assert_array_equal(rpL, rp1)
+    np.testing.assert_array_equal(ciL, ci1)
+    np.testing.assert_allclose(vL, L ** (dim - 2) * v1, rtol=1e-12, atol=1e-12 * np.abs(vL).max())
+    np.testing.assert_allclose(mL.volumes(), L ** dim * m1.volumes(), rtol=1e-15)
+    assert mL.volumes().sum() == pytest.approx(L ** dim, rel=1e-13)
+    x = mL.nodes()
+    assert x.min() == pytest.approx(-L / 2) and x[:, :dim].max() == pytest.approx(L / 2)
+
+
+@pytest.mark.parametrize("dim,N,field,edge", [(2, 21, (0.0, 0.0, 1.0), 10.0), (3, 7, BH3, 3.0)])
+def test_dmu_central_difference(oracle_mod, dim, N, field, edge):
+    """d GL / d mu against the central difference (GL(mu + e) - GL(mu - e)) / 2e
+    of two independently assembled meshes (error O(e^2))."""
+    mu, eps = 0.41, 1e-5
+    psi = gi.disk(N ** dim, 3)
+    d = oracle_mod.Mesh(dim, N, mu, field, edge=edge).residual_dmu(psi)
+    fd = (oracle_mod.Mesh(dim, N, mu + eps, field, edge=edge).residual(psi)
+          - oracle_mod.Mesh(dim, N, mu - eps, field, edge=edge).residual(psi)) / (2 * eps)
+    assert np.linalg.norm(d - fd) <= 1e-7 * np.linalg.norm(d), np.linalg.norm(d - fd) / np.linalg.norm(d)
+    # a gauge offset a0 does not enter d K / d mu beyond the phases it shifts:
+    # at psi = 1 and mu = 0 the derivative is i D^-1 sum_k alpha theta1 (a discrete divergence of A_1)
+    m0 = oracle_mod.Mesh(dim, N, 0.0, field, edge=edge)
+    d0 = m0.residual_dmu(np.ones(m0.n, complex))
+    assert np.abs(d0.real).max() <= 1e-14 * max(1.0, np.abs(d0).max())
+
+
+def test_dmu_is_orthogonal_to_the_gauge_direction(oracle_mod):
+    """<i psi, GL(psi)>_R = 0 for every psi and mu (phase invariance, Sec. 2), so its mu
+    derivative <i psi, d GL / d mu>_R vanishes: the bordered continuation system
+    stays consistent although J(psi)(i psi) = i GL(psi) is singular at solutions."""
+    m = oracle_mod.Mesh(2, 19, 0.6, edge=6.0)
+    psi = gi.disk(m.n, 8)
+    d = m.residual_dmu(psi)
+    assert abs(m.inner_r(1j * psi, d)) <= 1e-12 * np.sqrt(m.inner_r(d, d) * m.inner_r(psi, psi))
+    assert abs(m.inner_r(1j * psi, m.residual(psi))) <= 1e-12 * np.sqrt(m.inner_r(psi, psi)) * \
+        np.sqrt(m.inner_r(m.residual(psi), m.residual(psi)))
+
+
+@pytest.mark.parametrize("dim,edge", [(2, 10.0), (3, 4.0)])
+def test_energy_of_the_homogeneous_state(oracle_mod, dim, edge):
+    """psi = 1 without field: F_1 = 0 and F_2 = sum |V| (-1 + 1/2) = -|Omega| / 2, so
+    the energy per unit volume is -1/2 (the start of Fig. 4's energy curve)."""
+    N = 9
+    m = oracle_mod.Mesh(dim, N, 0.0, edge=edge)
+    F = m.energy(np.ones(m.n, complex))
+    assert F == pytest.approx(-0.5 * edge ** dim, rel=1e-13)
+    # a constant phase changes nothing; with a field, psi = 1 costs kinetic energy
+    assert m.energy(np.exp(0.7j) * np.ones(m.n)) == pytest.approx(F, rel=1e-13)
+    mf = oracle_mod.Mesh(dim, N, 0.5, edge=edge)
+    assert mf.energy(np.ones(m.n, complex)) > F
