@@ -114,6 +114,18 @@ def test_continuation_matches_oracle(oracle_mod):
         gl.gl_mesh_destroy(m)
 
 
+def read_fig4():
+    import os
+
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "fig4_continuation_states.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                mu, F = line.split()
+                rows.append((float(mu), float(F)))
+    return rows
+
+
 def test_continuation_fig4_shape():
     """Fig. 4 on a 201 x 201 mesh of the edge-10 square, 80 steps: the energy per
     unit volume starts at -1/2 and rises, the curve folds back (swallow tail)
@@ -142,5 +154,14 @@ def test_continuation_fig4_shape():
         assert folds >= 2 and len(pts) == 81
         late = its[(mus > 0.7) & (np.arange(len(mus)) > turn)]
         assert late.size and late.max() >= 3 * np.median(its[1:turn])
+        # the states printed in Fig. 4: where the curve first reaches mu = 0.47 (0.93)
+        # after its first fold, 2 F / |Omega| = -0.47 (-0.12), to the printed digits
+        first_fold = next(k for k in range(1, len(mus) - 1) if (mus[k] - mus[k - 1]) * (mus[k + 1] - mus[k]) < 0)
+        for mu_p, F_p in read_fig4():
+            k = next(k for k in range(first_fold, len(mus) - 1) if (mus[k] - mu_p) * (mus[k + 1] - mu_p) <= 0)
+            w = (mu_p - mus[k]) / (mus[k + 1] - mus[k])
+            F_here = 2.0 * ((1 - w) * F[k] + w * F[k + 1])
+            print(f"Fig. 4 state: mu {mu_p}: 2F/|Omega| = {F_here:.4f} (paper {F_p})")
+            assert abs(F_here - F_p) <= 0.01
     finally:
         gl.gl_mesh_destroy(m)

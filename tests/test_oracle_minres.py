@@ -93,7 +93,7 @@ def test_mesh_independent_iterations_like_fig3(oracle_mod):
         psi = np.ones(m.n, complex)
         b = gi.complex_normal(m.n, 5)
         it1.append(m.solve(psi, b, tol=1e-11, max_coarse=64)[1].iters)
-        itinf.append(m.solve(psi, b, tol=1e-11, max_coarse=64, cycles=10)[1].iters)
+        itinf.append(m.solve(psi, b, tol=1e-11, max_coarse=64, cycles=oracle_mod.CYCLES_INF)[1].iters)
         it0.append(m.solve(psi, b, tol=1e-11, cycles=0, maxit=2000)[1].iters)
     assert max(it1) - min(it1) <= 3, it1
     assert all(a < b for a, b in zip(itinf, it1)), (itinf, it1)
