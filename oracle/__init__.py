@@ -52,6 +52,7 @@ class Options(C.Structure):
         ("max_coarse", C.c_int),
         ("max_levels", C.c_int),
         ("power_its", C.c_int),
+        ("coloring", C.c_int),
     ]
 
 
@@ -100,6 +101,8 @@ def lib():
             L.glref_aggregate.argtypes = [C.c_int64, _i64p, _i32p, _i32p]
             L.glref_color_jp.restype = C.c_int32
             L.glref_color_jp.argtypes = [C.c_int64, _i64p, _i32p, _i32p]
+            L.glref_color_sl.restype = C.c_int32
+            L.glref_color_sl.argtypes = [C.c_int64, _i64p, _i32p, _i32p, _i32p]
             L.glref_precond_setup.restype = vp
             L.glref_precond_setup.argtypes = [vp, _c128p, C.POINTER(Options)]
             L.glref_precond_destroy.argtypes = [vp]
@@ -137,8 +140,12 @@ def _c128(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.complex128)
 
 
-def options(tol=1e-10, maxit=500, cycles=1, max_coarse=512, max_levels=10, power_its=20) -> Options:
-    return Options(tol, maxit, cycles, max_coarse, max_levels, power_its)
+COLOR_SL, COLOR_JP = 0, 1  # coarse-level colourings: smallest-last greedy (default), Jones-Plassmann
+
+
+def options(tol=1e-10, maxit=500, cycles=1, max_coarse=512, max_levels=10, power_its=20,
+            coloring=COLOR_SL) -> Options:
+    return Options(tol, maxit, cycles, max_coarse, max_levels, power_its, coloring)
 
 
 @dataclass
@@ -395,6 +402,17 @@ def color_jp(rp, ci):
     col = np.zeros(n, np.int32)
     nc = lib().glref_color_jp(n, rp, ci, col)
     return nc, col
+
+
+def color_sl(rp, ci):
+    """(ncolors, colours, order): smallest-last greedy colouring and its colouring order."""
+    rp = np.ascontiguousarray(rp, np.int64)
+    ci = np.ascontiguousarray(ci, np.int32)
+    n = len(rp) - 1
+    col = np.zeros(n, np.int32)
+    order = np.zeros(n, np.int32)
+    nc = lib().glref_color_sl(n, rp, ci, col, order)
+    return nc, col, order
 
 
 def simplex_alpha(dim: int, verts, method: str = "linsys"):

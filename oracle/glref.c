@@ -662,7 +662,11 @@ typedef struct {
     int max_coarse;    /* stop coarsening at or below this size */
     int max_levels;
     int power_its;     /* power iterations for the spectral radius of D^-1 A */
+    int coloring;      /* coarse-level colouring: GLREF_COLOR_SL (smallest-last greedy) or GLREF_COLOR_JP */
 } glref_options;
+
+#define GLREF_COLOR_SL 0
+#define GLREF_COLOR_JP 1
 
 typedef struct {
     csr A;            /* level operator (Hermitian) */
@@ -810,6 +814,90 @@ int32_t glref_color_jp(int64_t n, const int64_t *rp, const int32_t *ci, int32_t 
     return ncol;
 }
 
+/* Smallest-last greedy colouring (Matula & Beck's smallest-last ordering, then
+ * the greedy colouring in reverse removal order), made deterministic:
+ *   degree d(v) = off-diagonal entries of row v (the graph is symmetric);
+ *   vertices sit in degree buckets, each a list; they enter in ascending id,
+ *   each at the head of its bucket;
+ *   n times: take the head of the lowest non-empty bucket, remove it, and move
+ *   each of its remaining neighbours (ascending column order) to the head of
+ *   the bucket one degree lower;
+ *   then colour the vertices from the last removed to the first, each with the
+ *   smallest colour none of its coloured neighbours has.
+ * Every vertex is removed with at most the graph's degeneracy k remaining
+ * neighbours, all coloured after it, so at most k + 1 colours are used.
+ * Returns the number of colours. */
+int32_t glref_color_sl(int64_t n, const int64_t *rp, const int32_t *ci, int32_t *color, int32_t *order) {
+    int64_t *deg = xcalloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    int64_t maxd = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        for (int64_t p = rp[v]; p < rp[v + 1]; ++p)
+            if (ci[p] != v) ++deg[v];
+        if (deg[v] > maxd) maxd = deg[v];
+    }
+    int64_t *head = xcalloc((size_t)maxd + 1, sizeof(int64_t));
+    int64_t *next = xcalloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    int64_t *prev = xcalloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    uint8_t *gone = xcalloc((size_t)(n > 0 ? n : 1), 1);
+    for (int64_t d = 0; d <= maxd; ++d) head[d] = -1;
+    /* list operations: unlink v from bucket deg[v]; push v at the head of bucket deg[v] */
+#define SL_UNLINK(v)                                        \
+    do {                                                    \
+        if (prev[v] >= 0) next[prev[v]] = next[v];          \
+        else head[deg[v]] = next[v];                        \
+        if (next[v] >= 0) prev[next[v]] = prev[v];          \
+    } while (0)
+#define SL_PUSH(v)                                          \
+    do {                                                    \
+        prev[v] = -1;                                       \
+        next[v] = head[deg[v]];                             \
+        if (head[deg[v]] >= 0) prev[head[deg[v]]] = v;      \
+        head[deg[v]] = v;                                   \
+    } while (0)
+    for (int64_t v = 0; v < n; ++v) SL_PUSH(v);
+    int64_t lo = 0;
+    for (int64_t step = 0; step < n; ++step) {
+        while (head[lo] < 0) ++lo;
+        int64_t v = head[lo];
+        SL_UNLINK(v);
+        gone[v] = 1;
+        order[n - 1 - step] = (int32_t)v;
+        for (int64_t p = rp[v]; p < rp[v + 1]; ++p) {
+            int64_t u = ci[p];
+            if (u == v || gone[u]) continue;
+            SL_UNLINK(u);
+            --deg[u];
+            SL_PUSH(u);
+        }
+        lo = lo > 0 ? lo - 1 : 0;
+    }
+#undef SL_UNLINK
+#undef SL_PUSH
+    /* greedy in that order; stamp[c] = the vertex that last saw colour c taken */
+    int64_t *stamp = xcalloc((size_t)maxd + 2, sizeof(int64_t));
+    for (int64_t c = 0; c <= maxd + 1; ++c) stamp[c] = -1;
+    for (int64_t v = 0; v < n; ++v) color[v] = -1;
+    int32_t ncol = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t v = order[k];
+        for (int64_t p = rp[v]; p < rp[v + 1]; ++p) {
+            int64_t u = ci[p];
+            if (u != v && color[u] >= 0) stamp[color[u]] = v;
+        }
+        int32_t c = 0;
+        while (stamp[c] == v) ++c;
+        color[v] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+    }
+    free(deg);
+    free(head);
+    free(next);
+    free(prev);
+    free(gone);
+    free(stamp);
+    return ncol;
+}
+
 /* spectral radius estimate of D^-1 A: `its` power iterations from the fixed
  * start x_i = 1 + (i mod 7)/7, then the Rayleigh quotient in the D inner
  * product, Re(x^H A x) / (x^H D x). */
@@ -942,8 +1030,12 @@ glref_prec *glref_precond_setup(const glref_mesh *m, const cplx *psi, const glre
                 for (int j = 0; j < m->N; ++j)
                     for (int i = 0; i < m->N; ++i) L->color[node_id(m, i, j, k)] = (i + j + k) & 1;
             L->ncolors = (nl > 1) ? 2 : 1;
-        } else {
+        } else if (o->coloring == GLREF_COLOR_JP) {
             L->ncolors = glref_color_jp(nl, L->A.rp, L->A.ci, L->color);
+        } else {
+            int32_t *order = xcalloc((size_t)nl, sizeof(int32_t));
+            L->ncolors = glref_color_sl(nl, L->A.rp, L->A.ci, L->color, order);
+            free(order);
         }
         for (int w = 0; w < 3; ++w) p->work[l][w] = xcalloc((size_t)nl, sizeof(cplx));
         if (nl <= max_coarse || l + 1 >= maxlev) break;

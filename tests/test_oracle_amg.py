@@ -104,6 +104,51 @@ def test_jp_colouring_characterisation(oracle_mod, kind, dim, N):
         assert all(col[j] != col[i] for j in adj[i])
 
 
+@pytest.mark.parametrize("kind,dim,N", GRAPHS + [("coarse3", 3, 20)])
+def test_smallest_last_colouring(oracle_mod, kind, dim, N):
+    """Smallest-last greedy colouring (Matula & Beck): the reversed colouring order
+    removes, at every step, a vertex of minimum degree among those left; each
+    colour is the smallest not taken by neighbours coloured before; the colouring
+    is proper and uses at most degeneracy + 1 colours (the degeneracy counted by
+    brute force)."""
+    if kind == "coarse3":
+        m = oracle_mod.Mesh(3, N, 1.0, BH3)
+        P = oracle_mod.Precond(m, np.ones(m.n, complex), max_coarse=64, coloring=oracle_mod.COLOR_JP)
+        rp, ci, _ = P.level_matrix(1)
+    elif kind == "random":
+        rp, ci = random_graph(N, 3, 5)
+    else:
+        rp, ci = lattice_graph(oracle_mod, dim, N)
+    n = len(rp) - 1
+    ncol, col, order = oracle_mod.color_sl(rp, ci)
+    adj = graph_adj(rp, ci, n)
+    assert sorted(order) == list(range(n))
+    left = set(range(n))
+    deg = {v: len(adj[v]) for v in range(n)}
+    degeneracy = 0
+    for v in order[::-1]:
+        v = int(v)
+        assert deg[v] == min(deg[u] for u in left), v
+        degeneracy = max(degeneracy, deg[v])
+        left.remove(v)
+        for u in adj[v]:
+            if u in left:
+                deg[u] -= 1
+    pos = np.empty(n, np.int64)
+    pos[order] = np.arange(n)
+    for v in range(n):
+        before = {int(col[u]) for u in adj[v] if pos[u] < pos[v]}
+        c = 0
+        while c in before:
+            c += 1
+        assert col[v] == c
+        assert all(col[u] != col[v] for u in adj[v])
+    assert col.max() == ncol - 1 and ncol <= degeneracy + 1
+    if kind == "coarse3":
+        # fewer colours than Jones-Plassmann on a coarse AMG level
+        assert ncol < oracle_mod.color_jp(rp, ci)[0]
+
+
 @pytest.fixture(scope="module")
 def prec2d(oracle_mod):
     m = oracle_mod.Mesh(2, 32, 1.5)
