@@ -100,7 +100,15 @@ typedef struct {
     gl_warmstart warmstart; /* learned initial guess: when set, gl_jacobian_solve and gl_newton_step ignore the
                             x passed in, start from the network's x0, and fall back to x0 = 0 when
                             ||b - J x0||_D >= ||b||_D (default NULL: start from x as given) */
+    int coloring;        /* colouring of the coarse levels for the multicolour Gauss-Seidel steps:
+                            GL_COLOR_SL (smallest-last greedy, deterministic, on the host; default) or
+                            GL_COLOR_JP (Jones-Plassmann with hashed priorities, on the device).  Each
+                            colour is one dependent phase of a sweep.  The finest lattice level is
+                            always red-black. */
 } gl_options;
+
+#define GL_COLOR_SL 0
+#define GL_COLOR_JP 1
 
 /* Per-solve report. */
 typedef struct {

@@ -33,6 +33,7 @@ __all__ = [
 
 GL_FP64, GL_MIXED, GL_MIXED_PRECOND = 0, 1, 2
 GL_CYCLES_INF = -1  # options.cycles: R_inf, the V-cycle repeated until the 1e-12 residual test
+GL_COLOR_SL, GL_COLOR_JP = 0, 1  # options.coloring of the coarse levels
 STATUS = {0: "GL_OK", 1: "GL_ERR_ARG", 2: "GL_ERR_CUDA", 3: "GL_ERR_OOM", 4: "GL_ERR_NOT_CONVERGED",
           5: "GL_ERR_BREAKDOWN", 6: "GL_ERR_NAN", 7: "GL_ERR_TIMEOUT", 8: "GL_ERR_CAPACITY"}
 
@@ -64,7 +65,7 @@ class Options(C.Structure):
         ("max_levels", C.c_int), ("power_its", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double),
         ("max_outer", C.c_int), ("check_every", C.c_int), ("autotune", C.c_int), ("lattice", C.c_int),
         ("cluster_sweeps", C.c_int),
-        ("warmstart", C.c_void_p),
+        ("warmstart", C.c_void_p), ("coloring", C.c_int),
     ]
 
 

@@ -40,6 +40,7 @@ void check_opts(const gl_options *o) {
     GL_REQUIRE(o->precision == GL_FP64 || o->precision == GL_MIXED || o->precision == GL_MIXED_PRECOND, GL_ERR_ARG,
                "unknown precision");
     GL_REQUIRE(o->max_coarse <= MAX_COARSE_DENSE, GL_ERR_ARG, "max_coarse must be <= 4096");
+    GL_REQUIRE(o->coloring == GL_COLOR_SL || o->coloring == GL_COLOR_JP, GL_ERR_ARG, "unknown coloring");
 }
 
 void ensure_tmp(gl_mesh_s *m) {
@@ -77,6 +78,7 @@ gl_status gl_options_default(gl_options *o) {
     o->lattice = 1;
     o->cluster_sweeps = 1;
     o->warmstart = nullptr;
+    o->coloring = GL_COLOR_SL;
     return GL_OK;
 }
 

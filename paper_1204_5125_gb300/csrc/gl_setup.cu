@@ -234,6 +234,81 @@ static int color_jp(const CsrDev &A, int32_t *color, cudaStream_t s) {
     return hm + 1;
 }
 
+// Smallest-last greedy colouring (Matula & Beck) of the level graph, on the
+// host: a sequential order whose colour count is bounded by the graph's
+// degeneracy + 1 (fewer colours, so fewer dependent phases in every
+// multicolour sweep, than the parallel Jones-Plassmann colouring).  The order
+// is deterministic: vertices wait in degree buckets (intrusive lists; entered
+// in ascending id, each at the head), the head of the lowest non-empty bucket
+// leaves next, and each of its remaining neighbours, in row order, moves to the
+// head of the bucket one degree lower.  Colouring runs from the last vertex to
+// leave to the first, each taking the smallest colour none of its coloured
+// neighbours has.
+static int color_smallest_last(const CsrDev &A, int32_t *color_dev, cudaStream_t s) {
+    const int64_t n = A.n;
+    std::vector<int64_t> rp(n + 1);
+    std::vector<int32_t> ci(A.nnz > 0 ? A.nnz : 1);
+    GL_CUDA(cudaMemcpyAsync(rp.data(), A.rp.get(), (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (A.nnz > 0)
+        GL_CUDA(cudaMemcpyAsync(ci.data(), A.ci.get(), A.nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaStreamSynchronize(s));
+    std::vector<int64_t> d(n, 0);
+    int64_t dmax = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        for (int64_t q = rp[v]; q < rp[v + 1]; ++q) d[v] += (ci[q] != v);
+        dmax = std::max(dmax, d[v]);
+    }
+    std::vector<int64_t> first(dmax + 1, -1), nxt(n, -1), prv(n, -1);
+    auto unlink = [&](int64_t v) {
+        if (prv[v] >= 0)
+            nxt[prv[v]] = nxt[v];
+        else
+            first[d[v]] = nxt[v];
+        if (nxt[v] >= 0) prv[nxt[v]] = prv[v];
+    };
+    auto push = [&](int64_t v) {
+        prv[v] = -1;
+        nxt[v] = first[d[v]];
+        if (nxt[v] >= 0) prv[nxt[v]] = v;
+        first[d[v]] = v;
+    };
+    for (int64_t v = 0; v < n; ++v) push(v);
+    std::vector<int32_t> seq(n);
+    std::vector<char> out(n, 0);
+    int64_t b = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        while (first[b] < 0) ++b;
+        const int64_t v = first[b];
+        unlink(v);
+        out[v] = 1;
+        seq[n - 1 - k] = (int32_t)v;
+        for (int64_t q = rp[v]; q < rp[v + 1]; ++q) {
+            const int64_t u = ci[q];
+            if (u == v || out[u]) continue;
+            unlink(u);
+            --d[u];
+            push(u);
+        }
+        b = b > 0 ? b - 1 : 0;
+    }
+    std::vector<int32_t> col(n, -1);
+    std::vector<int64_t> seen(dmax + 2, -1);
+    int32_t ncol = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t v = seq[k];
+        for (int64_t q = rp[v]; q < rp[v + 1]; ++q)
+            if (ci[q] != v && col[ci[q]] >= 0) seen[col[ci[q]]] = v;
+        int32_t c = 0;
+        while (seen[c] == v) ++c;
+        col[v] = c;
+        ncol = std::max(ncol, c + 1);
+    }
+    GL_REQUIRE(ncol <= 256, GL_ERR_CAPACITY, "more than 256 colours needed");
+    GL_CUDA(cudaMemcpyAsync(color_dev, col.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    GL_CUDA(cudaStreamSynchronize(s));
+    return ncol;
+}
+
 // ------------------------------------------------------------------ candidate norms
 // members of each aggregate (the pattern of P_tent^T), sorted by node id
 __global__ void k_count_cols(int64_t nnz, const int32_t *col, int64_t *cnt) {
@@ -840,7 +915,8 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
         int64_t nl = L.n;
         if (l > 0) {
             L.color.alloc(nl);
-            L.ncolors = color_jp(L.A_can, L.color.get(), s);
+            L.ncolors = o.coloring == GL_COLOR_JP ? color_jp(L.A_can, L.color.get(), s)
+                                                  : color_smallest_last(L.A_can, L.color.get(), s);
         }
         if (nl <= max_coarse || l + 1 >= maxlev) break;
         L.agg.alloc(nl);

@@ -63,10 +63,18 @@ def test_level0_aggregation_full_size(big, oracle_mod):
         nagg, agg = oracle_mod.aggregate(rp, ci)
         np.testing.assert_array_equal(gl.gl_precond_level_aggregates(G, 0), agg)
         assert gl.gl_precond_level_info(G, 1)["n"] == nagg
-        # the level-1 colouring follows from the level-1 pattern by Jones-Plassmann
+        # the level-1 colouring follows from the level-1 pattern by the smallest-last
+        # greedy rule (the default) and, on request, by Jones-Plassmann
         lrp, lci, _ = gl.gl_precond_level_matrix(G, 1)
-        nc, col = oracle_mod.color_jp(lrp, lci)
+        nc, col, _ = oracle_mod.color_sl(lrp, lci)
         np.testing.assert_array_equal(gl.gl_precond_level_colors(G, 1), col)
+        Gj = gl.gl_precond_setup(gm, psi, gl.options(precision=gl.GL_MIXED, coloring=gl.GL_COLOR_JP))
+        try:
+            njp, coljp = oracle_mod.color_jp(lrp, lci)
+            np.testing.assert_array_equal(gl.gl_precond_level_colors(Gj, 1), coljp)
+            assert nc < njp
+        finally:
+            gl.gl_precond_destroy(Gj)
     finally:
         gl.gl_precond_destroy(G)
 
