@@ -218,6 +218,17 @@ GL_API gl_status gl_jacobian_apply_noalloc(gl_mesh mesh, const void *psi_dev, co
 GL_API gl_status gl_precond_setup(gl_mesh mesh, const void *psi_dev, const gl_options *opt, void *stream,
                            gl_prec *out);
 
+/* gl_precond_setup for a new psi (and the mesh's current mu) that takes over
+ * from `like`, an earlier preconditioner of the same mesh set up with the same
+ * max_coarse, max_levels and coloring, everything that depends on the sparsity
+ * alone: the aggregates (strength threshold 0), the colourings and the kernel
+ * choices its setup timed.  The hierarchy's values are computed afresh, so the
+ * result equals a gl_precond_setup whose timing picked the same kernels; along
+ * a continuation the sparsity never changes.  A `like` that does not match is
+ * ignored (a full setup runs).  `like` stays valid and owned by the caller. */
+GL_API gl_status gl_precond_setup_like(gl_mesh mesh, const void *psi_dev, const gl_options *opt, gl_prec like,
+                                       void *stream, gl_prec *out);
+
 /* z = R_k x: k V-cycles for (K-hat + 2 D|psi|^2) z = D x from z = 0 (Eq. prec2);
  * with cycles = GL_CYCLES_INF, R_inf: cycles until the residual test of
  * GL_CYCLES_INF holds (a device-side loop; no host round trip per cycle).

@@ -28,7 +28,8 @@ __all__ = [
     "gl_warmstart_create", "gl_warmstart_destroy", "gl_warmstart_get_params", "gl_warmstart_set_params",
     "gl_warmstart_predict", "gl_warmstart_grad", "gl_warmstart_train", "gl_warmstart_adam_step", "GL_WS_NPARAM",
     "gl_last_error", "EXPORTED", "GL_CYCLES_INF", "ContOptions", "ContPoint", "gl_mesh_create_edge",
-    "gl_mesh_set_mu", "gl_residual_dmu", "gl_energy", "cont_options", "gl_continuation",
+    "gl_mesh_set_mu", "gl_residual_dmu", "gl_energy", "cont_options", "gl_continuation", "gl_precond_setup_like",
+    "GL_COLOR_SL", "GL_COLOR_JP",
 ]
 
 GL_FP64, GL_MIXED, GL_MIXED_PRECOND = 0, 1, 2
@@ -47,7 +48,7 @@ EXPORTED = [
     "gl_batch_destroy", "gl_precond_cost", "gl_warmstart_create", "gl_warmstart_destroy", "gl_warmstart_get_params",
     "gl_warmstart_set_params", "gl_warmstart_predict", "gl_warmstart_grad", "gl_warmstart_train",
     "gl_warmstart_adam_step", "gl_last_error", "gl_mesh_create_edge", "gl_mesh_set_mu", "gl_residual_dmu",
-    "gl_energy", "gl_cont_options_default", "gl_continuation",
+    "gl_energy", "gl_cont_options_default", "gl_continuation", "gl_precond_setup_like",
 ]
 
 GL_WS_NPARAM = 4 * 64 * 128 + 2 * 64
@@ -157,6 +158,7 @@ def library(build_if_missing: bool = True):
             "gl_mesh_create_edge": [C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_double), vp,
                                     C.POINTER(vp)],
             "gl_mesh_set_mu": [vp, C.c_double, vp],
+            "gl_precond_setup_like": [vp, vp, C.POINTER(Options), vp, vp, C.POINTER(vp)],
             "gl_residual_dmu": [vp, vp, vp, vp],
             "gl_energy": [vp, vp, C.POINTER(C.c_double), vp],
             "gl_cont_options_default": [C.POINTER(ContOptions)],
@@ -326,6 +328,14 @@ def gl_precond_setup(mesh, psi, opts: Options | None = None, stream=None):
     out = C.c_void_p()
     o = opts if opts is not None else gl_options_default()
     _check(library().gl_precond_setup(mesh, _ptr(psi), C.byref(o), _stream(stream), C.byref(out)))
+    return out
+
+
+def gl_precond_setup_like(mesh, psi, like, opts: Options | None = None, stream=None):
+    """Setup for a new psi / mu taking over `like`'s aggregates, colours and kernel choices."""
+    out = C.c_void_p()
+    o = opts if opts is not None else gl_options_default()
+    _check(library().gl_precond_setup_like(mesh, _ptr(psi), C.byref(o), like, _stream(stream), C.byref(out)))
     return out
 
 

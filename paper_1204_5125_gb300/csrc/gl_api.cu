@@ -213,6 +213,25 @@ gl_status gl_precond_setup(gl_mesh m, const void *psi, const gl_options *opt, vo
     });
 }
 
+gl_status gl_precond_setup_like(gl_mesh m, const void *psi, const gl_options *opt, gl_prec like, void *stream,
+                                gl_prec *out) {
+    return guard([&] {
+        GL_REQUIRE(m && psi && out, GL_ERR_ARG, "NULL argument");
+        check_opts(opt);
+        *out = nullptr;
+        auto *p = new gl_prec_s();
+        try {
+            precond_setup(p, m, (const double2 *)psi, *opt, as_stream(stream), like);
+        } catch (...) {
+            cudaDeviceSynchronize();
+            delete p;
+            throw;
+        }
+        *out = p;
+        return GL_OK;
+    });
+}
+
 gl_status gl_precond_apply(gl_prec p, const void *x, void *z, void *stream) {
     return guard([&] {
         GL_REQUIRE(p && x && z, GL_ERR_ARG, "NULL argument");

@@ -7,6 +7,8 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -15,6 +17,14 @@
 namespace gl {
 
 // ---------------------------------------------------------------- errors
+// GL_VERBOSE=1 in the environment: setup decisions are reported on stderr
+inline bool verbose() {
+    static const bool v = [] {
+        const char *e = std::getenv("GL_VERBOSE");
+        return e && e[0] && e[0] != '0';
+    }();
+    return v;
+}
 void set_error(const std::string &msg);
 const char *last_error();
 

@@ -183,11 +183,12 @@ struct Cont {
     }
     void set_mu(double mu) { mesh_set_mu(m, mu, s); }
 
-    gl_prec setup(const double2 *psi) {
+    // R(psi), taking over the aggregates, colours and kernel choices of `like`
+    gl_prec setup(const double2 *psi, gl_prec like) {
         if (o.solver.cycles == 0) return nullptr;
         auto t0 = std::chrono::steady_clock::now();
         gl_prec p = nullptr;
-        gl_status st = gl_precond_setup(m, psi, &o.solver, sv(), &p);
+        gl_status st = gl_precond_setup_like(m, psi, &o.solver, like, sv(), &p);
         if (st != GL_OK) throw Error{st, last_error()};
         setup_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         return p;
@@ -296,7 +297,7 @@ gl_status gl_continuation(gl_mesh m, void *psi_v, const gl_cont_options *o, gl_c
                 break;
             }
             if (it == o->newton_maxit) break;
-            P.reset(C.setup(psi));
+            P.reset(C.setup(psi, P.p));
             k_scale_neg<<<C.G(), 256, 0, s>>>(n, W.r.get(), -1.0, W.b.get());
             GL_LAUNCH_CHECK();
             int k = C.solve(psi, P.p, W.b.get(), W.a.get());
@@ -312,7 +313,7 @@ gl_status gl_continuation(gl_mesh m, void *psi_v, const gl_cont_options *o, gl_c
         int np = 1;
 
         // first tangent: J c = -dGL/dmu, t = (c, 1) / norm
-        P.reset(C.setup(psi));
+        P.reset(C.setup(psi, P.p));
         residual_dmu(m, psi, W.r.get(), s);
         k_scale_neg<<<C.G(), 256, 0, s>>>(n, W.r.get(), -1.0, W.b.get());
         GL_LAUNCH_CHECK();
@@ -347,7 +348,7 @@ gl_status gl_continuation(gl_mesh m, void *psi_v, const gl_cont_options *o, gl_c
                     }
                     if (it == o->newton_maxit || !std::isfinite(g)) break;
                     const double ncond = C.ip(W.t.get(), psi) - t_psi_s + t_mu * (mu_n - mu_s) - ds;
-                    P.reset(C.setup(psi));
+                    P.reset(C.setup(psi, P.p));
                     k_scale_neg<<<C.G(), 256, 0, s>>>(n, W.r.get(), -1.0, W.b.get());
                     GL_LAUNCH_CHECK();
                     const int ka = C.solve(psi, P.p, W.b.get(), W.a.get());

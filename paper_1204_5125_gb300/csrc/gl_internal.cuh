@@ -118,6 +118,14 @@ struct gl_prec_s {
     gl::DBuf<double2> coarse_b64, coarse_x64;  // FP64 coarsest solve in mixed mode
     // cost model (matrix entries visited): one V-cycle, and the finest operator K-hat
     double cost_vcycle = 0, cost_fine = 0;
+    // the hierarchy-shaping options the setup ran with (a template must match them)
+    int64_t max_coarse_used = 0;
+    int maxlev_used = 0, coloring_used = 0;
+    // kernel choices taken over from a template instead of timing them again
+    struct Tuned {
+        int ag64 = 1, phg64 = 1, sgs64 = 1, ag32 = 1, phg32 = 1, sgs32 = 1, cl_size = 0, cl_chunk = 0;
+    } tuned[gl::MAX_LEVELS];
+    bool tuned64 = false, tuned32 = false;
     // R_inf: device loop state, the stream its loop body is captured on, and the
     // stream and events of an application outside stream capture
     bool rinf = false;
@@ -167,7 +175,12 @@ struct LatticeDfView {
 LatticeDfView lattice_df_view(const gl_mesh_s *m);
 
 // gl_setup.cu
-void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_options &o, cudaStream_t s);
+// `like` (nullable): an earlier preconditioner of the same mesh set up with the
+// same max_coarse / max_levels / coloring; its aggregates, colours and timed
+// kernel choices are taken over (they depend on the sparsity only), everything
+// numeric is computed for psi and the mesh's current mu
+void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_options &o, cudaStream_t s,
+                   const gl_prec_s *like = nullptr);
 // cost of R_k in matrix-vector-product equivalents (entries visited / entries of K-hat)
 double precond_cost(const gl_prec_s *p, int k);
 // R_inf counters: zeroed before a solve, read after it (synchronises s)

@@ -882,7 +882,8 @@ static void copy_csr(const CsrDev &a, CsrDev &b, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ driver
-void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_options &o, cudaStream_t s) {
+void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_options &o, cudaStream_t s,
+                   const gl_prec_s *like) {
     static std::atomic<int64_t> next_uid{1};
     p->uid = next_uid.fetch_add(1);
     p->mesh = m;
@@ -895,6 +896,15 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
     GL_REQUIRE(max_coarse <= MAX_COARSE_DENSE, GL_ERR_ARG, "max_coarse above 4096");
     int power_its = o.power_its > 0 ? o.power_its : 20;
     int64_t n = m->n;
+    p->max_coarse_used = max_coarse;
+    p->maxlev_used = maxlev;
+    p->coloring_used = o.coloring;
+    const gl_prec_s *T = like;
+    if (T && !(T->mesh == m && T->max_coarse_used == max_coarse && T->maxlev_used == maxlev &&
+               T->coloring_used == o.coloring && T->nlev >= 1))
+        T = nullptr;
+    // level l of the template can stand in for level l here (same size, so the same graph)
+    auto same = [&](int l, int64_t nl) { return T && l < T->nlev && T->L[l].n == nl; };
 
     // level 0: K-hat + 2 D |psi|^2 in node order
     Level &L0 = p->L[0];
@@ -915,12 +925,24 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
         int64_t nl = L.n;
         if (l > 0) {
             L.color.alloc(nl);
-            L.ncolors = o.coloring == GL_COLOR_JP ? color_jp(L.A_can, L.color.get(), s)
-                                                  : color_smallest_last(L.A_can, L.color.get(), s);
+            if (same(l, nl) && T->L[l].color.n == (size_t)nl) {
+                GL_CUDA(cudaMemcpyAsync(L.color.get(), T->L[l].color.get(), nl * sizeof(int32_t),
+                                        cudaMemcpyDeviceToDevice, s));
+                L.ncolors = T->L[l].ncolors;
+            } else {
+                L.ncolors = o.coloring == GL_COLOR_JP ? color_jp(L.A_can, L.color.get(), s)
+                                                      : color_smallest_last(L.A_can, L.color.get(), s);
+            }
         }
         if (nl <= max_coarse || l + 1 >= maxlev) break;
         L.agg.alloc(nl);
-        int64_t nc = aggregate(L.A_can, L.agg.get(), s);
+        int64_t nc;
+        if (same(l, nl) && l + 1 < T->nlev && T->L[l].agg.n == (size_t)nl) {
+            GL_CUDA(cudaMemcpyAsync(L.agg.get(), T->L[l].agg.get(), nl * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+            nc = T->L[l + 1].n;
+        } else {
+            nc = aggregate(L.A_can, L.agg.get(), s);
+        }
         if (nc >= nl || nc == 0) {
             L.agg.release();
             break;
@@ -1103,8 +1125,33 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
     p->autotune = o.autotune != 0;
     p->lattice = o.lattice != 0;
     p->cluster_sweeps = o.cluster_sweeps != 0;
-    if (p->autotune) autotune_levels(p, false, s);
-    plan_sweeps(p, false, s);
+    if (T && T->nlev == p->nlev && T->autotune == p->autotune && T->cluster_sweeps == p->cluster_sweeps) {
+        for (int k = 0; k < p->nlev; ++k) {
+            const Level &S = T->L[k];
+            auto &t = p->tuned[k];
+            t.ag64 = S.Ag.G;
+            t.phg64 = S.PHg.G;
+            t.sgs64 = S.sgs_G64;
+            t.ag32 = S.Ag32.G;
+            t.phg32 = S.PHg32.G;
+            t.sgs32 = S.sgs_G32;
+            t.cl_size = S.cl_size;
+            t.cl_chunk = S.cl_chunk;
+        }
+        p->tuned64 = true;
+        p->tuned32 = T->has32;
+    }
+    if (p->tuned64) {
+        for (int k = 0; k < p->nlev; ++k) {
+            Level &L = p->L[k];
+            L.Ag.G = p->tuned[k].ag64;
+            L.PHg.G = p->tuned[k].phg64;
+            L.sgs_G64 = p->tuned[k].sgs64;
+        }
+    } else {
+        if (p->autotune) autotune_levels(p, false, s);
+        plan_sweeps(p, false, s);
+    }
     if (o.precision != GL_FP64) precond_ensure_fp32(p, s);
 }
 
@@ -1141,8 +1188,19 @@ void precond_ensure_fp32(gl_prec_s *p, cudaStream_t s) {
         p->cyc_r32.alloc(m->n);
         p->cyc_e32.alloc(m->n);
     }
-    if (p->autotune) autotune_levels(p, true, s);
-    plan_sweeps(p, true, s);
+    if (p->tuned32) {
+        for (int k = 0; k < p->nlev; ++k) {
+            Level &L = p->L[k];
+            L.Ag32.G = p->tuned[k].ag32;
+            L.PHg32.G = p->tuned[k].phg32;
+            L.sgs_G32 = p->tuned[k].sgs32;
+            L.cl_size = p->tuned[k].cl_size;
+            L.cl_chunk = p->tuned[k].cl_chunk;
+        }
+    } else {
+        if (p->autotune) autotune_levels(p, true, s);
+        plan_sweeps(p, true, s);
+    }
     p->mp_in.alloc(m->n);
     p->mp_out.alloc(m->n);
     Level &Lb = p->L[p->nlev - 1];

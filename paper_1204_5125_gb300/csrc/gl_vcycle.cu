@@ -1173,6 +1173,8 @@ static void plan_sweeps_t(gl_prec_s *p, cudaStream_t s) {
                                                              L.barrier.get(), p->err.get(), nullptr, maxc, s)));
             });
             if (t < best) best = t, bestG = g;
+            if (verbose()) fprintf(stderr, "gl: level %d (n %lld, %d colours, %s) sweep G %d: %.1f us\n", l,
+                                   (long long)L.n, L.ncolors, sizeof(T) == 4 ? "FP32" : "FP64", g, 1e3 * t);
             if constexpr (sizeof(T) == 4) {
                 if (size > 0) {
                     float tc = time_it([&] {
@@ -1180,10 +1182,14 @@ static void plan_sweeps_t(gl_prec_s *p, cudaStream_t s) {
                                                                   size, chunk, nullptr, s)));
                     });
                     if (tc < best) best = tc, bestG = g, best_cluster = true;
+                    if (verbose()) fprintf(stderr, "gl: level %d cluster sweep G %d: %.1f us\n", l, g, 1e3 * tc);
                 }
             }
         }
         sG = bestG;
+        if (verbose())
+            fprintf(stderr, "gl: level %d %s sweep: G %d%s (largest colour %lld rows)\n", l,
+                    sizeof(T) == 4 ? "FP32" : "FP64", bestG, best_cluster ? ", cluster" : "", (long long)maxc);
         // the timing ran other grid sizes on this level's barrier counters
         GL_CUDA(cudaMemsetAsync(L.barrier.get(), 0, GRID_BARRIER_WORDS * sizeof(unsigned), s));
         GL_CUDA(cudaMemsetAsync(p->err.get(), 0, sizeof(int), s));

@@ -165,3 +165,56 @@ def test_continuation_fig4_shape():
             assert abs(F_here - F_p) <= 0.01
     finally:
         gl.gl_mesh_destroy(m)
+
+
+@pytest.mark.parametrize("autotune", [0, 1])
+def test_setup_like_reuses_the_symbolic_hierarchy(autotune):
+    """A setup for a new psi and mu that takes over an earlier preconditioner's
+    aggregates, colours and kernel choices gives the same hierarchy as a full
+    setup (aggregates, colours and level matrices bit for bit) and the same
+    solve (bit for bit when neither setup times kernels)."""
+    import time
+
+    N = 24
+    bh = gi.WORKLOADS["cube128"][3]
+    m = gl.gl_mesh_create(3, N, 0.4, bh, edge=4.0)
+    n = N ** 3
+    opts = gl.options(max_coarse=64, autotune=autotune, precision=gl.GL_MIXED_PRECOND)
+    psi1, psi2 = dev(gi.disk(n, 1)), dev(gi.psi_noisy_one(n, 2))
+    b = dev(gi.complex_normal(n, 3))
+    G1 = gl.gl_precond_setup(m, psi1, opts)
+    try:
+        gl.gl_mesh_set_mu(m, 0.9)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G2 = gl.gl_precond_setup_like(m, psi2, G1, opts)
+        t1 = time.perf_counter()
+        G3 = gl.gl_precond_setup(m, psi2, opts)
+        t2 = time.perf_counter()
+        try:
+            nl = gl.gl_precond_levels(G3)
+            assert gl.gl_precond_levels(G2) == nl >= 3
+            for lv in range(nl):
+                for a, c in zip(gl.gl_precond_level_matrix(G2, lv), gl.gl_precond_level_matrix(G3, lv)):
+                    np.testing.assert_array_equal(a, c)
+                np.testing.assert_array_equal(gl.gl_precond_level_colors(G2, lv), gl.gl_precond_level_colors(G3, lv))
+                if lv + 1 < nl:
+                    np.testing.assert_array_equal(gl.gl_precond_level_aggregates(G2, lv),
+                                                  gl.gl_precond_level_aggregates(G3, lv))
+            xs = []
+            for G in (G2, G3):
+                x = torch.zeros(n, dtype=torch.complex128, device=DEV)
+                st, info = gl.gl_jacobian_solve(m, psi2, G, b, x, opts)
+                assert st == 0 and info.converged
+                xs.append(x.cpu().numpy())
+            if autotune == 0:
+                np.testing.assert_array_equal(xs[0], xs[1])
+            else:
+                assert rel(xs[0], xs[1]) <= 1e-8
+            print(f"autotune {autotune}: setup taking over {1e3 * (t1 - t0):.1f} ms, full {1e3 * (t2 - t1):.1f} ms")
+        finally:
+            gl.gl_precond_destroy(G2)
+            gl.gl_precond_destroy(G3)
+    finally:
+        gl.gl_precond_destroy(G1)
+        gl.gl_mesh_destroy(m)
