@@ -69,3 +69,31 @@ def test_energy_of_the_homogeneous_state(oracle_mod, dim, edge):
     assert m.energy(np.exp(0.7j) * np.ones(m.n)) == pytest.approx(F, rel=1e-13)
     mf = oracle_mod.Mesh(dim, N, 0.5, edge=edge)
     assert mf.energy(np.ones(m.n, complex)) > F
+
+
+def test_oracle_continuation_reproduces_fig4(oracle_mod):
+    """The oracle's pseudo-arclength continuation on the edge-10 square (33 x 33,
+    from psi = 1 at mu = 0): it starts at F/|Omega| = -1/2, folds back first near
+    mu = 0.30 (Fig. 4's swallow tail), MINRES needs more iterations past the fold,
+    and where the curve first reaches mu = 0.47 after the fold 2F/|Omega| matches
+    the paper's printed -0.47 (tests/golden/fig4_continuation_states.txt)."""
+    import os
+
+    from oracle import continuation as ocont
+
+    N = 33
+    pts, psi, mu = ocont.continuation(2, N, 10.0, np.ones(N * N, complex), 0.0, ds=0.1, ds_max=0.3, max_steps=15,
+                                      mu_max=1.2)
+    mus = np.array([p["mu"] for p in pts])
+    F = np.array([p["energy"] for p in pts])
+    its = np.array([p["iters_last"] for p in pts])
+    assert F[0] == pytest.approx(-0.5, abs=1e-14) and all(p["gl_norm"] <= 1e-9 for p in pts)
+    fold = next(k for k in range(1, len(mus) - 1) if (mus[k] - mus[k - 1]) * (mus[k + 1] - mus[k]) < 0)
+    assert 0.29 <= mus[fold] <= 0.32, mus
+    assert np.all(np.diff(F[: fold + 1]) > 0)
+    assert np.median(its[fold + 1:]) > np.median(its[1:fold])
+    with open(os.path.join(os.path.dirname(__file__), "golden", "fig4_continuation_states.txt")) as f:
+        mu_p, F_p = [tuple(map(float, ln.split())) for ln in f if ln.strip() and not ln.startswith("#")][0]
+    k = next(k for k in range(fold, len(mus) - 1) if (mus[k] - mu_p) * (mus[k + 1] - mu_p) <= 0)
+    w = (mu_p - mus[k]) / (mus[k + 1] - mus[k])
+    assert abs(2.0 * ((1 - w) * F[k] + w * F[k + 1]) - F_p) <= 0.01
