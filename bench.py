@@ -382,7 +382,8 @@ def main():
         "gs0": ("k_gs_lat (Gauss-Seidel colour sweep, finest level, FP32, tabulated lattice stencil)"
                 if infos[-1].lattice_stencil else "k_gs (Gauss-Seidel colour sweep, finest level, FP32)"),
         "gs": "k_sgs_cluster / k_sgs_coop (symmetric Gauss-Seidel step, coarse levels, FP32)",
-        "jz": "k_jz (Jacobian apply fused with the Lanczos dot, FP64)",
+        "jz": ("k_jz_latdf (double-FP32 Jacobian apply fused with the Lanczos dot; SM-pipe bound)"
+               if infos[-1].df_jacobian else "k_jz (Jacobian apply fused with the Lanczos dot, FP64)"),
     }
     profs = {}
     for cls in ("gs0", "gs", "jz"):
