@@ -13,9 +13,10 @@ sizes below are structured node lattices of those domains):
 
 * ``square64``   2D, 64 x 64 nodes, mu = 1, field along z, psi uniform in the
                  unit disk (seed 1), b complex normal (seed 1).
-* ``square1024`` 2D, 1024 x 1024 nodes, mu = 2, psi0 = 1 + 0.1 * (uniform in
-                 the unit disk) (seed 2) followed by Newton steps, b complex
-                 normal (seed 3).
+* ``square1024`` 2D, 1024 x 1024 nodes, mu = 2, psi = (Newton steps from
+                 psi = 1, at most five, until ||GL||_R <= 1e-7) + 0.1 * (uniform
+                 in the unit disk) (seed 2); the solve is that state's Newton
+                 system.
 * ``cube128``    3D, 128^3 nodes, mu = 1, field along (1,1,1)/sqrt(3),
                  psi == 1 (the state the paper's Section 4 experiments use) or
                  psi uniform in the unit disk (seed 4); b complex normal (seed 5).

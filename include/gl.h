@@ -54,7 +54,9 @@ typedef enum {
     GL_ERR_ARG = 1,           /* invalid argument (null handle, bad size, ...) */
     GL_ERR_CUDA = 2,          /* a CUDA runtime call or kernel failed */
     GL_ERR_OOM = 3,           /* device allocation failed */
-    GL_ERR_NOT_CONVERGED = 4, /* solve stopped at maxit; x holds the last iterate */
+    GL_ERR_NOT_CONVERGED = 4, /* solve stopped at maxit, or (FP64) its true residual stayed above tol while
+                                 the MINRES estimate fell six decades below it (the attainable accuracy
+                                 of the iterate); x holds the last iterate */
     GL_ERR_BREAKDOWN = 5,     /* preconditioner not positive definite (<v, R v>_R < 0) */
     GL_ERR_NAN = 6,           /* a non-finite residual or scalar appeared */
     GL_ERR_TIMEOUT = 7,       /* a bounded device-side wait ran out */
