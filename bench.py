@@ -43,6 +43,23 @@ METRIC = "Jacobian solves/s @1e-10 rel-res (3D 128^3): mixed+learned vs FP64 GPU
 UNIT = "solves/s"
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest of every rank's x (the slowest rank's time); x itself on one rank."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units of work all ranks processed (replicas: the same on each) per second of
+    the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -275,11 +292,7 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
         prof = gl.gl_profile_end() if profiling else None
-        ms = ev0.elapsed_time(ev1)
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
         return ms, infos, prof
 
     # FP64 GPU form (context and the ratio the metric asks for)
@@ -363,16 +376,12 @@ def main():
             solve(opts_final)
             x_pin.copy_(x, non_blocking=True)
         torch.cuda.synchronize()
-        te = time.perf_counter() - te0
-        if dist:
-            t = torch.tensor([te], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * args.steps / te, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
+        te = max_over_ranks(time.perf_counter() - te0, dist, dev)
+        e2e = {"value": whole_job_rate(args.steps, world, te), "unit": UNIT, "h2d_bytes_per_step": 16 * n,
                "d2h_bytes_per_step": 16 * n}
 
-    value = world * args.steps / (ms / 1e3)
-    value64 = world * len(infos64) / (ms64 / 1e3)
+    value = whole_job_rate(args.steps, world, ms / 1e3)
+    value64 = whole_job_rate(len(infos64), world, ms64 / 1e3)
     peak, peak_kind = peaks()
 
     # live per-class timing (CUDA events around every launch of the class, on the
