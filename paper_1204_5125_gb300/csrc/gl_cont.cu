@@ -117,7 +117,8 @@ __global__ void k_scaled_diff(int64_t n, const double2 *__restrict__ x, const do
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) t[i] = make_double2(sc * (x[i].x - y[i].x), sc * (x[i].y - y[i].y));
 }
-__global__ void k_scale_neg(int64_t n, const double2 *__restrict__ x, double sc, double2 *__restrict__ y) {
+// y = sc x
+__global__ void k_scale(int64_t n, const double2 *__restrict__ x, double sc, double2 *__restrict__ y) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) y[i] = make_double2(sc * x[i].x, sc * x[i].y);
 }
@@ -298,7 +299,7 @@ gl_status gl_continuation(gl_mesh m, void *psi_v, const gl_cont_options *o, gl_c
             }
             if (it == o->newton_maxit) break;
             P.reset(C.setup(psi, P.p));
-            k_scale_neg<<<C.G(), 256, 0, s>>>(n, W.r.get(), -1.0, W.b.get());
+            k_scale<<<C.G(), 256, 0, s>>>(n, W.r.get(), -1.0, W.b.get());
             GL_LAUNCH_CHECK();
             int k = C.solve(psi, P.p, W.b.get(), W.a.get());
             if (k < 0) break;
@@ -315,11 +316,11 @@ gl_status gl_continuation(gl_mesh m, void *psi_v, const gl_cont_options *o, gl_c
         // first tangent: J c = -dGL/dmu, t = (c, 1) / norm
         P.reset(C.setup(psi, P.p));
         residual_dmu(m, psi, W.r.get(), s);
-        k_scale_neg<<<C.G(), 256, 0, s>>>(n, W.r.get(), -1.0, W.b.get());
+        k_scale<<<C.G(), 256, 0, s>>>(n, W.r.get(), -1.0, W.b.get());
         GL_LAUNCH_CHECK();
         GL_REQUIRE(C.solve(psi, P.p, W.b.get(), W.c.get()) >= 0, GL_ERR_NOT_CONVERGED, "tangent solve failed");
         double nrm = std::sqrt(C.ip(W.c.get(), W.c.get()) + 1.0);
-        k_scale_neg<<<C.G(), 256, 0, s>>>(n, W.c.get(), 1.0 / nrm, W.t.get());
+        k_scale<<<C.G(), 256, 0, s>>>(n, W.c.get(), 1.0 / nrm, W.t.get());
         GL_LAUNCH_CHECK();
         double t_mu = 1.0 / nrm;
         double ds = o->ds;
@@ -349,12 +350,12 @@ gl_status gl_continuation(gl_mesh m, void *psi_v, const gl_cont_options *o, gl_c
                     if (it == o->newton_maxit || !std::isfinite(g)) break;
                     const double ncond = C.ip(W.t.get(), psi) - t_psi_s + t_mu * (mu_n - mu_s) - ds;
                     P.reset(C.setup(psi, P.p));
-                    k_scale_neg<<<C.G(), 256, 0, s>>>(n, W.r.get(), -1.0, W.b.get());
+                    k_scale<<<C.G(), 256, 0, s>>>(n, W.r.get(), -1.0, W.b.get());
                     GL_LAUNCH_CHECK();
                     const int ka = C.solve(psi, P.p, W.b.get(), W.a.get());
                     if (ka < 0) break;
                     residual_dmu(m, psi, W.r.get(), s);
-                    k_scale_neg<<<C.G(), 256, 0, s>>>(n, W.r.get(), -1.0, W.b.get());
+                    k_scale<<<C.G(), 256, 0, s>>>(n, W.r.get(), -1.0, W.b.get());
                     GL_LAUNCH_CHECK();
                     if (C.solve(psi, P.p, W.b.get(), W.c.get()) < 0) break;
                     const double dmu = (-ncond - C.ip(W.t.get(), W.a.get())) / (t_mu + C.ip(W.t.get(), W.c.get()));
@@ -382,7 +383,7 @@ gl_status gl_continuation(gl_mesh m, void *psi_v, const gl_cont_options *o, gl_c
             GL_LAUNCH_CHECK();
             const double dmu = mu_n - mu_s;
             nrm = std::sqrt(C.ip(W.a.get(), W.a.get()) + dmu * dmu);
-            k_scale_neg<<<C.G(), 256, 0, s>>>(n, W.a.get(), 1.0 / nrm, W.t.get());
+            k_scale<<<C.G(), 256, 0, s>>>(n, W.a.get(), 1.0 / nrm, W.t.get());
             GL_LAUNCH_CHECK();
             t_mu = dmu / nrm;
             C.record(pts[np], psi, g, ds, steps, last, retries);
