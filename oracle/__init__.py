@@ -75,6 +75,10 @@ def lib():
             L.glref_mesh_create.argtypes = [C.c_int, C.c_int, C.c_double, _f64p, _f64p]
             L.glref_mesh_create_edge.restype = vp
             L.glref_mesh_create_edge.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _f64p, _f64p]
+            L.glref_mesh_create_dipole.restype = vp
+            L.glref_mesh_create_dipole.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _f64p, _f64p]
+            L.glref_edge_integral1.restype = C.c_double
+            L.glref_edge_integral1.argtypes = [vp, _f64p, _f64p]
             L.glref_residual_dmu.argtypes = [vp, _c128p, _c128p]
             L.glref_mesh_destroy.argtypes = [vp]
             for f in ("glref_mesh_n", "glref_mesh_nedges", "glref_mesh_nnz"):
@@ -161,11 +165,18 @@ class Mesh:
     """Structured square (dim=2) or cube (dim=3) mesh of N nodes per side on the
     square/cube of side `edge` centred at the origin, with A(x) = (mu/2) bhat x x + a0."""
 
-    def __init__(self, dim: int, N: int, mu: float, bhat=(0.0, 0.0, 1.0), a0=(0.0, 0.0, 0.0), edge: float = 1.0):
+    def __init__(self, dim: int, N: int, mu: float, bhat=(0.0, 0.0, 1.0), a0=(0.0, 0.0, 0.0), edge: float = 1.0,
+                 dipole=None):
+        """dipole=(x0, m): A = mu A_d, the field of a dipole of moment m at x0 (bhat, a0 unused)."""
         self._lib = lib()
         b = np.ascontiguousarray(bhat, dtype=np.float64)
         a = np.ascontiguousarray(a0, dtype=np.float64)
-        self.ptr = self._lib.glref_mesh_create_edge(dim, N, float(edge), float(mu), b, a)
+        if dipole is None:
+            self.ptr = self._lib.glref_mesh_create_edge(dim, N, float(edge), float(mu), b, a)
+        else:
+            xd = np.ascontiguousarray(dipole[0], dtype=np.float64)
+            md = np.ascontiguousarray(dipole[1], dtype=np.float64)
+            self.ptr = self._lib.glref_mesh_create_dipole(dim, N, float(edge), float(mu), xd, md)
         if not self.ptr:
             raise ValueError("glref_mesh_create failed")
         self.dim, self.N, self.mu, self.edge = dim, N, float(mu), float(edge)
@@ -225,6 +236,11 @@ class Mesh:
         y = np.zeros(self.n, np.complex128)
         self._lib.glref_jacobian_apply(self.ptr, _c128(psi), _c128(phi), y)
         return y
+
+    def edge_integral1(self, xa, xb) -> float:
+        """Integral of the mesh's potential per unit mu along the segment xa -> xb."""
+        return self._lib.glref_edge_integral1(self.ptr, np.ascontiguousarray(xa, dtype=np.float64),
+                                              np.ascontiguousarray(xb, dtype=np.float64))
 
     def residual_dmu(self, psi):
         """d GL / d mu at fixed psi."""

@@ -275,6 +275,8 @@ typedef struct glref_mesh {
     int dim, N;
     int64_t n;
     double h, mu, bhat[3], a0[3], edge;
+    int dipole;                 /* 0: A = (mu/2) bhat x x + a0; 1: A = mu A_d (dipole at xd, moment md) */
+    double xd[3], md[3];
     double *x;     /* n x 3 node coordinates (z = 0 in 2D) */
     double *vol;   /* |V_j| */
     int64_t ne;    /* kept edges, (j < k) lexicographic */
@@ -296,9 +298,71 @@ static void vector_potential(const glref_mesh *m, const double *x, double *A) {
     A[2] = 0.5 * m->mu * (b[0] * x[1] - b[1] * x[0]) + m->a0[2];
 }
 
-/* integral of A . dl along the straight edge from xa to xb.  A is affine, so the
- * midpoint rule is exact (the quadrature remark after Eq. link variable). */
+/* Gauss-Legendre rule of GLREF_GL_POINTS points on [-1, 1]: the nodes are the
+ * roots of the Legendre polynomial P_Q, found by Newton's method from the
+ * Chebyshev-like start cos(pi (i + 3/4) / (Q + 1/2)), and the weights are
+ * 2 / ((1 - x^2) P_Q'(x)^2). */
+#define GLREF_GL_POINTS 8
+static void gauss_legendre(int q, double *x, double *w) {
+    for (int i = 0; i < q; ++i) {
+        double z = cos(acos(-1.0) * (i + 0.75) / (q + 0.5)), dp = 0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1, p1 = z;  /* P_0, P_1, then the three-term recurrence up to P_q */
+            for (int k = 2; k <= q; ++k) {
+                double p2 = ((2.0 * k - 1) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = q * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+/* the dipole potential A_d(x) = m x (x - x0) / |x - x0|^3 (Sec. 4), per unit mu */
+static void dipole_potential(const glref_mesh *m, const double *x, double *A) {
+    double r[3] = {x[0] - m->xd[0], x[1] - m->xd[1], x[2] - m->xd[2]};
+    double r2 = dot3(r, r), ir3 = 1.0 / (r2 * sqrt(r2));
+    A[0] = (m->md[1] * r[2] - m->md[2] * r[1]) * ir3;
+    A[1] = (m->md[2] * r[0] - m->md[0] * r[2]) * ir3;
+    A[2] = (m->md[0] * r[1] - m->md[1] * r[0]) * ir3;
+}
+
+/* integral of A . dl along the straight edge from xa to xb per unit mu of the
+ * mu-dependent part (the link phase is mu times this plus the a0 part) */
+static double edge_integral1(const glref_mesh *m, const double *xa, const double *xb) {
+    double d[3];
+    for (int c = 0; c < 3; ++c) d[c] = xb[c] - xa[c];
+    if (!m->dipole) {
+        /* affine A: the midpoint rule is exact (the quadrature remark after Eq. link variable) */
+        double mid[3], A[3];
+        const double *b = m->bhat;
+        for (int c = 0; c < 3; ++c) mid[c] = 0.5 * (xa[c] + xb[c]);
+        A[0] = 0.5 * (b[1] * mid[2] - b[2] * mid[1]);
+        A[1] = 0.5 * (b[2] * mid[0] - b[0] * mid[2]);
+        A[2] = 0.5 * (b[0] * mid[1] - b[1] * mid[0]);
+        return dot3(A, d);
+    }
+    /* A_d is not polynomial: Gauss-Legendre along the edge (the quadrature
+     * remark after Eq. link variable) */
+    double gx[GLREF_GL_POINTS], gw[GLREF_GL_POINTS], s = 0;
+    gauss_legendre(GLREF_GL_POINTS, gx, gw);
+    for (int i = 0; i < GLREF_GL_POINTS; ++i) {
+        double t = 0.5 * (1.0 + gx[i]), x[3], A[3];
+        for (int c = 0; c < 3; ++c) x[c] = xa[c] + t * d[c];
+        dipole_potential(m, x, A);
+        s += 0.5 * gw[i] * dot3(A, d);
+    }
+    return s;
+}
+
+/* integral of A . dl along the straight edge from xa to xb */
 static double edge_integral(const glref_mesh *m, const double *xa, const double *xb) {
+    if (m->dipole) return m->mu * edge_integral1(m, xa, xb);
     double mid[3], d[3], A[3];
     for (int c = 0; c < 3; ++c) {
         mid[c] = 0.5 * (xa[c] + xb[c]);
@@ -306,6 +370,11 @@ static double edge_integral(const glref_mesh *m, const double *xa, const double 
     }
     vector_potential(m, mid, A);
     return dot3(A, d);
+}
+
+/* exposed for the tests: the per-unit-mu edge integral on this mesh's potential */
+double glref_edge_integral1(const glref_mesh *m, const double *xa, const double *xb) {
+    return edge_integral1(m, xa, xb);
 }
 
 /* per-node neighbour table used while summing simplex contributions */
@@ -366,19 +435,45 @@ static int cell_simplices(const glref_mesh *m, int i, int j, int k, int64_t vid[
 
 /* The square/cube of side `edge` centred at the origin (the paper's domains have
  * edge lengths of order 10; the unit domain is glref_mesh_create). */
+static glref_mesh *mesh_assemble(glref_mesh *m);
+
 glref_mesh *glref_mesh_create_edge(int dim, int N, double edge, double mu, const double *bhat, const double *a0) {
     if ((dim != 2 && dim != 3) || N < 2 || !(edge > 0)) return NULL;
     glref_mesh *m = xcalloc(1, sizeof *m);
     m->dim = dim;
     m->N = N;
-    m->n = (dim == 2) ? (int64_t)N * N : (int64_t)N * N * N;
-    m->h = edge / (N - 1);
     m->edge = edge;
     m->mu = mu;
     for (int c = 0; c < 3; ++c) {
         m->bhat[c] = bhat ? bhat[c] : (c == 2 ? 1.0 : 0.0);
         m->a0[c] = a0 ? a0[c] : 0.0;
     }
+    return mesh_assemble(m);
+}
+
+/* The same domain in mu A_d, the field of a magnetic dipole of moment md at xd
+ * (Sec. 4: xd = (0,0,1) for the 2D domains, (0,0,6) for the 3D ones, md = e_z). */
+glref_mesh *glref_mesh_create_dipole(int dim, int N, double edge, double mu, const double *xd, const double *md) {
+    if ((dim != 2 && dim != 3) || N < 2 || !(edge > 0) || !xd || !md) return NULL;
+    glref_mesh *m = xcalloc(1, sizeof *m);
+    m->dim = dim;
+    m->N = N;
+    m->edge = edge;
+    m->mu = mu;
+    m->dipole = 1;
+    for (int c = 0; c < 3; ++c) {
+        m->bhat[c] = c == 2 ? 1.0 : 0.0;
+        m->xd[c] = xd[c];
+        m->md[c] = md[c];
+    }
+    return mesh_assemble(m);
+}
+
+static glref_mesh *mesh_assemble(glref_mesh *m) {
+    const int dim = m->dim, N = m->N;
+    const double edge = m->edge;
+    m->n = (dim == 2) ? (int64_t)N * N : (int64_t)N * N * N;
+    m->h = edge / (N - 1);
     int64_t n = m->n;
     int nz = (dim == 2) ? 1 : N;
 
@@ -621,17 +716,7 @@ void glref_residual_dmu(const glref_mesh *m, const cplx *psi, cplx *out) {
     for (int64_t i = 0; i < m->n; ++i) out[i] = 0;
     for (int64_t e = 0; e < m->ne; ++e) {
         const int64_t j = m->ej[e], k = m->ek[e];
-        const double *xa = m->x + 3 * j, *xb = m->x + 3 * k;
-        double mid[3], d[3], A1[3];
-        for (int c = 0; c < 3; ++c) {
-            mid[c] = 0.5 * (xa[c] + xb[c]);
-            d[c] = xb[c] - xa[c];
-        }
-        const double *b = m->bhat;
-        A1[0] = 0.5 * (b[1] * mid[2] - b[2] * mid[1]);
-        A1[1] = 0.5 * (b[2] * mid[0] - b[0] * mid[2]);
-        A1[2] = 0.5 * (b[0] * mid[1] - b[1] * mid[0]);
-        const double th1 = dot3(A1, d);
+        const double th1 = edge_integral1(m, m->x + 3 * j, m->x + 3 * k);
         const cplx djk = I * th1 * m->alpha[e] * cexp(-I * m->theta[e]);
         out[j] += djk * psi[k];
         out[k] += conj(djk) * psi[j];
