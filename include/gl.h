@@ -55,7 +55,7 @@ typedef enum {
     GL_ERR_CUDA = 2,          /* a CUDA runtime call or kernel failed */
     GL_ERR_OOM = 3,           /* device allocation failed */
     GL_ERR_NOT_CONVERGED = 4, /* solve stopped at maxit, or (FP64) its true residual stayed above tol while
-                                 the MINRES estimate fell six decades below it (the attainable accuracy
+                                 the MINRES estimate fell nine decades below it (the attainable accuracy
                                  of the iterate); x holds the last iterate */
     GL_ERR_BREAKDOWN = 5,     /* preconditioner not positive definite (<v, R v>_R < 0) */
     GL_ERR_NAN = 6,           /* a non-finite residual or scalar appeared */
@@ -156,6 +156,16 @@ GL_API gl_status gl_mesh_create(int dim, int n_per_side, double mu, const double
  * square of edge 10). */
 GL_API gl_status gl_mesh_create_edge(int dim, int n_per_side, double edge, double mu, const double *bhat_host,
                                      void *stream, gl_mesh *out);
+/* The same domain in mu A_d, the field of a magnetic dipole (Sec. 4):
+ * A_d(x) = m x (x - x0) / |x - x0|^3, m = mom_host, x0 = x0_host (3 doubles
+ * each; the paper takes m = e_z and x0 = (0,0,1) in 2D, (0,0,6) in 3D).  The
+ * link phases are integrals of A_d along each edge by an 8-point
+ * Gauss-Legendre rule (A_d is not polynomial; the quadrature remark after Eq.
+ * link variable); they vary along every axis, so the lattice-table stencil is
+ * not used on such meshes.  x0 must lie outside the closed domain.
+ * gl_mesh_set_mu scales A_d by the new mu. */
+GL_API gl_status gl_mesh_create_dipole(int dim, int n_per_side, double edge, double mu, const double *x0_host,
+                                       const double *mom_host, void *stream, gl_mesh *out);
 GL_API gl_status gl_mesh_destroy(gl_mesh mesh);
 
 /* Changes the field strength of A = (mu/2) bhat x x in place: only the link

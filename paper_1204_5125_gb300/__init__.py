@@ -29,7 +29,7 @@ __all__ = [
     "gl_warmstart_predict", "gl_warmstart_grad", "gl_warmstart_train", "gl_warmstart_adam_step", "GL_WS_NPARAM",
     "gl_last_error", "EXPORTED", "GL_CYCLES_INF", "ContOptions", "ContPoint", "gl_mesh_create_edge",
     "gl_mesh_set_mu", "gl_residual_dmu", "gl_energy", "cont_options", "gl_continuation", "gl_precond_setup_like",
-    "GL_COLOR_SL", "GL_COLOR_JP",
+    "GL_COLOR_SL", "GL_COLOR_JP", "gl_mesh_create_dipole",
 ]
 
 GL_FP64, GL_MIXED, GL_MIXED_PRECOND = 0, 1, 2
@@ -48,7 +48,7 @@ EXPORTED = [
     "gl_batch_destroy", "gl_precond_cost", "gl_warmstart_create", "gl_warmstart_destroy", "gl_warmstart_get_params",
     "gl_warmstart_set_params", "gl_warmstart_predict", "gl_warmstart_grad", "gl_warmstart_train",
     "gl_warmstart_adam_step", "gl_last_error", "gl_mesh_create_edge", "gl_mesh_set_mu", "gl_residual_dmu",
-    "gl_energy", "gl_cont_options_default", "gl_continuation", "gl_precond_setup_like",
+    "gl_energy", "gl_cont_options_default", "gl_continuation", "gl_precond_setup_like", "gl_mesh_create_dipole",
 ]
 
 GL_WS_NPARAM = 4 * 64 * 128 + 2 * 64
@@ -158,6 +158,8 @@ def library(build_if_missing: bool = True):
             "gl_mesh_create_edge": [C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_double), vp,
                                     C.POINTER(vp)],
             "gl_mesh_set_mu": [vp, C.c_double, vp],
+            "gl_mesh_create_dipole": [C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), vp, C.POINTER(vp)],
             "gl_precond_setup_like": [vp, vp, C.POINTER(Options), vp, vp, C.POINTER(vp)],
             "gl_residual_dmu": [vp, vp, vp, vp],
             "gl_energy": [vp, vp, C.POINTER(C.c_double), vp],
@@ -233,6 +235,17 @@ def gl_mesh_create_edge(dim: int, n_per_side: int, edge: float, mu: float, bhat=
     b = (C.c_double * 3)(*bhat)
     out = C.c_void_p()
     _check(library().gl_mesh_create_edge(dim, n_per_side, float(edge), float(mu), b, _stream(stream), C.byref(out)))
+    return out
+
+
+def gl_mesh_create_dipole(dim: int, n_per_side: int, edge: float, mu: float, x0=(0.0, 0.0, 6.0),
+                          mom=(0.0, 0.0, 1.0), stream=None):
+    """Mesh in mu A_d, the field of a dipole of moment `mom` at `x0`."""
+    a = (C.c_double * 3)(*x0)
+    b = (C.c_double * 3)(*mom)
+    out = C.c_void_p()
+    _check(library().gl_mesh_create_dipole(dim, n_per_side, float(edge), float(mu), a, b, _stream(stream),
+                                           C.byref(out)))
     return out
 
 

@@ -96,6 +96,23 @@ gl_status gl_mesh_set_mu(gl_mesh m, double mu, void *stream) {
     });
 }
 
+gl_status gl_mesh_create_dipole(int dim, int n_per_side, double edge, double mu, const double *x0, const double *mom,
+                                void *stream, gl_mesh *out) {
+    return guard([&] {
+        GL_REQUIRE(out && x0 && mom, GL_ERR_ARG, "NULL argument");
+        *out = nullptr;
+        auto *m = new gl_mesh_s();
+        try {
+            mesh_create(m, dim, n_per_side, edge, mu, nullptr, as_stream(stream), x0, mom);
+        } catch (...) {
+            delete m;
+            throw;
+        }
+        *out = m;
+        return GL_OK;
+    });
+}
+
 gl_status gl_mesh_create_edge(int dim, int n_per_side, double edge, double mu, const double *bhat, void *stream,
                               gl_mesh *out) {
     return guard([&] {

@@ -9,6 +9,7 @@ struct gl_mesh_s {
     int64_t n = 0;
     double h = 0, mu = 0, bhat[3] = {0, 0, 1};
     double edge = 1;                      // side of the square / cube
+    int dipole = 0;                       // 1: A = mu A_d (dipole field) instead of (mu/2) bhat x x
     int64_t version = 0;                  // bumped by every change of mu (gl_mesh_set_mu)
     // canonical (node-order) data
     gl::CsrDev khat;                      // K-hat, columns ascending
@@ -138,7 +139,9 @@ struct gl_prec_s {
 namespace gl {
 
 // gl_mesh.cu
-void mesh_create(gl_mesh_s *m, int dim, int N, double edge, double mu, const double *bhat, cudaStream_t s);
+// dip_x0, dip_m (both or neither): A = mu A_d, the field of a dipole of moment dip_m at dip_x0
+void mesh_create(gl_mesh_s *m, int dim, int N, double edge, double mu, const double *bhat, cudaStream_t s,
+                 const double *dip_x0 = nullptr, const double *dip_m = nullptr);
 // new field strength: rewrites every phase-dependent value in place (K-hat, K, the
 // FP32 copy and the lattice tables); bumps m->version
 void mesh_set_mu(gl_mesh_s *m, double mu, cudaStream_t s);

@@ -14,10 +14,16 @@
 namespace gl {
 
 // ---------------------------------------------------------------- lattice geometry
+constexpr int GL_QUAD = 8;  // Gauss-Legendre points of the dipole's edge phases
+
 struct Lattice {
     int dim, N;
     double h, mu, b[3];
     double x0;  // coordinate of the first node on every axis (-edge / 2)
+    // A = mu A_d, the dipole field (moment md at xd), when dipole != 0; its edge
+    // phases use the Gauss-Legendre rule (gx, gw) on [-1, 1]
+    int dipole;
+    double xd[3], md[3], gx[GL_QUAD], gw[GL_QUAD];
     __device__ __host__ int64_t id(int i, int j, int k) const { return (int64_t)i + (int64_t)N * ((int64_t)j + (int64_t)N * k); }
     __device__ __host__ void coords(int64_t v, int &i, int &j, int &k) const {
         i = (int)(v % N);
@@ -252,8 +258,12 @@ __global__ void k_row_len(Lattice L, int64_t n, int ndir, const double *ealpha, 
     fwd[v] = f;
 }
 
-// integral of A = (mu/2) bhat x x along the straight edge from xa to xb (midpoint rule)
+__device__ double edge_phase1(const Lattice &L, const double *xa, const double *xb);
+
+// integral of A = (mu/2) bhat x x along the straight edge from xa to xb (midpoint
+// rule, exact for the affine A), or of mu A_d for the dipole
 __device__ double edge_phase(const Lattice &L, const double *xa, const double *xb) {
+    if (L.dipole) return L.mu * edge_phase1(L, xa, xb);
     double m[3], d[3];
     for (int c = 0; c < 3; ++c) {
         m[c] = 0.5 * (xa[c] + xb[c]);
@@ -265,12 +275,29 @@ __device__ double edge_phase(const Lattice &L, const double *xa, const double *x
     return A0 * d[0] + A1 * d[1] + A2 * d[2];
 }
 
-// the same integral per unit mu (A_1 = (1/2) bhat x x): theta = mu theta1
+// the same integral per unit mu (A_1 = (1/2) bhat x x): theta = mu theta1; for
+// the dipole A_1 = A_d = md x (x - xd) / |x - xd|^3, which is not polynomial,
+// integrated with the Gauss-Legendre rule along the edge
 __device__ double edge_phase1(const Lattice &L, const double *xa, const double *xb) {
     double m[3], d[3];
     for (int c = 0; c < 3; ++c) {
         m[c] = 0.5 * (xa[c] + xb[c]);
         d[c] = xb[c] - xa[c];
+    }
+    if (L.dipole) {
+        double sum = 0;
+        for (int q = 0; q < GL_QUAD; ++q) {
+            const double t = 0.5 * (1.0 + L.gx[q]);
+            double r[3];
+            for (int c = 0; c < 3; ++c) r[c] = xa[c] + t * d[c] - L.xd[c];
+            const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+            const double ir3 = 1.0 / (r2 * sqrt(r2));
+            const double A0 = (L.md[1] * r[2] - L.md[2] * r[1]) * ir3;
+            const double A1 = (L.md[2] * r[0] - L.md[0] * r[2]) * ir3;
+            const double A2 = (L.md[0] * r[1] - L.md[1] * r[0]) * ir3;
+            sum += 0.5 * L.gw[q] * (A0 * d[0] + A1 * d[1] + A2 * d[2]);
+        }
+        return sum;
     }
     double A0 = 0.5 * (L.b[1] * m[2] - L.b[2] * m[1]);
     double A1 = 0.5 * (L.b[2] * m[0] - L.b[0] * m[2]);
@@ -561,7 +588,32 @@ void to_float(const double *in, float *out, int64_t n, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- mesh creation
-void mesh_create(gl_mesh_s *m, int dim, int N, double edge, double mu, const double *bhat, cudaStream_t s) {
+// nodes and weights of the q-point Gauss-Legendre rule on [-1, 1]: the roots of
+// the Legendre polynomial P_q by Newton's method (three-term recurrence for P_q,
+// P_q' from P_q and P_{q-1}), weights 2 / ((1 - x^2) P_q'(x)^2)
+static void legendre_rule(int q, double *x, double *w) {
+    const double pi = std::acos(-1.0);
+    for (int i = 0; i < q; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (q + 0.5)), der = 0;
+        for (int it = 0; it < 100; ++it) {
+            double pm = 1, pc = z;
+            for (int k = 2; k <= q; ++k) {
+                const double pn = ((2.0 * k - 1) * z * pc - (k - 1.0) * pm) / k;
+                pm = pc;
+                pc = pn;
+            }
+            der = q * (z * pc - pm) / (z * z - 1.0);
+            const double step = pc / der;
+            z -= step;
+            if (std::fabs(step) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * der * der);
+    }
+}
+
+void mesh_create(gl_mesh_s *m, int dim, int N, double edge, double mu, const double *bhat, cudaStream_t s,
+                 const double *dip_x0, const double *dip_m) {
     GL_REQUIRE(dim == 2 || dim == 3, GL_ERR_ARG, "dim must be 2 or 3");
     GL_REQUIRE(N >= 2, GL_ERR_ARG, "n_per_side must be >= 2");
     GL_REQUIRE(edge > 0 && std::isfinite(edge), GL_ERR_ARG, "edge length must be positive");
@@ -573,6 +625,20 @@ void mesh_create(gl_mesh_s *m, int dim, int N, double edge, double mu, const dou
     L.h = edge / (N - 1);
     L.x0 = -0.5 * edge;
     L.mu = mu;
+    L.dipole = (dip_x0 && dip_m) ? 1 : 0;
+    for (int c = 0; c < 3; ++c) {
+        L.xd[c] = L.dipole ? dip_x0[c] : 0.0;
+        L.md[c] = L.dipole ? dip_m[c] : 0.0;
+    }
+    legendre_rule(GL_QUAD, L.gx, L.gw);
+    if (L.dipole) {
+        // the dipole must lie outside the closed domain
+        bool inside = true;
+        for (int c = 0; c < dim; ++c) inside = inside && std::fabs(dip_x0[c]) <= 0.5 * edge;
+        if (dim == 2) inside = inside && dip_x0[2] == 0.0;
+        GL_REQUIRE(!inside, GL_ERR_ARG, "the dipole must lie outside the domain");
+    }
+    m->dipole = L.dipole;
     double b[3] = {0, 0, 1};
     if (bhat) {
         double nb = std::sqrt(bhat[0] * bhat[0] + bhat[1] * bhat[1] + bhat[2] * bhat[2]);

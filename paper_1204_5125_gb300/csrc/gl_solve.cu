@@ -732,10 +732,10 @@ static MinresResult minres(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, con
     }
     // Stall test: with the double-FP32 Jacobian the ~48-bit apply limits the true
     // residual, so a recurrence three decades past tol hands over to FP64; in
-    // FP64 a true residual that stays above tol while the recurrence runs six
+    // FP64 a true residual that stays above tol while the recurrence runs nine
     // decades past it has reached the attainable accuracy (the rounding floor of
     // J applied to the iterate), and further iterations only repeat the test.
-    k_set_params<<<1, 1, 0, s>>>(S, tol, maxit, use_true ? 1 : 0, !use_true ? 0.0 : (df ? 1e-3 : 1e-6));
+    k_set_params<<<1, 1, 0, s>>>(S, tol, maxit, use_true ? 1 : 0, !use_true ? 0.0 : (df ? 1e-3 : 1e-9));
     GL_LAUNCH_CHECK();
     replay(W.init, s);
     MinresDev h;
