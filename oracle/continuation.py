@@ -49,6 +49,18 @@ def _defaults(**kw):
     return o
 
 
+def bordered_step(mesh, psi, t_psi, t_mu, ncond, r, vol_tot, **solver):
+    """One corrector step: solves J a = -r and J c = -dGL/dmu with one R_1(psi)
+    and eliminates the border row <t_psi, .>_R / |Omega| + t_mu (.) = -ncond.
+    Returns (dpsi, dmu, info_a, info_c)."""
+    ip = lambda x, y: mesh.inner_r(x, y) / vol_tot  # noqa: E731
+    P = Precond(mesh, psi, **solver)
+    a, ia = P.minres(-r)
+    c, ic = P.minres(-mesh.residual_dmu(psi))
+    dmu = (-ncond - ip(t_psi, a)) / (t_mu + ip(t_psi, c))
+    return a + dmu * c, dmu, ia, ic
+
+
 def _newton_fixed_mu(dim, N, edge, bhat, mu, psi, o):
     """Newton at fixed mu: returns (psi, steps, last iterations, total iterations, gnorm)."""
     steps = last = total = 0
@@ -109,14 +121,12 @@ def continuation(dim, N, edge, psi0, mu0, bhat=(0.0, 0.0, 1.0), **kw):
                 if it == o["newton_maxit"]:
                     break
                 ncond = ip(mn, t_psi, psi_n - psi) + t_mu * (mu_n - mu) - ds
-                P = Precond(mn, psi_n, tol=o["linear_tol"], maxit=o["maxit"], max_coarse=o["max_coarse"])
-                a, ia = P.minres(-r)
-                c, ic = P.minres(-mn.residual_dmu(psi_n))
+                dpsi, dmu, ia, ic = bordered_step(mn, psi_n, t_psi, t_mu, ncond, r, vol_tot, tol=o["linear_tol"],
+                                                  maxit=o["maxit"], max_coarse=o["max_coarse"])
                 total += ia.iters + ic.iters
                 if not (ia.converged and ic.converged):
                     break
-                dmu = (-ncond - ip(mn, t_psi, a)) / (t_mu + ip(mn, t_psi, c))
-                psi_n = psi_n + a + dmu * c
+                psi_n = psi_n + dpsi
                 mu_n = mu_n + dmu
                 steps += 1
                 last = ia.iters

@@ -97,3 +97,37 @@ def test_oracle_continuation_reproduces_fig4(oracle_mod):
     k = next(k for k in range(fold, len(mus) - 1) if (mus[k] - mu_p) * (mus[k + 1] - mu_p) <= 0)
     w = (mu_p - mus[k]) / (mus[k + 1] - mus[k])
     assert abs(2.0 * ((1 - w) * F[k] + w * F[k + 1]) - F_p) <= 0.01
+
+
+def test_bordered_step_solves_the_bordered_system(oracle_mod):
+    """The corrector's block elimination (two MINRES solves with J and a scalar
+    border equation) against a dense solve of the realified bordered system
+    [J, dGL/dmu; t^T W, t_mu] (dpsi, dmu) = -(GL, n), W the |V|/|Omega| weights
+    of the arclength row, on a 5 x 5 mesh."""
+    from oracle import continuation as ocont
+
+    N, edge, mu = 5, 4.0, 0.6
+    m = oracle_mod.Mesh(2, N, mu, edge=edge)
+    n, vol_tot = m.n, edge ** 2
+    psi = gi.psi_noisy_one(n, 11, amplitude=0.3)
+    g = np.random.default_rng(12)
+    t_psi = g.standard_normal(n) + 1j * g.standard_normal(n)
+    t_mu, ncond = 0.7, 0.05
+    r = m.residual(psi)
+    dpsi, dmu, ia, ic = ocont.bordered_step(m, psi, t_psi, t_mu, ncond, r, vol_tot, tol=1e-13, maxit=2000,
+                                            max_coarse=4)
+    assert ia.converged and ic.converged
+    Jr = m.jacobian_dense_real(psi)
+    gm = m.residual_dmu(psi)
+    vol = m.volumes()
+    A = np.zeros((2 * n + 1, 2 * n + 1))
+    A[:2 * n, :2 * n] = Jr
+    A[:2 * n, 2 * n] = np.concatenate([gm.real, gm.imag])
+    # <t, x>_R / |Omega| = sum |V| (Re t Re x + Im t Im x) / |Omega|
+    A[2 * n, :2 * n] = np.concatenate([vol * t_psi.real, vol * t_psi.imag]) / vol_tot
+    A[2 * n, 2 * n] = t_mu
+    rhs = -np.concatenate([r.real, r.imag, [ncond]])
+    sol = np.linalg.solve(A, rhs)
+    ref = sol[:n] + 1j * sol[n:2 * n]
+    assert np.linalg.norm(dpsi - ref) <= 1e-8 * np.linalg.norm(ref)
+    assert dmu == pytest.approx(sol[2 * n], rel=1e-8, abs=1e-12)
