@@ -97,3 +97,15 @@ def test_fig3_cube_in_dipole_shape(oracle_mod):
     assert its["unprec"][1] > 1.3 * its["unprec"][0]
     assert abs(its["R1"][1] - its["R1"][0]) <= 2 and abs(its["R1"][1] - fig["R1"][2]) <= 4
     assert abs(its["Rinf"][1] - its["Rinf"][0]) <= 1 and max(its["Rinf"]) < min(its["R1"])
+
+
+@pytest.mark.parametrize("dim,N,L,x0", [(3, 6, L3, X0_3D), (2, 9, L2, X0_2D)])
+def test_dmu_on_dipole_meshes(oracle_mod, dim, N, L, x0):
+    """d GL / d mu on a dipole mesh (phase per unit mu from the quadrature) against
+    the central difference of two independently assembled meshes."""
+    mu, eps = 0.9, 1e-5
+    psi = np.ones(N ** dim, complex) + 0.2 * np.exp(1j * np.arange(N ** dim))
+    d = oracle_mod.Mesh(dim, N, mu, edge=L, dipole=(x0, MOM)).residual_dmu(psi)
+    fd = (oracle_mod.Mesh(dim, N, mu + eps, edge=L, dipole=(x0, MOM)).residual(psi)
+          - oracle_mod.Mesh(dim, N, mu - eps, edge=L, dipole=(x0, MOM)).residual(psi)) / (2 * eps)
+    assert np.linalg.norm(d - fd) <= 1e-7 * np.linalg.norm(d)
