@@ -208,17 +208,19 @@ GL_API gl_status gl_jacobian_apply(gl_mesh mesh, const void *psi_dev, const void
                             int precision, void *stream);
 
 /* The same Jacobian apply (FP64) as gl_jacobian_apply, for callers that cannot
- * let the library allocate device memory during the call: code inside CUDA
- * stream capture, applications with a fixed device-memory budget or their own
- * pool, and latency-critical loops (cudaMalloc/cudaFree may synchronise the
- * device).  The paper has no counterpart; this is an interface convenience.
+ * let the library allocate device memory during the call: applications with a
+ * fixed device-memory budget or their own pool (an allocation behind their back
+ * can fail or fragment it), and latency-critical loops (cudaMalloc/cudaFree may
+ * synchronise the device).  The paper has no counterpart; this is an interface
+ * convenience.
  * It allocates nothing: its working buffers live in one static device array of
  * GL_NOALLOC_MAX_NODES = 262144 nodes x 3 complex doubles (12 MiB) that every
  * GPU loading the library holds until exit.  Meshes with more nodes are rejected
  * with GL_ERR_CAPACITY.  All calls on a device share that array (it keeps the
  * last call's contents; nothing needs to start at zero), so calls whose work
  * overlaps on the GPU race.  The first call on each device looks up the array's
- * device address with that device current; make it before any stream capture.
+ * device address with that device current; that first call should come before
+ * any stream capture.
  * Arguments and layouts as gl_jacobian_apply. */
 GL_API gl_status gl_jacobian_apply_noalloc(gl_mesh mesh, const void *psi_dev, const void *phi_dev, void *y_dev,
                                            void *stream);

@@ -3,13 +3,12 @@
 //
 // gl_jacobian_apply keeps its three reordering buffers (psi, phi and y in the
 // red-black solve ordering) in per-mesh memory that it allocates with
-// cudaMalloc on first use.  Some callers cannot let a call allocate: code that
-// runs inside CUDA stream capture (cudaMalloc is illegal while a stream
-// captures), applications that manage a fixed device-memory budget or their own
-// pool, and latency-critical loops (cudaMalloc/cudaFree can synchronise the
-// device).  This entry point takes the three buffers from one file-scope
-// __device__ array instead, of a fixed size that every GPU loading the library
-// holds until the process exits.
+// cudaMalloc on first use.  Some callers cannot let a call allocate:
+// applications that manage a fixed device-memory budget or their own pool (an
+// allocation behind their back can fail or fragment it), and latency-critical
+// loops (cudaMalloc/cudaFree can synchronise the device).  This entry point
+// takes the three buffers from one file-scope __device__ array instead, of a
+// fixed size that every GPU loading the library holds until the process exits.
 //
 // Notes for callers:
 //   * capacity: n <= GL_NOALLOC_MAX_NODES nodes (the array holds 3 n complex
@@ -19,8 +18,8 @@
 //     before it is read within a call), but two calls whose work overlaps on
 //     the GPU (different streams, or different host threads) race on it;
 //   * the first call on each device looks up the device address of the array
-//     (cudaGetSymbolAddress) with that device current; make that first call
-//     before any stream capture on the device.
+//     (cudaGetSymbolAddress) with that device current; that first call should
+//     come before any stream capture on the device.
 #include <mutex>
 
 #include "gl_internal.cuh"
@@ -73,5 +72,11 @@ extern "C" gl_status gl_jacobian_apply_noalloc(gl_mesh m, const void *psi, const
     } catch (const gl::Error &e) {
         gl::set_error(e.msg);
         return e.code;
+    } catch (const std::bad_alloc &) {
+        gl::set_error("host allocation failed");
+        return GL_ERR_OOM;
+    } catch (const std::exception &e) {
+        gl::set_error(e.what());
+        return GL_ERR_CUDA;
     }
 }
