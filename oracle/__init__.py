@@ -29,11 +29,12 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile glref.c into a shared library with gcc (plain C11, -O2)."""
+    """Compile glref.c into a shared library with gcc (plain C11, -O2, OpenMP for the
+    optional multi-threaded row loops)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -65,6 +66,14 @@ class Info(C.Structure):
     ]
 
 
+def set_threads(n: int) -> int:
+    """Host threads for the oracle's row loops (results do not depend on it); 0 or
+    less: every processor.  Returns the count now in use."""
+    L = lib()
+    L.glref_set_threads(int(n) if n > 0 else L.glref_max_threads())
+    return L.glref_get_threads()
+
+
 def lib():
     global _lib
     with _lock:
@@ -77,6 +86,9 @@ def lib():
             L.glref_mesh_create_edge.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _f64p, _f64p]
             L.glref_mesh_create_dipole.restype = vp
             L.glref_mesh_create_dipole.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _f64p, _f64p]
+            L.glref_set_threads.argtypes = [C.c_int]
+            L.glref_get_threads.restype = C.c_int
+            L.glref_max_threads.restype = C.c_int
             L.glref_edge_integral1.restype = C.c_double
             L.glref_edge_integral1.argtypes = [vp, _f64p, _f64p]
             L.glref_residual_dmu.argtypes = [vp, _c128p, _c128p]

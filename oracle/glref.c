@@ -2,9 +2,12 @@
  * glref.c -- the CPU oracle for the Jacobian solve of the extreme type-II
  * Ginzburg-Landau problem (Schloemer & Vanroose, arXiv:1204.5125).
  *
- * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, single-threaded FP64
- * restatement of the paper's method, written to be checked against the paper
- * by eye.  Only the test suite, the smoke check and the benchmark's CPU
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow FP64 restatement of
+ * the paper's method, written to be checked against the paper by eye.  It runs
+ * on one host thread unless glref_set_threads asks for more; then only loops
+ * whose iterations write disjoint rows are shared out (OpenMP), while every sum
+ * across rows stays serial in index order, so the results are bit-identical for
+ * any thread count.  Only the test suite, the smoke check and the benchmark's CPU
  * baseline may load it.  It shares no code, header, table or helper with the
  * CUDA library, and the CUDA library never calls it.
  *
@@ -35,6 +38,24 @@
 #include <string.h>
 
 typedef double complex cplx;
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* host threads for the row loops (1 unless glref_set_threads says otherwise) */
+static int glref_threads = 1;
+void glref_set_threads(int n) { glref_threads = n > 0 ? n : 1; }
+int glref_get_threads(void) { return glref_threads; }
+int glref_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_num_procs();
+#else
+    return 1;
+#endif
+}
+/* a loop over rows whose iterations each write only their own row */
+#define ROWS_PARALLEL _Pragma("omp parallel for schedule(static) num_threads(glref_threads)")
 
 #define GLREF_MAXDEG 16
 #define GLREF_MAXLEV 16
@@ -70,6 +91,7 @@ static void csr_free(csr *a) {
 
 /* y = A x */
 static void csr_matvec(const csr *a, const cplx *x, cplx *y) {
+    ROWS_PARALLEL
     for (int64_t i = 0; i < a->n; ++i) {
         cplx s = 0;
         for (int64_t p = a->rp[i]; p < a->rp[i + 1]; ++p) s += a->v[p] * x[a->ci[p]];
@@ -670,12 +692,14 @@ void glref_mesh_khat(const glref_mesh *m, int64_t *rp, int32_t *ci, cplx *v) {
 /* (K psi)_i = (K-hat psi)_i / |V_i|  (Remark rmk:dk: K = D^-1 K-hat) */
 void glref_kinetic_apply(const glref_mesh *m, const cplx *psi, cplx *y) {
     csr_matvec(&m->K, psi, y);
+    ROWS_PARALLEL
     for (int64_t i = 0; i < m->n; ++i) y[i] /= m->vol[i];
 }
 
 /* Eq. discr ginla: GL(psi)_i = (K psi)_i - psi_i (1 - |psi_i|^2) */
 void glref_residual(const glref_mesh *m, const cplx *psi, cplx *r) {
     glref_kinetic_apply(m, psi, r);
+    ROWS_PARALLEL
     for (int64_t i = 0; i < m->n; ++i) {
         double a2 = creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);
         r[i] -= psi[i] * (1.0 - a2);
@@ -685,6 +709,7 @@ void glref_residual(const glref_mesh *m, const cplx *psi, cplx *r) {
 /* Discrete Jacobian (Sec. 3): (J phi)_i = (K phi)_i + (-1 + 2|psi_i|^2) phi_i + psi_i^2 conj(phi_i) */
 void glref_jacobian_apply(const glref_mesh *m, const cplx *psi, const cplx *phi, cplx *y) {
     glref_kinetic_apply(m, phi, y);
+    ROWS_PARALLEL
     for (int64_t i = 0; i < m->n; ++i) {
         double a2 = creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);
         y[i] += (-1.0 + 2.0 * a2) * phi[i] + psi[i] * psi[i] * conj(phi[i]);
@@ -1236,6 +1261,8 @@ void glref_prec_level_colors(const glref_prec *p, int l, int32_t *color) {
  * x_i <- (b_i - sum_{j != i} A_ij x_j) / A_ii */
 static void gs_color(const level_t *L, int32_t c, const cplx *b, cplx *x) {
     const csr *A = &L->A;
+    /* rows of one colour are not coupled: any order gives the same values */
+    ROWS_PARALLEL
     for (int64_t i = 0; i < A->n; ++i) {
         if (L->color[i] != c) continue;
         cplx s = b[i];
@@ -1268,13 +1295,16 @@ static void vcycle(const glref_prec *p, int l, const cplx *b, cplx *x) {
     }
     cplx *r = p->work[l][0];
     cplx *bc = p->work[l + 1][1], *xc = p->work[l + 1][2];
+    ROWS_PARALLEL
     for (int64_t i = 0; i < n; ++i) x[i] = 0;
     sgs(L, b, x);
     csr_matvec(&L->A, x, r);
+    ROWS_PARALLEL
     for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
     csr_matvec(&L->PH, r, bc);
     vcycle(p, l + 1, bc, xc);
     csr_matvec(&L->P, xc, r);
+    ROWS_PARALLEL
     for (int64_t i = 0; i < n; ++i) x[i] += r[i];
     sgs(L, b, x);
 }
@@ -1290,16 +1320,18 @@ int glref_precond_apply_count(const glref_prec *p, const cplx *v, cplx *z) {
     cplx *b = xcalloc((size_t)n, sizeof(cplx)), *e = xcalloc((size_t)n, sizeof(cplx));
     cplx *r = xcalloc((size_t)n, sizeof(cplx));
     double v2 = 0;
+    ROWS_PARALLEL
     for (int64_t i = 0; i < n; ++i) {
         b[i] = m->vol[i] * v[i];
         z[i] = 0;
-        v2 += m->vol[i] * (creal(v[i]) * creal(v[i]) + cimag(v[i]) * cimag(v[i]));
     }
+    for (int64_t i = 0; i < n; ++i) v2 += m->vol[i] * (creal(v[i]) * creal(v[i]) + cimag(v[i]) * cimag(v[i]));
     const int inf = p->cycles == GLREF_CYCLES_INF;
     const int kmax = inf ? GLREF_RINF_MAXCYC : p->cycles;
     int k = 0;
     for (;;) {
         csr_matvec(&p->L[0].A, z, r);
+        ROWS_PARALLEL
         for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
         if (inf && k > 0) {
             /* ||D^-1 r||_D^2 = sum |r_i|^2 / |V_i| */
@@ -1309,6 +1341,7 @@ int glref_precond_apply_count(const glref_prec *p, const cplx *v, cplx *z) {
         }
         if (k == kmax) break;
         vcycle(p, 0, r, e);
+        ROWS_PARALLEL
         for (int64_t i = 0; i < n; ++i) z[i] += e[i];
         ++k;
     }
@@ -1339,6 +1372,7 @@ static double norm_r(const glref_mesh *m, const cplx *x) { return sqrt(glref_inn
 static double true_relres(const glref_mesh *m, const cplx *psi, const cplx *b, const cplx *x, double bnorm,
                           cplx *tmp) {
     glref_jacobian_apply(m, psi, x, tmp);
+    ROWS_PARALLEL
     for (int64_t i = 0; i < m->n; ++i) tmp[i] = b[i] - tmp[i];
     return norm_r(m, tmp) / bnorm;
 }
@@ -1379,6 +1413,7 @@ int glref_minres(const glref_mesh *m, const cplx *psi, const glref_prec *prec, c
     }
     /* v_1 = b - J x_0, z_1 = R v_1, gamma_1 = sqrt(<v_1, z_1>_R) */
     glref_jacobian_apply(m, psi, x, q);
+    ROWS_PARALLEL
     for (int64_t i = 0; i < n; ++i) v[i] = b[i] - q[i];
     apply_prec(prec, n, v, z);
     double gamma = glref_inner_r(m, v, z);
@@ -1398,9 +1433,11 @@ int glref_minres(const glref_mesh *m, const cplx *psi, const glref_prec *prec, c
     }
     for (int it = 1; it <= o->maxit; ++it) {
         /* Lanczos step: z <- z / gamma, delta = <J z, z>_R */
+        ROWS_PARALLEL
         for (int64_t i = 0; i < n; ++i) z[i] /= gamma;
         glref_jacobian_apply(m, psi, z, q);
         double delta = glref_inner_r(m, q, z);
+        ROWS_PARALLEL
         for (int64_t i = 0; i < n; ++i) v_new[i] = q[i] - (delta / gamma) * v[i] - (gamma / gamma_old) * v_old[i];
         apply_prec(prec, n, v_new, z_new);
         double gamma_new = glref_inner_r(m, v_new, z_new);
@@ -1417,7 +1454,9 @@ int glref_minres(const glref_mesh *m, const cplx *psi, const glref_prec *prec, c
         double a3 = s_old * gamma;
         double c_new = a0 / a1, s_new = gamma_new / a1;
         /* search direction and update */
+        ROWS_PARALLEL
         for (int64_t i = 0; i < n; ++i) w_new[i] = (z[i] - a3 * w_old[i] - a2 * w[i]) / a1;
+        ROWS_PARALLEL
         for (int64_t i = 0; i < n; ++i) x[i] += c_new * eta * w_new[i];
         eta = -s_new * eta;
         /* shift */

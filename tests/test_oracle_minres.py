@@ -195,3 +195,20 @@ def test_rinf_is_the_exact_inverse(oracle_mod, dim, N, mc, field):
     zk = oracle_mod.Precond(m, psi, cycles=k, max_coarse=mc).apply(v)
     np.testing.assert_array_equal(zk, z)
     assert P.cost_inf(k) == pytest.approx(P.cost(k) + 1.0)
+
+
+def test_threads_give_bit_identical_results(oracle_mod):
+    """The row loops shared over host threads write disjoint rows and every sum
+    across rows stays serial: the solve is the same bit for bit."""
+    m = oracle_mod.Mesh(3, 14, 1.0, gi.WORKLOADS["cube128"][3])
+    psi, b = gi.disk(m.n, 51), gi.complex_normal(m.n, 52)
+    out = []
+    try:
+        for t in (1, 4):
+            oracle_mod.set_threads(t)
+            x, info = m.solve(psi, b, max_coarse=32)
+            out.append((x, info.iters, info.true_relres))
+    finally:
+        oracle_mod.set_threads(1)
+    assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
+    assert np.array_equal(out[0][0], out[1][0])
