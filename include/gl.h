@@ -107,6 +107,13 @@ typedef struct {
                             GL_COLOR_JP (Jones-Plassmann with hashed priorities, on the device).  Each
                             colour is one dependent phase of a sweep.  The finest lattice level is
                             always red-black. */
+    int sweep_sync;      /* synchronisation between the colours of a coarse-level Gauss-Seidel step:
+                            0 = chosen per level (timed at setup with autotune; else the neighbour flags
+                            where their partition fits), 1 = a grid-wide barrier, 2 = neighbour flags
+                            (each CTA waits only for the CTAs whose rows its rows read; the grid barrier
+                            where no partition fits).  The result is the same; only the time differs.
+                            Every wait is bounded (1 s); one that runs out ends the call with
+                            GL_ERR_TIMEOUT (default 0) */
 } gl_options;
 
 #define GL_COLOR_SL 0
@@ -203,7 +210,13 @@ GL_API gl_status gl_energy(gl_mesh mesh, const void *psi_dev, double *energy_hos
 /* Discrete Jacobian (Sec. 3):
  *   y_i = (K phi)_i + (-1 + 2|psi_i|^2) phi_i + psi_i^2 conj(phi_i).
  * psi, phi, y: n complex FP64; y may not alias psi or phi.  With GL_MIXED the
- * operator and arithmetic are FP32 (inputs rounded to FP32, output widened). */
+ * operator and arithmetic are FP32 (inputs rounded to FP32, output widened).
+ * With GL_MIXED_PRECOND: the double-FP32 form that GL_MIXED_PRECOND solves use on
+ * meshes with an even number of nodes per side (edge magnitudes and phases of
+ * the checked lattice stencil as FP32 hi + lo pairs, error-free transformations,
+ * about 48 significant bits) applied to phi rounded to FP32 (in the solve the
+ * vectors it meets are FP32 values, so there the rounding is exact); y in FP64.
+ * GL_ERR_ARG on a mesh without that stencil (odd N).  Synchronises `stream`. */
 GL_API gl_status gl_jacobian_apply(gl_mesh mesh, const void *psi_dev, const void *phi_dev, void *y_dev,
                             int precision, void *stream);
 
@@ -246,8 +259,32 @@ GL_API gl_status gl_precond_setup_like(gl_mesh mesh, const void *psi_dev, const 
 /* z = R_k x: k V-cycles for (K-hat + 2 D|psi|^2) z = D x from z = 0 (Eq. prec2);
  * with cycles = GL_CYCLES_INF, R_inf: cycles until the residual test of
  * GL_CYCLES_INF holds (a device-side loop; no host round trip per cycle).
- * x_dev, z_dev: n complex FP64, may not alias.  FP64 arithmetic. */
+ * x_dev, z_dev: n complex FP64, may not alias.  FP64 arithmetic.  Synchronises
+ * `stream` to read the coarse sweeps' error word: GL_ERR_TIMEOUT if one of their
+ * bounded waits ran out (z is then not R x; the synchronisation state is reset,
+ * so the next call runs normally). */
 GL_API gl_status gl_precond_apply(gl_prec prec, const void *x_dev, void *z_dev, void *stream);
+
+/* gl_precond_apply with the V-cycle in a chosen arithmetic: GL_FP64 as
+ * gl_precond_apply; GL_MIXED or GL_MIXED_PRECOND the FP32 V-cycle those solves
+ * run (x rounded to FP32 on entry, FP32 level operators and sweeps, the lattice
+ * stencil on the finest level where options.lattice allows it, the coarsest
+ * solve in FP64, z widened to FP64).  Builds the FP32 copies on first use.
+ * Errors as gl_precond_apply; GL_ERR_ARG for R_inf in FP32. */
+GL_API gl_status gl_precond_apply_precision(gl_prec prec, const void *x_dev, void *z_dev, int precision,
+                                            void *stream);
+
+/* Fault injection for tests of the failure handling; no counterpart in the
+ * paper.  GL_DEBUG_STALL_SWEEPS: every wait of the next coarse-level sweeps
+ * waits for a count that no CTA reaches, so it runs out after its 1 s bound,
+ * the call that ran it returns GL_ERR_TIMEOUT and resets the state (later calls
+ * run normally).  GL_DEBUG_NEGATE_COARSEST: multiplies the coarsest level's
+ * dense inverse by -1, which makes R_k indefinite on a one-level hierarchy
+ * (solves then end with GL_ERR_BREAKDOWN); permanent for this handle.
+ * Synchronises the device. */
+#define GL_DEBUG_STALL_SWEEPS 1
+#define GL_DEBUG_NEGATE_COARSEST 2
+GL_API gl_status gl_precond_debug(gl_prec prec, int action);
 GL_API gl_status gl_precond_destroy(gl_prec prec);
 
 /* Cost of applying R_k (k = cycles >= 1) in matrix-vector-product equivalents,
@@ -266,6 +303,14 @@ GL_API gl_status gl_precond_cost(gl_prec prec, int cycles, double *matvecs);
 GL_API gl_status gl_precond_levels(gl_prec prec, int *nlevels);
 GL_API gl_status gl_precond_level_info(gl_prec prec, int level, int64_t *n, int64_t *nnz, int32_t *ncolors,
                                 int64_t *p_nnz, double *omega);
+/* How level l's Gauss-Seidel steps run in the given precision's V-cycle
+ * (GL_FP64, or GL_MIXED / GL_MIXED_PRECOND for the FP32 V-cycle once built):
+ * *lanes = lanes per row, *sync = 0 for a cooperative grid with a grid
+ * barrier between colours, 1 for neighbour flags (*ctas = CTAs of the launch),
+ * 3 for one thread-block cluster (*ctas = its size); 0 / -1 / 0 on the lattice
+ * and the coarsest level, which have no such sweep.  Any output may be NULL. */
+GL_API gl_status gl_precond_level_sweep(gl_prec prec, int level, int precision, int *lanes, int *sync, int *ctas);
+
 /* agg_host: n int32, the coarse node of each node of this level (not the coarsest). */
 GL_API gl_status gl_precond_level_aggregates(gl_prec prec, int level, int32_t *agg_host);
 /* color_host: n int32 smoothing colours of this level. */
@@ -322,6 +367,13 @@ GL_API gl_status gl_batch_destroy(gl_batch batch);
 GL_API gl_status gl_batch_solve(int count, const gl_mesh *meshes, const void *const *psi_dev, const void *const *b_dev,
                                 void *const *x_dev, const gl_options *opt, gl_solve_info *infos, void *stream);
 
+/* Measured arithmetic peak of the current GPU for the rooflines (not a paper
+ * quantity): fused multiply-adds of independent chains on every SM, timed with
+ * CUDA events; precision GL_FP64 for FP64, GL_MIXED for FP32.  *gflops_host =
+ * GFLOP/s (2 per FMA), the best of repetitions grown to >= 20 ms.  Synchronises
+ * `stream`. */
+GL_API gl_status gl_measure_fma_peak(int precision, double *gflops_host, void *stream);
+
 /* Measurement instrumentation (no counterpart in the paper).
  * gl_profile_begin resets the count of hot-path kernel launches and, when
  * kernel_class is not NULL, records a pair of CUDA events on the launching
@@ -337,6 +389,12 @@ GL_API gl_status gl_batch_solve(int count, const gl_mesh *meshes, const void *co
  * summed algorithmic bytes.  Not thread-safe; one profile at a time. */
 GL_API gl_status gl_profile_begin(const char *kernel_class, int max_launches);
 GL_API gl_status gl_profile_end(int64_t *launches, int64_t *timed, double *total_ms, double *alg_bytes);
+/* Arithmetic of the launches timed by the last gl_profile_begin / gl_profile_end
+ * pair, for the classes whose kernels may be bound by an arithmetic pipe (the
+ * FP64 Jacobian, the FP64 sweeps, the double-FP32 Jacobian: flops, an FMA or
+ * an FP32 operation of an error-free transformation counted as 2); 0 for
+ * other classes.  Host output. */
+GL_API gl_status gl_profile_flops(double *alg_flops_host);
 
 /* ---------------------------------------------------------------------------
  * Learned warm start.  The paper has no counterpart: its Newton-Krylov solves

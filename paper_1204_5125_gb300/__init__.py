@@ -29,12 +29,15 @@ __all__ = [
     "gl_warmstart_predict", "gl_warmstart_grad", "gl_warmstart_train", "gl_warmstart_adam_step", "GL_WS_NPARAM",
     "gl_last_error", "EXPORTED", "GL_CYCLES_INF", "ContOptions", "ContPoint", "gl_mesh_create_edge",
     "gl_mesh_set_mu", "gl_residual_dmu", "gl_energy", "cont_options", "gl_continuation", "gl_precond_setup_like",
-    "GL_COLOR_SL", "GL_COLOR_JP", "gl_mesh_create_dipole",
+    "GL_COLOR_SL", "GL_COLOR_JP", "gl_mesh_create_dipole", "gl_precond_apply_precision", "gl_precond_debug",
+    "GL_DEBUG_STALL_SWEEPS", "GL_DEBUG_NEGATE_COARSEST", "gl_precond_level_sweep", "gl_measure_fma_peak",
+    "gl_profile_flops",
 ]
 
 GL_FP64, GL_MIXED, GL_MIXED_PRECOND = 0, 1, 2
 GL_CYCLES_INF = -1  # options.cycles: R_inf, the V-cycle repeated until the 1e-12 residual test
 GL_COLOR_SL, GL_COLOR_JP = 0, 1  # options.coloring of the coarse levels
+GL_DEBUG_STALL_SWEEPS, GL_DEBUG_NEGATE_COARSEST = 1, 2  # gl_precond_debug actions (fault injection for tests)
 STATUS = {0: "GL_OK", 1: "GL_ERR_ARG", 2: "GL_ERR_CUDA", 3: "GL_ERR_OOM", 4: "GL_ERR_NOT_CONVERGED",
           5: "GL_ERR_BREAKDOWN", 6: "GL_ERR_NAN", 7: "GL_ERR_TIMEOUT", 8: "GL_ERR_CAPACITY"}
 
@@ -49,6 +52,8 @@ EXPORTED = [
     "gl_warmstart_set_params", "gl_warmstart_predict", "gl_warmstart_grad", "gl_warmstart_train",
     "gl_warmstart_adam_step", "gl_last_error", "gl_mesh_create_edge", "gl_mesh_set_mu", "gl_residual_dmu",
     "gl_energy", "gl_cont_options_default", "gl_continuation", "gl_precond_setup_like", "gl_mesh_create_dipole",
+    "gl_precond_apply_precision", "gl_precond_debug", "gl_precond_level_sweep", "gl_measure_fma_peak",
+    "gl_profile_flops",
 ]
 
 GL_WS_NPARAM = 4 * 64 * 128 + 2 * 64
@@ -66,7 +71,7 @@ class Options(C.Structure):
         ("max_levels", C.c_int), ("power_its", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double),
         ("max_outer", C.c_int), ("check_every", C.c_int), ("autotune", C.c_int), ("lattice", C.c_int),
         ("cluster_sweeps", C.c_int),
-        ("warmstart", C.c_void_p), ("coloring", C.c_int),
+        ("warmstart", C.c_void_p), ("coloring", C.c_int), ("sweep_sync", C.c_int),
     ]
 
 
@@ -128,6 +133,12 @@ def library(build_if_missing: bool = True):
             "gl_jacobian_apply": [vp, vp, vp, vp, C.c_int, vp],
             "gl_precond_setup": [vp, vp, C.POINTER(Options), vp, C.POINTER(vp)],
             "gl_precond_apply": [vp, vp, vp, vp],
+            "gl_precond_apply_precision": [vp, vp, vp, C.c_int, vp],
+            "gl_precond_debug": [vp, C.c_int],
+            "gl_measure_fma_peak": [C.c_int, C.POINTER(C.c_double), vp],
+            "gl_profile_flops": [C.POINTER(C.c_double)],
+            "gl_precond_level_sweep": [vp, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_int)],
             "gl_precond_destroy": [vp],
             "gl_precond_levels": [vp, C.POINTER(C.c_int)],
             "gl_precond_level_info": [vp, C.c_int, i64p, i64p, C.POINTER(C.c_int32), i64p, C.POINTER(C.c_double)],
@@ -356,6 +367,29 @@ def gl_precond_apply(prec, x, z, stream=None):
     _check(library().gl_precond_apply(prec, _ptr(x), _ptr(z), _stream(stream)))
 
 
+def gl_precond_apply_precision(prec, x, z, precision=GL_FP64, stream=None):
+    _check(library().gl_precond_apply_precision(prec, _ptr(x), _ptr(z), precision, _stream(stream)))
+
+
+def gl_precond_debug(prec, action: int):
+    _check(library().gl_precond_debug(prec, action))
+
+
+def gl_precond_level_sweep(prec, level: int, precision=GL_FP64) -> dict:
+    """How a level's Gauss-Seidel steps run: lanes per row, sync (0 grid barrier,
+    1 neighbour flags, 3 cluster, -1 none) and CTAs."""
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    _check(library().gl_precond_level_sweep(prec, level, precision, C.byref(a), C.byref(b), C.byref(c)))
+    return dict(lanes=a.value, sync=b.value, ctas=c.value)
+
+
+def gl_measure_fma_peak(precision=GL_FP64, stream=None) -> float:
+    """Measured FMA rate of the GPU in GFLOP/s (GL_FP64 or GL_MIXED for FP32)."""
+    g = C.c_double()
+    _check(library().gl_measure_fma_peak(precision, C.byref(g), _stream(stream)))
+    return g.value
+
+
 def gl_precond_destroy(prec):
     _check(library().gl_precond_destroy(prec))
 
@@ -465,7 +499,9 @@ def gl_profile_end() -> dict:
     la, ti = C.c_int64(), C.c_int64()
     ms, by = C.c_double(), C.c_double()
     _check(library().gl_profile_end(C.byref(la), C.byref(ti), C.byref(ms), C.byref(by)))
-    return dict(launches=la.value, timed=ti.value, ms=ms.value, bytes=by.value)
+    fl = C.c_double()
+    _check(library().gl_profile_flops(C.byref(fl)))
+    return dict(launches=la.value, timed=ti.value, ms=ms.value, bytes=by.value, flops=fl.value)
 
 
 def _f32(a):

@@ -41,6 +41,7 @@ void check_opts(const gl_options *o) {
                "unknown precision");
     GL_REQUIRE(o->max_coarse <= MAX_COARSE_DENSE, GL_ERR_ARG, "max_coarse must be <= 4096");
     GL_REQUIRE(o->coloring == GL_COLOR_SL || o->coloring == GL_COLOR_JP, GL_ERR_ARG, "unknown coloring");
+    GL_REQUIRE(o->sweep_sync >= 0 && o->sweep_sync <= 2, GL_ERR_ARG, "sweep_sync must be 0, 1 or 2");
 }
 
 void ensure_tmp(gl_mesh_s *m) {
@@ -79,6 +80,7 @@ gl_status gl_options_default(gl_options *o) {
     o->cluster_sweeps = 1;
     o->warmstart = nullptr;
     o->coloring = GL_COLOR_SL;
+    o->sweep_sync = 0;
     return GL_OK;
 }
 
@@ -196,12 +198,15 @@ gl_status gl_jacobian_apply(gl_mesh m, const void *psi, const void *phi, void *y
     return guard([&] {
         GL_REQUIRE(m && psi && phi && y, GL_ERR_ARG, "NULL argument");
         GL_REQUIRE(y != psi && y != phi, GL_ERR_ARG, "y must not alias psi or phi");
-        GL_REQUIRE(precision == GL_FP64 || precision == GL_MIXED, GL_ERR_ARG, "unknown precision");
+        GL_REQUIRE(precision == GL_FP64 || precision == GL_MIXED || precision == GL_MIXED_PRECOND, GL_ERR_ARG,
+                   "unknown precision");
         cudaStream_t s = as_stream(stream);
         ensure_tmp(m);
         permute_in(m->n, m->perm.get(), (const double2 *)psi, m->t0.get(), s);
         permute_in(m->n, m->perm.get(), (const double2 *)phi, m->t1.get(), s);
-        if (precision == GL_MIXED) {
+        if (precision == GL_MIXED_PRECOND) {
+            jacobian_apply_pdf(m, m->t0.get(), m->t1.get(), m->t2.get(), s);
+        } else if (precision == GL_MIXED) {
             mesh_ensure_fp32(m, s);
             jacobian_apply_p32(m, m->t0.get(), m->t1.get(), m->t2.get(), s);
         } else {
@@ -260,6 +265,51 @@ gl_status gl_precond_apply(gl_prec p, const void *x, void *z, void *stream) {
         permute_in(m->n, m->perm.get(), (const double2 *)x, m->t0.get(), s);
         precond_apply_p(p, m->t0.get(), m->t1.get(), nullptr, s);
         permute_out(m->n, m->perm.get(), m->t1.get(), (double2 *)z, s);
+        if (sweeps_failed(p, s)) {
+            sweeps_reset(p, s);
+            GL_CUDA(cudaStreamSynchronize(s));
+            GL_REQUIRE(false, GL_ERR_TIMEOUT, "a coarse-level Gauss-Seidel wait ran out; z is not R x");
+        }
+        return GL_OK;
+    });
+}
+
+gl_status gl_precond_apply_precision(gl_prec p, const void *x, void *z, int precision, void *stream) {
+    return guard([&] {
+        GL_REQUIRE(p && x && z, GL_ERR_ARG, "NULL argument");
+        GL_REQUIRE(x != z, GL_ERR_ARG, "x and z must not alias");
+        GL_REQUIRE(precision == GL_FP64 || precision == GL_MIXED || precision == GL_MIXED_PRECOND, GL_ERR_ARG,
+                   "unknown precision");
+        if (precision == GL_FP64) return gl_precond_apply(p, x, z, stream);
+        GL_REQUIRE(!p->rinf, GL_ERR_ARG, "R_inf runs in FP64 only");
+        gl_mesh_s *m = p->mesh;
+        GL_REQUIRE(p->mesh_version == m->version, GL_ERR_ARG, "preconditioner set up before the mesh's mu changed");
+        cudaStream_t s = as_stream(stream);
+        precond_ensure_fp32(p, s);
+        ensure_tmp(m);
+        permute_in(m->n, m->perm.get(), (const double2 *)x, m->t0.get(), s);
+        precond_apply_p64_via32(p, m->t0.get(), m->t1.get(), nullptr, s);
+        permute_out(m->n, m->perm.get(), m->t1.get(), (double2 *)z, s);
+        if (sweeps_failed(p, s)) {
+            sweeps_reset(p, s);
+            GL_CUDA(cudaStreamSynchronize(s));
+            GL_REQUIRE(false, GL_ERR_TIMEOUT, "a coarse-level Gauss-Seidel wait ran out; z is not R x");
+        }
+        return GL_OK;
+    });
+}
+
+gl_status gl_precond_debug(gl_prec p, int action) {
+    return guard([&] {
+        GL_REQUIRE(p, GL_ERR_ARG, "NULL argument");
+        if (action == GL_DEBUG_STALL_SWEEPS) {
+            const unsigned long long far = 1ull << 40;
+            GL_CUDA(cudaMemcpy(p->wait_extra.get(), &far, sizeof far, cudaMemcpyHostToDevice));
+        } else if (action == GL_DEBUG_NEGATE_COARSEST) {
+            precond_negate_coarsest(p, nullptr);
+        } else {
+            GL_REQUIRE(false, GL_ERR_ARG, "unknown debug action");
+        }
         return GL_OK;
     });
 }
@@ -302,6 +352,31 @@ gl_status gl_precond_level_info(gl_prec p, int l, int64_t *n, int64_t *nnz, int3
         if (ncolors) *ncolors = L.ncolors;
         if (p_nnz) *p_nnz = last ? 0 : L.P_can.nnz;
         if (omega) *omega = last ? 0.0 : L.omega;
+        return GL_OK;
+    });
+}
+
+gl_status gl_precond_level_sweep(gl_prec p, int l, int precision, int *lanes, int *sync, int *ctas) {
+    return guard([&] {
+        GL_REQUIRE(p && l >= 0 && l < p->nlev, GL_ERR_ARG, "bad level");
+        GL_REQUIRE(precision == GL_FP64 || ((precision == GL_MIXED || precision == GL_MIXED_PRECOND) && p->has32),
+                   GL_ERR_ARG, "no sweep of that precision (FP32 copies not built)");
+        const Level &L = p->L[l];
+        const bool f32 = precision != GL_FP64;
+        const bool coarse = l > 0 && l < p->nlev - 1;
+        if (lanes) *lanes = coarse ? (f32 ? L.sgs_G32 : L.sgs_G64) : 0;
+        int sy = -1, nb = 0;
+        if (coarse) {
+            if (f32 && L.cl_size > 0 && p->cluster_sweeps) {
+                sy = 3;
+                nb = L.cl_size;
+            } else {
+                sy = f32 ? L.sync32 : L.sync64;
+                nb = sy == 1 ? (f32 ? L.fl32.nb : L.fl64.nb) : 0;
+            }
+        }
+        if (sync) *sync = sy;
+        if (ctas) *ctas = nb;
         return GL_OK;
     });
 }
@@ -478,15 +553,24 @@ gl_status gl_profile_begin(const char *kernel_class, int max_launches) {
         p.ev.resize(2 * (size_t)slots);
         for (auto &e : p.ev) GL_CUDA(cudaEventCreate(&e));
         p.slot_bytes.assign(slots, 0.0);
+        p.slot_flops.assign(slots, 0.0);
         p.free_slots.clear();
         for (int i = slots - 1; i >= 0; --i) p.free_slots.push_back(i);
         p.pending.clear();
         p.capture = nullptr;
-        p.total_ms = p.total_bytes = 0;
+        p.total_ms = p.total_bytes = p.total_flops = 0;
         p.timed = p.dropped = 0;
         p.launches.store(0);
         p.retarget(p.name);
         p.active = true;
+        return GL_OK;
+    });
+}
+
+gl_status gl_profile_flops(double *alg_flops) {
+    return guard([&] {
+        GL_REQUIRE(alg_flops, GL_ERR_ARG, "NULL argument");
+        *alg_flops = profiler().last_flops;
         return GL_OK;
     });
 }
@@ -501,6 +585,7 @@ gl_status gl_profile_end(int64_t *launches, int64_t *timed, double *total_ms, do
         if (timed) *timed = p.timed;
         if (total_ms) *total_ms = p.total_ms;
         if (alg_bytes) *alg_bytes = p.total_bytes;
+        p.last_flops = p.total_flops;
         for (auto e : p.ev) cudaEventDestroy(e);
         p.ev.clear();
         p.free_slots.clear();

@@ -48,6 +48,29 @@ constexpr int MAX_LEVELS = 16;
 // counter for the FP32 and one for the FP64 sweep
 constexpr int GRID_BARRIER_WORDS = 4;
 constexpr int MAX_COARSE_DENSE = 4096;
+// neighbour-flag form of the coarse sweeps: one completed-phase counter per
+// CTA, FLAG_STRIDE 64-bit words apart, at most MAX_FLAG_CTAS CTAs per launch,
+// and at most FLAG_MAXN neighbour CTAs per (CTA, colour)
+constexpr int FLAG_STRIDE = 16;
+constexpr int MAX_FLAG_CTAS = 1024;
+constexpr int FLAG_MAXN = 32;
+// status word value a bounded device-side wait writes when it runs out
+constexpr int STATUS_TIMEOUT = 6;
+// bound of every device-side wait of the coarse sweeps (globaltimer ns)
+constexpr long long SWEEP_WAIT_NS = 1000000000ll;
+
+// Partition and dependency lists of the neighbour-flag sweep of one level in one
+// precision: CTA b owns, in every colour, the rows whose level node id lies in
+// [floor(b n / nb), floor((b + 1) n / nb)), so its rows in all colours sit in
+// one spatial block; before a phase it waits only for the CTAs owning columns
+// of its rows in that phase's colour.
+struct FlagPlan {
+    int nb = 0;                  // CTAs of the launch (0: no plan)
+    int G = 0;                   // lanes per row the plan was built for
+    DBuf<int64_t> rstart;        // [colour][nb + 1]: first solve position of each CTA's rows in the colour
+    DBuf<int32_t> nbr;           // [cta][colour][FLAG_MAXN]: CTAs whose rows those rows read
+    DBuf<int32_t> nbrc;          // [cta][colour]: lengths of those lists
+};
 
 struct Level {
     int64_t n = 0;
@@ -71,6 +94,9 @@ struct Level {
     CsrG<double2> Ag, PHg;          // grouped-CSR forms: coarse-level A (ell >= 1) and P^H
     DBuf<int64_t> cstart_dev;       // cstart on the device (cooperative sweeps)
     DBuf<unsigned> barrier;         // grid-barrier state of the cooperative coarse sweeps
+    DBuf<unsigned long long> flags; // neighbour-flag sweeps: [precision][MAX_FLAG_CTAS][FLAG_STRIDE] counters
+    FlagPlan fl32, fl64;            // their partitions (FP32 / FP64 sweep)
+    int sync32 = 0, sync64 = 0;     // coarse sweep synchronisation: 0 grid barrier, 1 neighbour flags
     DBuf<double2> b, x, r;          // level vectors (solve ordering)
     DBuf<double2> Ainv;             // coarsest: dense inverse, row-major
     // FP32 copies (mixed precision)
@@ -105,6 +131,8 @@ struct gl_prec_s {
     gl_mesh_s *mesh = nullptr;
     int64_t mesh_version = 0;         // the mesh's version (mu) the operator was built for
     gl::DBuf<int> err;                // set by a device-side wait that ran out
+    gl::DBuf<unsigned long long> wait_extra;  // added to every sweep wait target: 0, or huge after
+                                      // gl_precond_debug(GL_DEBUG_STALL_SWEEPS) (reset with the error word)
     int nlev = 0;
     int cycles = 1;
     bool has32 = false;
@@ -125,7 +153,9 @@ struct gl_prec_s {
     // kernel choices taken over from a template instead of timing them again
     struct Tuned {
         int ag64 = 1, phg64 = 1, sgs64 = 1, ag32 = 1, phg32 = 1, sgs32 = 1, cl_size = 0, cl_chunk = 0;
+        int sync64 = 0, nb64 = 0, sync32 = 0, nb32 = 0;
     } tuned[gl::MAX_LEVELS];
+    int sweep_sync = 0;               // gl_options.sweep_sync the setup ran with
     bool tuned64 = false, tuned32 = false;
     // R_inf: device loop state, the stream its loop body is captured on, and the
     // stream and events of an application outside stream capture
@@ -190,12 +220,17 @@ double precond_cost(const gl_prec_s *p, int k);
 void rinf_reset(gl_prec_s *p, cudaStream_t s);
 RinfDev rinf_read(gl_prec_s *p, cudaStream_t s);
 void precond_ensure_fp32(gl_prec_s *p, cudaStream_t s);
+// multiplies the coarsest level's dense inverse by -1 (gl_precond_debug)
+void precond_negate_coarsest(gl_prec_s *p, cudaStream_t s);
 
 // gl_ops.cu (solve ordering)
 void permute_in(int64_t n, const int32_t *perm, const double2 *nat, double2 *sol, cudaStream_t s);
 void permute_out(int64_t n, const int32_t *perm, const double2 *sol, double2 *nat, cudaStream_t s);
 void jacobian_apply_p(const gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s);
 void jacobian_apply_p32(const gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s);
+// gl_solve.cu: the double-float lattice Jacobian of the GL_MIXED_PRECOND solve on
+// phi rounded to FP32 (solve ordering; GL_ERR_ARG without a lattice stencil)
+void jacobian_apply_pdf(gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s);
 void residual_p(const gl_mesh_s *m, const double2 *psi, double2 *r, cudaStream_t s);
 // node order: r <- -r, returns ||r||_R (part: RED_BLOCKS doubles, scal: 1 double)
 double newton_rhs(const gl_mesh_s *m, double2 *r, double *part, double *scal, cudaStream_t s);
@@ -207,9 +242,17 @@ void precond_apply_p(gl_prec_s *p, const double2 *v, double2 *z, const int *stop
 void precond_apply_p32(gl_prec_s *p, const float2 *v, float2 *z, const int *stop, cudaStream_t s);
 // autotuner: picks the lanes-per-row width of every grouped-CSR operator by timing
 void autotune_levels(gl_prec_s *p, bool fp32, cudaStream_t s);
-// picks, per coarse level, the lanes per row of the Gauss-Seidel sweep and (FP32)
-// the thread-block-cluster or the cooperative-grid form (timed when autotuning)
+// picks, per coarse level, the lanes per row of the Gauss-Seidel sweep, its
+// synchronisation (grid barrier or neighbour flags) and (FP32) the
+// thread-block-cluster form (timed when autotuning)
 void plan_sweeps(gl_prec_s *p, bool fp32, cudaStream_t s);
+// rebuilds the neighbour-flag partitions of the sweep choices taken over from a template
+void rebuild_flag_plans(gl_prec_s *p, bool fp32, cudaStream_t s);
+// after a wait of the coarse sweeps ran out: zeroes every level's barrier
+// counters and flags and the error word, so later launches start in step
+void sweeps_reset(gl_prec_s *p, cudaStream_t s);
+// 1 if a device-side wait of p's sweeps ran out since the last reset (synchronises s)
+int sweeps_failed(gl_prec_s *p, cudaStream_t s);
 // z = R_k v with FP64 vectors and an FP32 V-cycle
 void precond_apply_p64_via32(gl_prec_s *p, const double2 *v, double2 *z, const int *stop, cudaStream_t s);
 

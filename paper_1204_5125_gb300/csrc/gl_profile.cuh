@@ -31,10 +31,11 @@ struct Profiler {
     bool active = false;
     std::string name;                  // kernel class timed with events ("" = none)
     std::vector<cudaEvent_t> ev;       // 2 per slot
-    std::vector<double> slot_bytes;
+    std::vector<double> slot_bytes, slot_flops;
     std::vector<int> free_slots, pending;
     std::vector<int> *capture = nullptr;  // slots of the graph being captured
-    double total_ms = 0, total_bytes = 0;
+    double total_ms = 0, total_bytes = 0, total_flops = 0;
+    double last_flops = 0;  // total_flops of the last ended profile
     int64_t timed = 0, dropped = 0;
 
     bool timing(const char *cls) const { return active && !name.empty() && name == cls; }
@@ -45,6 +46,7 @@ struct Profiler {
             if (cudaEventElapsedTime(&t, ev[2 * sl], ev[2 * sl + 1]) == cudaSuccess) {
                 total_ms += t;
                 total_bytes += slot_bytes[sl];
+                total_flops += slot_flops[sl];
                 ++timed;
             }
         }
@@ -60,9 +62,11 @@ Profiler &profiler();
 inline void note_launch(int k = 1) { profiler().launches.fetch_add(k, std::memory_order_relaxed); }
 
 // Brackets one launch: records events around it when its class is being timed.
+// alg_flops: the launch's arithmetic (flops, an FMA counted as 2) where a kernel
+// may be bound by an arithmetic pipe rather than by memory; 0 where not counted.
 class ProfScope {
    public:
-    ProfScope(const char *cls, double alg_bytes, cudaStream_t s) : s_(s) {
+    ProfScope(const char *cls, double alg_bytes, cudaStream_t s, double alg_flops = 0) : s_(s) {
         Profiler &p = profiler();
         note_launch();
         if (!p.timing(cls)) return;
@@ -73,6 +77,7 @@ class ProfScope {
         slot_ = p.free_slots.back();
         p.free_slots.pop_back();
         p.slot_bytes[slot_] = alg_bytes;
+        p.slot_flops[slot_] = alg_flops;
         graph_ = p.capture != nullptr;
         if (graph_)
             p.capture->push_back(slot_);

@@ -844,6 +844,18 @@ __global__ void k_fill_d(int64_t n, double *x, double v) {
     if (i < n) x[i] = v;
 }
 
+// M[p][q] = Ainv[perm[p]][perm[q]] vol[perm[q]]: the node-order inverse of the
+// level-0 operator as the map from v to z = Ainv D v in the solve ordering
+__global__ void k_dense_perm_scale(int64_t n, const double2 *__restrict__ Ainv, const int32_t *__restrict__ perm,
+                                   const double *__restrict__ vol, double2 *__restrict__ M) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * n) return;
+    const int64_t p = t / n, q = t % n;
+    const int64_t i = perm[p], j = perm[q];
+    const double2 a = Ainv[i * n + j];
+    M[t] = make_double2(a.x * vol[j], a.y * vol[j]);
+}
+
 static void colour_ordering(Level &L, cudaStream_t s) {
     int64_t n = L.n;
     L.perm_own.alloc(n);
@@ -1031,10 +1043,21 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
             colour_ordering(L, s);
         }
     }
+    if (p->nlev == 1) {
+        // the finest level is also the coarsest: the V-cycle there is z = P-hat^-1 D v
+        // in the solve ordering, so the dense inverse is permuted and scaled by D
+        DBuf<double2> M(n * n);
+        k_dense_perm_scale<<<grid_for(n * n, 256), 256, 0, s>>>(n, Lb.Ainv.get(), m->perm.get(), m->vol.get(),
+                                                               M.get());
+        GL_LAUNCH_CHECK();
+        Lb.Ainv = std::move(M);
+    }
     p->psi_p.alloc(n);
     permute_in(n, m->perm.get(), psi_nat, p->psi_p.get(), s);
     p->err.alloc(1);
     GL_CUDA(cudaMemsetAsync(p->err.get(), 0, sizeof(int), s));
+    p->wait_extra.alloc(1);
+    GL_CUDA(cudaMemsetAsync(p->wait_extra.get(), 0, sizeof(unsigned long long), s));
     for (int k = 0; k < p->nlev; ++k) {
         Level &L = p->L[k];
         bool coarsest = (k == p->nlev - 1);
@@ -1051,6 +1074,8 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
                                     cudaMemcpyHostToDevice, s));
             L.barrier.alloc(GRID_BARRIER_WORDS);
             GL_CUDA(cudaMemsetAsync(L.barrier.get(), 0, GRID_BARRIER_WORDS * sizeof(unsigned), s));
+            L.flags.alloc(2 * (size_t)MAX_FLAG_CTAS * FLAG_STRIDE);
+            GL_CUDA(cudaMemsetAsync(L.flags.get(), 0, L.flags.bytes(), s));
         }
         if (!coarsest) {
             Level &Lc = p->L[k + 1];
@@ -1125,7 +1150,9 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
     p->autotune = o.autotune != 0;
     p->lattice = o.lattice != 0;
     p->cluster_sweeps = o.cluster_sweeps != 0;
-    if (T && T->nlev == p->nlev && T->autotune == p->autotune && T->cluster_sweeps == p->cluster_sweeps) {
+    p->sweep_sync = o.sweep_sync;
+    if (T && T->nlev == p->nlev && T->autotune == p->autotune && T->cluster_sweeps == p->cluster_sweeps &&
+        T->sweep_sync == p->sweep_sync) {
         for (int k = 0; k < p->nlev; ++k) {
             const Level &S = T->L[k];
             auto &t = p->tuned[k];
@@ -1137,6 +1164,10 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
             t.sgs32 = S.sgs_G32;
             t.cl_size = S.cl_size;
             t.cl_chunk = S.cl_chunk;
+            t.sync64 = S.sync64;
+            t.nb64 = S.fl64.nb;
+            t.sync32 = S.sync32;
+            t.nb32 = S.fl32.nb;
         }
         p->tuned64 = true;
         p->tuned32 = T->has32;
@@ -1147,7 +1178,9 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
             L.Ag.G = p->tuned[k].ag64;
             L.PHg.G = p->tuned[k].phg64;
             L.sgs_G64 = p->tuned[k].sgs64;
+            L.sync64 = p->tuned[k].sync64;
         }
+        rebuild_flag_plans(p, false, s);
     } else {
         if (p->autotune) autotune_levels(p, false, s);
         plan_sweeps(p, false, s);
@@ -1196,7 +1229,9 @@ void precond_ensure_fp32(gl_prec_s *p, cudaStream_t s) {
             L.sgs_G32 = p->tuned[k].sgs32;
             L.cl_size = p->tuned[k].cl_size;
             L.cl_chunk = p->tuned[k].cl_chunk;
+            L.sync32 = p->tuned[k].sync32;
         }
+        rebuild_flag_plans(p, true, s);
     } else {
         if (p->autotune) autotune_levels(p, true, s);
         plan_sweeps(p, true, s);
@@ -1208,6 +1243,19 @@ void precond_ensure_fp32(gl_prec_s *p, cudaStream_t s) {
     p->coarse_x64.alloc(Lb.n);
     GL_CUDA(cudaStreamSynchronize(s));
     p->has32 = true;
+}
+
+__global__ void k_negate(int64_t n, double2 *a) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) a[i] = make_double2(-a[i].x, -a[i].y);
+}
+
+void precond_negate_coarsest(gl_prec_s *p, cudaStream_t s) {
+    Level &L = p->L[p->nlev - 1];
+    const int64_t nn = L.n * L.n;
+    k_negate<<<grid_for(nn, 256), 256, 0, s>>>(nn, L.Ainv.get());
+    GL_LAUNCH_CHECK();
+    GL_CUDA(cudaStreamSynchronize(s));
 }
 
 void rinf_reset(gl_prec_s *p, cudaStream_t s) {

@@ -28,7 +28,8 @@ struct MinresDev {
     double stall;     // > 0: stop with ST_STALL once the estimate is below stall * tol while the true
                       // residual is still above tol (0: never)
 };
-enum { ST_RUN = 0, ST_CONV = 1, ST_BREAK = 2, ST_NAN = 3, ST_MAXIT = 4, ST_STALL = 5 };
+enum { ST_RUN = 0, ST_CONV = 1, ST_BREAK = 2, ST_NAN = 3, ST_MAXIT = 4, ST_STALL = 5, ST_TIMEOUT = 6 };
+static_assert(ST_TIMEOUT == STATUS_TIMEOUT, "the sweeps write STATUS_TIMEOUT into the status word");
 
 template <typename T>
 struct SolveOps;
@@ -243,6 +244,34 @@ __global__ void __launch_bounds__(RED_THREADS) k_jz_latdf(int64_t n, LatticeDfVi
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
+__global__ void k_round32(int64_t n, const double2 *a, float2 *b) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < n) b[p] = to32(a[p]);
+}
+
+// y = J(psi) phi by the double-float lattice kernel the GL_MIXED_PRECOND solve
+// runs, for phi rounded to FP32 (in the solve that rounding is exact); solve
+// ordering, synchronises s
+void jacobian_apply_pdf(gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s) {
+    mesh_ensure_fp32(m, s);
+    GL_REQUIRE(m->lat_ok, GL_ERR_ARG,
+               "the double-FP32 Jacobian needs a mesh with an even number of nodes per side (checked lattice stencil)");
+    const int64_t n = m->n;
+    DBuf<float2> d(n), z(n);
+    DBuf<float4> p2(n);
+    DBuf<double> part(RED_BLOCKS);
+    DBuf<int> stop(1);
+    GL_CUDA(cudaMemsetAsync(stop.get(), 0, sizeof(int), s));
+    const int G = grid_for(n, 256);
+    note_launch(3);
+    k_jz_coef<<<G, 256, 0, s>>>(n, m->lat_krem.get(), psi, d.get(), p2.get());
+    k_round32<<<G, 256, 0, s>>>(n, phi, z.get());
+    k_jz_latdf<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, lattice_df_view(m), m->lat_hd, d.get(), p2.get(), z.get(), y,
+                                                  part.get(), stop.get());
+    GL_LAUNCH_CHECK();
+    GL_CUDA(cudaStreamSynchronize(s));
+}
+
 // v_new = q / gamma - (delta / gamma) v - (gamma / gamma_old) v_old
 template <typename C, typename R>
 __global__ void k_vnew(int64_t n, const MinresDev *S, const C *q, const C *v, const C *v_old, C *v_new) {
@@ -424,10 +453,46 @@ __global__ void k_scal_givens(MinresDev *S, const double *part) {
     S->check_true = (S->est <= S->tol) || S->lucky;
 }
 
-__global__ void k_scal_true(MinresDev *S, const double *part) {
+// Conditional-node handles of the device-side MINRES loop (all unused when n = 0):
+// h[0] the WHILE node around a body of ITER_UNROLL iterations, h[k] (k >= 1) the
+// IF node around iteration k of the body.
+struct Gates {
+    cudaGraphConditionalHandle h[6];
+    int n;
+};
+
+// after iteration k of a loop body: the IF nodes of the body's later iterations
+// open only while the solve runs; every gate this iteration can reach is
+// written, so no value is left from an earlier body
+__device__ void set_gates(MinresDev *S, const Gates &g, int k) {
+    const unsigned run = S->status == ST_RUN ? 1u : 0u;
+    for (int j = k + 1; j < g.n; ++j) cudaGraphSetConditional(g.h[j], run);
+}
+
+__global__ void k_loop_begin(cudaGraphConditionalHandle h, const MinresDev *S) {
+    cudaGraphSetConditional(h, S->status == ST_RUN ? 1u : 0u);
+}
+
+// end of a loop body: another body while the solve runs, at most maxit / 6 + 2
+// bodies (then ST_MAXIT), so the loop ends whatever the state
+__global__ void k_loop_next(cudaGraphConditionalHandle h, MinresDev *S) {
+    S->replays += 1;
+    bool run = S->status == ST_RUN;
+    if (run && S->replays >= S->maxit / 6 + 2) {
+        S->status = ST_MAXIT;
+        run = false;
+    }
+    cudaGraphSetConditional(h, run ? 1u : 0u);
+}
+
+__global__ void k_scal_true(MinresDev *S, const double *part, Gates g, int k) {
     __shared__ double sh[32];
     double r2 = sum_parts(part, sh);
-    if (threadIdx.x || S->status) return;
+    if (threadIdx.x) return;
+    if (S->status) {
+        set_gates(S, g, k);
+        return;
+    }
     if (S->check_true) {
         if (S->use_true) {
             S->true_rel = sqrt(r2) / S->bnorm;
@@ -443,6 +508,7 @@ __global__ void k_scal_true(MinresDev *S, const double *part) {
         if (!S->status && S->lucky) S->status = ST_MAXIT;  // Krylov space exhausted above tol
     }
     if (!S->status && S->it >= S->maxit) S->status = ST_MAXIT;
+    set_gates(S, g, k);
 }
 
 __global__ void k_scal_final(MinresDev *S, const double *part) {
@@ -459,6 +525,7 @@ __global__ void k_scal_final(MinresDev *S, const double *part) {
 // two z and three w buffers rotate, so the body holds a multiple of 6 iterations
 // and starts every replay with the same buffer roles.
 constexpr int ITER_UNROLL = 6;
+static_assert(ITER_UNROLL == 6, "k_loop_next bounds the device loop by maxit / 6 + 2 bodies");
 
 struct Graph {
     cudaGraphExec_t exec = nullptr;
@@ -475,10 +542,11 @@ struct Graph {
 struct GraphKey {
     const void *m = nullptr, *psi = nullptr, *b = nullptr, *x = nullptr;
     int64_t prec_uid = -1, generation = -1, mesh_version = -1;
-    int vc32 = 0, df = 0;
+    int vc32 = 0, df = 0, loop = 0;
     bool operator==(const GraphKey &o) const {
         return m == o.m && psi == o.psi && b == o.b && x == o.x && prec_uid == o.prec_uid &&
-               generation == o.generation && mesh_version == o.mesh_version && vc32 == o.vc32 && df == o.df;
+               generation == o.generation && mesh_version == o.mesh_version && vc32 == o.vc32 && df == o.df &&
+               loop == o.loop;
     }
 };
 
@@ -491,14 +559,21 @@ struct MinresWork {
     DBuf<double> part;
     DBuf<MinresDev> S;
     int64_t n = 0;
-    cudaStream_t cap = nullptr;
+    cudaStream_t cap = nullptr, cap_body = nullptr, cap_if = nullptr;
     GraphKey key;
     Graph init, body;
+    // the device-side loop: the whole solve in one graph; launches of its initial
+    // phase and of one iteration (counted at capture)
+    Graph loop;
+    int64_t loop_init_launches = 0, loop_iter_launches = 0;
     void ensure(int64_t nn) {
         if (!cap) GL_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        if (!cap_body) GL_CUDA(cudaStreamCreateWithFlags(&cap_body, cudaStreamNonBlocking));
+        if (!cap_if) GL_CUDA(cudaStreamCreateWithFlags(&cap_if, cudaStreamNonBlocking));
         if (n == nn) return;
         init.reset();
         body.reset();
+        loop.reset();
         key = GraphKey{};
         for (auto &b : v) b.alloc(nn);
         for (auto &b : z) b.alloc(nn);
@@ -631,10 +706,14 @@ static void enqueue_init(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const
 }
 
 // Enqueues ITER_UNROLL MINRES iterations on `cs` (buffer roles rotate inside
-// and return to the starting roles at the end).
+// and return to the starting roles at the end).  With `gates` (the device-side
+// loop; cs captures into the loop body) iterations 1.. each sit in an IF node,
+// captured on cs_child, which the previous iteration opens only while the solve
+// runs.
 template <typename T>
 static void enqueue_body(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const cplx_t<T> *b, cplx_t<T> *x,
-                         bool vc32, bool df, MinresWork<T> &W, cudaStream_t cs) {
+                         bool vc32, bool df, MinresWork<T> &W, cudaStream_t cs, const Gates *gates = nullptr,
+                         cudaStream_t cs_child = nullptr) {
     using O = SolveOps<T>;
     using C = cplx_t<T>;
     int64_t n = m->n;
@@ -648,7 +727,31 @@ static void enqueue_body(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const
     C *v_old = W.v[0].get(), *v = W.v[1].get(), *v_new = W.v[2].get();
     C *z = W.z[0].get(), *z_new = W.z[1].get();
     C *w_old = W.w[0].get(), *w = W.w[1].get(), *w_new = W.w[2].get();
+    const Gates nog{{}, 0};
+    const Gates &g = gates ? *gates : nog;
     for (int k = 0; k < ITER_UNROLL; ++k) {
+        cudaStream_t ks = cs;
+        cudaGraph_t child = nullptr;
+        if (gates && k > 0) {
+            cudaStreamCaptureStatus cst;
+            cudaGraph_t cg = nullptr;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t ndeps = 0;
+            GL_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = g.h[k];
+            cp.conditional.type = cudaGraphCondTypeIf;
+            cp.conditional.size = 1;
+            cudaGraphNode_t inode;
+            GL_CUDA(cudaGraphAddNode(&inode, cg, deps, nullptr, ndeps, &cp));
+            child = cp.conditional.phGraph_out[0];
+            GL_CUDA(cudaStreamUpdateCaptureDependencies(cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
+            GL_CUDA(cudaStreamBeginCaptureToGraph(cs_child, child, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal));
+            ks = cs_child;
+        }
+        try {
         {
             // algorithmic bytes of the fused Jacobian + dot: off-diagonals, K_ii,
             // |V|, psi, z (own row; neighbours cached) and the written q
@@ -658,45 +761,59 @@ static void enqueue_body(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const
             if (use_df) {
                 // z32 (8 B), d and psi^2 (24 B) and the written q (16 B) per row; the
                 // neighbours' z and the tables from cache
-                ProfScope ps("jz", (double)n * (8 + 24 + 16), cs);
-                k_jz_latdf<<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, lattice_df_view(m), m->lat_hd, W.jd.get(),
+                // FP32 operations of the error-free transformations, counted from the
+                // kernel: about 84 per stored neighbour and 100 per row, as flop
+                // equivalents (2 per operation: each takes an FMA issue slot)
+                ProfScope ps("jz", (double)n * (8 + 24 + 16), ks,
+                             2.0 * (84.0 * (double)m->K.nnz_real + 100.0 * (double)n));
+                k_jz_latdf<<<RED_BLOCKS, RED_THREADS, 0, ks>>>(n, lattice_df_view(m), m->lat_hd, W.jd.get(),
                                                                W.jp2.get(), p->mp_out.get(), (double2 *)W.q.get(),
                                                                part, stop);
             } else {
                 double jb = (double)nnz * (sizeof(C) + 4) + (double)n * (2 * sizeof(T) + 3 * sizeof(C));
-                ProfScope ps("jz", jb, cs);
-                k_jz<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, K, kd, vol, psi, z, W.q.get(), part, stop);
+                // a complex FMA (8 flops) per stored entry; per row the local terms
+                // (K_ii - 1 + 2|psi|^2) z + psi^2 conj(z) (20) and the dot (5)
+                ProfScope ps("jz", jb, ks, 8.0 * (double)nnz + 25.0 * (double)n);
+                k_jz<C, T><<<RED_BLOCKS, RED_THREADS, 0, ks>>>(n, K, kd, vol, psi, z, W.q.get(), part, stop);
             }
         }
         note_launch(2);
-        k_scal_delta<<<1, 1024, 0, cs>>>(S, part);
+        k_scal_delta<<<1, 1024, 0, ks>>>(S, part);
         bool fused = false;
         if constexpr (std::is_same<T, double>::value) fused = vc32 && p;
         if (fused) {
             // FP32 V-cycle between the two fused passes
-            k_vnew_mp<<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, S, (const double2 *)W.q.get(), (const double2 *)v,
+            k_vnew_mp<<<RED_BLOCKS, RED_THREADS, 0, ks>>>(n, S, (const double2 *)W.q.get(), (const double2 *)v,
                                                           (const double2 *)v_old, (double2 *)v_new,
                                                           p->mp_in.get());
-            precond_apply_p32(p, p->mp_in.get(), p->mp_out.get(), stop, cs);
+            precond_apply_p32(p, p->mp_in.get(), p->mp_out.get(), stop, ks);
             note_launch(5);
-            k_widen_dot<<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, m->volp.get(), (const double2 *)v_new,
+            k_widen_dot<<<RED_BLOCKS, RED_THREADS, 0, ks>>>(n, m->volp.get(), (const double2 *)v_new,
                                                             p->mp_out.get(), (double2 *)z_new, part, stop);
         } else {
-            k_vnew<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, S, W.q.get(), v, v_old, v_new);
+            k_vnew<C, T><<<RED_BLOCKS, RED_THREADS, 0, ks>>>(n, S, W.q.get(), v, v_old, v_new);
             if (p) {
-                precond_apply_any<T>(p, v_new, z_new, stop, vc32, cs);
+                precond_apply_any<T>(p, v_new, z_new, stop, vc32, ks);
             } else {
                 note_launch();
-                k_copy_if<C><<<G, 256, 0, cs>>>(n, v_new, z_new, stop);
+                k_copy_if<C><<<G, 256, 0, ks>>>(n, v_new, z_new, stop);
             }
             note_launch(5);
-            k_dot<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, vol, v_new, z_new, part, stop);
+            k_dot<C, T><<<RED_BLOCKS, RED_THREADS, 0, ks>>>(n, vol, v_new, z_new, part, stop);
         }
-        k_scal_givens<<<1, 1024, 0, cs>>>(S, part);
-        k_update<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, S, z, w_old, w, w_new, x);
-        k_true_resid<C, T><<<RED_BLOCKS, RED_THREADS, 0, cs>>>(n, K, kd, vol, psi, b, x, part, S, 0);
-        k_scal_true<<<1, 1024, 0, cs>>>(S, part);
+        k_scal_givens<<<1, 1024, 0, ks>>>(S, part);
+        k_update<C, T><<<RED_BLOCKS, RED_THREADS, 0, ks>>>(n, S, z, w_old, w, w_new, x);
+        k_true_resid<C, T><<<RED_BLOCKS, RED_THREADS, 0, ks>>>(n, K, kd, vol, psi, b, x, part, S, 0);
+        k_scal_true<<<1, 1024, 0, ks>>>(S, part, g, k);
         GL_LAUNCH_CHECK();
+        } catch (...) {
+            if (child) {
+                cudaGraph_t dummy = nullptr;
+                cudaStreamEndCapture(cs_child, &dummy);
+            }
+            throw;
+        }
+        if (child) GL_CUDA(cudaStreamEndCapture(cs_child, &child));
         C *t = v_old;
         v_old = v;
         v = v_new;
@@ -724,11 +841,64 @@ static MinresResult minres(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, con
     if (df) W.ensure_df();
     MinresDev *S = W.S.get();
     double *part = W.part.get();
-    GraphKey key{m, psi, b, x, p ? p->uid : -1, profiler().generation, m->version, vc32 ? 1 : 0, df ? 1 : 0};
-    if (!(key == W.key) || !W.init.exec || !W.body.exec) {
+    // The device-side loop (the whole solve in one graph: the initial phase, then a
+    // WHILE node over bodies of ITER_UNROLL iterations whose later iterations sit in
+    // IF nodes) whenever no kernel class is being timed (the profiler's event
+    // nodes cannot sit in conditional bodies) and R_inf does not nest its own loop.
+    const bool timing_class = profiler().active && !profiler().name.empty();
+    const bool loop = !timing_class && !(p && p->rinf);
+    GraphKey key{m, psi, b, x, p ? p->uid : -1, profiler().generation, m->version, vc32 ? 1 : 0, df ? 1 : 0,
+                 loop ? 1 : 0};
+    if (!(key == W.key) || (loop ? !W.loop.exec : (!W.init.exec || !W.body.exec))) {
         W.key = key;
-        capture(W.init, W.cap, [&](cudaStream_t cs) { enqueue_init<T>(m, p, psi, b, x, vc32, df, W, cs); });
-        capture(W.body, W.cap, [&](cudaStream_t cs) { enqueue_body<T>(m, p, psi, b, x, vc32, df, W, cs); });
+        if (loop) {
+            capture(W.loop, W.cap, [&](cudaStream_t cs) {
+                Profiler &pr = profiler();
+                const int64_t l0 = pr.launches.load();
+                enqueue_init<T>(m, p, psi, b, x, vc32, df, W, cs);
+                const int64_t l1 = pr.launches.load();
+                cudaStreamCaptureStatus cst;
+                cudaGraph_t cg = nullptr;
+                const cudaGraphNode_t *deps = nullptr;
+                size_t ndeps = 0;
+                GL_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
+                Gates g{};
+                g.n = ITER_UNROLL;
+                GL_CUDA(cudaGraphConditionalHandleCreate(&g.h[0], cg, 0, cudaGraphCondAssignDefault));
+                note_launch();
+                k_loop_begin<<<1, 1, 0, cs>>>(g.h[0], S);
+                GL_LAUNCH_CHECK();
+                GL_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
+                cudaGraphNodeParams cp = {};
+                cp.type = cudaGraphNodeTypeConditional;
+                cp.conditional.handle = g.h[0];
+                cp.conditional.type = cudaGraphCondTypeWhile;
+                cp.conditional.size = 1;
+                cudaGraphNode_t wnode;
+                GL_CUDA(cudaGraphAddNode(&wnode, cg, deps, nullptr, ndeps, &cp));
+                cudaGraph_t body = cp.conditional.phGraph_out[0];
+                GL_CUDA(cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+                for (int k = 1; k < ITER_UNROLL; ++k)
+                    GL_CUDA(cudaGraphConditionalHandleCreate(&g.h[k], body, 0, cudaGraphCondAssignDefault));
+                GL_CUDA(cudaStreamBeginCaptureToGraph(W.cap_body, body, nullptr, nullptr, 0,
+                                                      cudaStreamCaptureModeThreadLocal));
+                const int64_t l2 = pr.launches.load();
+                try {
+                    enqueue_body<T>(m, p, psi, b, x, vc32, df, W, W.cap_body, &g, W.cap_if);
+                    k_loop_next<<<1, 1, 0, W.cap_body>>>(g.h[0], S);
+                    GL_LAUNCH_CHECK();
+                } catch (...) {
+                    cudaStreamEndCapture(W.cap_body, &body);
+                    throw;
+                }
+                GL_CUDA(cudaStreamEndCapture(W.cap_body, &body));
+                W.loop_init_launches = l1 - l0 + 1;  // + k_loop_begin
+                W.loop_iter_launches = (pr.launches.load() - l2) / ITER_UNROLL;
+            });
+        } else {
+            capture(W.init, W.cap, [&](cudaStream_t cs) { enqueue_init<T>(m, p, psi, b, x, vc32, df, W, cs); });
+            capture(W.body, W.cap, [&](cudaStream_t cs) { enqueue_body<T>(m, p, psi, b, x, vc32, df, W, cs); });
+        }
     }
     // Stall test: with the double-FP32 Jacobian the ~48-bit apply limits the true
     // residual, so a recurrence three decades past tol hands over to FP64; in
@@ -737,8 +907,16 @@ static MinresResult minres(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, con
     // J applied to the iterate), and further iterations only repeat the test.
     k_set_params<<<1, 1, 0, s>>>(S, tol, maxit, use_true ? 1 : 0, !use_true ? 0.0 : (df ? 1e-3 : 1e-9));
     GL_LAUNCH_CHECK();
-    replay(W.init, s);
     MinresDev h;
+    if (loop) {
+        GL_CUDA(cudaGraphLaunch(W.loop.exec, s));
+        GL_CUDA(cudaMemcpyAsync(&h, S, sizeof(MinresDev), cudaMemcpyDeviceToHost, s));
+        GL_CUDA(cudaStreamSynchronize(s));
+        // the kernels that ran: the initial phase and one iteration's launches per iteration
+        note_launch((int)(W.loop_init_launches + (int64_t)h.it * W.loop_iter_launches + h.replays));
+        GL_REQUIRE(h.status != ST_RUN, GL_ERR_TIMEOUT, "MINRES status word was not updated");
+    } else {
+    replay(W.init, s);
     int64_t polls = 0, max_polls = (int64_t)maxit / ITER_UNROLL + 3;
     bool init_timed = false;  // the initial phase's profiler events are summed once per solve
     for (;;) {
@@ -755,6 +933,7 @@ static MinresResult minres(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, con
         GL_CUDA(cudaStreamSynchronize(s));
         harvest(W.body);
         if (h.status != ST_RUN) break;
+    }
     }
     if (use_true) {
         note_launch(2);
@@ -773,6 +952,7 @@ static gl_status status_of(int st) {
         case ST_CONV: return GL_OK;
         case ST_BREAK: return GL_ERR_BREAKDOWN;
         case ST_NAN: return GL_ERR_NAN;
+        case ST_TIMEOUT: return GL_ERR_TIMEOUT;
         default: return GL_ERR_NOT_CONVERGED;
     }
 }
@@ -1015,6 +1195,12 @@ gl_status batch_run(gl_batch_s *B, const double2 *const *b, double2 *const *x, g
         }
         gl_status st = (h.status == ST_CONV) ? (h.true_rel <= B->o.tol ? GL_OK : GL_ERR_NOT_CONVERGED)
                                              : status_of(h.status);
+        if (st == GL_ERR_TIMEOUT) {
+            sweeps_reset(B->inst[i]->p, s);
+            GL_CUDA(cudaStreamSynchronize(s));
+            st = GL_ERR_TIMEOUT;
+            if (infos) infos[i].converged = 0;
+        }
         if (st != GL_OK && first == GL_OK) first = st;
     }
     return first;
@@ -1104,7 +1290,7 @@ gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, con
                                            o.maxit - total, false, false, W.w32, s);
             total += r.iters;
             est = r.est;
-            if (r.status == ST_BREAK || r.status == ST_NAN) {
+            if (r.status == ST_BREAK || r.status == ST_NAN || r.status == ST_TIMEOUT) {
                 st = status_of(r.status);
                 break;
             }
@@ -1119,6 +1305,14 @@ gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, con
     }
     GL_CUDA(cudaStreamSynchronize(s));
     auto t1 = std::chrono::steady_clock::now();
+    // a coarse-sweep wait that ran out (it wrote the status word) left the
+    // sweeps' counters out of step
+    if (p && st == GL_ERR_TIMEOUT) {
+        sweeps_reset(p, s);
+        GL_CUDA(cudaStreamSynchronize(s));
+        st = GL_ERR_TIMEOUT;
+        inf.converged = 0;
+    }
     inf.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     inf.warmstart_used = o.warmstart ? warmstart_used(o.warmstart, s) : 0;
     inf.lattice_stencil = (p && p->has32 && o.precision != GL_FP64 && p->lattice && m->lat_ok) ? 1 : 0;

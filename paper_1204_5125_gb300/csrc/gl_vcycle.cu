@@ -227,10 +227,42 @@ __global__ void __launch_bounds__(256) k_resid_g(CsrGView<C> A, const R *__restr
 }
 
 // ---------------------------------------------------------------- coarse-level SGS
-// Grid-wide barrier for a cooperative launch (all blocks co-resident), split
-// into arrive and wait so that independent work can run in between.  The wait
-// is bounded: after ~2^24 polls it records an error and lets the block go on,
-// so a broken launch ends instead of hanging.
+// Every wait of the coarse sweeps is bounded by SWEEP_WAIT_NS of the global
+// timer.  A wait that runs out sets the preconditioner's error word and, when
+// the launch belongs to a solve, the solve's status word to STATUS_TIMEOUT, so
+// every later kernel of the solve returns at once and the host reports
+// GL_ERR_TIMEOUT; every sweep launch returns at once while the error word is
+// set, until the host resets the synchronisation state (sweeps_reset).
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// spins until *p >= want; false if SWEEP_WAIT_NS passed first
+__device__ __forceinline__ bool spin_geq(const unsigned long long *p, unsigned long long want) {
+    if (ld_acquire_u64(p) >= want) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (unsigned spins = 1;; ++spins) {
+        if (ld_acquire_u64(p) >= want) return true;
+        if ((spins & 63u) == 0 && globaltimer_ns() - t0 > (unsigned long long)SWEEP_WAIT_NS) return false;
+    }
+}
+__device__ __forceinline__ void report_timeout(int *err, int *stop) {
+    atomicExch(err, 1);
+    if (stop) atomicExch(stop, STATUS_TIMEOUT);
+}
+__device__ __forceinline__ bool sweep_halted(const int *stop, const int *err) {
+    return (stop && *(volatile const int *)stop) || *(volatile const int *)err;
+}
+
 // Grid barrier of the cooperative sweeps: one 64-bit arrival counter per
 // (level, precision) that only grows.  Every launch on a counter uses the same
 // number of CTAs nb, so the counter is a multiple of nb between launches.  At
@@ -243,12 +275,8 @@ __global__ void __launch_bounds__(256) k_resid_g(CsrGView<C> A, const R *__restr
 // and the loads that see it.  The release/acquire pair, after a CTA-wide
 // __syncthreads on both sides, orders every thread's x writes before the other
 // CTAs' reads.  (A flag per CTA polled by one warp, and a counter reset by the
-// last arriver, measured slower.)
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
+// last arriver, measured slower.)  A CTA that gives up a wait leaves the
+// counter out of step; the host zeroes it (sweeps_reset) before the next use.
 // arrival at barrier k; thread 0's base is set at k = 0
 __device__ __forceinline__ void grid_arrive(unsigned long long *cnt, unsigned k, unsigned long long &base) {
     __syncthreads();
@@ -262,22 +290,16 @@ __device__ __forceinline__ void grid_arrive(unsigned long long *cnt, unsigned k,
         }
     }
 }
-// waits for barrier k; false if the wait ran out (thread 0 holds base)
+// waits for barrier k; false if the wait ran out (thread 0 holds base and the
+// extra offset of every wait target, nonzero only when a test has asked for
+// waits that cannot end)
 __device__ __forceinline__ bool grid_wait(const unsigned long long *cnt, unsigned k, unsigned long long base,
-                                          int *err) {
+                                          unsigned long long extra, int *err, int *stop) {
     __shared__ int ok;
     if (threadIdx.x == 0) {
-        const unsigned long long want = base + (unsigned long long)(k + 1) * gridDim.x;
-        unsigned spins = 0;
-        int good = 1;
-        while (ld_acquire_u64(cnt) < want) {
-            if (++spins > (1u << 24)) {
-                atomicExch(err, 1);
-                good = 0;
-                break;
-            }
-        }
-        ok = good;
+        const unsigned long long want = base + (unsigned long long)(k + 1) * gridDim.x + extra;
+        ok = spin_geq(cnt, want) ? 1 : 0;
+        if (!ok) report_timeout(err, stop);
     }
     __syncthreads();
     return ok;
@@ -298,27 +320,27 @@ constexpr int coop_threads() {
     return sizeof(R) == 8 ? 512 : 1024;  // FP64 rows need more registers per thread
 }
 
+// relaxes the rows [lo, hi) of colour c (first round prefetched) with gpn groups
+// of G lanes; `lim`: only columns below it are read (first sweep from zero)
 template <int G, typename C, typename R>
-__global__ void __launch_bounds__(coop_threads<R>()) k_sgs_coop(CsrGView<C> A, const R *__restrict__ diag,
-                                                                const int64_t *__restrict__ cstart, int ncolors,
-                                                                const C *__restrict__ b, C *x, int zero_start,
-                                                                unsigned *bar, int *err,
-                                                                const int *__restrict__ stop) {
-    if (stop && *stop) return;
-    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(bar) + (sizeof(R) == 4 ? 0 : 1);
-    unsigned long long base = 0;
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t grp = t / G, ngroups = (int64_t)gridDim.x * blockDim.x / G;
-    int lane = (int)(t % G);
-    int nphase = 2 * ncolors - 1;
+struct SweepRows {
+    CsrGView<C> A;
+    const R *__restrict__ diag;
+    const C *__restrict__ b;
+    C *x;
+    int lane;
     int32_t pcol[PF];
     C pval[PF];
     C pb;
     R pd = 1;
     int64_t pq0 = 0, pq1 = 0;
-    auto colour_of = [&](int ph) { return ph < ncolors ? ph : 2 * ncolors - 2 - ph; };
+    __device__ SweepRows(const CsrGView<C> &A_, const R *d_, const C *b_, C *x_, int lane_)
+        : A(A_), diag(d_), b(b_), x(x_), lane(lane_) {
+        pb.x = 0;
+        pb.y = 0;
+    }
     // loads the x-independent data of row `row` (first round of a phase)
-    auto prefetch = [&](int64_t row, bool ok) {
+    __device__ __forceinline__ void prefetch(int64_t row, bool ok) {
         pq0 = pq1 = 0;
         if (ok) {
             pq0 = A.rp[row];
@@ -334,10 +356,62 @@ __global__ void __launch_bounds__(coop_threads<R>()) k_sgs_coop(CsrGView<C> A, c
                 pval[k] = A.val[q];
             }
         }
-    };
+    }
+    // one round: row (of this group) relaxed; k == 0 uses the prefetched data;
+    // none: every neighbour still holds zero (first colour from a zero guess)
+    __device__ __forceinline__ void relax(int64_t row, bool ok, int64_t k, int64_t lim, bool none) {
+        C acc;
+        acc.x = 0;
+        acc.y = 0;
+        if (!none) {
+            if (k == 0) {
+#pragma unroll
+                for (int e = 0; e < PF; ++e) {
+                    int64_t q = pq0 + lane + (int64_t)e * G;
+                    if (q < pq1 && pcol[e] < lim) cfma(acc, pval[e], __ldcg(x + pcol[e]));
+                }
+                for (int64_t q = pq0 + lane + (int64_t)PF * G; q < pq1; q += G) {
+                    int32_t cc = __ldg(A.col + q);
+                    if (cc < lim) cfma(acc, A.val[q], __ldcg(x + cc));
+                }
+            } else if (ok) {
+                for (int64_t q = A.rp[row] + lane; q < A.rp[row + 1]; q += G) {
+                    int32_t cc = __ldg(A.col + q);
+                    if (cc < lim) cfma(acc, A.val[q], __ldcg(x + cc));
+                }
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            acc.x += __shfl_down_sync(0xffffffffu, acc.x, o, G);
+            acc.y += __shfl_down_sync(0xffffffffu, acc.y, o, G);
+        }
+        if (ok && lane == 0) {
+            C bb = (k == 0) ? pb : b[row];
+            R d = (R)1 / ((k == 0) ? pd : diag[row]);
+            x[row] = mk((bb.x - acc.x) * d, (bb.y - acc.y) * d);
+        }
+    }
+};
+
+template <int G, typename C, typename R>
+__global__ void __launch_bounds__(coop_threads<R>()) k_sgs_coop(CsrGView<C> A, const R *__restrict__ diag,
+                                                                const int64_t *__restrict__ cstart, int ncolors,
+                                                                const C *__restrict__ b, C *x, int zero_start,
+                                                                unsigned *bar, const unsigned long long *extra_p,
+                                                                int *err, int *stop) {
+    if (sweep_halted(stop, err)) return;
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(bar) + (sizeof(R) == 4 ? 0 : 1);
+    unsigned long long base = 0;
+    const unsigned long long extra = threadIdx.x == 0 ? *extra_p : 0ull;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t grp = t / G, ngroups = (int64_t)gridDim.x * blockDim.x / G;
+    SweepRows<G, C, R> S(A, diag, b, x, (int)(t % G));
+    int nphase = 2 * ncolors - 1;
+    auto colour_of = [&](int ph) { return ph < ncolors ? ph : 2 * ncolors - 2 - ph; };
     {
         int c = colour_of(0);
-        prefetch(cstart[c] + grp, cstart[c] + grp < cstart[c + 1]);
+        S.prefetch(cstart[c] + grp, cstart[c] + grp < cstart[c + 1]);
     }
     for (int ph = 0; ph < nphase; ++ph) {
         int c = colour_of(ph);
@@ -347,64 +421,175 @@ __global__ void __launch_bounds__(coop_threads<R>()) k_sgs_coop(CsrGView<C> A, c
         int64_t rounds = (hi - lo + ngroups - 1) / ngroups;
         for (int64_t k = 0; k < rounds; ++k) {
             int64_t row = lo + k * ngroups + grp;
-            bool ok = row < hi;
-            C acc;
-            acc.x = 0;
-            acc.y = 0;
-            if (!(first && lo == 0)) {
-                if (k == 0) {
-#pragma unroll
-                    for (int e = 0; e < PF; ++e) {
-                        int64_t q = pq0 + lane + (int64_t)e * G;
-                        if (q < pq1 && pcol[e] < lim) cfma(acc, pval[e], __ldcg(x + pcol[e]));
-                    }
-                    for (int64_t q = pq0 + lane + (int64_t)PF * G; q < pq1; q += G) {
-                        int32_t cc = __ldg(A.col + q);
-                        if (cc < lim) cfma(acc, A.val[q], __ldcg(x + cc));
-                    }
-                } else if (ok) {
-                    for (int64_t q = A.rp[row] + lane; q < A.rp[row + 1]; q += G) {
-                        int32_t cc = __ldg(A.col + q);
-                        if (cc < lim) cfma(acc, A.val[q], __ldcg(x + cc));
-                    }
-                }
-            }
-#pragma unroll
-            for (int o = G / 2; o > 0; o >>= 1) {
-                acc.x += __shfl_down_sync(0xffffffffu, acc.x, o, G);
-                acc.y += __shfl_down_sync(0xffffffffu, acc.y, o, G);
-            }
-            if (ok && lane == 0) {
-                C bb = (k == 0) ? pb : b[row];
-                R d = (R)1 / ((k == 0) ? pd : diag[row]);
-                x[row] = mk((bb.x - acc.x) * d, (bb.y - acc.y) * d);
-            }
+            S.relax(row, row < hi, k, lim, first && lo == 0);
         }
         if (ph + 1 < nphase) {
             // arrive, load the next colour's x-independent data, then wait
             grid_arrive(cnt, (unsigned)ph, base);
             int cn = colour_of(ph + 1);
-            prefetch(cstart[cn] + grp, cstart[cn] + grp < cstart[cn + 1]);
-            if (!grid_wait(cnt, (unsigned)ph, base, err)) return;
+            S.prefetch(cstart[cn] + grp, cstart[cn] + grp < cstart[cn + 1]);
+            if (!grid_wait(cnt, (unsigned)ph, base, extra, err, stop)) return;
         }
     }
 }
 
+// The same symmetric step with neighbour flags instead of the grid barrier.
+// CTA b owns a spatial block of the level's nodes (FlagPlan) and after each
+// phase publishes, with a release store, the number of phases it has
+// completed; before phase ph (colour c) it waits, with acquiring loads by one
+// warp, only until every CTA owning a column of its colour-c rows has
+// completed phase ph - 1.  That CTA's last write of any such column came in a
+// phase <= ph - 1, and its reads of b's colour-c rows since their previous
+// relaxation also lie in phases <= ph - 1, so every row reads exactly the
+// values the grid-barrier sweep gives it: the two forms are bit-identical for
+// the same G.  Blocks far apart may then run several phases apart.  Counters
+// only grow: a launch adds 2 nc - 1 to each, so all CTAs of a launch start from
+// the same value (a CTA reads its own at the start); a CTA without rows in a
+// colour only counts the phase.
 template <int G, typename C, typename R>
-static void launch_sgs_coop(const CsrG<C> &A, const R *diag, const int64_t *cstart, int nc, const C *b, C *x,
-                            int zero_start, unsigned *bar, int *err, const int *stop, int64_t max_colour,
-                            cudaStream_t s) {
-    static int per_sm = -1, nsm = 0;
-    const int threads = coop_threads<R>();
-    if (per_sm < 0) {
-        int dev = 0;
-        GL_CUDA(cudaGetDevice(&dev));
-        GL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        GL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sgs_coop<G, C, R>, threads, 0));
-        GL_REQUIRE(per_sm > 0, GL_ERR_CUDA, "cooperative sweep kernel cannot be resident");
+__global__ void __launch_bounds__(coop_threads<R>()) k_sgs_flags(CsrGView<C> A, const R *__restrict__ diag,
+                                                                 const int64_t *__restrict__ cstart, int ncolors,
+                                                                 const int64_t *__restrict__ rstart,
+                                                                 const int32_t *__restrict__ nbr,
+                                                                 const int32_t *__restrict__ nbrc,
+                                                                 const C *__restrict__ b, C *x, int zero_start,
+                                                                 unsigned long long *flags,
+                                                                 const unsigned long long *extra_p, int *err,
+                                                                 int *stop) {
+    if (sweep_halted(stop, err)) return;
+    constexpr int GPB = coop_threads<R>() / G;  // groups (rows per round) of a CTA
+    const int nb = gridDim.x, cta = blockIdx.x;
+    const int grp = threadIdx.x / G;
+    unsigned long long *mine = flags + (size_t)cta * FLAG_STRIDE;
+    // the launch's starting count, and the offset of every wait target (nonzero
+    // only when a test asks for waits that cannot end), kept in shared memory
+    __shared__ unsigned long long s_base, s_target0;
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        s_base = *(volatile unsigned long long *)mine;
+        s_target0 = s_base + *extra_p;
     }
-    int64_t want = (max_colour * G + threads - 1) / threads;
-    int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)per_sm * nsm);
+    __syncthreads();
+    SweepRows<G, C, R> S(A, diag, b, x, (int)(threadIdx.x % G));
+    const int nphase = 2 * ncolors - 1;
+    auto colour_of = [&](int ph) { return ph < ncolors ? ph : 2 * ncolors - 2 - ph; };
+    {
+        const int c = colour_of(0);
+        const int64_t lo = rstart[(int64_t)c * (nb + 1) + cta], hi = rstart[(int64_t)c * (nb + 1) + cta + 1];
+        S.prefetch(lo + grp, lo + grp < hi);
+    }
+    for (int ph = 0; ph < nphase; ++ph) {
+        const int c = colour_of(ph);
+        const bool first = zero_start && ph < ncolors;
+        const int64_t clo = cstart[c];
+        const int64_t lim = first ? clo : INT64_MAX;
+        const int64_t lo = rstart[(int64_t)c * (nb + 1) + cta], hi = rstart[(int64_t)c * (nb + 1) + cta + 1];
+        if (ph > 0 && hi > lo) {
+            if (threadIdx.x < 32) {
+                const int64_t li = (int64_t)cta * ncolors + c;
+                const int cnt = nbrc[li];
+                bool ok = true;
+                if ((int)threadIdx.x < cnt)
+                    ok = spin_geq(flags + (size_t)nbr[li * FLAG_MAXN + threadIdx.x] * FLAG_STRIDE,
+                                  s_target0 + (unsigned long long)ph);
+                ok = __all_sync(0xffffffffu, ok);
+                if (threadIdx.x == 0) {
+                    s_ok = ok ? 1 : 0;
+                    if (!ok) report_timeout(err, stop);
+                }
+            }
+            __syncthreads();
+            if (!s_ok) return;
+        }
+        const int64_t rounds = (hi - lo + GPB - 1) / GPB;
+        for (int64_t k = 0; k < rounds; ++k) {
+            const int64_t row = lo + k * GPB + grp;
+            S.relax(row, row < hi, k, lim, first && clo == 0);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) st_release_u64(mine, s_base + (unsigned long long)ph + 1);
+        if (ph + 1 < nphase) {
+            const int cn = colour_of(ph + 1);
+            const int64_t nlo = rstart[(int64_t)cn * (nb + 1) + cta], nhi = rstart[(int64_t)cn * (nb + 1) + cta + 1];
+            S.prefetch(nlo + grp, nlo + grp < nhi);
+        }
+    }
+}
+
+// ---- partition of the neighbour-flag sweep
+// owner CTA of level node v when CTA b owns node ids [floor(b n / nb), floor((b + 1) n / nb))
+__device__ __forceinline__ int flag_owner(int64_t v, int64_t n, int nb) {
+    int64_t o = v * nb / n;
+    while (o + 1 < nb && (o + 1) * n / nb <= v) ++o;
+    while (o > 0 && o * n / nb > v) --o;
+    return (int)o;
+}
+// rstart[c (nb + 1) + b] = first solve position of colour c whose node id is
+// >= floor(b n / nb) (positions of a colour hold ascending node ids)
+__global__ void k_flag_rstart(int64_t n, int nb, int ncolors, const int64_t *__restrict__ cstart,
+                              const int32_t *__restrict__ perm, int64_t *__restrict__ rstart) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)ncolors * (nb + 1)) return;
+    const int c = (int)(i / (nb + 1));
+    const int bb = (int)(i % (nb + 1));
+    const int64_t key = (int64_t)bb * n / nb;
+    int64_t lo = cstart[c], hi = cstart[c + 1];
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (perm[mid] < key)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    rstart[i] = lo;
+}
+// the CTAs owning a column of CTA b's colour-c rows (b itself left out); the
+// list length is stored even when it exceeds FLAG_MAXN (the host then drops
+// the plan)
+template <typename C>
+__global__ void __launch_bounds__(256) k_flag_nbrs(CsrGView<C> A, int64_t n, int nb, int ncolors,
+                                                   const int32_t *__restrict__ perm,
+                                                   const int64_t *__restrict__ rstart, int32_t *__restrict__ nbr,
+                                                   int32_t *__restrict__ nbrc) {
+    __shared__ unsigned bits[MAX_FLAG_CTAS / 32];
+    const int bb = blockIdx.x, c = blockIdx.y;
+    for (int w = threadIdx.x; w < MAX_FLAG_CTAS / 32; w += blockDim.x) bits[w] = 0u;
+    __syncthreads();
+    const int64_t lo = rstart[(int64_t)c * (nb + 1) + bb], hi = rstart[(int64_t)c * (nb + 1) + bb + 1];
+    for (int64_t row = lo + threadIdx.x; row < hi; row += blockDim.x)
+        for (int64_t q = A.rp[row]; q < A.rp[row + 1]; ++q) {
+            const int o = flag_owner(perm[A.col[q]], n, nb);
+            if (o != bb) atomicOr(&bits[o >> 5], 1u << (o & 31));
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int64_t li = (int64_t)bb * ncolors + c;
+        int cnt = 0;
+        for (int w = 0; w < MAX_FLAG_CTAS / 32; ++w) {
+            unsigned m = bits[w];
+            while (m) {
+                const int o = w * 32 + __ffs(m) - 1;
+                m &= m - 1;
+                if (cnt < FLAG_MAXN) nbr[li * FLAG_MAXN + cnt] = o;
+                ++cnt;
+            }
+        }
+        nbrc[li] = cnt;
+    }
+}
+
+// resident CTAs per SM of a sweep kernel and the SM count (queried once per kernel)
+template <typename K>
+static void sweep_residency(K kern, int threads, int &per_sm, int &nsm) {
+    int dev = 0;
+    GL_CUDA(cudaGetDevice(&dev));
+    GL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    GL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
+    GL_REQUIRE(per_sm > 0, GL_ERR_CUDA, "cooperative sweep kernel cannot be resident");
+}
+
+template <typename K, typename... Args>
+static void launch_coop(K kern, int grid, int threads, cudaStream_t s, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(threads);
@@ -414,8 +599,66 @@ static void launch_sgs_coop(const CsrG<C> &A, const R *diag, const int64_t *csta
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    GL_CUDA(cudaLaunchKernelEx(&cfg, k_sgs_coop<G, C, R>, A.view(), diag, cstart, nc, b, x, zero_start, bar, err,
-                               stop));
+    GL_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
+}
+
+template <int G, typename C, typename R>
+static void launch_sgs_coop(const CsrG<C> &A, const R *diag, const int64_t *cstart, int nc, const C *b, C *x,
+                            int zero_start, unsigned *bar, const unsigned long long *extra, int *err, int *stop,
+                            int64_t max_colour, cudaStream_t s) {
+    static int per_sm = -1, nsm = 0;
+    const int threads = coop_threads<R>();
+    if (per_sm < 0) sweep_residency(k_sgs_coop<G, C, R>, threads, per_sm, nsm);
+    int64_t want = (max_colour * G + threads - 1) / threads;
+    int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)per_sm * nsm);
+    launch_coop(k_sgs_coop<G, C, R>, grid, threads, s, A.view(), diag, cstart, nc, b, x, zero_start, bar, extra, err,
+                stop);
+}
+
+// most CTAs a neighbour-flag sweep of G lanes per row may use (all resident)
+template <int G, typename C, typename R>
+static int flags_max_ctas() {
+    static int per_sm = -1, nsm = 0;
+    if (per_sm < 0) sweep_residency(k_sgs_flags<G, C, R>, coop_threads<R>(), per_sm, nsm);
+    return std::min(per_sm * nsm, MAX_FLAG_CTAS);
+}
+
+template <int G, typename C, typename R>
+static void launch_sgs_flags(const CsrG<C> &A, const R *diag, const int64_t *cstart, int nc, const FlagPlan &F,
+                             const C *b, C *x, int zero_start, unsigned long long *flags,
+                             const unsigned long long *extra, int *err, int *stop, cudaStream_t s) {
+    const bool matches = F.nb > 0 && F.nb <= flags_max_ctas<G, C, R>() && F.G == G;
+    GL_REQUIRE(matches, GL_ERR_ARG, "neighbour-flag sweep without a matching partition");
+    launch_coop(k_sgs_flags<G, C, R>, F.nb, coop_threads<R>(), s, A.view(), diag, cstart, nc,
+                (const int64_t *)F.rstart.get(), (const int32_t *)F.nbr.get(), (const int32_t *)F.nbrc.get(), b, x,
+                zero_start, flags, extra, err, stop);
+}
+
+// Builds the neighbour-flag partition of a coarse level for nb CTAs of G lanes
+// per row.  Returns the longest neighbour list (the plan is usable if it is at
+// most FLAG_MAXN); synchronises s.
+template <typename C>
+static int build_flag_plan(const Level &L, const CsrG<C> &A, int G, int nb, FlagPlan &F, cudaStream_t s) {
+    F.nb = 0;
+    F.G = G;
+    GL_REQUIRE(nb >= 1 && nb <= MAX_FLAG_CTAS, GL_ERR_ARG, "neighbour-flag sweep: bad CTA count");
+    const int nc = L.ncolors;
+    F.rstart.alloc((size_t)nc * (nb + 1));
+    F.nbr.alloc((size_t)nb * nc * FLAG_MAXN);
+    F.nbrc.alloc((size_t)nb * nc);
+    k_flag_rstart<<<grid_for((int64_t)nc * (nb + 1), 256), 256, 0, s>>>(L.n, nb, nc, L.cstart_dev.get(), L.perm,
+                                                                         F.rstart.get());
+    GL_LAUNCH_CHECK();
+    k_flag_nbrs<C><<<dim3(nb, nc), 256, 0, s>>>(A.view(), L.n, nb, nc, L.perm, F.rstart.get(), F.nbr.get(),
+                                                F.nbrc.get());
+    GL_LAUNCH_CHECK();
+    std::vector<int32_t> cnt((size_t)nb * nc);
+    GL_CUDA(cudaMemcpyAsync(cnt.data(), F.nbrc.get(), cnt.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaStreamSynchronize(s));
+    int mx = 0;
+    for (int32_t v : cnt) mx = std::max(mx, (int)v);
+    if (mx <= FLAG_MAXN) F.nb = nb;
+    return mx;
 }
 
 // ---------------------------------------------------------------- cluster sweeps
@@ -756,7 +999,9 @@ static void gs_sweep(Level &L, int level, const typename LevelOps<T>::C *b, type
     double bytes = rows * (sizeof(T) + 2 * sizeof(C));
     if (!(first && lo == 0))
         bytes += (double)L.cnnz[c] * (sizeof(C) + 4) + (double)(first ? lo : L.n - (hi - lo)) * sizeof(C);
-    ProfScope ps(level == 0 ? "gs0" : "gs", bytes, s);
+    // a complex FMA (8 flops) per entry read, (b - acc) / diag per row (6)
+    const double flops = (first && lo == 0 ? 0.0 : 8.0 * (double)L.cnnz[c]) + 6.0 * rows;
+    ProfScope ps(level == 0 ? "gs0" : "gs", bytes, s, flops);
     k_gs<C, T><<<grid_for(hi - lo, 256), 256, 0, s>>>(lo, hi, O::A(L).view(), O::diag(L), b, x, first ? 1 : 0, stop);
 }
 
@@ -818,14 +1063,18 @@ static void smooth(gl_prec_s *p, int l, const typename LevelOps<T>::C *b, typena
     // algorithmic bytes of one symmetric step: every visit of a colour reads its
     // rows' stored entries (value + column) and b, diagonal and writes x; the
     // first colour from a zero guess reads no entries
-    double bytes = 0;
+    double bytes = 0, flops = 0;
     for (int ph = 0; ph < 2 * L.ncolors - 1; ++ph) {
         int c = ph < L.ncolors ? ph : 2 * L.ncolors - 2 - ph;
         double rows = (double)(L.cstart[c + 1] - L.cstart[c]);
         bytes += rows * (2 * sizeof(C) + sizeof(T));
-        if (!(zero_start && ph == 0)) bytes += (double)L.cnnz[c] * (sizeof(C) + 4);
+        flops += 6.0 * rows;
+        if (!(zero_start && ph == 0)) {
+            bytes += (double)L.cnnz[c] * (sizeof(C) + 4);
+            flops += 8.0 * (double)L.cnnz[c];
+        }
     }
-    ProfScope ps("gs", bytes, s);
+    ProfScope ps("gs", bytes, s, flops);
     const int sG = sizeof(T) == 4 ? L.sgs_G32 : L.sgs_G64;
     if constexpr (sizeof(T) == 4) {
         if (L.cl_size > 0 && p->cluster_sweeps) {
@@ -834,8 +1083,20 @@ static void smooth(gl_prec_s *p, int l, const typename LevelOps<T>::C *b, typena
             return;
         }
     }
+    // the status word of the solve this sweep belongs to: a wait that runs out writes it
+    int *status = const_cast<int *>(stop);
+    const int sync = sizeof(T) == 4 ? L.sync32 : L.sync64;
+    if (sync == 1) {
+        const FlagPlan &F = sizeof(T) == 4 ? L.fl32 : L.fl64;
+        unsigned long long *flags = L.flags.get() + (sizeof(T) == 4 ? 0 : (size_t)MAX_FLAG_CTAS * FLAG_STRIDE);
+        GL_DISPATCH_G(sG, (launch_sgs_flags<GG, C, T>(A, O::diag(L), L.cstart_dev.get(), L.ncolors, F, b, x,
+                                                       zero_start ? 1 : 0, flags, p->wait_extra.get(), p->err.get(),
+                                                       status, s)));
+        return;
+    }
     GL_DISPATCH_G(sG, (launch_sgs_coop<GG, C, T>(A, O::diag(L), L.cstart_dev.get(), L.ncolors, b, x,
-                                                  zero_start ? 1 : 0, L.barrier.get(), p->err.get(), stop, maxc, s)));
+                                                  zero_start ? 1 : 0, L.barrier.get(), p->wait_extra.get(),
+                                                  p->err.get(), status, maxc, s)));
 }
 
 template <typename T>
@@ -1110,38 +1371,82 @@ void precond_apply_p64_via32(gl_prec_s *p, const double2 *v, double2 *z, const i
     GL_LAUNCH_CHECK();
 }
 
+// CTAs of a neighbour-flag sweep by default: about 3/4 of a round of rows per
+// CTA in the largest colour (the node-range partition spreads a colour unevenly)
+template <typename T>
+static int flags_default_nb(const Level &L, int G, int max_ctas) {
+    int64_t maxc = 0;
+    for (int c = 0; c < L.ncolors; ++c) maxc = std::max(maxc, L.cstart[c + 1] - L.cstart[c]);
+    const int64_t per = std::max<int64_t>(1, (int64_t)(coop_threads<T>() / G) * 3 / 4);
+    return (int)std::min<int64_t>(std::max<int64_t>((maxc + per - 1) / per, 1), max_ctas);
+}
+
+template <typename T>
+static int flags_max_ctas_g(int G) {
+    using C = typename LevelOps<T>::C;
+    int r = 0;
+    GL_DISPATCH_G(G, (r = flags_max_ctas<GG, C, T>()));
+    return r;
+}
+
+static void zero_flags(Level &L, bool fp32, cudaStream_t s) {
+    const size_t words = (size_t)MAX_FLAG_CTAS * FLAG_STRIDE;
+    GL_CUDA(cudaMemsetAsync(L.flags.get() + (fp32 ? 0 : words), 0, words * sizeof(unsigned long long), s));
+}
+
 // chooses how every coarse level runs its symmetric Gauss-Seidel steps: the
-// lanes-per-row width G of the cooperative-grid sweep (a latency-bound kernel
-// wants more lanes per row than the throughput-bound SpMV that set the operator's
-// own G) and, in FP32, the thread-block-cluster sweep for levels whose vector
-// fits a cluster.  With autotuning every candidate (G = 2, 4, 8, 16) is timed on
-// this GPU (best of two after a warm-up launch, on zero vectors) and the fastest
-// kept; without it the operator's G, and the cluster sweep wherever it fits.
+// lanes-per-row width G (a latency-bound kernel wants more lanes per row than
+// the throughput-bound SpMV that set the operator's own G), the synchronisation
+// between colours (grid barrier, or neighbour flags with nb CTAs) and, in FP32,
+// the thread-block-cluster sweep for levels whose vector fits a cluster.  With
+// autotuning every candidate (G = 2, 4, 8, 16; for the flags the default CTA
+// count and the most that stay resident) is timed on this GPU (best of two after
+// a warm-up launch, on zero vectors) and the fastest kept; without it the
+// operator's G, the flags where their partition fits (else the grid barrier),
+// and the cluster sweep wherever it fits.  options.sweep_sync = 1 or 2 keeps
+// only the grid-barrier or only the flag candidates (the flags fall back to the
+// barrier where no partition fits).  All of them give the same rows for the
+// same G.
 template <typename T>
 static void plan_sweeps_t(gl_prec_s *p, cudaStream_t s) {
     using O = LevelOps<T>;
     using C = typename O::C;
+    constexpr bool fp32 = sizeof(T) == 4;
     cudaEvent_t e0, e1;
     GL_CUDA(cudaEventCreate(&e0));
     GL_CUDA(cudaEventCreate(&e1));
+    const bool try_grid = p->sweep_sync != 2, try_flags = p->sweep_sync != 1;
     for (int l = 1; l < p->nlev - 1; ++l) {
         Level &L = p->L[l];
         const CsrG<C> &A = O::Ag(L);
-        int &sG = sizeof(T) == 4 ? L.sgs_G32 : L.sgs_G64;
+        int &sG = fp32 ? L.sgs_G32 : L.sgs_G64;
+        int &sync = fp32 ? L.sync32 : L.sync64;
+        FlagPlan &F = fp32 ? L.fl32 : L.fl64;
         sG = A.G;
-        if constexpr (sizeof(T) == 4) {
+        sync = 0;
+        F = FlagPlan{};
+        if constexpr (fp32) {
             L.cl_size = 0;
             L.cl_chunk = 0;
         }
         int size = 0, chunk = 0;
-        if constexpr (sizeof(T) == 4) {
-            if (p->cluster_sweeps && L.n <= INT32_MAX) GL_DISPATCH_G(A.G, (plan_sgs_cluster<GG>(L.n, size, chunk)));
+        if constexpr (fp32) {
+            if (p->cluster_sweeps && p->sweep_sync == 0 && L.n <= INT32_MAX)
+                GL_DISPATCH_G(A.G, (plan_sgs_cluster<GG>(L.n, size, chunk)));
         }
         if (!p->autotune) {
-            if constexpr (sizeof(T) == 4) {
+            if (try_flags) {
+                const int nb = flags_default_nb<T>(L, sG, flags_max_ctas_g<T>(sG));
+                if (build_flag_plan<C>(L, A, sG, nb, F, s) <= FLAG_MAXN)
+                    sync = 1;
+                else
+                    F = FlagPlan{};
+            }
+            if constexpr (fp32) {
                 L.cl_size = size;
                 L.cl_chunk = chunk;
             }
+            zero_flags(L, fp32, s);
             continue;
         }
         int64_t maxc = 0;
@@ -1163,37 +1468,74 @@ static void plan_sweeps_t(gl_prec_s *p, cudaStream_t s) {
             return best;
         };
         float best = 1e30f;
-        int bestG = A.G;
+        int bestG = A.G, best_sync = 0, best_nb = 0;
         bool best_cluster = false;
+        unsigned long long *flags = L.flags.get() + (fp32 ? 0 : (size_t)MAX_FLAG_CTAS * FLAG_STRIDE);
         for (int g : {2, 4, 8, 16}) {
-            // a new grid size on this level's barrier counter: start it from zero
-            GL_CUDA(cudaMemsetAsync(L.barrier.get(), 0, GRID_BARRIER_WORDS * sizeof(unsigned), s));
-            float t = time_it([&] {
-                GL_DISPATCH_G(g, (launch_sgs_coop<GG, C, T>(A, O::diag(L), L.cstart_dev.get(), L.ncolors, b, x, 0,
-                                                             L.barrier.get(), p->err.get(), nullptr, maxc, s)));
-            });
-            if (t < best) best = t, bestG = g;
-            if (verbose()) fprintf(stderr, "gl: level %d (n %lld, %d colours, %s) sweep G %d: %.1f us\n", l,
-                                   (long long)L.n, L.ncolors, sizeof(T) == 4 ? "FP32" : "FP64", g, 1e3 * t);
-            if constexpr (sizeof(T) == 4) {
+            if (try_grid) {
+                // a new grid size on this level's barrier counter: start it from zero
+                GL_CUDA(cudaMemsetAsync(L.barrier.get(), 0, GRID_BARRIER_WORDS * sizeof(unsigned), s));
+                float t = time_it([&] {
+                    GL_DISPATCH_G(g, (launch_sgs_coop<GG, C, T>(A, O::diag(L), L.cstart_dev.get(), L.ncolors, b, x,
+                                                                 0, L.barrier.get(), p->wait_extra.get(),
+                                                                 p->err.get(), nullptr, maxc, s)));
+                });
+                if (t < best) best = t, bestG = g, best_sync = 0, best_cluster = false;
+                if (verbose()) fprintf(stderr, "gl: level %d (n %lld, %d colours, %s) sweep G %d grid: %.1f us\n", l,
+                                       (long long)L.n, L.ncolors, fp32 ? "FP32" : "FP64", g, 1e3 * t);
+            }
+            if (try_flags) {
+                const int mx = flags_max_ctas_g<T>(g);
+                const int nb0 = flags_default_nb<T>(L, g, mx);
+                std::vector<int> nbs{nb0};
+                if (mx != nb0) nbs.push_back(mx);
+                for (int nb : nbs) {
+                    FlagPlan cand;
+                    const int longest = build_flag_plan<C>(L, A, g, nb, cand, s);
+                    if (longest > FLAG_MAXN) {
+                        if (verbose()) fprintf(stderr, "gl: level %d flags G %d nb %d: %d neighbours, too many\n", l,
+                                               g, nb, longest);
+                        continue;
+                    }
+                    zero_flags(L, fp32, s);
+                    float t = time_it([&] {
+                        GL_DISPATCH_G(g, (launch_sgs_flags<GG, C, T>(A, O::diag(L), L.cstart_dev.get(), L.ncolors,
+                                                                      cand, b, x, 0, flags, p->wait_extra.get(),
+                                                                      p->err.get(), nullptr, s)));
+                    });
+                    if (verbose())
+                        fprintf(stderr, "gl: level %d sweep G %d flags nb %d (<= %d neighbours): %.1f us\n", l, g,
+                                nb, longest, 1e3 * t);
+                    if (t < best) {
+                        best = t, bestG = g, best_sync = 1, best_nb = nb, best_cluster = false;
+                        F = std::move(cand);
+                    }
+                }
+            }
+            if constexpr (fp32) {
                 if (size > 0) {
                     float tc = time_it([&] {
                         GL_DISPATCH_G(g, (launch_sgs_cluster<GG>(A, O::diag(L), L.cstart_dev.get(), L.ncolors, b, x, 0,
                                                                   size, chunk, nullptr, s)));
                     });
-                    if (tc < best) best = tc, bestG = g, best_cluster = true;
+                    if (tc < best) best = tc, bestG = g, best_cluster = true, best_sync = 0;
                     if (verbose()) fprintf(stderr, "gl: level %d cluster sweep G %d: %.1f us\n", l, g, 1e3 * tc);
                 }
             }
         }
         sG = bestG;
+        sync = best_sync;
+        if (sync != 1) F = FlagPlan{};
         if (verbose())
-            fprintf(stderr, "gl: level %d %s sweep: G %d%s (largest colour %lld rows)\n", l,
-                    sizeof(T) == 4 ? "FP32" : "FP64", bestG, best_cluster ? ", cluster" : "", (long long)maxc);
-        // the timing ran other grid sizes on this level's barrier counters
+            fprintf(stderr, "gl: level %d %s sweep: G %d%s%s (largest colour %lld rows)\n", l, fp32 ? "FP32" : "FP64",
+                    bestG, best_cluster ? ", cluster" : "",
+                    best_sync == 1 ? (std::string(", flags nb ") + std::to_string(best_nb)).c_str() : "",
+                    (long long)maxc);
+        // the timing ran other launch shapes on this level's counters
         GL_CUDA(cudaMemsetAsync(L.barrier.get(), 0, GRID_BARRIER_WORDS * sizeof(unsigned), s));
+        zero_flags(L, fp32, s);
         GL_CUDA(cudaMemsetAsync(p->err.get(), 0, sizeof(int), s));
-        if constexpr (sizeof(T) == 4) {
+        if constexpr (fp32) {
             if (best_cluster) {
                 L.cl_size = size;
                 L.cl_chunk = chunk;
@@ -1202,6 +1544,54 @@ static void plan_sweeps_t(gl_prec_s *p, cudaStream_t s) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+}
+
+// the partitions of sweep choices taken over from a template (same sparsity)
+template <typename T>
+static void rebuild_flag_plans_t(gl_prec_s *p, const int *nbs, cudaStream_t s) {
+    using O = LevelOps<T>;
+    using C = typename O::C;
+    constexpr bool fp32 = sizeof(T) == 4;
+    for (int l = 1; l < p->nlev - 1; ++l) {
+        Level &L = p->L[l];
+        int &sync = fp32 ? L.sync32 : L.sync64;
+        FlagPlan &F = fp32 ? L.fl32 : L.fl64;
+        F = FlagPlan{};
+        if (sync == 1) {
+            const int G = fp32 ? L.sgs_G32 : L.sgs_G64;
+            if (nbs[l] < 1 || nbs[l] > flags_max_ctas_g<T>(G) || build_flag_plan<C>(L, O::Ag(L), G, nbs[l], F, s) > FLAG_MAXN) {
+                F = FlagPlan{};
+                sync = 0;
+            }
+        }
+        zero_flags(L, fp32, s);
+    }
+}
+
+void rebuild_flag_plans(gl_prec_s *p, bool fp32, cudaStream_t s) {
+    int nbs[MAX_LEVELS];
+    for (int l = 0; l < MAX_LEVELS; ++l) nbs[l] = fp32 ? p->tuned[l].nb32 : p->tuned[l].nb64;
+    if (fp32)
+        rebuild_flag_plans_t<float>(p, nbs, s);
+    else
+        rebuild_flag_plans_t<double>(p, nbs, s);
+}
+
+void sweeps_reset(gl_prec_s *p, cudaStream_t s) {
+    for (int l = 1; l < p->nlev - 1; ++l) {
+        Level &L = p->L[l];
+        if (L.barrier.get()) GL_CUDA(cudaMemsetAsync(L.barrier.get(), 0, GRID_BARRIER_WORDS * sizeof(unsigned), s));
+        if (L.flags.get()) GL_CUDA(cudaMemsetAsync(L.flags.get(), 0, L.flags.bytes(), s));
+    }
+    GL_CUDA(cudaMemsetAsync(p->err.get(), 0, sizeof(int), s));
+    GL_CUDA(cudaMemsetAsync(p->wait_extra.get(), 0, sizeof(unsigned long long), s));
+}
+
+int sweeps_failed(gl_prec_s *p, cudaStream_t s) {
+    int h = 0;
+    GL_CUDA(cudaMemcpyAsync(&h, p->err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaStreamSynchronize(s));
+    return h;
 }
 
 void plan_sweeps(gl_prec_s *p, bool fp32, cudaStream_t s) {

@@ -57,7 +57,12 @@ def test_batch_matches_single_solves(oracle_mod, precision):
             assert true_relres(om, psi, b, xs[k].cpu().numpy()) <= 1.01e-10
             x1 = torch.zeros_like(bs[k])
             st1, info1 = gl.gl_jacobian_solve(meshes[k], psis[k], None, bs[k], x1, opts)
-            assert st1 == 0 and abs(info1.iters - infos[k].iters) <= 1
+            # iteration counts: within one in FP64; with the FP32 V-cycle the count
+            # depends on FP32 rounding (the batch keeps the FP64 Jacobian where a
+            # single solve on an even-N lattice takes the double-FP32 one, and the
+            # setup timing may pick other lanes per row), so a few more may differ
+            slack = 1 if precision == gl.GL_FP64 else 3
+            assert st1 == 0 and abs(info1.iters - infos[k].iters) <= slack, (N, info1.iters, infos[k].iters)
             assert torch.linalg.norm(x1 - xs[k]) <= 1e-8 * torch.linalg.norm(x1)
     finally:
         for m in meshes:
