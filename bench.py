@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--max-coarse", type=int, default=4096, help="coarsest-level size bound of the AMG hierarchy")
     ap.add_argument("--no-learned", action="store_true", help="skip training and timing the learned warm start")
     ap.add_argument("--ws-steps", type=int, default=200, help="Adam steps of warm-start training")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batch64 and 2D workload measurements")
     return ap.parse_args()
 
 
@@ -160,12 +161,11 @@ def workload(N):
     return dim, mu, bh, n
 
 
-def cpu_baseline(N, b, x_gpu, max_coarse):
-    """The oracle's FP64 R_1-MINRES solve of the same system on the host (setup
-    excluded, like the GPU number); also the GPU solution's error against it."""
-    import oracle
-
+def _oracle_solve_timed(oracle, N, b, max_coarse, threads):
+    """One full FP64 R_1-MINRES solve of the oracle on `threads` host threads (0: all
+    processors); returns (seconds of the solve, solution, info, threads used, setup s)."""
     dim, mu, bh, n = workload(N)
+    used = oracle.set_threads(threads)
     t0 = time.perf_counter()
     m = oracle.Mesh(dim, N, mu, bh)
     psi = np.ones(n, complex)
@@ -173,20 +173,35 @@ def cpu_baseline(N, b, x_gpu, max_coarse):
     t1 = time.perf_counter()
     x, info = P.minres(b)
     t2 = time.perf_counter()
+    return t2 - t1, x, info, used, t1 - t0
+
+
+def cpu_baseline(N, b, x_gpu, max_coarse):
+    """The oracle's FP64 R_1-MINRES solve of the same system on the host (setup
+    excluded, like the GPU number), on one thread and on all host processors (the
+    oracle shares out only its row loops, so both give the same bits); also the
+    GPU solution's error against it."""
+    import oracle
+
+    t1, x, info, _, setup1 = _oracle_solve_timed(oracle, N, b, max_coarse, 1)
+    tall, xall, infoall, cores, _ = _oracle_solve_timed(oracle, N, b, max_coarse, 0)
+    oracle.set_threads(1)
     err = float(np.linalg.norm(x_gpu - x) / np.linalg.norm(x)) if x_gpu is not None else None
     return {
-        "value": 1.0 / (t2 - t1), "unit": UNIT, "cores": 1, "kind": "oracle",
-        "sample": f"one full FP64 R_1-MINRES solve of the {N}^3 cube system on 1 host thread "
-                  f"({info.iters} iterations, true relres {info.true_relres:.2e}; "
-                  f"mesh+setup {t1 - t0:.1f} s untimed)",
-        "iters": info.iters,
+        "value": 1.0 / tall, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "sample": f"one full FP64 R_1-MINRES solve of the {N}^3 cube system on {cores} host threads "
+                  f"({infoall.iters} iterations, true relres {infoall.true_relres:.2e}; mesh+setup untimed)",
+        "iters": infoall.iters, "same_bits_as_one_thread": bool(np.array_equal(x, xall)),
+        "one_thread": {"value": 1.0 / t1, "unit": UNIT, "cores": 1, "seconds": t1,
+                       "mesh_setup_s": setup1},
     }, err
 
 
 def run_reference(args):
-    """The oracle timed on the host cores, in the bench's metric and config.  Each
-    step is a bounded sample: 3 MINRES iterations, scaled by the iteration count of
-    one full oracle solve done during warm-up."""
+    """The oracle timed on the host processors, in the bench's metric and config:
+    every step is one whole FP64 R_1-MINRES solve of the workload's system (setup
+    once, untimed), on all host processors (the oracle's row loops; its sums stay
+    serial, so the result does not depend on the thread count)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -194,34 +209,150 @@ def run_reference(args):
 
     N = args.N
     dim, mu, bh, n = workload(N)
+    cores = oracle.set_threads(0)
     m = oracle.Mesh(dim, N, mu, bh)
     psi = np.ones(n, complex)
     b = gi.complex_normal(n, 5)
     P = oracle.Precond(m, psi, max_coarse=args.max_coarse)
-    x, info = P.minres(b)
-    full_iters = info.iters
-    per_it = []
-    P.opts.tol = 1e-300
-    P.opts.maxit = 3
+    secs, iters = [], []
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        P.minres(b)
+        _, info = P.minres(b)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
-            per_it.append(dt / 3)
-    t_it = float(np.mean(per_it))
-    value = 1.0 / (t_it * full_iters)
+            secs.append(dt)
+            iters.append(info.iters)
+    total = float(np.sum(secs))
+    value = args.steps / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_it * full_iters,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"cube{N}^3 mu=1 bhat=(1,1,1)/sqrt3 psi=1 b=CN(0,1) seed 5",
                    "n": n, "tol": 1e-10, "l2": "inputs larger than L2"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"3 MINRES iterations per step x {full_iters} iterations per full solve"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"one whole FP64 R_1-MINRES solve per step ({iters[0] if iters else 0} "
+                                   f"iterations) on {cores} host threads, setup untimed"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def alu_roofline(pr, nsolves, peak_gbs, peak_gflops, kernel, peak_kind):
+    """Roofline of a kernel class bounded by min(HBM, arithmetic pipe): the bound is
+    whichever of bytes / HBM peak and flops / FMA peak takes longer."""
+    sec = pr["ms"] / 1e3
+    t_hbm = pr["bytes"] / (peak_gbs * 1e9)
+    t_alu = pr["flops"] / (peak_gflops * 1e9) if pr["flops"] > 0 else 0.0
+    alu = t_alu > t_hbm
+    r = {
+        "bound": "alu" if alu else "hbm", "kernel": kernel,
+        "unit": "GFLOP/s" if alu else "GB/s",
+        "achieved": (pr["flops"] / sec / 1e9) if alu else (pr["bytes"] / sec / 1e9),
+        "peak": peak_gflops if alu else peak_gbs,
+        "frac": max(t_hbm, t_alu) / sec, "frac_hbm": t_hbm / sec, "frac_alu": t_alu / sec,
+        "alg_bytes_per_launch": pr["bytes"] / pr["timed"], "alg_flops_per_launch": pr["flops"] / pr["timed"],
+        "launches_timed": pr["timed"], "avg_launch_us": 1e3 * pr["ms"] / pr["timed"],
+        "ms_per_solve": pr["ms"] / nsolves, "peak_kind": peak_kind,
+    }
+    return r
+
+
+def run_batch64(gl, torch, dev, steps=3):
+    """The batched-continuation workload: 64 2D squares, N_s log-uniform in [32, 512]
+    (seed 6), mu_s = 2 (s + 1) / 64, psi_s = 1 + 0.1 disk noise (seed 7 + s), b_s
+    complex normal (seed 100 + s); one CUDA-graph launch per run."""
+    sizes = gi.batch_sizes(64, seed=6)
+    meshes, psis, bs = [], [], []
+    for s_, N in enumerate(sizes):
+        n = N * N
+        meshes.append(gl.gl_mesh_create(2, N, 2.0 * (s_ + 1) / 64))
+        psis.append(torch.from_numpy(gi.psi_noisy_one(n, 7 + s_)).to(dev))
+        bs.append(torch.from_numpy(gi.complex_normal(n, 100 + s_)).to(dev))
+    xs = [torch.zeros_like(b) for b in bs]
+    out = {"instances": len(sizes), "unknowns": int(sum(N * N for N in sizes)),
+           "sizes": f"{min(sizes)}^2..{max(sizes)}^2"}
+    try:
+        for name, prec in (("fp64", gl.GL_FP64), ("fp32_vcycle", gl.GL_MIXED_PRECOND)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B = gl.gl_batch_create(meshes, psis, gl.options(precision=prec))
+            torch.cuda.synchronize()
+            setup = time.perf_counter() - t0
+            try:
+                st, infos = gl.gl_batch_run(B, bs, xs)
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record()
+                for _ in range(steps):
+                    for x in xs:
+                        x.zero_()
+                    st, infos = gl.gl_batch_run(B, bs, xs)
+                ev1.record()
+                torch.cuda.synchronize()
+                ms = ev0.elapsed_time(ev1) / steps
+                out[name] = {"solves_per_s": 1e3 * len(sizes) / ms, "ms_per_batch": ms, "setup_s": setup,
+                             "status": st, "all_converged": all(i.converged for i in infos),
+                             "max_true_relres": max(i.true_relres for i in infos),
+                             "iters_max": max(i.iters for i in infos)}
+            finally:
+                gl.gl_batch_destroy(B)
+    finally:
+        for m in meshes:
+            gl.gl_mesh_destroy(m)
+    return out
+
+
+def run_square(gl, torch, dev, name, steps=5):
+    """Solves/s on the 2D workloads: square64 (psi uniform in the unit disk, seed 1,
+    b ~ CN(0,1) seed 1, FP64) and square1024 (the Newton system of the state from
+    Newton at mu = 2 started at psi = 1, plus 0.1 disk noise seed 2; FP64 and the
+    FP32 V-cycle)."""
+    dim, N, mu, bh = gi.WORKLOADS[name]
+    n = N * N
+    m = gl.gl_mesh_create(dim, N, mu, bh)
+    out = {"n": n}
+    try:
+        if name == "square64":
+            psi = torch.from_numpy(gi.disk(n, 1)).to(dev)
+            b = torch.from_numpy(gi.complex_normal(n, 1)).to(dev)
+            forms = (("fp64", gl.GL_FP64),)
+        else:
+            psi = torch.ones(n, dtype=torch.complex128, device=dev)
+            for _ in range(5):
+                r = torch.zeros_like(psi)
+                gl.gl_residual(m, psi, r)
+                if float(torch.sqrt(torch.sum(torch.abs(r) ** 2))) / (N - 1) <= 1e-7:
+                    break
+                gl.gl_newton_step(m, psi, gl.options(max_coarse=512, tol=1e-8))
+            psi += torch.from_numpy(0.1 * gi.disk(n, 2)).to(dev)
+            r = torch.zeros_like(psi)
+            gl.gl_residual(m, psi, r)
+            b = -r
+            forms = (("fp64", gl.GL_FP64), ("fp32_vcycle", gl.GL_MIXED_PRECOND))
+        x = torch.zeros_like(psi)
+        for fname, prec in forms:
+            o = gl.options(precision=prec, max_coarse=512)
+            P = gl.gl_precond_setup(m, psi, o)
+            try:
+                infos = []
+                for rep in range(1 + steps):
+                    if rep == 1:
+                        torch.cuda.synchronize()
+                        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        ev0.record()
+                    x.zero_()
+                    st, info = gl.gl_jacobian_solve(m, psi, P, b, x, o)
+                    infos.append(info)
+                ev1.record()
+                torch.cuda.synchronize()
+                ms = ev0.elapsed_time(ev1) / steps
+                out[fname] = {"solves_per_s": 1e3 / ms, "iters": infos[-1].iters,
+                              "true_relres": max(i.true_relres for i in infos), "status": st}
+            finally:
+                gl.gl_precond_destroy(P)
+    finally:
+        gl.gl_mesh_destroy(m)
+    return out
 
 
 def main():
@@ -384,13 +515,31 @@ def main():
     value64 = whole_job_rate(len(infos64), world, ms64 / 1e3)
     peak, peak_kind = peaks()
 
+    # setup-inclusive rates: a preconditioner built from scratch (aggregation,
+    # colouring, Galerkin products, the dense coarsest inverse, the setup-time
+    # kernel timing, the FP32 copies) or taking over an earlier one's symbolic part
+    torch.cuda.synchronize()
+    ts0 = time.perf_counter()
+    prec_like = gl.gl_precond_setup_like(mesh, psi, prec, opts_mixed)
+    torch.cuda.synchronize()
+    like_s = time.perf_counter() - ts0
+    gl.gl_precond_destroy(prec_like)
+    setup_inclusive = {
+        "from_scratch": {"setup_s": t2 - t1, "solves_per_s": 1.0 / (t2 - t1 + ms / 1e3 / args.steps)},
+        "setup_like": {"setup_s": like_s, "solves_per_s": 1.0 / (like_s + ms / 1e3 / args.steps)},
+    }
+
+    # measured arithmetic peaks of this GPU (own FMA kernel, CUDA events)
+    fp64_gflops = gl.gl_measure_fma_peak(gl.GL_FP64)
+    fp32_gflops = gl.gl_measure_fma_peak(gl.GL_MIXED)
+
     # live per-class timing (CUDA events around every launch of the class, on the
     # launching stream): the finest-level sweep from the headline run, then the
     # coarse-level sweeps and the Jacobian in two short runs of the same form
     KERNELS = {
         "gs0": ("k_gs_lat (Gauss-Seidel colour sweep, finest level, FP32, tabulated lattice stencil)"
                 if infos[-1].lattice_stencil else "k_gs (Gauss-Seidel colour sweep, finest level, FP32)"),
-        "gs": "k_sgs_cluster / k_sgs_coop (symmetric Gauss-Seidel step, coarse levels, FP32)",
+        "gs": "k_sgs_flags / k_sgs_coop / k_sgs_cluster (symmetric Gauss-Seidel step, coarse levels, FP32)",
         "jz": ("k_jz_latdf (double-FP32 Jacobian apply fused with the Lanczos dot; SM-pipe bound)"
                if infos[-1].df_jacobian else "k_jz (Jacobian apply fused with the Lanczos dot, FP64)"),
     }
@@ -411,10 +560,29 @@ def main():
             "launches_timed": pr["timed"], "avg_launch_us": 1e3 * pr["ms"] / pr["timed"],
             "ms_per_solve": pr["ms"] / nsolves, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
         }
+    # the double-FP32 Jacobian is bounded by the FP32 pipe: its min(HBM, ALU) roofline
+    if "jz" in rooflines and profs["jz"][0]["flops"] > 0 and infos[-1].df_jacobian:
+        rooflines["jz"]["alu"] = alu_roofline(profs["jz"][0], 2, peak, fp32_gflops,
+                                              KERNELS["jz"], "measured FP32 FMA peak (own kernel)")
+    # the FP64 form's classes against min(HBM, FP64 ALU)
+    rooflines_fp64 = {}
+    KERNELS64 = {"gs0": "k_gs (Gauss-Seidel colour sweep, finest level, FP64)",
+                 "gs": "k_sgs_flags / k_sgs_coop (symmetric Gauss-Seidel step, coarse levels, FP64)",
+                 "jz": "k_jz (Jacobian apply fused with the Lanczos dot, FP64)"}
+    for cls in ("gs0", "gs", "jz"):
+        _, _, pr = timed(opts_fp64, 2, 1, profile_class=cls)
+        if pr and pr["timed"] and pr["ms"] > 0:
+            rooflines_fp64[cls] = alu_roofline(pr, 2, peak, fp64_gflops, KERNELS64[cls],
+                                               f"{peak_kind} hbm_gbs (copy) / measured FP64 FMA peak (own kernel)")
     dominant = max(rooflines, key=lambda k: rooflines[k]["ms_per_solve"]) if rooflines else None
     roofline = dict(rooflines[dominant]) if dominant else None
     if roofline:
         roofline["class"] = dominant
+
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra:
+        extra = {"batch64": run_batch64(gl, torch, dev), "square64": run_square(gl, torch, dev, "square64"),
+                 "square1024": run_square(gl, torch, dev, "square1024")}
 
     cpu = None
     err_vs_oracle = None
@@ -429,7 +597,10 @@ def main():
             "config": {"workload": f"cube{N}^3 mu=1 bhat=(1,1,1)/sqrt3 psi=1 b=CN(0,1) seed 5",
                        "n": n, "tol": 1e-10, "form": form, "max_coarse": args.max_coarse,
                        "l2": "inputs larger than L2 (operators ~0.5 GB)", "levels": [lv["n"] for lv in levels],
-                       "colors": [lv["ncolors"] for lv in levels], "parallelism": f"replicas x{world}"},
+                       "colors": [lv["ncolors"] for lv in levels], "parallelism": f"replicas x{world}",
+                       "coarse_sweeps": {"fp32": gl.gl_precond_level_sweep(prec, 1, gl.GL_MIXED_PRECOND),
+                                         "fp64": gl.gl_precond_level_sweep(prec, 1, gl.GL_FP64)}
+                       if nlev > 2 else None},
             "iters_mixed": [i.iters for i in infos], "outer_mixed": [i.outer_iters for i in infos],
             "mixed_forms": quick, "learned": learned, "warmstart_used": [i.warmstart_used for i in infos],
             "true_relres_mixed": max(i.true_relres for i in infos),
@@ -437,8 +608,11 @@ def main():
             "true_relres_fp64": max(i.true_relres for i in infos64),
             "mixed_over_fp64": value / value64, "err_mixed_vs_fp64_gpu": err_mixed_vs_fp64,
             "err_mixed_vs_fp64_oracle": err_vs_oracle,
-            "setup_s": {"mesh": t1 - t0, "precond": t2 - t1},
-            "roofline": roofline, "rooflines": rooflines, "cpu_baseline": cpu, "e2e": e2e,
+            "setup_s": {"mesh": t1 - t0, "precond": t2 - t1}, "setup_inclusive": setup_inclusive,
+            "peaks": {"hbm_gbs": peak, "hbm_kind": peak_kind, "fp64_gflops_measured": fp64_gflops,
+                      "fp32_gflops_measured": fp32_gflops},
+            "roofline": roofline, "rooflines": rooflines, "rooflines_fp64": rooflines_fp64,
+            "workloads": extra, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": count["launches"] if count else None, "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -85,7 +85,8 @@ typedef struct {
     int max_coarse;      /* stop coarsening at or below this many nodes (default 512, max 4096) */
     int max_levels;      /* hierarchy depth cap (default 10, max 16) */
     int power_its;       /* power iterations for rho(D^-1 A) in prolongator smoothing (default 20) */
-    int precision;       /* gl_precision (default GL_FP64); the coarsest solve is FP64 in every mode */
+    int precision;       /* gl_precision (default GL_FP64); the coarsest solve keeps FP64 accuracy in
+                            every mode (see coarse_df) */
     double inner_tol;    /* GL_MIXED: relative reduction asked of each FP32 inner solve (default 1e-5) */
     int max_outer;       /* GL_MIXED: cap on FP64 refinement steps (default 20) */
     int check_every;     /* host polls the device convergence flag every this many iterations (default 6) */
@@ -114,6 +115,11 @@ typedef struct {
                             where no partition fits).  The result is the same; only the time differs.
                             Every wait is bounded (1 s); one that runs out ends the call with
                             GL_ERR_TIMEOUT (default 0) */
+    int coarse_df;       /* the dense coarsest product of the FP32 V-cycle (GL_MIXED, GL_MIXED_PRECOND):
+                            1 = double-FP32 arithmetic (the FP64 inverse as FP32 hi + lo pairs, error-free
+                            products and compensated sums, about 48 significant bits: the FP64 product's
+                            value before its FP32 rounding, at the FP32 rate); 0 = FP64 arithmetic.  The
+                            FP64 V-cycle always uses FP64 (default 1) */
 } gl_options;
 
 #define GL_COLOR_SL 0

@@ -71,7 +71,7 @@ class Options(C.Structure):
         ("max_levels", C.c_int), ("power_its", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double),
         ("max_outer", C.c_int), ("check_every", C.c_int), ("autotune", C.c_int), ("lattice", C.c_int),
         ("cluster_sweeps", C.c_int),
-        ("warmstart", C.c_void_p), ("coloring", C.c_int), ("sweep_sync", C.c_int),
+        ("warmstart", C.c_void_p), ("coloring", C.c_int), ("sweep_sync", C.c_int), ("coarse_df", C.c_int),
     ]
 
 

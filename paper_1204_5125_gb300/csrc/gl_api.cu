@@ -81,6 +81,7 @@ gl_status gl_options_default(gl_options *o) {
     o->warmstart = nullptr;
     o->coloring = GL_COLOR_SL;
     o->sweep_sync = 0;
+    o->coarse_df = 1;
     return GL_OK;
 }
 

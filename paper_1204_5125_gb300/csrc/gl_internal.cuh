@@ -106,7 +106,7 @@ struct Level {
     Sell<float2> P32, PH32;
     CsrG<float2> Ag32, PHg32;
     DBuf<float2> b32, x32, r32;
-    DBuf<float2> Ainv32;            // unused: the coarsest solve stays FP64
+    DBuf<float4> Ainv_df;           // coarsest: the dense inverse as double-FP32 (re hi, re lo, im hi, im lo)
     int cl_size = 0, cl_chunk = 0;  // FP32 sweeps by one thread-block cluster (0: cooperative grid)
     int sgs_G32 = 1, sgs_G64 = 1;   // lanes per row of the coarse Gauss-Seidel sweeps
 };
@@ -156,6 +156,7 @@ struct gl_prec_s {
         int sync64 = 0, nb64 = 0, sync32 = 0, nb32 = 0;
     } tuned[gl::MAX_LEVELS];
     int sweep_sync = 0;               // gl_options.sweep_sync the setup ran with
+    bool coarse_df = true;            // FP32 V-cycle: double-FP32 coarsest product (else FP64)
     bool tuned64 = false, tuned32 = false;
     // R_inf: device loop state, the stream its loop body is captured on, and the
     // stream and events of an application outside stream capture
@@ -253,6 +254,8 @@ void rebuild_flag_plans(gl_prec_s *p, bool fp32, cudaStream_t s);
 void sweeps_reset(gl_prec_s *p, cudaStream_t s);
 // 1 if a device-side wait of p's sweeps ran out since the last reset (synchronises s)
 int sweeps_failed(gl_prec_s *p, cudaStream_t s);
+// the coarsest level's dense inverse as double-FP32 pairs for the FP32 V-cycle
+void coarse_inverse_df(Level &L, cudaStream_t s);
 // z = R_k v with FP64 vectors and an FP32 V-cycle
 void precond_apply_p64_via32(gl_prec_s *p, const double2 *v, double2 *z, const int *stop, cudaStream_t s);
 

@@ -6,6 +6,30 @@
 
 namespace gl {
 
+// ---- double-FP32 arithmetic (hi + lo FP32 pairs, about 48 significant bits)
+__device__ __forceinline__ float2 split_df(double x) {
+    float hi = __double2float_rn(x);
+    return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+// (s, c) += p exactly: s + p = t + e (TwoSum), the error e joins the compensation c
+__device__ __forceinline__ void dot2_add(float &s, float &c, float p) {
+    float t = __fadd_rn(s, p);
+    float bp = __fadd_rn(t, -s);
+    float e = __fadd_rn(__fadd_rn(s, -__fadd_rn(t, -bp)), __fadd_rn(p, -bp));
+    s = t;
+    c = __fadd_rn(c, e);
+}
+// (s, c) += a b, a = a.x + a.y: the exact product of the high part (TwoProd) and
+// the low part's product into the compensation
+__device__ __forceinline__ void dot2_df(float &s, float &c, float2 a, float b) {
+    float p = __fmul_rn(a.x, b);
+    float e = __fmaf_rn(a.x, b, -p);
+    dot2_add(s, c, p);
+    c = __fadd_rn(c, e);
+    c = __fmaf_rn(a.y, b, c);
+}
+
+
 // sum_k A[p][k] * x[col[p][k]] over the stored off-diagonals of row p of a sliced
 // ELL matrix (a warp reads 32 consecutive entries per k)
 template <typename C, typename X>

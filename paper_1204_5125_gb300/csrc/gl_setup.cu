@@ -1151,6 +1151,7 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
     p->lattice = o.lattice != 0;
     p->cluster_sweeps = o.cluster_sweeps != 0;
     p->sweep_sync = o.sweep_sync;
+    p->coarse_df = o.coarse_df != 0;
     if (T && T->nlev == p->nlev && T->autotune == p->autotune && T->cluster_sweeps == p->cluster_sweeps &&
         T->sweep_sync == p->sweep_sync) {
         for (int k = 0; k < p->nlev; ++k) {
@@ -1239,6 +1240,7 @@ void precond_ensure_fp32(gl_prec_s *p, cudaStream_t s) {
     p->mp_in.alloc(m->n);
     p->mp_out.alloc(m->n);
     Level &Lb = p->L[p->nlev - 1];
+    if (p->coarse_df) coarse_inverse_df(Lb, s);
     p->coarse_b64.alloc(Lb.n);
     p->coarse_x64.alloc(Lb.n);
     GL_CUDA(cudaStreamSynchronize(s));

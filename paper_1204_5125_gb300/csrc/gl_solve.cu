@@ -124,28 +124,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_jz(int64_t n, SellView<C> K, co
 // running sum and an FP32 compensation collecting the exact rounding errors):
 // about 48 significant bits, against 53 in FP64.  The solve watches for the
 // consequence (see k_scal_true) and finishes with the FP64 apply if it stalls.
-__device__ __forceinline__ float2 split_df(double x) {
-    float hi = __double2float_rn(x);
-    return make_float2(hi, __double2float_rn(x - (double)hi));
-}
-// (s, c) += p exactly: s + p = t + e (TwoSum), the error e joins the compensation c
-__device__ __forceinline__ void dot2_add(float &s, float &c, float p) {
-    float t = __fadd_rn(s, p);
-    float bp = __fadd_rn(t, -s);
-    float e = __fadd_rn(__fadd_rn(s, -__fadd_rn(t, -bp)), __fadd_rn(p, -bp));
-    s = t;
-    c = __fadd_rn(c, e);
-}
-// (s, c) += a b, a = a.x + a.y: the exact product of the high part (TwoProd) and
-// the low part's product into the compensation
-__device__ __forceinline__ void dot2_df(float &s, float &c, float2 a, float b) {
-    float p = __fmul_rn(a.x, b);
-    float e = __fmaf_rn(a.x, b, -p);
-    dot2_add(s, c, p);
-    c = __fadd_rn(c, e);
-    c = __fmaf_rn(a.y, b, c);
-}
-
 // per-solve coefficients of the local part: d = r - 1 + 2|psi|^2 and psi^2
 __global__ void k_jz_coef(int64_t n, const double *__restrict__ rem, const double2 *__restrict__ psi,
                           float2 *__restrict__ d, float4 *__restrict__ p2) {
@@ -276,8 +254,25 @@ void jacobian_apply_pdf(gl_mesh_s *m, const double2 *psi, const double2 *phi, do
 template <typename C, typename R>
 __global__ void k_vnew(int64_t n, const MinresDev *S, const C *q, const C *v, const C *v_old, C *v_new) {
     if (S->status) return;
+    // the scalars once per thread (a fixed grid: FP64 divisions are costly here),
+    // four rows per step with every load issued first
     R ig = (R)(1.0 / S->gamma), dg = (R)(S->delta / S->gamma), go = (R)(S->gamma / S->gamma_old);
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; p + 3 * stride < n; p += 4 * stride) {
+        C a[4], b[4], c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            a[u] = q[p + u * stride];
+            b[u] = v[p + u * stride];
+            c[u] = v_old[p + u * stride];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            v_new[p + u * stride] =
+                mk(a[u].x * ig - dg * b[u].x - go * c[u].x, a[u].y * ig - dg * b[u].y - go * c[u].y);
+    }
+    for (; p < n; p += stride) {
         C a = q[p], b = v[p], c = v_old[p];
         v_new[p] = mk(a.x * ig - dg * b.x - go * c.x, a.y * ig - dg * b.y - go * c.y);
     }
@@ -290,7 +285,25 @@ __global__ void k_vnew_mp(int64_t n, const MinresDev *S, const double2 *q, const
                           double2 *v_new, float2 *v32) {
     if (S->status) return;
     double ig = 1.0 / S->gamma, dg = S->delta / S->gamma, go = S->gamma / S->gamma_old;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; p + 3 * stride < n; p += 4 * stride) {
+        double2 a[4], b[4], c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            a[u] = q[p + u * stride];
+            b[u] = v[p + u * stride];
+            c[u] = v_old[p + u * stride];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const double2 r =
+                make_double2(a[u].x * ig - dg * b[u].x - go * c[u].x, a[u].y * ig - dg * b[u].y - go * c[u].y);
+            v_new[p + u * stride] = r;
+            v32[p + u * stride] = to32(r);
+        }
+    }
+    for (; p < n; p += stride) {
         double2 a = q[p], b = v[p], c = v_old[p];
         double2 r = make_double2(a.x * ig - dg * b.x - go * c.x, a.y * ig - dg * b.y - go * c.y);
         v_new[p] = r;
@@ -303,7 +316,27 @@ __global__ void __launch_bounds__(RED_THREADS) k_widen_dot(int64_t n, const doub
     __shared__ double sh[32];
     if (*stop) return;
     double a = 0;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // four rows per step, every load issued before the first use
+    for (; p + 3 * stride < n; p += 4 * stride) {
+        float2 zr[4];
+        double2 vv[4];
+        double vo[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            zr[u] = z32[p + u * stride];
+            vv[u] = v[p + u * stride];
+            vo[u] = vol[p + u * stride];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const double2 zz = to64(zr[u]);
+            z[p + u * stride] = zz;
+            a += vo[u] * redot(vv[u], zz);
+        }
+    }
+    for (; p < n; p += stride) {
         double2 zz = to64(z32[p]);
         z[p] = zz;
         a += vol[p] * redot(v[p], zz);
@@ -318,7 +351,26 @@ __global__ void k_update(int64_t n, const MinresDev *S, const C *z, const C *w_o
     if (S->status) return;
     R ig = (R)(1.0 / S->gamma_cur), a2 = (R)S->a2, a3 = (R)S->a3, ia1 = (R)(1.0 / S->a1);
     R ce = (R)(S->c_new * S->eta_prev);
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; p + 3 * stride < n; p += 4 * stride) {
+        C zz[4], wo[4], ww[4], xx[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            zz[u] = z[p + u * stride];
+            wo[u] = w_old[p + u * stride];
+            ww[u] = w[p + u * stride];
+            xx[u] = x[p + u * stride];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            C wn = mk((zz[u].x * ig - a3 * wo[u].x - a2 * ww[u].x) * ia1,
+                      (zz[u].y * ig - a3 * wo[u].y - a2 * ww[u].y) * ia1);
+            w_new[p + u * stride] = wn;
+            x[p + u * stride] = mk(xx[u].x + ce * wn.x, xx[u].y + ce * wn.y);
+        }
+    }
+    for (; p < n; p += stride) {
         C zz = z[p], wo = w_old[p], ww = w[p];
         C wn = mk((zz.x * ig - a3 * wo.x - a2 * ww.x) * ia1, (zz.y * ig - a3 * wo.y - a2 * ww.y) * ia1);
         w_new[p] = wn;

@@ -158,12 +158,13 @@ __global__ void __launch_bounds__(256) k_resid_lat(int64_t n, LatticeView L, con
     }
 }
 
-// y = S x (add = 0) or y += S x (add = 1) for a rectangular sliced-ELL S
+// y = S x (add = 0) or y += S x (add = 1) for the rows [lo, n) of a rectangular
+// sliced-ELL S
 template <typename C>
-__global__ void __launch_bounds__(256) k_spmv(int64_t n, SellView<C> S, const C *__restrict__ x, C *__restrict__ y,
-                                              int add, const int *__restrict__ stop) {
+__global__ void __launch_bounds__(256) k_spmv(int64_t lo, int64_t n, SellView<C> S, const C *__restrict__ x,
+                                              C *__restrict__ y, int add, const int *__restrict__ stop) {
     if (stop && *stop) return;
-    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t p = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= n) return;
     C acc = sell_row<C, C>(S, p, x);
     if (add) acc = cadd(acc, y[p]);
@@ -933,6 +934,91 @@ __global__ void __launch_bounds__(32 * DMV_WARPS) k_dense_mv(int64_t n, const do
     if (lane == 0) x[row] = make_double2(sx, sy);
 }
 
+// x = M b for the FP32 V-cycle: b is an FP32 vector (exact), M the dense
+// coarsest inverse as double-FP32 pairs, every product error-free and every sum
+// compensated (Dot2), so the value carries about 48 significant bits before it
+// is rounded to FP32 - the FP64 product's value, at the FP32 pipe's rate (the
+// FP64 form of this product is bound by the FP64 pipe).  The product is a
+// stream of the matrix (16 B per entry), so one block of DMV_DF_THREADS takes a
+// row and every thread keeps several entries in flight; partial (sum,
+// compensation) pairs are combined by shuffles and through shared memory.
+constexpr int DMV_DF_THREADS = 128;
+__global__ void __launch_bounds__(DMV_DF_THREADS) k_dense_mv_df(int64_t n, const float4 *__restrict__ M,
+                                                                const float2 *__restrict__ b,
+                                                                float2 *__restrict__ x, const int *__restrict__ stop) {
+    if (stop && *stop) return;
+    __shared__ float4 part[DMV_DF_THREADS / 32];
+    const int64_t row = blockIdx.x;
+    const float4 *mr = M + row * n;
+    float rs[2] = {0.f, 0.f}, rc[2] = {0.f, 0.f}, is[2] = {0.f, 0.f}, ic[2] = {0.f, 0.f};
+    int64_t j = threadIdx.x;
+    constexpr int U = 4;
+    for (; j + (U - 1) * DMV_DF_THREADS < n; j += U * DMV_DF_THREADS) {
+        float4 m[U];
+        float2 bb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            m[u] = mr[j + u * DMV_DF_THREADS];
+            bb[u] = __ldg(b + j + u * DMV_DF_THREADS);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int a = u & 1;
+            dot2_df(rs[a], rc[a], make_float2(m[u].x, m[u].y), bb[u].x);
+            dot2_df(rs[a], rc[a], make_float2(-m[u].z, -m[u].w), bb[u].y);
+            dot2_df(is[a], ic[a], make_float2(m[u].x, m[u].y), bb[u].y);
+            dot2_df(is[a], ic[a], make_float2(m[u].z, m[u].w), bb[u].x);
+        }
+    }
+    for (; j < n; j += DMV_DF_THREADS) {
+        const float4 m = mr[j];
+        const float2 bb = __ldg(b + j);
+        dot2_df(rs[0], rc[0], make_float2(m.x, m.y), bb.x);
+        dot2_df(rs[0], rc[0], make_float2(-m.z, -m.w), bb.y);
+        dot2_df(is[0], ic[0], make_float2(m.x, m.y), bb.y);
+        dot2_df(is[0], ic[0], make_float2(m.z, m.w), bb.x);
+    }
+    dot2_add(rs[0], rc[0], rs[1]);
+    rc[0] = __fadd_rn(rc[0], rc[1]);
+    dot2_add(is[0], ic[0], is[1]);
+    ic[0] = __fadd_rn(ic[0], ic[1]);
+    for (int o = 16; o > 0; o >>= 1) {
+        const float a = __shfl_down_sync(0xffffffffu, rs[0], o), ac = __shfl_down_sync(0xffffffffu, rc[0], o);
+        const float c = __shfl_down_sync(0xffffffffu, is[0], o), cc = __shfl_down_sync(0xffffffffu, ic[0], o);
+        dot2_add(rs[0], rc[0], a);
+        rc[0] = __fadd_rn(rc[0], ac);
+        dot2_add(is[0], ic[0], c);
+        ic[0] = __fadd_rn(ic[0], cc);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) part[warp] = make_float4(rs[0], rc[0], is[0], ic[0]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float4 t = part[0];
+        for (int w = 1; w < DMV_DF_THREADS / 32; ++w) {
+            dot2_add(t.x, t.y, part[w].x);
+            t.y = __fadd_rn(t.y, part[w].y);
+            dot2_add(t.z, t.w, part[w].z);
+            t.w = __fadd_rn(t.w, part[w].w);
+        }
+        x[row] = make_float2(__fadd_rn(t.x, t.y), __fadd_rn(t.z, t.w));
+    }
+}
+
+__global__ void k_split_dense_df(int64_t nn, const double2 *__restrict__ a, float4 *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    const float2 re = split_df(a[i].x), im = split_df(a[i].y);
+    out[i] = make_float4(re.x, re.y, im.x, im.y);
+}
+
+void coarse_inverse_df(Level &L, cudaStream_t s) {
+    const int64_t nn = L.n * L.n;
+    L.Ainv_df.alloc(nn);
+    k_split_dense_df<<<grid_for(nn, 256), 256, 0, s>>>(nn, L.Ainv.get(), L.Ainv_df.get());
+    GL_LAUNCH_CHECK();
+}
+
 template <typename C>
 __global__ void k_axpy_t(int64_t n, const C *__restrict__ e, C *__restrict__ z, const int *__restrict__ stop) {
     if (stop && *stop) return;
@@ -961,6 +1047,12 @@ void coarse_solve<double>(gl_prec_s *, Level &L, const double2 *b, double2 *x, c
 }
 template <>
 void coarse_solve<float>(gl_prec_s *p, Level &L, const float2 *b, float2 *x, const int *stop, cudaStream_t s) {
+    if (L.Ainv_df.get()) {
+        // double-FP32 product of the FP32 right-hand side
+        ProfScope ps("coarse", (double)L.n * L.n * sizeof(float4), s);
+        k_dense_mv_df<<<(unsigned)L.n, DMV_DF_THREADS, 0, s>>>(L.n, L.Ainv_df.get(), b, x, stop);
+        return;
+    }
     // the FP32 right-hand side widened once, the FP64 solve, the result narrowed
     note_launch(2);
     k_f2d<<<grid_for(L.n, 256), 256, 0, s>>>(L.n, b, p->coarse_b64.get(), stop);
@@ -1140,8 +1232,13 @@ static void vcycle(gl_prec_s *p, int l, const typename LevelOps<T>::C *b, typena
     }
     vcycle<T>(p, l + 1, O::b(Lc), O::x(Lc), stop, s);
     {
+        // x += P e_c.  The post-smoothing that follows relaxes colour 0 first, and a
+        // Gauss-Seidel relaxation of a row does not read the row's own old value,
+        // so the correction of colour-0 rows would be overwritten unread: only the
+        // rows of the other colours are corrected (the same values, bit for bit)
+        const int64_t lo = L.ncolors > 1 ? L.cstart[1] : 0;
         ProfScope ps("prolong", 0, s);
-        k_spmv<C><<<grid_for(L.n, 256), 256, 0, s>>>(L.n, O::P(L).view(), O::x(Lc), x, 1, stop);
+        k_spmv<C><<<grid_for(L.n - lo, 256), 256, 0, s>>>(lo, L.n, O::P(L).view(), O::x(Lc), x, 1, stop);
     }
     smooth<T>(p, l, b, x, false, stop, s);
     GL_LAUNCH_CHECK();
