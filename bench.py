@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip training and timing the learned warm start")
     ap.add_argument("--ws-steps", type=int, default=200, help="Adam steps of warm-start training")
     ap.add_argument("--no-extra", action="store_true", help="skip the batch64 and 2D workload measurements")
+    ap.add_argument("--sweep-sync", type=int, default=0, choices=[0, 1, 2],
+                    help="coarse-sweep synchronisation (options.sweep_sync; 0 = timed at setup)")
     return ap.parse_args()
 
 
@@ -387,8 +389,8 @@ def main():
     t0 = time.perf_counter()
     mesh = gl.gl_mesh_create(dim, N, mu, bh)
     t1 = time.perf_counter()
-    opts_mixed = gl.options(precision=gl.GL_MIXED, max_coarse=args.max_coarse)
-    opts_fp64 = gl.options(precision=gl.GL_FP64, max_coarse=args.max_coarse)
+    opts_mixed = gl.options(precision=gl.GL_MIXED, max_coarse=args.max_coarse, sweep_sync=args.sweep_sync)
+    opts_fp64 = gl.options(precision=gl.GL_FP64, max_coarse=args.max_coarse, sweep_sync=args.sweep_sync)
     prec = gl.gl_precond_setup(mesh, psi, opts_mixed)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
