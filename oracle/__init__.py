@@ -117,6 +117,8 @@ def lib():
             L.glref_aggregate.argtypes = [C.c_int64, _i64p, _i32p, _i32p]
             L.glref_color_jp.restype = C.c_int32
             L.glref_color_jp.argtypes = [C.c_int64, _i64p, _i32p, _i32p]
+            L.glref_color_psl.restype = C.c_int32
+            L.glref_color_psl.argtypes = [C.c_int64, _i64p, _i32p, _i32p, _i32p]
             L.glref_color_sl.restype = C.c_int32
             L.glref_color_sl.argtypes = [C.c_int64, _i64p, _i32p, _i32p, _i32p]
             L.glref_precond_setup.restype = vp
@@ -156,11 +158,13 @@ def _c128(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.complex128)
 
 
-COLOR_SL, COLOR_JP = 0, 1  # coarse-level colourings: smallest-last greedy (default), Jones-Plassmann
+# coarse-level colourings: smallest-last greedy, Jones-Plassmann, smallest-last in rounds (default)
+COLOR_SL, COLOR_JP, COLOR_PSL = 0, 1, 2
+PSL_SLACK = 4  # degree slack of one removal round of COLOR_PSL
 
 
 def options(tol=1e-10, maxit=500, cycles=1, max_coarse=512, max_levels=10, power_its=20,
-            coloring=COLOR_SL) -> Options:
+            coloring=COLOR_PSL) -> Options:
     return Options(tol, maxit, cycles, max_coarse, max_levels, power_its, coloring)
 
 
@@ -430,6 +434,17 @@ def color_jp(rp, ci):
     col = np.zeros(n, np.int32)
     nc = lib().glref_color_jp(n, rp, ci, col)
     return nc, col
+
+
+def color_psl(rp, ci):
+    """(ncolors, colours, levels): smallest-last colouring in removal rounds."""
+    rp = np.ascontiguousarray(rp, np.int64)
+    ci = np.ascontiguousarray(ci, np.int32)
+    n = len(rp) - 1
+    col = np.zeros(n, np.int32)
+    level = np.zeros(n, np.int32)
+    nc = lib().glref_color_psl(n, rp, ci, col, level)
+    return nc, col, level
 
 
 def color_sl(rp, ci):

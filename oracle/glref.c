@@ -772,11 +772,14 @@ typedef struct {
     int max_coarse;    /* stop coarsening at or below this size */
     int max_levels;
     int power_its;     /* power iterations for the spectral radius of D^-1 A */
-    int coloring;      /* coarse-level colouring: GLREF_COLOR_SL (smallest-last greedy) or GLREF_COLOR_JP */
+    int coloring;      /* coarse-level colouring: GLREF_COLOR_PSL (default), GLREF_COLOR_SL or GLREF_COLOR_JP */
 } glref_options;
 
 #define GLREF_COLOR_SL 0
 #define GLREF_COLOR_JP 1
+#define GLREF_COLOR_PSL 2
+/* degree slack of one removal round of the round-based smallest-last order */
+#define GLREF_PSL_SLACK 4
 
 typedef struct {
     csr A;            /* level operator (Hermitian) */
@@ -921,6 +924,78 @@ int32_t glref_color_jp(int64_t n, const int64_t *rp, const int32_t *ci, int32_t 
         }
     }
     free(pick);
+    return ncol;
+}
+
+/* Smallest-last colouring in rounds: Matula & Beck's smallest-last order with
+ * whole sets removed at once, so that a parallel machine needs few rounds:
+ *   degree d(v) = off-diagonal entries of row v among the vertices not yet
+ *   removed (the graph is symmetric);
+ *   round r = 0, 1, ...: with d_min the smallest degree of the remaining
+ *   vertices, every remaining vertex with d(v) <= d_min + GLREF_PSL_SLACK (degrees
+ *   as at the start of the round) is removed and gets level r;
+ *   then the vertices are coloured greedily in decreasing (level, prio_key)
+ *   order, each with the smallest colour that none of its already coloured
+ *   neighbours has (a vertex removed later, i.e. in a denser remainder, first).
+ * This is the greedy colouring of a total order, so a Jones-Plassmann colouring
+ * with the key (level, prio_key) gives the same colours.  level (nullable): the
+ * removal round of each vertex.  Returns the number of colours. */
+static const int32_t *psl_level;
+static int psl_cmp(const void *a, const void *b) {
+    const int64_t u = *(const int64_t *)a, v = *(const int64_t *)b;
+    if (psl_level[u] != psl_level[v]) return psl_level[u] > psl_level[v] ? -1 : 1;
+    const uint64_t ku = prio_key(u), kv = prio_key(v);
+    return ku > kv ? -1 : (ku < kv ? 1 : 0);
+}
+int32_t glref_color_psl(int64_t n, const int64_t *rp, const int32_t *ci, int32_t *color, int32_t *level_out) {
+    int64_t *deg = xcalloc((size_t)n, sizeof(int64_t));
+    int32_t *level = xcalloc((size_t)n, sizeof(int32_t));
+    uint8_t *sel = xcalloc((size_t)n, 1);
+    for (int64_t v = 0; v < n; ++v) {
+        level[v] = -1;
+        for (int64_t q = rp[v]; q < rp[v + 1]; ++q) deg[v] += (ci[q] != v);
+    }
+    int64_t remaining = n;
+    for (int32_t r = 0; remaining > 0; ++r) {
+        int64_t dmin = INT64_MAX;
+        for (int64_t v = 0; v < n; ++v)
+            if (level[v] < 0 && deg[v] < dmin) dmin = deg[v];
+        for (int64_t v = 0; v < n; ++v) sel[v] = (level[v] < 0 && deg[v] <= dmin + GLREF_PSL_SLACK);
+        for (int64_t v = 0; v < n; ++v)
+            if (sel[v]) {
+                level[v] = r;
+                --remaining;
+            }
+        for (int64_t v = 0; v < n; ++v) {
+            if (!sel[v]) continue;
+            for (int64_t q = rp[v]; q < rp[v + 1]; ++q)
+                if (ci[q] != v && level[ci[q]] < 0) --deg[ci[q]];
+        }
+    }
+    int64_t *order = xcalloc((size_t)n, sizeof(int64_t));
+    for (int64_t v = 0; v < n; ++v) order[v] = v;
+    psl_level = level;
+    qsort(order, (size_t)n, sizeof(int64_t), psl_cmp);
+    for (int64_t v = 0; v < n; ++v) color[v] = -1;
+    int32_t ncol = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t v = order[k];
+        int32_t c = 0;
+        for (;;) {
+            int used = 0;
+            for (int64_t q = rp[v]; q < rp[v + 1]; ++q)
+                if (ci[q] != v && color[ci[q]] == c) used = 1;
+            if (!used) break;
+            ++c;
+        }
+        color[v] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+    }
+    if (level_out) memcpy(level_out, level, sizeof(int32_t) * (size_t)n);
+    free(order);
+    free(deg);
+    free(level);
+    free(sel);
     return ncol;
 }
 
@@ -1142,6 +1217,8 @@ glref_prec *glref_precond_setup(const glref_mesh *m, const cplx *psi, const glre
             L->ncolors = (nl > 1) ? 2 : 1;
         } else if (o->coloring == GLREF_COLOR_JP) {
             L->ncolors = glref_color_jp(nl, L->A.rp, L->A.ci, L->color);
+        } else if (o->coloring == GLREF_COLOR_PSL) {
+            L->ncolors = glref_color_psl(nl, L->A.rp, L->A.ci, L->color, NULL);
         } else {
             int32_t *order = xcalloc((size_t)nl, sizeof(int32_t));
             L->ncolors = glref_color_sl(nl, L->A.rp, L->A.ci, L->color, order);

@@ -149,6 +149,55 @@ def test_smallest_last_colouring(oracle_mod, kind, dim, N):
         assert ncol < oracle_mod.color_jp(rp, ci)[0]
 
 
+@pytest.mark.parametrize("kind,dim,N", GRAPHS + [("coarse3", 3, 20)])
+def test_round_smallest_last_colouring(oracle_mod, kind, dim, N):
+    """Smallest-last colouring in removal rounds: the levels come from removing, in
+    each round, every remaining vertex whose remaining degree is within the slack
+    of the round's minimum (checked by a brute-force replay of the rounds); each
+    colour is the smallest not taken by the neighbours that come earlier in
+    decreasing (level, priority) order; proper; never more colours than
+    Jones-Plassmann, and within one of the one-at-a-time smallest-last colouring
+    on a coarse AMG level."""
+    if kind == "coarse3":
+        m = oracle_mod.Mesh(3, N, 1.0, BH3)
+        P = oracle_mod.Precond(m, np.ones(m.n, complex), max_coarse=64, coloring=oracle_mod.COLOR_JP)
+        rp, ci, _ = P.level_matrix(1)
+    elif kind == "random":
+        rp, ci = random_graph(N, 3, 5)
+    else:
+        rp, ci = lattice_graph(oracle_mod, dim, N)
+    n = len(rp) - 1
+    ncol, col, level = oracle_mod.color_psl(rp, ci)
+    adj = graph_adj(rp, ci, n)
+    # replay the removal rounds
+    left = set(range(n))
+    deg = {v: len(adj[v]) for v in range(n)}
+    r = 0
+    while left:
+        dmin = min(deg[v] for v in left)
+        out = {v for v in left if deg[v] <= dmin + oracle_mod.PSL_SLACK}
+        assert {int(v) for v in np.nonzero(level == r)[0]} == out, r
+        left -= out
+        for v in out:
+            for u in adj[v]:
+                if u in left:
+                    deg[u] -= 1
+        r += 1
+    assert level.max() == r - 1
+    for v in range(n):
+        kv = (int(level[v]), key(oracle_mod, v))
+        earlier = {int(col[u]) for u in adj[v] if (int(level[u]), key(oracle_mod, u)) > kv}
+        c = 0
+        while c in earlier:
+            c += 1
+        assert col[v] == c
+        assert all(col[u] != col[v] for u in adj[v])
+    assert col.max() == ncol - 1
+    assert ncol <= oracle_mod.color_jp(rp, ci)[0]
+    if kind == "coarse3":
+        assert ncol <= oracle_mod.color_sl(rp, ci)[0] + 1
+
+
 @pytest.fixture(scope="module")
 def prec2d(oracle_mod):
     m = oracle_mod.Mesh(2, 32, 1.5)
