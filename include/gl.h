@@ -104,10 +104,13 @@ typedef struct {
                             x passed in, start from the network's x0, and fall back to x0 = 0 when
                             ||b - J x0||_D >= ||b||_D (default NULL: start from x as given) */
     int coloring;        /* colouring of the coarse levels for the multicolour Gauss-Seidel steps:
-                            GL_COLOR_SL (smallest-last greedy, deterministic, on the host; default) or
-                            GL_COLOR_JP (Jones-Plassmann with hashed priorities, on the device).  Each
-                            colour is one dependent phase of a sweep.  The finest lattice level is
-                            always red-black. */
+                            GL_COLOR_PSL (smallest-last in removal rounds, on the device: each round
+                            removes every vertex within 4 of the smallest remaining degree, then the
+                            greedy colouring in decreasing (round, hashed id) order by Jones-Plassmann
+                            rounds; default), GL_COLOR_SL (smallest-last one vertex at a time, on the
+                            host) or GL_COLOR_JP (Jones-Plassmann with hashed priorities, on the
+                            device).  Each colour is one dependent phase of a sweep.  The finest lattice
+                            level is always red-black. */
     int sweep_sync;      /* synchronisation between the colours of a coarse-level Gauss-Seidel step:
                             0 = chosen per level (timed at setup with autotune; else the neighbour flags
                             where their partition fits), 1 = a grid-wide barrier, 2 = neighbour flags
@@ -124,6 +127,7 @@ typedef struct {
 
 #define GL_COLOR_SL 0
 #define GL_COLOR_JP 1
+#define GL_COLOR_PSL 2
 
 /* Per-solve report. */
 typedef struct {

@@ -29,14 +29,14 @@ __all__ = [
     "gl_warmstart_predict", "gl_warmstart_grad", "gl_warmstart_train", "gl_warmstart_adam_step", "GL_WS_NPARAM",
     "gl_last_error", "EXPORTED", "GL_CYCLES_INF", "ContOptions", "ContPoint", "gl_mesh_create_edge",
     "gl_mesh_set_mu", "gl_residual_dmu", "gl_energy", "cont_options", "gl_continuation", "gl_precond_setup_like",
-    "GL_COLOR_SL", "GL_COLOR_JP", "gl_mesh_create_dipole", "gl_precond_apply_precision", "gl_precond_debug",
+    "GL_COLOR_SL", "GL_COLOR_JP", "GL_COLOR_PSL", "gl_mesh_create_dipole", "gl_precond_apply_precision", "gl_precond_debug",
     "GL_DEBUG_STALL_SWEEPS", "GL_DEBUG_NEGATE_COARSEST", "gl_precond_level_sweep", "gl_measure_fma_peak",
     "gl_profile_flops",
 ]
 
 GL_FP64, GL_MIXED, GL_MIXED_PRECOND = 0, 1, 2
 GL_CYCLES_INF = -1  # options.cycles: R_inf, the V-cycle repeated until the 1e-12 residual test
-GL_COLOR_SL, GL_COLOR_JP = 0, 1  # options.coloring of the coarse levels
+GL_COLOR_SL, GL_COLOR_JP, GL_COLOR_PSL = 0, 1, 2  # options.coloring of the coarse levels
 GL_DEBUG_STALL_SWEEPS, GL_DEBUG_NEGATE_COARSEST = 1, 2  # gl_precond_debug actions (fault injection for tests)
 STATUS = {0: "GL_OK", 1: "GL_ERR_ARG", 2: "GL_ERR_CUDA", 3: "GL_ERR_OOM", 4: "GL_ERR_NOT_CONVERGED",
           5: "GL_ERR_BREAKDOWN", 6: "GL_ERR_NAN", 7: "GL_ERR_TIMEOUT", 8: "GL_ERR_CAPACITY"}

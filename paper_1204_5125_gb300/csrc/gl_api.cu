@@ -40,7 +40,8 @@ void check_opts(const gl_options *o) {
     GL_REQUIRE(o->precision == GL_FP64 || o->precision == GL_MIXED || o->precision == GL_MIXED_PRECOND, GL_ERR_ARG,
                "unknown precision");
     GL_REQUIRE(o->max_coarse <= MAX_COARSE_DENSE, GL_ERR_ARG, "max_coarse must be <= 4096");
-    GL_REQUIRE(o->coloring == GL_COLOR_SL || o->coloring == GL_COLOR_JP, GL_ERR_ARG, "unknown coloring");
+    GL_REQUIRE(o->coloring == GL_COLOR_SL || o->coloring == GL_COLOR_JP || o->coloring == GL_COLOR_PSL, GL_ERR_ARG,
+               "unknown coloring");
     GL_REQUIRE(o->sweep_sync >= 0 && o->sweep_sync <= 2, GL_ERR_ARG, "sweep_sync must be 0, 1 or 2");
 }
 
@@ -79,7 +80,7 @@ gl_status gl_options_default(gl_options *o) {
     o->lattice = 1;
     o->cluster_sweeps = 1;
     o->warmstart = nullptr;
-    o->coloring = GL_COLOR_SL;
+    o->coloring = GL_COLOR_PSL;
     o->sweep_sync = 0;
     o->coarse_df = 1;
     return GL_OK;

@@ -234,8 +234,112 @@ static int color_jp(const CsrDev &A, int32_t *color, cudaStream_t s) {
     return hm + 1;
 }
 
+// Smallest-last colouring in removal rounds, on the device (the default):
+// round r removes every remaining vertex whose remaining degree is within
+// PSL_SLACK of the round's smallest (degrees as at the start of the round) and
+// gives it level r; then Jones-Plassmann rounds with the key (level, prio)
+// colour each vertex once all its higher-key neighbours are coloured, with the
+// smallest colour none of them has - the greedy colouring in decreasing key
+// order (a later-removed vertex first).  Few rounds in both phases (a few
+// hundred on the 128^3 cube's level 1) and the one-at-a-time order's colour
+// count there.
+constexpr int PSL_SLACK = 4;
+constexpr int PSL_BATCH = 32;  // rounds launched between two checks of the host
+
+__global__ void k_psl_deg(int64_t n, const int64_t *rp, const int32_t *ci, int32_t *deg, int32_t *level) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t d = 0;
+    for (int64_t q = rp[v]; q < rp[v + 1]; ++q) d += (ci[q] != v);
+    deg[v] = d;
+    level[v] = -1;
+}
+__global__ void k_psl_min(int64_t n, const int32_t *level, const int32_t *deg, int32_t *mn) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v < n && level[v] < 0) atomicMin(mn, deg[v]);
+}
+__global__ void k_psl_mark(int64_t n, int32_t *level, const int32_t *deg, const int32_t *mn, int32_t r) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int32_t m = *mn;
+    if (v < n && m != INT32_MAX && level[v] < 0 && deg[v] <= m + PSL_SLACK) level[v] = r;
+}
+__global__ void k_psl_dec(int64_t n, const int64_t *rp, const int32_t *ci, const int32_t *level, int32_t *deg,
+                          int32_t r) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n || level[v] != r) return;
+    for (int64_t q = rp[v]; q < rp[v + 1]; ++q) {
+        const int32_t u = ci[q];
+        if (u != v && level[u] < 0) atomicSub(deg + u, 1);
+    }
+}
+__global__ void k_psl_alive(int64_t n, const int32_t *level, uint8_t *alive) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v < n) alive[v] = level[v] < 0 ? 1 : 0;
+}
+// an uncoloured vertex is picked when no uncoloured neighbour has a higher (level, prio) key
+__global__ void k_jpl_pick(int64_t n, const int64_t *rp, const int32_t *ci, const int32_t *level,
+                           const int32_t *color, uint8_t *pick) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint8_t ok = 0;
+    if (color[i] < 0) {
+        ok = 1;
+        const int32_t li = level[i];
+        const uint64_t ki = prio(i);
+        for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
+            const int64_t j = ci[q];
+            if (j != i && color[j] < 0 && (level[j] > li || (level[j] == li && prio(j) > ki))) ok = 0;
+        }
+    }
+    pick[i] = ok;
+}
+
+static int color_psl(const CsrDev &A, int32_t *color, cudaStream_t s) {
+    const int64_t n = A.n;
+    const int G = grid_for(n, 256);
+    DBuf<int32_t> deg(n), level(n), mn(PSL_BATCH);
+    DBuf<uint8_t> flag(n), pick(n);
+    DBuf<int> err(1);
+    GL_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    k_psl_deg<<<G, 256, 0, s>>>(n, A.rp.get(), A.ci.get(), deg.get(), level.get());
+    GL_LAUNCH_CHECK();
+    int32_t r = 0;
+    for (;;) {
+        GL_REQUIRE(r <= n + PSL_BATCH, GL_ERR_CAPACITY, "colouring rounds did not terminate");
+        k_fill_i32<<<1, PSL_BATCH, 0, s>>>(PSL_BATCH, mn.get(), INT32_MAX);
+        for (int k = 0; k < PSL_BATCH; ++k, ++r) {
+            k_psl_min<<<G, 256, 0, s>>>(n, level.get(), deg.get(), mn.get() + k);
+            k_psl_mark<<<G, 256, 0, s>>>(n, level.get(), deg.get(), mn.get() + k, r);
+            k_psl_dec<<<G, 256, 0, s>>>(n, A.rp.get(), A.ci.get(), level.get(), deg.get(), r);
+        }
+        GL_LAUNCH_CHECK();
+        k_psl_alive<<<G, 256, 0, s>>>(n, level.get(), flag.get());
+        if (count_nonzero_u8(flag.get(), n, s) == 0) break;
+    }
+    k_fill_i32<<<G, 256, 0, s>>>(n, color, -1);
+    for (int round = 0;; round += 8) {
+        GL_REQUIRE(round <= n + 8, GL_ERR_CAPACITY, "colouring did not terminate");
+        for (int k = 0; k < 8; ++k) {
+            k_jpl_pick<<<G, 256, 0, s>>>(n, A.rp.get(), A.ci.get(), level.get(), color, pick.get());
+            k_jp_assign<<<G, 256, 0, s>>>(n, A.rp.get(), A.ci.get(), pick.get(), color, flag.get(), err.get());
+        }
+        GL_LAUNCH_CHECK();
+        if (count_nonzero_u8(flag.get(), n, s) == 0) break;
+    }
+    DBuf<int32_t> mx(1);
+    k_max_i32<<<1, 256, 0, s>>>(color, n, mx.get());
+    GL_LAUNCH_CHECK();
+    int32_t hm = 0;
+    int herr = 0;
+    GL_CUDA(cudaMemcpyAsync(&hm, mx.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaMemcpyAsync(&herr, err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaStreamSynchronize(s));
+    GL_REQUIRE(herr == 0, GL_ERR_CAPACITY, "more than 256 colours needed");
+    return hm + 1;
+}
+
 // Smallest-last greedy colouring (Matula & Beck) of the level graph, on the
-// host: a sequential order whose colour count is bounded by the graph's
+// host (option GL_COLOR_SL): a sequential order whose colour count is bounded by the graph's
 // degeneracy + 1 (fewer colours, so fewer dependent phases in every
 // multicolour sweep, than the parallel Jones-Plassmann colouring).  The order
 // is deterministic: vertices wait in degree buckets (intrusive lists; entered
@@ -942,8 +1046,9 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
                                         cudaMemcpyDeviceToDevice, s));
                 L.ncolors = T->L[l].ncolors;
             } else {
-                L.ncolors = o.coloring == GL_COLOR_JP ? color_jp(L.A_can, L.color.get(), s)
-                                                      : color_smallest_last(L.A_can, L.color.get(), s);
+                L.ncolors = o.coloring == GL_COLOR_JP    ? color_jp(L.A_can, L.color.get(), s)
+                            : o.coloring == GL_COLOR_PSL ? color_psl(L.A_can, L.color.get(), s)
+                                                         : color_smallest_last(L.A_can, L.color.get(), s);
             }
         }
         if (nl <= max_coarse || l + 1 >= maxlev) break;

@@ -63,18 +63,23 @@ def test_level0_aggregation_full_size(big, oracle_mod):
         nagg, agg = oracle_mod.aggregate(rp, ci)
         np.testing.assert_array_equal(gl.gl_precond_level_aggregates(G, 0), agg)
         assert gl.gl_precond_level_info(G, 1)["n"] == nagg
-        # the level-1 colouring follows from the level-1 pattern by the smallest-last
-        # greedy rule (the default) and, on request, by Jones-Plassmann
+        # the level-1 colouring follows from the level-1 pattern by the round-based
+        # smallest-last rule (the default, on the device), and on request by the
+        # one-at-a-time smallest-last rule (host) and by Jones-Plassmann
         lrp, lci, _ = gl.gl_precond_level_matrix(G, 1)
-        nc, col, _ = oracle_mod.color_sl(lrp, lci)
-        np.testing.assert_array_equal(gl.gl_precond_level_colors(G, 1), col)
-        Gj = gl.gl_precond_setup(gm, psi, gl.options(precision=gl.GL_MIXED, coloring=gl.GL_COLOR_JP))
-        try:
-            njp, coljp = oracle_mod.color_jp(lrp, lci)
-            np.testing.assert_array_equal(gl.gl_precond_level_colors(Gj, 1), coljp)
-            assert nc < njp
-        finally:
-            gl.gl_precond_destroy(Gj)
+        npsl, colpsl, levels = oracle_mod.color_psl(lrp, lci)
+        np.testing.assert_array_equal(gl.gl_precond_level_colors(G, 1), colpsl)
+        print(f"level 1: {len(lrp) - 1} nodes, {npsl} colours in {levels.max() + 1} removal rounds")
+        others = {}
+        for name, c in (("sl", gl.GL_COLOR_SL), ("jp", gl.GL_COLOR_JP)):
+            Gc = gl.gl_precond_setup(gm, psi, gl.options(precision=gl.GL_MIXED, coloring=c))
+            try:
+                nref, cref = (oracle_mod.color_sl(lrp, lci)[:2] if name == "sl" else oracle_mod.color_jp(lrp, lci))
+                np.testing.assert_array_equal(gl.gl_precond_level_colors(Gc, 1), cref)
+                others[name] = nref
+            finally:
+                gl.gl_precond_destroy(Gc)
+        assert npsl <= others["sl"] and npsl < others["jp"]
     finally:
         gl.gl_precond_destroy(G)
 
