@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the batch64 and 2D workload measurements")
     ap.add_argument("--sweep-sync", type=int, default=0, choices=[0, 1, 2],
                     help="coarse-sweep synchronisation (options.sweep_sync; 0 = timed at setup)")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="MINRES iterations replayed by the host instead of the device-side graph loop "
+                         "(options.device_loop = 0; for launch lists of profilers that skip conditional graphs)")
     return ap.parse_args()
 
 
@@ -389,8 +392,11 @@ def main():
     t0 = time.perf_counter()
     mesh = gl.gl_mesh_create(dim, N, mu, bh)
     t1 = time.perf_counter()
-    opts_mixed = gl.options(precision=gl.GL_MIXED, max_coarse=args.max_coarse, sweep_sync=args.sweep_sync)
-    opts_fp64 = gl.options(precision=gl.GL_FP64, max_coarse=args.max_coarse, sweep_sync=args.sweep_sync)
+    dl = 0 if args.host_loop else 1
+    opts_mixed = gl.options(precision=gl.GL_MIXED, max_coarse=args.max_coarse, sweep_sync=args.sweep_sync,
+                            device_loop=dl)
+    opts_fp64 = gl.options(precision=gl.GL_FP64, max_coarse=args.max_coarse, sweep_sync=args.sweep_sync,
+                           device_loop=dl)
     prec = gl.gl_precond_setup(mesh, psi, opts_mixed)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
@@ -434,7 +440,7 @@ def main():
     # the two mixed forms: FP32 inner solves in FP64 defect correction, and an
     # FP32 V-cycle inside FP64 MINRES; the faster one is the headline
     forms = {"mixed_inner": opts_mixed, "mixed_precond": gl.options(precision=gl.GL_MIXED_PRECOND,
-                                                                     max_coarse=args.max_coarse)}
+                                                                     max_coarse=args.max_coarse, device_loop=dl)}
     quick = {}
     for name, o in forms.items():
         q_ms, q_inf, _ = timed(o, 2, 1)
@@ -465,7 +471,7 @@ def main():
         gl.gl_jacobian_apply(mesh, psi, x0, jx)
         guess_rel = float(torch.sqrt(torch.sum(vol * torch.abs(b - jx) ** 2) / torch.sum(vol * torch.abs(b) ** 2)))
         del x0, jx, vol
-        opts_learned = gl.options(precision=opts_head.precision, max_coarse=args.max_coarse)
+        opts_learned = gl.options(precision=opts_head.precision, max_coarse=args.max_coarse, device_loop=dl)
         opts_learned.warmstart = wsh.value
         q_ms, q_inf, _ = timed(opts_learned, 2, 1)
         wsf_ms, _, wsf_prof = timed(opts_learned, 2, 1, profile_class="wsf")

@@ -123,6 +123,12 @@ typedef struct {
                             products and compensated sums, about 48 significant bits: the FP64 product's
                             value before its FP32 rounding, at the FP32 rate); 0 = FP64 arithmetic.  The
                             FP64 V-cycle always uses FP64 (default 1) */
+    int device_loop;     /* 1: a solve runs as one CUDA graph whose MINRES iterations loop on the device
+                            (conditional WHILE / IF nodes; no kernel after convergence, one host wait);
+                            0: the same six-iteration body graph replayed by the host, which polls the
+                            status word between replays (for profilers that cannot see inside
+                            conditional graphs).  Solves that time a kernel class with gl_profile_begin,
+                            and R_inf, always use 0 (default 1) */
 } gl_options;
 
 #define GL_COLOR_SL 0

@@ -72,6 +72,7 @@ class Options(C.Structure):
         ("max_outer", C.c_int), ("check_every", C.c_int), ("autotune", C.c_int), ("lattice", C.c_int),
         ("cluster_sweeps", C.c_int),
         ("warmstart", C.c_void_p), ("coloring", C.c_int), ("sweep_sync", C.c_int), ("coarse_df", C.c_int),
+        ("device_loop", C.c_int),
     ]
 
 

@@ -83,6 +83,7 @@ gl_status gl_options_default(gl_options *o) {
     o->coloring = GL_COLOR_PSL;
     o->sweep_sync = 0;
     o->coarse_df = 1;
+    o->device_loop = 1;
     return GL_OK;
 }
 

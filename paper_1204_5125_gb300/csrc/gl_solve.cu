@@ -883,7 +883,7 @@ static void enqueue_body(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const
 template <typename T>
 static MinresResult minres(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const cplx_t<T> *b, cplx_t<T> *x,
                            double tol, int maxit, bool use_true, bool vc32, MinresWork<T> &W, cudaStream_t s,
-                           bool df = false) {
+                           bool df = false, bool device_loop = true) {
     using O = SolveOps<T>;
     using C = cplx_t<T>;
     int64_t n = m->n;
@@ -896,7 +896,7 @@ static MinresResult minres(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, con
     // IF nodes) whenever no kernel class is being timed (the profiler's event
     // nodes cannot sit in conditional bodies) and R_inf does not nest its own loop.
     const bool timing_class = profiler().active && !profiler().name.empty();
-    const bool loop = !timing_class && !(p && p->rinf);
+    const bool loop = device_loop && !timing_class && !(p && p->rinf);
     GraphKey key{m, psi, b, x, p ? p->uid : -1, profiler().generation, m->version, vc32 ? 1 : 0, df ? 1 : 0,
                  loop ? 1 : 0};
     if (!(key == W.key) || (loop ? !W.loop.exec : (!W.init.exec || !W.body.exec))) {
@@ -1273,11 +1273,13 @@ gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, con
         // the FP64 true residual above tol, MINRES restarts from the current x
         // with the FP64 Jacobian
         const bool df = vc32 && p->lattice && m->lat_ok;
-        MinresResult r = minres<double>(m, p, psi_p, b_p, x_p, o.tol, o.maxit, true, vc32, W.w64, s, df);
+        const bool dl = o.device_loop != 0;
+        MinresResult r = minres<double>(m, p, psi_p, b_p, x_p, o.tol, o.maxit, true, vc32, W.w64, s, df, dl);
         inf.df_jacobian = df ? 1 : 0;
         if (df && r.status == ST_STALL) {
             int used = r.iters;
-            r = minres<double>(m, p, psi_p, b_p, x_p, o.tol, std::max(o.maxit - used, 1), true, vc32, W.w64, s, false);
+            r = minres<double>(m, p, psi_p, b_p, x_p, o.tol, std::max(o.maxit - used, 1), true, vc32, W.w64, s, false,
+                               dl);
             r.iters += used;
             inf.stall_restarts = 1;
         }
@@ -1337,7 +1339,7 @@ gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, con
             k_down<<<G, 256, 0, s>>>(n, W.r.get(), scale, W.r32.get(), W.e32.get());
             GL_LAUNCH_CHECK();
             MinresResult r = minres<float>(m, p, W.psi32.get(), W.r32.get(), W.e32.get(), inner_tol,
-                                           o.maxit - total, false, false, W.w32, s);
+                                           o.maxit - total, false, false, W.w32, s, false, o.device_loop != 0);
             total += r.iters;
             est = r.est;
             if (r.status == ST_BREAK || r.status == ST_NAN || r.status == ST_TIMEOUT) {

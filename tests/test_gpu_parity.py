@@ -298,3 +298,35 @@ def test_newton_step_matches_oracle(oracle_mod):
         assert st == 0 and gn == pytest.approx(gno, rel=1e-9)
     np.testing.assert_allclose(host(t), p_ref, rtol=0, atol=1e-8)
     gl.gl_mesh_destroy(m)
+
+
+@pytest.mark.parametrize("precision", [gl.GL_FP64, gl.GL_MIXED_PRECOND, gl.GL_MIXED])
+def test_device_loop_matches_host_replays(precision):
+    """The solve as one graph looping on the device (conditional nodes) and the same
+    body graph replayed by the host run the same kernels on the same data: the
+    same iterate bit for bit and the same iteration count; a zero iteration cap
+    and an early convergence are honoured by both."""
+    m = gl.gl_mesh_create(3, 20, 1.0, BH3)
+    n = 20 ** 3
+    psi, b = dev(gi.disk(n, 61)), dev(gi.complex_normal(n, 62))
+    # one preconditioner for both (the setup-time timing may pick other lanes per row)
+    G = gl.gl_precond_setup(m, psi, gl.options(max_coarse=64, precision=precision))
+    try:
+        out = []
+        for dl in (1, 0):
+            x = torch.zeros_like(psi)
+            st, info = gl.gl_jacobian_solve(m, psi, G, b, x,
+                                            gl.options(max_coarse=64, precision=precision, device_loop=dl))
+            assert st == 0 and info.converged
+            out.append((x, info.iters))
+        assert out[0][1] == out[1][1]
+        assert torch.equal(out[0][0], out[1][0])
+        for dl in (1, 0):
+            x = torch.zeros_like(psi)
+            st, info = gl.gl_jacobian_solve(m, psi, G, b, x,
+                                            gl.options(max_coarse=64, maxit=7, precision=precision, device_loop=dl),
+                                            raise_on_fail=False)
+            assert st == 4 and info.iters == 7
+    finally:
+        gl.gl_precond_destroy(G)
+        gl.gl_mesh_destroy(m)
