@@ -15,10 +15,23 @@ which is scale-equivariant because the solve is linear in b.  K_ii is the
 diagonal of K = D^-1 K-hat (Eq. (10), Remark 2.3), so the identity network gives
 the Jacobi guess b / diag(K).
 
+With a hint a (a vector the caller expects to resemble the solution, e.g. the
+same Newton step's correction at the previous field strength of a
+continuation), the guess is that vector's best multiple plus the network's
+correction for what it leaves:
+
+    alpha = <J a, b>_R / <J a, J a>_R  (0 when J a = 0),   r = b - alpha J a,
+    x0 = alpha a + ||r||_D * ( y(psi, r / ||r||_D, a / ||a||_D) / K_ii ),
+
+where alpha minimises ||b - J (alpha a)||_D; without a hint a = 0, alpha = 0 and
+r = b (the form above).
+
 Network (4 layers of 64 real channels = 32 complex channel pairs):
 
-* input h^0_i = [Re b^_i, Im b^_i, Re psi_i, Im psi_i, |psi_i|^2, 0, ..., 0, 1]
-  (channel 63 is the constant 1 in every layer; it carries the biases).
+* input h^0_i = [Re r^_i, Im r^_i, Re psi_i, Im psi_i, |psi_i|^2, 0, Re a^_i,
+  Im a^_i, 0, ..., 0, 1] with r^ = r / ||r||_D and a^ = a / ||a||_D (zeros
+  without a hint; the hint is the complex channel pair (6, 7); channel 63 is the
+  constant 1 in every layer; it carries the biases).
 * twisted aggregation, acting on each complex channel pair (2c, 2c + 1):
       (S u)_i = sum_{k != i} w_ik u_k,    w_ik = -K-hat_ik / K-hat_ii,
   i.e. S = I - diag(K-hat)^-1 K-hat, the magnetic Jacobi operator: the edge
@@ -30,10 +43,10 @@ Network (4 layers of 64 real channels = 32 complex channel pairs):
 Parameters, one flat float vector: W^0..W^3 (64 x 128 each, row-major: out x in),
 then U (2 x 64).  Rows 63 of the W^l only feed the discarded channel 63.
 
-Training loss of one sample (psi, b):  L = ||b^ - J(psi) x^||_D^2  with
-x^ = y / K_ii, which is ||b - J x0||_D^2 / ||b||_D^2 -- the squared relative
-true-Jacobian residual of the predicted guess (the quantity the zero-guess
-fallback tests).  For a triple (psi, b, x*) with J x* = b it equals
+Training loss of one sample (psi, b[, a]):  L = ||r^ - J(psi) x^||_D^2  with
+x^ = y / K_ii, which is ||b - J x0||_D^2 / ||r||_D^2 -- the squared true-Jacobian
+residual of the predicted guess relative to what the hint leaves (without a
+hint: to ||b||_D, the quantity the zero-guess fallback tests).  For a triple (psi, b, x*) with J x* = b it equals
 ||J (x^ - x*/||b||_D)||_D^2.
 
 J(psi) phi = K phi + (-1 + 2|psi|^2) phi + psi^2 conj(phi) is the Jacobian of
@@ -94,21 +107,43 @@ class Graph:
         return float(np.sqrt(np.sum(self.vol * np.abs(x) ** 2)))
 
 
-def features(g: Graph, psi, bhat):
+def features(g: Graph, psi, bhat, ahat=None):
     h = np.zeros((g.n, C))
     h[:, 0], h[:, 1] = bhat.real, bhat.imag
     h[:, 2], h[:, 3] = psi.real, psi.imag
     h[:, 4] = np.abs(psi) ** 2
+    if ahat is not None:
+        h[:, 6], h[:, 7] = ahat.real, ahat.imag
     h[:, C - 1] = 1.0
     return h
 
 
-def forward(theta, g: Graph, psi, b):
-    """Returns (xhat, cache): xhat = y / K_ii for b^ = b / ||b||_D."""
+def inner_r(g: Graph, x, y) -> float:
+    return float(np.sum(g.vol * np.real(np.conj(x) * y)))
+
+
+def hint_split(g: Graph, psi, b, hint):
+    """(alpha, r, a^): the hint's minimal-residual multiple, the residual it leaves,
+    and the normalised hint (alpha = 0, r = b, a^ = None without a hint)."""
+    if hint is None:
+        return 0.0, b, None
+    an = g.dnorm(hint)
+    if an == 0:
+        return 0.0, b, np.zeros(g.n, complex)
+    q = g.mesh.jacobian(psi, hint)
+    qq = inner_r(g, q, q)
+    alpha = inner_r(g, q, b) / qq if qq > 0 else 0.0
+    return alpha, b - alpha * q, hint / an
+
+
+def forward(theta, g: Graph, psi, b, hint=None):
+    """Returns (xhat, cache): xhat = y / K_ii for r^ = r / ||r||_D, r the residual
+    the hint's multiple leaves (r = b without a hint)."""
     Ws, U = split(theta)
-    bn = g.dnorm(b)
-    bhat = b / bn
-    h = features(g, psi, bhat)
+    alpha, r, ahat = hint_split(g, psi, b, hint)
+    bn = g.dnorm(r)
+    bhat = r / bn
+    h = features(g, psi, bhat, ahat)
     hs, As = [h], []
     for W in Ws:
         a = np.concatenate([h, g.aggregate(h)], axis=1)
@@ -119,13 +154,16 @@ def forward(theta, g: Graph, psi, b):
         hs.append(h)
     y = hs[-1] @ U.T
     xhat = (y[:, 0] + 1j * y[:, 1]) / g.kdiag
-    return xhat, dict(bn=bn, bhat=bhat, hs=hs, As=As)
+    return xhat, dict(bn=bn, bhat=bhat, hs=hs, As=As, alpha=alpha)
 
 
-def predict(theta, g: Graph, psi, b):
-    """x0 = ||b||_D * xhat."""
-    xhat, cache = forward(theta, g, psi, b)
-    return cache["bn"] * xhat
+def predict(theta, g: Graph, psi, b, hint=None):
+    """x0 = alpha a + ||r||_D * xhat (x0 = ||b||_D * xhat without a hint)."""
+    xhat, cache = forward(theta, g, psi, b, hint)
+    x0 = cache["bn"] * xhat
+    if hint is not None:
+        x0 = x0 + cache["alpha"] * hint
+    return x0
 
 
 def loss(g: Graph, psi, bhat, xhat) -> float:
@@ -133,10 +171,10 @@ def loss(g: Graph, psi, bhat, xhat) -> float:
     return float(np.sum(g.vol * np.abs(r) ** 2))
 
 
-def loss_and_grad(theta, g: Graph, psi, b):
+def loss_and_grad(theta, g: Graph, psi, b, hint=None):
     """L and dL/dtheta (flat, same layout as theta) for one sample."""
     Ws, U = split(theta)
-    xhat, cache = forward(theta, g, psi, b)
+    xhat, cache = forward(theta, g, psi, b, hint)
     bhat, hs, As = cache["bhat"], cache["hs"], cache["As"]
     r = bhat - g.mesh.jacobian(psi, xhat)
     L = float(np.sum(g.vol * np.abs(r) ** 2))

@@ -156,3 +156,56 @@ def test_adam_constant_gradient_closed_form():
         th, m, v = ws.adam_step(th, g, m, v, t, lr, eps=eps)
         expect = expect - lr * g / (np.abs(g) + eps)
         np.testing.assert_allclose(th, expect, rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------- the hint
+@pytest.mark.parametrize("dim,N", [(2, 6), (3, 4)])
+def test_gradient_central_differences_with_hint(oracle_mod, dim, N):
+    """With a hint the network sees two more input channels (the normalised hint)
+    and the residual the hint's multiple leaves; the backward pass still matches
+    central differences, including the weights reading the hint channels."""
+    m, g, psi, b = small_case(oracle_mod, dim, N)
+    hint = gi.complex_normal(m.n, 21)
+    theta = gi.warmstart_init(6).astype(np.float64)
+    L, grad = ws.loss_and_grad(theta, g, psi, b, hint)
+    Ws, _ = ws.split(np.arange(ws.NPARAM))
+    rng = gi.rng(10)
+    # layer 0's columns 6, 7 read the hint pair (and 64 + 6, 64 + 7 its aggregate)
+    cols = [Ws[0][:, 6], Ws[0][:, 7], Ws[0][:, C + 6], Ws[0][:, C + 7]]
+    idx = np.concatenate([c[:C - 1] for c in cols])
+    gmax = np.max(np.abs(grad))
+    assert np.max(np.abs(grad[idx])) > 1e-3 * gmax
+    for j in rng.choice(idx, size=12, replace=False):
+        h = 1e-6
+        tp, tm = theta.copy(), theta.copy()
+        tp[j] += h
+        tm[j] -= h
+        fd = (ws.loss_and_grad(tp, g, psi, b, hint)[0] - ws.loss_and_grad(tm, g, psi, b, hint)[0]) / (2 * h)
+        assert abs(fd - grad[j]) <= 1e-6 * gmax + 1e-6 * abs(grad[j]), (j, fd, grad[j])
+    # without the hint channels' signal (a hint of zero) those weights get no gradient
+    _, g0 = ws.loss_and_grad(theta, g, psi, b, np.zeros(m.n, complex))
+    assert np.all(g0[idx] == 0.0)
+
+
+def test_hint_multiple_is_minimal_residual(oracle_mod):
+    """With the network's head at zero the guess is alpha a, and alpha minimises
+    ||b - J (t a)||_D over t (checked against a fine scan); a hint that solves the
+    system exactly is returned as it is (alpha = 1, zero residual)."""
+    m, g, psi, b = small_case(oracle_mod)
+    theta = np.zeros(ws.NPARAM)
+    a = gi.complex_normal(m.n, 22)
+    x0 = ws.predict(theta, g, psi, b, a)
+    alpha = x0[0] / a[0]
+    np.testing.assert_allclose(x0, alpha * a, rtol=1e-12, atol=0)
+    assert abs(alpha.imag) <= 1e-14 * abs(alpha)
+    res = lambda t: g.dnorm(b - m.jacobian(psi, t * a))  # noqa: E731
+    ts = alpha.real + np.linspace(-1e-3, 1e-3, 41) * (1 + abs(alpha.real))
+    assert res(alpha.real) <= min(res(t) for t in ts) * (1 + 1e-12)
+    # the exact solution as hint
+    xs = m.dense_solve(psi, b)
+    x0 = ws.predict(theta, g, psi, b, xs)
+    assert g.dnorm(b - m.jacobian(psi, x0)) <= 1e-9 * g.dnorm(b)
+    # no hint is the original form; a zero hint changes nothing either
+    theta = gi.warmstart_init(7).astype(np.float64)
+    np.testing.assert_array_equal(ws.predict(theta, g, psi, b, np.zeros(m.n, complex)),
+                                  ws.predict(theta, g, psi, b))
