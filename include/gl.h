@@ -101,8 +101,9 @@ typedef struct {
                             colours) instead of a cooperative grid: with autotune, where the setup timing
                             finds it faster; without, wherever it fits; 0: always the grid (default 1) */
     gl_warmstart warmstart; /* learned initial guess: when set, gl_jacobian_solve and gl_newton_step ignore the
-                            x passed in, start from the network's x0, and fall back to x0 = 0 when
-                            ||b - J x0||_D >= ||b||_D (default NULL: start from x as given) */
+                            x passed in, start from the network's x0 (with warmstart_hint, below), and fall
+                            back to x0 = 0 when ||b - J x0||_D >= ||b||_D (default NULL: start from x as
+                            given) */
     int coloring;        /* colouring of the coarse levels for the multicolour Gauss-Seidel steps:
                             GL_COLOR_PSL (smallest-last in removal rounds, on the device: each round
                             removes every vertex within 4 of the smallest remaining degree, then the
@@ -129,6 +130,11 @@ typedef struct {
                             status word between replays (for profilers that cannot see inside
                             conditional graphs).  Solves that time a kernel class with gl_profile_begin,
                             and R_inf, always use 0 (default 1) */
+    const void *warmstart_hint; /* with warmstart: a device vector (n complex FP64, node order) the solution
+                            is expected to resemble, e.g. the same Newton step's correction at the
+                            previous mu of a continuation; the guess is then its minimal-residual
+                            multiple plus the network's correction (see gl_warmstart_predict)
+                            (default NULL) */
 } gl_options;
 
 #define GL_COLOR_SL 0
@@ -435,20 +441,27 @@ GL_API gl_status gl_warmstart_destroy(gl_warmstart ws);
 /* Copy the FP32 parameters out / in (set also resets the Adam state). */
 GL_API gl_status gl_warmstart_get_params(gl_warmstart ws, float *params_host);
 GL_API gl_status gl_warmstart_set_params(gl_warmstart ws, const float *params_host);
-/* x0 = network guess for (psi, b); x0_dev must not alias psi or b. */
+/* x0 = network guess for (psi, b); x0_dev must not alias psi or b.  hint_dev
+ * (nullable, n complex FP64, node order): a vector the solution is expected to
+ * resemble; the guess is then
+ *     x0 = alpha a + ||r||_D y(psi, r / ||r||_D, a / ||a||_D) / K_ii,
+ *     alpha = <J a, b>_R / <J a, J a>_R (0 when J a = 0),   r = b - alpha J a,
+ * alpha the multiple of the hint with the smallest ||b - J alpha a||_D (FP64), and
+ * the normalised hint the network's input channel pair (6, 7). */
 GL_API gl_status gl_warmstart_predict(gl_warmstart ws, gl_mesh mesh, const void *psi_dev, const void *b_dev,
-                                      void *x0_dev, void *stream);
-/* Loss ||b^ - J x^||_D^2 of one sample and its gradient (host, GL_WS_NPARAM
- * floats, nullable) with respect to the parameters. */
+                                      const void *hint_dev, void *x0_dev, void *stream);
+/* Loss ||r^ - J x^||_D^2 of one sample (r = b without a hint) and its gradient
+ * (host, GL_WS_NPARAM floats, nullable) with respect to the parameters. */
 GL_API gl_status gl_warmstart_grad(gl_warmstart ws, gl_mesh mesh, const void *psi_dev, const void *b_dev,
-                                   float *grad_host, double *loss_out, void *stream);
+                                   const void *hint_dev, float *grad_host, double *loss_out, void *stream);
 /* `steps` Adam steps with learning rate lr; step t averages the losses and
  * gradients of samples (t * batch + j) mod count, j < batch.  Sample k is
- * (meshes[k], psi_dev[k], b_dev[k]); meshes may differ between samples.
+ * (meshes[k], psi_dev[k], b_dev[k], hint_dev[k]); meshes may differ between
+ * samples; hint_dev (nullable array, nullable entries) gives the hints.
  * loss_out (host, nullable) receives the mean loss of every step. */
 GL_API gl_status gl_warmstart_train(gl_warmstart ws, int count, const gl_mesh *meshes, const void *const *psi_dev,
-                                    const void *const *b_dev, int steps, int batch, float lr, double *loss_out,
-                                    void *stream);
+                                    const void *const *b_dev, const void *const *hint_dev, int steps, int batch,
+                                    float lr, double *loss_out, void *stream);
 /* One Adam step with the given gradient (host, GL_WS_NPARAM floats). */
 GL_API gl_status gl_warmstart_adam_step(gl_warmstart ws, const float *grad_host, float lr);
 

@@ -72,7 +72,7 @@ class Options(C.Structure):
         ("max_outer", C.c_int), ("check_every", C.c_int), ("autotune", C.c_int), ("lattice", C.c_int),
         ("cluster_sweeps", C.c_int),
         ("warmstart", C.c_void_p), ("coloring", C.c_int), ("sweep_sync", C.c_int), ("coarse_df", C.c_int),
-        ("device_loop", C.c_int),
+        ("device_loop", C.c_int), ("warmstart_hint", C.c_void_p),
     ]
 
 
@@ -162,10 +162,10 @@ def library(build_if_missing: bool = True):
             "gl_warmstart_destroy": [vp],
             "gl_warmstart_get_params": [vp, vp],
             "gl_warmstart_set_params": [vp, vp],
-            "gl_warmstart_predict": [vp, vp, vp, vp, vp, vp],
-            "gl_warmstart_grad": [vp, vp, vp, vp, vp, C.POINTER(C.c_double), vp],
-            "gl_warmstart_train": [vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.c_int, C.c_int,
-                                   C.c_float, vp, vp],
+            "gl_warmstart_predict": [vp, vp, vp, vp, vp, vp, vp],
+            "gl_warmstart_grad": [vp, vp, vp, vp, vp, vp, C.POINTER(C.c_double), vp],
+            "gl_warmstart_train": [vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.c_int,
+                                   C.c_int, C.c_float, vp, vp],
             "gl_warmstart_adam_step": [vp, vp, C.c_float],
             "gl_mesh_create_edge": [C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_double), vp,
                                     C.POINTER(vp)],
@@ -535,24 +535,35 @@ def gl_warmstart_set_params(ws, params):
     _check(library().gl_warmstart_set_params(ws, p.ctypes.data_as(vp)))
 
 
-def gl_warmstart_predict(ws, mesh, psi, b, x0, stream=None):
-    _check(library().gl_warmstart_predict(ws, mesh, _ptr(psi), _ptr(b), _ptr(x0), _stream(stream)))
+def _optptr(t):
+    return _ptr(t) if t is not None else None
 
 
-def gl_warmstart_grad(ws, mesh, psi, b, stream=None):
+def gl_warmstart_predict(ws, mesh, psi, b, x0, stream=None, hint=None):
+    """x0 = the network's guess; hint (nullable): a vector the solution should resemble."""
+    _check(library().gl_warmstart_predict(ws, mesh, _ptr(psi), _ptr(b), _optptr(hint), _ptr(x0), _stream(stream)))
+
+
+def gl_warmstart_grad(ws, mesh, psi, b, stream=None, hint=None):
     """(loss, gradient as GL_WS_NPARAM float32) of one sample."""
     g = np.zeros(GL_WS_NPARAM, np.float32)
     L = C.c_double()
-    _check(library().gl_warmstart_grad(ws, mesh, _ptr(psi), _ptr(b), g.ctypes.data_as(vp), C.byref(L),
+    _check(library().gl_warmstart_grad(ws, mesh, _ptr(psi), _ptr(b), _optptr(hint), g.ctypes.data_as(vp), C.byref(L),
                                        _stream(stream)))
     return L.value, g
 
 
-def gl_warmstart_train(ws, meshes, psis, bs, steps: int, batch: int = 1, lr: float = 1e-3, stream=None):
-    """Adam training on samples (meshes[k], psis[k], bs[k]); returns the mean loss of every step."""
+def gl_warmstart_train(ws, meshes, psis, bs, steps: int, batch: int = 1, lr: float = 1e-3, stream=None,
+                       hints=None):
+    """Adam training on samples (meshes[k], psis[k], bs[k][, hints[k]]); returns the mean
+    loss of every step.  hints: None, or one tensor or None per sample."""
     losses = np.zeros(max(steps, 1), np.float64)
-    _check(library().gl_warmstart_train(ws, len(meshes), _vparr(meshes), _vparr(psis), _vparr(bs), int(steps),
-                                        int(batch), float(lr), losses.ctypes.data_as(vp), _stream(stream)))
+    harr = None
+    if hints is not None:
+        harr = (vp * len(hints))(*[_ptr(h).value if h is not None else None for h in hints])
+    _check(library().gl_warmstart_train(ws, len(meshes), _vparr(meshes), _vparr(psis), _vparr(bs), harr,
+                                        int(steps), int(batch), float(lr), losses.ctypes.data_as(vp),
+                                        _stream(stream)))
     return losses[:steps]
 
 

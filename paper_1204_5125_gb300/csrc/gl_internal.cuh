@@ -259,10 +259,11 @@ void coarse_inverse_df(Level &L, cudaStream_t s);
 // z = R_k v with FP64 vectors and an FP32 V-cycle
 void precond_apply_p64_via32(gl_prec_s *p, const double2 *v, double2 *z, const int *stop, cudaStream_t s);
 
-// gl_warmstart.cu (solve ordering): x_p = network guess for b_p, replaced by 0
-// when ||b - J x||_D >= ||b||_D; warmstart_used() reads that decision (after a sync)
+// gl_warmstart.cu (solve ordering): x_p = network guess for b_p (with the hint
+// hint_nat, node order, nullable), replaced by 0 when ||b - J x||_D >= ||b||_D;
+// warmstart_used() reads that decision (after a sync)
 void warmstart_apply_p(gl_warmstart_s *w, gl_mesh_s *m, const double2 *psi_p, const double2 *b_p, double2 *x_p,
-                       cudaStream_t s);
+                       cudaStream_t s, const double2 *hint_nat = nullptr);
 int warmstart_used(gl_warmstart_s *w, cudaStream_t s);
 
 // gl_solve.cu

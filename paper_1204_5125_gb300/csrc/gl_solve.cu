@@ -1264,7 +1264,7 @@ gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, con
     gl_solve_info inf{};
     GL_REQUIRE(!(p && p->rinf) || o.precision == GL_FP64, GL_ERR_ARG, "R_inf needs precision GL_FP64");
     rinf_reset(p, s);
-    if (o.warmstart) warmstart_apply_p(o.warmstart, m, psi_p, b_p, x_p, s);
+    if (o.warmstart) warmstart_apply_p(o.warmstart, m, psi_p, b_p, x_p, s, (const double2 *)o.warmstart_hint);
     bool mixed = (o.precision == GL_MIXED) && p;
     if (!mixed) {
         bool vc32 = (o.precision == GL_MIXED_PRECOND) && p;

@@ -1496,8 +1496,8 @@ static void zero_flags(Level &L, bool fp32, cudaStream_t s) {
 // the throughput-bound SpMV that set the operator's own G), the synchronisation
 // between colours (grid barrier, or neighbour flags with nb CTAs) and, in FP32,
 // the thread-block-cluster sweep for levels whose vector fits a cluster.  With
-// autotuning every candidate (G = 2, 4, 8, 16; for the flags the default CTA
-// count and the most that stay resident) is timed on this GPU (best of two after
+// autotuning every candidate (G = 2, 4, 8, 16; the flags with CTAs in
+// proportion to the level's largest colour) is timed on this GPU (best of two after
 // a warm-up launch, on zero vectors) and the fastest kept; without it the
 // operator's G, the flags where their partition fits (else the grid barrier),
 // and the cluster sweep wherever it fits.  options.sweep_sync = 1 or 2 keeps
@@ -1582,11 +1582,10 @@ static void plan_sweeps_t(gl_prec_s *p, cudaStream_t s) {
                                        (long long)L.n, L.ncolors, fp32 ? "FP32" : "FP64", g, 1e3 * t);
             }
             if (try_flags) {
-                const int mx = flags_max_ctas_g<T>(g);
-                const int nb0 = flags_default_nb<T>(L, g, mx);
-                std::vector<int> nbs{nb0};
-                if (mx != nb0) nbs.push_back(mx);
-                for (int nb : nbs) {
+                // CTAs in proportion to the level (never the whole GPU for a small
+                // level: in a batch, instances' sweeps run side by side)
+                const int nb0 = flags_default_nb<T>(L, g, flags_max_ctas_g<T>(g));
+                for (int nb : {nb0}) {
                     FlagPlan cand;
                     const int longest = build_flag_plan<C>(L, A, g, nb, cand, s);
                     if (longest > FLAG_MAXN) {

@@ -271,15 +271,78 @@ __global__ void k_bnorm_final(const double *part, int np, double *bn) {
     }
 }
 
-// h^0 rows
+// ---- the hint: alpha = <J a, b>_R / <J a, J a>_R, r = b - alpha J a
+// partials of <q, b>_R, <q, q>_R and ||a||_D^2 (q = J a)
+__global__ void k_hint_part(int64_t n, const double *__restrict__ vol, const double2 *__restrict__ q,
+                            const double2 *__restrict__ b, const double2 *__restrict__ a, double *part) {
+    __shared__ double sh[32];
+    double qb = 0, qq = 0, aa = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 qv = q[i], bv = b[i], av = a[i];
+        const double w = vol[i];
+        qb += w * (qv.x * bv.x + qv.y * bv.y);
+        qq += w * (qv.x * qv.x + qv.y * qv.y);
+        aa += w * (av.x * av.x + av.y * av.y);
+    }
+    const double t0 = block_sum(qb, sh);
+    const double t1 = block_sum(qq, sh);
+    const double t2 = block_sum(aa, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = t0;
+        part[RED_BLOCKS + blockIdx.x] = t1;
+        part[2 * RED_BLOCKS + blockIdx.x] = t2;
+    }
+}
+// hs[0] = alpha (0 when J a = 0), hs[1] = 1 / ||a||_D (0 when a = 0)
+__global__ void k_hint_final(const double *part, double *hs) {
+    __shared__ double sh[32];
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) {
+        s0 += part[i];
+        s1 += part[RED_BLOCKS + i];
+        s2 += part[2 * RED_BLOCKS + i];
+    }
+    const double qb = block_sum(s0, sh);
+    const double qq = block_sum(s1, sh);
+    const double aa = block_sum(s2, sh);
+    if (threadIdx.x == 0) {
+        hs[0] = (aa > 0 && qq > 0) ? qb / qq : 0.0;
+        hs[1] = aa > 0 ? 1.0 / sqrt(aa) : 0.0;
+    }
+}
+// r = b - alpha q
+__global__ void k_hint_resid(int64_t n, const double *__restrict__ hs, const double2 *__restrict__ b,
+                             const double2 *__restrict__ q, double2 *__restrict__ r) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double al = hs[0];
+    r[i] = make_double2(b[i].x - al * q[i].x, b[i].y - al * q[i].y);
+}
+// x0 += alpha a
+__global__ void k_hint_add(int64_t n, const double *__restrict__ hs, const double2 *__restrict__ a,
+                           double2 *__restrict__ x0) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double al = hs[0];
+    x0[i] = make_double2(x0[i].x + al * a[i].x, x0[i].y + al * a[i].y);
+}
+
+// h^0 rows: [Re r^, Im r^, Re psi, Im psi, |psi|^2, 0, Re a^, Im a^, 0 ..., 1]
+// (the hint a^ = a / ||a||_D as the complex channel pair (6, 7), zero without one)
 __global__ void k_features(int64_t n, const double2 *__restrict__ b, const double2 *__restrict__ psi,
-                           const double *__restrict__ bn, uint4 *__restrict__ H0) {
+                           const double *__restrict__ bn, const double2 *__restrict__ hint,
+                           const double *__restrict__ hs, uint4 *__restrict__ H0) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= n) return;
     double inv = bn[1];
     double2 bv = b[p], ps = psi[p];
     float f[8] = {(float)(bv.x * inv), (float)(bv.y * inv), (float)ps.x, (float)ps.y,
                   (float)(ps.x * ps.x + ps.y * ps.y), 0.f, 0.f, 0.f};
+    if (hint) {
+        const double ia = hs[1];
+        f[6] = (float)(hint[p].x * ia);
+        f[7] = (float)(hint[p].y * ia);
+    }
     float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float last[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
     uint4 *row = H0 + p * 8;
@@ -862,6 +925,10 @@ struct gl_warmstart_s {
     DBuf<int> err;
     DBuf<int> used;          // zero-guess fallback decision of the last solve
     DBuf<double> fpart;      // its partials
+    // the hint: J a, the residual r = b - alpha J a, the hint in the solve ordering,
+    // partials and (alpha, 1 / ||a||_D)
+    DBuf<double2> qa, rb, hp;
+    DBuf<double> hpart, hsc;
     int fwd_grid = 0, bwd_grid = 0;
 };
 
@@ -896,6 +963,9 @@ void ws_reserve(gl_warmstart_s *w, int64_t n) {
     w->xh.alloc(n);
     w->r.alloc(n);
     w->dy.alloc(n);
+    w->qa.alloc(n);
+    w->rb.alloc(n);
+    w->hp.alloc(n);
     w->cap = n;
 }
 
@@ -947,17 +1017,37 @@ void ws_setup_kernels(gl_warmstart_s *w) {
     GL_CUDA(cudaMemset(w->err.get(), 0, sizeof(int)));
     w->used.alloc(1);
     w->fpart.alloc(2 * RED_BLOCKS);
+    w->hpart.alloc(3 * RED_BLOCKS);
+    w->hsc.alloc(2);
+}
+
+// with a hint (solve ordering): alpha and 1 / ||a||_D into hsc, and the residual
+// b - alpha J a the network works on; returns the right-hand side to use
+const double2 *ws_hint(gl_warmstart_s *w, gl_mesh_s *m, const double2 *psi_p, const double2 *b_p,
+                       const double2 *hint_p, cudaStream_t s) {
+    if (!hint_p) return b_p;
+    const int64_t n = m->n;
+    jacobian_apply_p(m, psi_p, hint_p, w->qa.get(), s);
+    note_launch(3);
+    k_hint_part<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, m->volp.get(), w->qa.get(), b_p, hint_p, w->hpart.get());
+    k_hint_final<<<1, 1024, 0, s>>>(w->hpart.get(), w->hsc.get());
+    k_hint_resid<<<grid_for(n, 256), 256, 0, s>>>(n, w->hsc.get(), b_p, w->qa.get(), w->rb.get());
+    GL_LAUNCH_CHECK();
+    return w->rb.get();
 }
 
 __nv_bfloat16 *Hbuf(gl_warmstart_s *w, int l) { return w->H.get() + (size_t)l * w->cap * CH; }
 
-// forward pass in the solve ordering; train: keep h^1..h^4 and x^, else write x0
+// forward pass in the solve ordering; train: keep h^1..h^4 and x^, else write x0.
+// b_p is the network's right-hand side (the residual the hint leaves, when there
+// is one: see ws_hint); hint_p (nullable) fills the hint channels
 void ws_forward(gl_warmstart_s *w, gl_mesh_s *m, const double2 *psi_p, const double2 *b_p, bool train, double2 *x0_p,
-                cudaStream_t s) {
+                cudaStream_t s, const double2 *hint_p = nullptr) {
     const int64_t n = m->n;
     k_bnorm_part<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, m->volp.get(), b_p, w->part.get());
     k_bnorm_final<<<1, 1024, 0, s>>>(w->part.get(), RED_BLOCKS, w->bn.get());
-    k_features<<<grid_for(n, 256), 256, 0, s>>>(n, b_p, psi_p, w->bn.get(), reinterpret_cast<uint4 *>(Hbuf(w, 0)));
+    k_features<<<grid_for(n, 256), 256, 0, s>>>(n, b_p, psi_p, w->bn.get(), hint_p, w->hsc.get(),
+                                                reinterpret_cast<uint4 *>(Hbuf(w, 0)));
     GL_LAUNCH_CHECK();
     note_launch(3);
     const int64_t ntiles = (n + TILE - 1) / TILE;
@@ -1074,18 +1164,30 @@ void ensure_mesh_scratch(gl_mesh_s *m) {
 
 namespace gl {
 
-// x0_p = network guess for b_p (solve ordering); used by the solver
+// x0_p = network guess for b_p (solve ordering; hint_p nullable, solve ordering)
 void warmstart_predict_p(gl_warmstart_s *w, gl_mesh_s *m, const double2 *psi_p, const double2 *b_p, double2 *x0_p,
-                         cudaStream_t s) {
+                         cudaStream_t s, const double2 *hint_p) {
     mesh_ensure_fp32(m, s);
     ws_setup_kernels(w);
     ws_reserve(w, m->n);
-    ws_forward(w, m, psi_p, b_p, false, x0_p, s);
+    const double2 *r_p = ws_hint(w, m, psi_p, b_p, hint_p, s);
+    ws_forward(w, m, psi_p, r_p, false, x0_p, s, hint_p);
+    if (hint_p) {
+        note_launch();
+        k_hint_add<<<grid_for(m->n, 256), 256, 0, s>>>(m->n, w->hsc.get(), hint_p, x0_p);
+        GL_LAUNCH_CHECK();
+    }
 }
 
 void warmstart_apply_p(gl_warmstart_s *w, gl_mesh_s *m, const double2 *psi_p, const double2 *b_p, double2 *x_p,
-                       cudaStream_t s) {
-    warmstart_predict_p(w, m, psi_p, b_p, x_p, s);
+                       cudaStream_t s, const double2 *hint_nat) {
+    const double2 *hint_p = nullptr;
+    if (hint_nat) {
+        ws_reserve(w, m->n);
+        permute_in(m->n, m->perm.get(), hint_nat, w->hp.get(), s);
+        hint_p = w->hp.get();
+    }
+    warmstart_predict_p(w, m, psi_p, b_p, x_p, s, hint_p);
     note_launch(3);
     k_fallback_part<<<RED_BLOCKS, RED_THREADS, 0, s>>>(m->n, m->K.view(), m->kdiag.get(), m->volp.get(), psi_p, b_p,
                                                        x_p, w->fpart.get());
@@ -1167,22 +1269,30 @@ gl_status gl_warmstart_set_params(gl_warmstart w, const float *params) {
     });
 }
 
-gl_status gl_warmstart_predict(gl_warmstart w, gl_mesh m, const void *psi, const void *b, void *x0, void *stream) {
+gl_status gl_warmstart_predict(gl_warmstart w, gl_mesh m, const void *psi, const void *b, const void *hint, void *x0,
+                               void *stream) {
     return ws_guard([&] {
         GL_REQUIRE(w && m && psi && b && x0, GL_ERR_ARG, "NULL argument");
         cudaStream_t s = as_stream(stream);
         ensure_mesh_scratch(m);
         permute_in(m->n, m->perm.get(), (const double2 *)psi, m->t0.get(), s);
         permute_in(m->n, m->perm.get(), (const double2 *)b, m->t1.get(), s);
-        warmstart_predict_p(w, m, m->t0.get(), m->t1.get(), m->t2.get(), s);
+        const double2 *hp = nullptr;
+        if (hint) {
+            ws_setup_kernels(w);
+            ws_reserve(w, m->n);
+            permute_in(m->n, m->perm.get(), (const double2 *)hint, w->hp.get(), s);
+            hp = w->hp.get();
+        }
+        warmstart_predict_p(w, m, m->t0.get(), m->t1.get(), m->t2.get(), s, hp);
         permute_out(m->n, m->perm.get(), m->t2.get(), (double2 *)x0, s);
         check_err(w, s);
         return GL_OK;
     });
 }
 
-gl_status gl_warmstart_grad(gl_warmstart w, gl_mesh m, const void *psi, const void *b, float *grad_host,
-                            double *loss_out, void *stream) {
+gl_status gl_warmstart_grad(gl_warmstart w, gl_mesh m, const void *psi, const void *b, const void *hint,
+                            float *grad_host, double *loss_out, void *stream) {
     return ws_guard([&] {
         GL_REQUIRE(w && m && psi && b, GL_ERR_ARG, "NULL argument");
         cudaStream_t s = as_stream(stream);
@@ -1192,10 +1302,16 @@ gl_status gl_warmstart_grad(gl_warmstart w, gl_mesh m, const void *psi, const vo
         ws_reserve(w, m->n);
         permute_in(m->n, m->perm.get(), (const double2 *)psi, m->t0.get(), s);
         permute_in(m->n, m->perm.get(), (const double2 *)b, m->t1.get(), s);
+        const double2 *hp = nullptr;
+        if (hint) {
+            permute_in(m->n, m->perm.get(), (const double2 *)hint, w->hp.get(), s);
+            hp = w->hp.get();
+        }
         GL_CUDA(cudaMemsetAsync(w->grad.get(), 0, NPARAM * sizeof(float), s));
         GL_CUDA(cudaMemsetAsync(w->loss.get(), 0, sizeof(double), s));
-        ws_forward(w, m, m->t0.get(), m->t1.get(), true, nullptr, s);
-        ws_backward(w, m, m->t0.get(), m->t1.get(), 1.0, w->loss.get(), 0, s);
+        const double2 *r_p = ws_hint(w, m, m->t0.get(), m->t1.get(), hp, s);
+        ws_forward(w, m, m->t0.get(), r_p, true, nullptr, s, hp);
+        ws_backward(w, m, m->t0.get(), r_p, 1.0, w->loss.get(), 0, s);
         check_err(w, s);
         if (grad_host) GL_CUDA(cudaMemcpy(grad_host, w->grad.get(), NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
         if (loss_out) GL_CUDA(cudaMemcpy(loss_out, w->loss.get(), sizeof(double), cudaMemcpyDeviceToHost));
@@ -1204,7 +1320,8 @@ gl_status gl_warmstart_grad(gl_warmstart w, gl_mesh m, const void *psi, const vo
 }
 
 gl_status gl_warmstart_train(gl_warmstart w, int count, const gl_mesh *meshes, const void *const *psi,
-                             const void *const *b, int steps, int batch, float lr, double *loss_out, void *stream) {
+                             const void *const *b, const void *const *hints, int steps, int batch, float lr,
+                             double *loss_out, void *stream) {
     return ws_guard([&] {
         GL_REQUIRE(w && meshes && psi && b, GL_ERR_ARG, "NULL argument");
         GL_REQUIRE(count > 0 && steps >= 0 && batch > 0 && lr > 0, GL_ERR_ARG, "bad count, steps, batch or lr");
@@ -1226,8 +1343,14 @@ gl_status gl_warmstart_train(gl_warmstart w, int count, const gl_mesh *meshes, c
                 gl_mesh_s *m = meshes[k];
                 permute_in(m->n, m->perm.get(), (const double2 *)psi[k], m->t0.get(), s);
                 permute_in(m->n, m->perm.get(), (const double2 *)b[k], m->t1.get(), s);
-                ws_forward(w, m, m->t0.get(), m->t1.get(), true, nullptr, s);
-                ws_backward(w, m, m->t0.get(), m->t1.get(), 1.0 / batch, losses.get(), st, s);
+                const double2 *hp = nullptr;
+                if (hints && hints[k]) {
+                    permute_in(m->n, m->perm.get(), (const double2 *)hints[k], w->hp.get(), s);
+                    hp = w->hp.get();
+                }
+                const double2 *r_p = ws_hint(w, m, m->t0.get(), m->t1.get(), hp, s);
+                ws_forward(w, m, m->t0.get(), r_p, true, nullptr, s, hp);
+                ws_backward(w, m, m->t0.get(), r_p, 1.0 / batch, losses.get(), st, s);
             }
             w->t += 1;
             float c1 = 1.f - powf(b1, (float)w->t), c2 = 1.f - powf(b2, (float)w->t);

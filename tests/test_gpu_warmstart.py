@@ -87,6 +87,47 @@ def test_gradient_matches_oracle(oracle_mod, dim, N, mu, field):
         gl.gl_mesh_destroy(m)
 
 
+@pytest.mark.parametrize("dim,N,mu,field", CASES)
+def test_hint_forward_and_gradient_match_oracle(oracle_mod, dim, N, mu, field):
+    """With a hint: the FP64 minimal-residual multiple alpha a matches the oracle's
+    to FP64 rounding (zero network), the network's correction at the BF16 bar,
+    and the gradient (including the weights reading the hint channels) too."""
+    om = oracle_mod.Mesh(dim, N, mu, field)
+    g = ows.Graph(om)
+    psi = gi.disk(om.n, 41)
+    b = gi.complex_normal(om.n, 42)
+    a = gi.complex_normal(om.n, 43) + 0.5 * b
+    m = gl.gl_mesh_create(dim, N, mu, field)
+    ws = gl.gl_warmstart_create(np.zeros(gl.GL_WS_NPARAM, np.float32))
+    try:
+        x0 = torch.zeros(om.n, dtype=torch.complex128, device=DEV)
+        gl.gl_warmstart_predict(ws, m, dev(psi), dev(b), x0, hint=dev(a))
+        torch.cuda.synchronize()
+        base = ows.predict(np.zeros(ows.NPARAM), g, psi, b, a)
+        assert rel(x0.cpu().numpy(), base) <= 1e-12
+        theta = gi.warmstart_init(8)
+        gl.gl_warmstart_set_params(ws, theta)
+        gl.gl_warmstart_predict(ws, m, dev(psi), dev(b), x0, hint=dev(a))
+        torch.cuda.synchronize()
+        expect = ows.predict(theta.astype(np.float64), g, psi, b, a)
+        got = x0.cpu().numpy()
+        assert rel(got - base, expect - base) <= 2e-2, rel(got - base, expect - base)
+        L, grad = gl.gl_warmstart_grad(ws, m, dev(psi), dev(b), hint=dev(a))
+        Lo, go = ows.loss_and_grad(theta.astype(np.float64), g, psi, b, a)
+        assert abs(L - Lo) <= 1e-2 * Lo, (L, Lo)
+        Ws, U = ows.split(np.arange(ows.NPARAM))
+        for name, idx in [("W0", Ws[0]), ("W3", Ws[3]), ("U", U),
+                          ("W0 hint columns", np.concatenate([Ws[0][:, 6], Ws[0][:, 7], Ws[0][:, ows.C + 6],
+                                                              Ws[0][:, ows.C + 7]]))]:
+            x, e = grad[idx.ravel()].astype(np.float64), go[idx.ravel()]
+            # two more BF16-rounded input channels (the hint pair) than without a
+            # hint: 3e-2 per tensor (measured 2.1-2.9e-2), cosine >= 0.999
+            assert rel(x, e) <= 3e-2 and cosine(x, e) >= 0.999, (name, rel(x, e), cosine(x, e))
+    finally:
+        gl.gl_warmstart_destroy(ws)
+        gl.gl_mesh_destroy(m)
+
+
 def test_adam_matches_oracle():
     theta = gi.warmstart_init(5)
     ws = gl.gl_warmstart_create(theta)
@@ -163,22 +204,27 @@ def test_continuation_gain(oracle_mod):
     """Natural-parameter continuation in mu on a 2D square (from psi = 1 at mu = 0,
     Sec. 4): Newton steps J d = -GL(psi), psi += d, until ||GL(psi)||_R <= 1e-8
     (below that the round-off in GL(psi) has a component along the near-null
-    direction i psi of J that no solve can reduce 1e-10-fold).
-    The network is trained on the (psi, b) pairs of the first half of the
+    direction i psi of J that no solve can reduce 1e-10-fold).  Every Newton
+    system comes with a hint: the correction of the same Newton step at the
+    previous mu.  The network is trained on the systems of the first half of the
     continuation and used on the second half; every warm-started solve is
-    compared with the zero-guess solve of the same system.  Reported: the
-    relative residual of the guess and the iterations and time it saves."""
+    compared with the zero-guess solve of the same system and with the guess the
+    hint alone gives (its minimal-residual multiple, a zero network).  Reported:
+    the guesses' relative residuals and the iterations and time they save."""
     N, steps = 64, 24
     mus = [2.0 * (s + 1) / steps for s in range(steps)]
     n = N * N
     psi = torch.ones(n, dtype=torch.complex128, device=DEV)
     opts = gl.options(max_coarse=64)
-    train_m, train_psi, train_b, held = [], [], [], []
+    train = dict(m=[], psi=[], b=[], hint=[])
+    held = []
     meshes = []
+    prev = []  # the Newton corrections at the previous mu
     try:
         for s, mu in enumerate(mus):
             m = gl.gl_mesh_create(2, N, mu)
             meshes.append(m)
+            cur = []
             for it in range(8):
                 r = torch.zeros_like(psi)
                 gl.gl_residual(m, psi, r)
@@ -190,41 +236,59 @@ def test_continuation_gain(oracle_mod):
                 d = torch.zeros_like(psi)
                 st, inf = gl.gl_jacobian_solve(m, psi, None, b, d, opts)
                 assert st == 0
-                if s < steps // 2:
-                    train_m.append(m)
-                    train_psi.append(psi.clone())
-                    train_b.append(b.clone())
-                else:
-                    held.append((m, mu, psi.clone(), b.clone(), inf.iters, inf.solve_ms))
+                hint = prev[it] if it < len(prev) else None
+                if hint is not None:
+                    if s < steps // 2:
+                        train["m"].append(m)
+                        train["psi"].append(psi.clone())
+                        train["b"].append(b.clone())
+                        train["hint"].append(hint)
+                    else:
+                        held.append((m, mu, psi.clone(), b.clone(), hint, inf.iters, inf.solve_ms))
+                cur.append(d.clone())
                 psi = psi + d
-        assert len(train_b) >= 8 and len(held) >= 8
+            prev = cur
+        assert len(train["b"]) >= 8 and len(held) >= 8
         ws = gl.gl_warmstart_create(gi.warmstart_init(12))
         try:
-            losses = gl.gl_warmstart_train(ws, train_m, train_psi, train_b, steps=400, batch=4, lr=2e-3)
+            losses = gl.gl_warmstart_train(ws, train["m"], train["psi"], train["b"], steps=400, batch=4, lr=2e-3,
+                                           hints=train["hint"])
             assert losses[-20:].mean() < losses[:20].mean()
-            wopts = gl.options(max_coarse=64)
-            wopts.warmstart = ws.value
-            it0 = it1 = used = 0
-            t0 = t1 = 0.0
-            res = []
-            for m, mu, p, b, iters0, ms0 in held:
-                x0 = torch.zeros_like(b)
-                gl.gl_warmstart_predict(ws, m, p, b, x0)
-                om = oracle_mod.Mesh(2, N, mu)
-                pn, bn = p.cpu().numpy(), b.cpu().numpy()
-                res.append(true_relres(om, pn, bn, x0.cpu().numpy()))
-                x = torch.zeros_like(b)
-                st, inf = gl.gl_jacobian_solve(m, p, None, b, x, wopts)
-                assert st == 0 and true_relres(om, pn, bn, x.cpu().numpy()) <= 1.01e-10
-                assert inf.iters <= iters0 + 1
-                it0 += iters0
-                it1 += inf.iters
-                used += inf.warmstart_used
-                t0 += ms0
-                t1 += inf.solve_ms
-            print(f"continuation: {len(train_b)} training solves, {len(held)} held-out solves; guess residual "
-                  f"median {np.median(res):.3f} (min {min(res):.3f}, max {max(res):.3f}); warm start used "
-                  f"{used}/{len(held)}; iterations {it0} -> {it1}; solve ms {t0:.1f} -> {t1:.1f}")
+            trained = gl.gl_warmstart_get_params(ws)
+            out = {}
+            for label, params in (("hint alone", np.zeros(gl.GL_WS_NPARAM, np.float32)), ("hint + network", trained)):
+                gl.gl_warmstart_set_params(ws, params)
+                its = used = 0
+                ms = 0.0
+                res = []
+                for m, mu, p, b, hint, iters0, ms0 in held:
+                    x0 = torch.zeros_like(b)
+                    gl.gl_warmstart_predict(ws, m, p, b, x0, hint=hint)
+                    om = oracle_mod.Mesh(2, N, mu)
+                    pn, bn = p.cpu().numpy(), b.cpu().numpy()
+                    res.append(true_relres(om, pn, bn, x0.cpu().numpy()))
+                    wopts = gl.options(max_coarse=64)
+                    wopts.warmstart = ws.value
+                    wopts.warmstart_hint = hint.data_ptr()
+                    x = torch.zeros_like(b)
+                    st, inf = gl.gl_jacobian_solve(m, p, None, b, x, wopts)
+                    assert st == 0 and true_relres(om, pn, bn, x.cpu().numpy()) <= 1.01e-10
+                    assert inf.iters <= iters0 + 1
+                    its += inf.iters
+                    used += inf.warmstart_used
+                    ms += inf.solve_ms
+                out[label] = (its, used, ms, res)
+            it0 = sum(h[5] for h in held)
+            ms0 = sum(h[6] for h in held)
+            print(f"continuation: {len(train['b'])} training solves, {len(held)} held-out solves, zero guess "
+                  f"{it0} iterations ({ms0:.1f} ms)")
+            for label, (its, used, ms, res) in out.items():
+                print(f"  {label}: guess residual median {np.median(res):.2e} (max {max(res):.2e}); used "
+                      f"{used}/{len(held)}; iterations {it0} -> {its}; solve ms {ms0:.1f} -> {ms:.1f}")
+            # the hint's multiple alone already saves iterations; the trained
+            # network must not lose what it gives
+            assert out["hint alone"][0] < it0
+            assert out["hint + network"][0] <= out["hint alone"][0] + len(held) // 4
         finally:
             gl.gl_warmstart_destroy(ws)
     finally:
