@@ -1465,9 +1465,12 @@ static void apply_prec(const glref_prec *p, int64_t n, const cplx *v, cplx *z) {
 /* Preconditioned MINRES (Paige & Saunders 1975) for J(psi) x = b, J self-adjoint
  * in <.,.>_R (Sec. 3), preconditioner R_k (Eq. prec2), self-adjoint positive
  * definite in the same inner product.  x holds the initial guess on entry.
- * Stopping: once the recurrence estimate |eta|/eta_0 is <= tol, the true
- * residual ||b - J x||_D / ||b||_D is computed; the iteration stops when that is
- * <= tol as well.  Returns 0 when converged, 1 at maxit, 2 on breakdown. */
+ * Stopping: the tolerance is relative to b (Sec. 4: the relative residual in the
+ * norm of Eq. disc inner2).  The recurrence's estimate |eta| / eta_0 is relative
+ * to the initial residual r_0 = b - J x_0, so it is scaled by
+ * rho_0 = ||r_0||_D / ||b||_D (1 from x_0 = 0); once rho_0 |eta| / eta_0 <= tol the
+ * true residual ||b - J x||_D / ||b||_D is computed, and the iteration stops when
+ * that is <= tol as well.  Returns 0 when converged, 1 at maxit, 2 on breakdown. */
 int glref_minres(const glref_mesh *m, const cplx *psi, const glref_prec *prec, const cplx *b, cplx *x,
                  const glref_options *o, glref_info *info) {
     int64_t n = m->n;
@@ -1503,6 +1506,7 @@ int glref_minres(const glref_mesh *m, const cplx *psi, const glref_prec *prec, c
     double eta = gamma, eta0 = gamma;
     double c_old = 1, c = 1, s_old = 0, s = 0;
     info->true_relres = true_relres(m, psi, b, x, bnorm, tmp);
+    const double rho0 = info->true_relres;  /* ||r_0||_D / ||b||_D */
     if (gamma == 0 || info->true_relres <= o->tol) {
         info->converged = 1;
         status = 0;
@@ -1548,7 +1552,7 @@ int glref_minres(const glref_mesh *m, const cplx *psi, const glref_prec *prec, c
         s_old = s;
         s = s_new;
         info->iters = it;
-        info->est_relres = fabs(eta) / eta0;
+        info->est_relres = rho0 * fabs(eta) / eta0;
         if (info->est_relres <= o->tol) {
             info->true_relres = true_relres(m, psi, b, x, bnorm, tmp);
             if (info->true_relres <= o->tol) {

@@ -212,3 +212,26 @@ def test_threads_give_bit_identical_results(oracle_mod):
         oracle_mod.set_threads(1)
     assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
     assert np.array_equal(out[0][0], out[1][0])
+
+
+def test_warm_start_tolerance_is_relative_to_b(oracle_mod):
+    """The tolerance is relative to b: from a guess whose residual is 1e-3 of b the
+    solve needs about three decades less reduction, so fewer iterations than from
+    zero, and it still ends at ||b - J x||_D <= tol ||b||_D.  (An estimate relative
+    to the guess's residual would over-solve by those three decades and save
+    nothing.)"""
+    m = oracle_mod.Mesh(2, 40, 1.0)
+    psi, b = gi.disk(m.n, 71), gi.complex_normal(m.n, 72)
+    xz, iz = m.solve(psi, b, max_coarse=64, tol=1e-12)
+    # a guess with relative residual ~1e-3: the accurate solution plus a smooth error
+    vol = m.volumes()
+    dn = lambda v: np.sqrt(np.sum(vol * np.abs(v) ** 2))  # noqa: E731
+    e = np.exp(1j * np.linspace(0, 3, m.n))
+    x0 = xz + (1e-3 * dn(b) / dn(m.jacobian(psi, e))) * e
+    rho = dn(b - m.jacobian(psi, x0)) / dn(b)
+    assert 5e-4 <= rho <= 2e-3, rho
+    x0_zero, info0 = m.solve(psi, b, max_coarse=64, tol=1e-10)
+    xw, infow = m.solve(psi, b, x0=x0, max_coarse=64, tol=1e-10)
+    assert info0.converged and infow.converged
+    assert infow.true_relres <= 1e-10
+    assert infow.iters <= info0.iters - 3, (infow.iters, info0.iters)
