@@ -75,6 +75,10 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the batch64 and 2D workload measurements")
     ap.add_argument("--sweep-sync", type=int, default=0, choices=[0, 1, 2],
                     help="coarse-sweep synchronisation (options.sweep_sync; 0 = timed at setup)")
+    ap.add_argument("--workload", default="cube", choices=["cube", "cube-continuation"],
+                    help="cube: the headline solve; cube-continuation: the field-strength continuation with the "
+                         "learned warm start (its own JSON line)")
+    ap.add_argument("--cont-steps", type=int, default=64, help="continuation steps (cube-continuation)")
     ap.add_argument("--host-loop", action="store_true",
                     help="MINRES iterations replayed by the host instead of the device-side graph loop "
                          "(options.device_loop = 0; for launch lists of profilers that skip conditional graphs)")
@@ -360,10 +364,121 @@ def run_square(gl, torch, dev, name, steps=5):
     return out
 
 
+def run_continuation(args):
+    """The continuation workload on the N^3 cube (the 256^3 configuration at --N 256):
+    natural-parameter continuation in mu over [0, 1.5] in --cont-steps steps from
+    psi = 1 (Sec. 4), Newton at every mu (J d = -GL(psi), FP32 V-cycle inside FP64
+    MINRES, corrections to 1e-8, while ||GL||_R > 1e-7; the preconditioner of each
+    Newton step takes over the previous one's symbolic part).  Every Newton system
+    has a hint: the correction of the same Newton step at the previous mu.  The warm
+    start is trained on the systems of the first half; on the second half every
+    system is solved from zero, from the hint's multiple alone and from hint +
+    network, with the same preconditioner; iterations and device time (inference
+    and fallback check included) are summed."""
+    import torch
+
+    import paper_1204_5125_gb300 as gl
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    N, steps = args.N, args.cont_steps
+    dim, _, _, bh = gi.WORKLOADS["cube128"]
+    n = N ** 3
+    mus = [1.5 * s / (steps - 1) for s in range(steps)]
+    mesh = gl.gl_mesh_create(dim, N, mus[0], bh)
+    psi = torch.ones(n, dtype=torch.complex128, device=dev)
+    o = gl.options(precision=gl.GL_MIXED_PRECOND, max_coarse=args.max_coarse, tol=1e-8)
+    t_start = time.perf_counter()
+    train, held, prev, like = dict(psi=[], b=[], hint=[]), [], [], None
+    newton_total = 0
+    try:
+        for s_, mu in enumerate(mus):
+            if s_ > 0:
+                gl.gl_mesh_set_mu(mesh, mu)
+            cur = []
+            for it in range(8):
+                r = torch.zeros_like(psi)
+                gl.gl_residual(mesh, psi, r)
+                if float(torch.sqrt(torch.sum(torch.abs(r) ** 2))) / (N - 1) ** 1.5 <= 1e-7:
+                    break
+                b = -r
+                P = gl.gl_precond_setup_like(mesh, psi, like, o) if like is not None else gl.gl_precond_setup(mesh, psi, o)
+                if like is not None:
+                    gl.gl_precond_destroy(like)
+                like = P
+                d = torch.zeros_like(psi)
+                st, inf = gl.gl_jacobian_solve(mesh, psi, P, b, d, o)
+                newton_total += 1
+                hint = prev[it] if it < len(prev) else None
+                if hint is not None:
+                    if s_ < steps // 2:
+                        train["psi"].append(psi.clone())
+                        train["b"].append(b.clone())
+                        train["hint"].append(hint)
+                    else:
+                        held.append((mu, psi.clone(), b.clone(), hint))
+                cur.append(d.clone())
+                psi = psi + d
+            prev = cur
+        gen_s = time.perf_counter() - t_start
+        ws = gl.gl_warmstart_create(gi.warmstart_init(12))
+        t0 = time.perf_counter()
+        losses = gl.gl_warmstart_train(ws, [mesh] * len(train["b"]), train["psi"], train["b"], steps=args.ws_steps,
+                                       batch=2, lr=2e-3, hints=train["hint"])
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        trained = gl.gl_warmstart_get_params(ws)
+        forms = {"zero guess": None, "hint alone": np.zeros(gl.GL_WS_NPARAM, np.float32), "hint + network": trained}
+        res = {k: {"iters": 0, "ms": 0.0, "used": 0, "max_true_relres": 0.0} for k in forms}
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for mu, p, b, hint in held:
+            gl.gl_mesh_set_mu(mesh, mu)
+            P = gl.gl_precond_setup_like(mesh, p, like, o)
+            try:
+                for k, params in forms.items():
+                    oo = gl.options(precision=gl.GL_MIXED_PRECOND, max_coarse=args.max_coarse, tol=1e-8)
+                    if params is not None:
+                        gl.gl_warmstart_set_params(ws, params)
+                        oo.warmstart = ws.value
+                        oo.warmstart_hint = hint.data_ptr()
+                    x = torch.zeros_like(b)
+                    ev0.record()
+                    st, inf = gl.gl_jacobian_solve(mesh, p, P, b, x, oo)
+                    ev1.record()
+                    torch.cuda.synchronize()
+                    res[k]["iters"] += inf.iters
+                    res[k]["ms"] += ev0.elapsed_time(ev1)
+                    res[k]["used"] += inf.warmstart_used
+                    res[k]["max_true_relres"] = max(res[k]["max_true_relres"], inf.true_relres)
+            finally:
+                gl.gl_precond_destroy(P)
+        gl.gl_warmstart_destroy(ws)
+    finally:
+        if like is not None:
+            gl.gl_precond_destroy(like)
+        gl.gl_mesh_destroy(mesh)
+    z = res["zero guess"]
+    line = {
+        "metric": "MINRES iterations and ms on held-out continuation Newton systems: zero guess vs learned warm start",
+        "workload": f"cube{N}^3 continuation mu in [0, 1.5], {steps} steps, bhat=(1,1,1)/sqrt3, Newton corrections "
+                    f"to 1e-8, GL_MIXED_PRECOND",
+        "newton_systems": newton_total, "training_systems": len(train["b"]), "held_out_systems": len(held),
+        "generation_s": gen_s, "train_steps": args.ws_steps, "train_s": train_s,
+        "train_loss_first": float(np.mean(losses[:10])), "train_loss_last": float(np.mean(losses[-10:])),
+        "forms": res,
+        "iterations_saved": {k: z["iters"] - v["iters"] for k, v in res.items()},
+        "ms_saved": {k: z["ms"] - v["ms"] for k, v in res.items()},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "cube-continuation":
+        run_continuation(args)
         return
     import torch
 

@@ -15,6 +15,8 @@
 //   * coarsest level: dense FP64 inverse by Gauss-Jordan elimination
 #include <atomic>
 
+#include <chrono>
+
 #include "gl_internal.cuh"
 
 namespace gl {
@@ -1004,6 +1006,15 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
     p->uid = next_uid.fetch_add(1);
     p->mesh = m;
     p->mesh_version = m->version;
+    // GL_VERBOSE: wall time of the setup's phases (synchronising at each mark)
+    auto t_last = std::chrono::steady_clock::now();
+    auto mark = [&](const char *what) {
+        if (!verbose()) return;
+        GL_CUDA(cudaStreamSynchronize(s));
+        const auto t = std::chrono::steady_clock::now();
+        fprintf(stderr, "gl: setup %-28s %8.2f ms\n", what, std::chrono::duration<double, std::milli>(t - t_last).count());
+        t_last = t;
+    };
     p->rinf = (o.cycles == CYCLES_INF);
     GL_REQUIRE(!p->rinf || o.precision == GL_FP64, GL_ERR_ARG, "R_inf (cycles = -1) needs precision GL_FP64");
     p->cycles = o.cycles > 0 ? o.cycles : 1;
@@ -1125,7 +1136,9 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
 
     // coarsest level: dense inverse, identity ordering
     Level &Lb = p->L[l];
+    mark("hierarchy (aggregation, P, RAP)");
     dense_inverse(Lb.A_can, Lb.Ainv, s);
+    mark("dense coarsest inverse");
 
     // solve-ordering structures
     for (int k = 0; k < p->nlev; ++k) {
@@ -1157,6 +1170,7 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
         GL_LAUNCH_CHECK();
         Lb.Ainv = std::move(M);
     }
+    mark("solve orderings");
     p->psi_p.alloc(n);
     permute_in(n, m->perm.get(), psi_nat, p->psi_p.get(), s);
     p->err.alloc(1);
@@ -1278,6 +1292,7 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
         p->tuned64 = true;
         p->tuned32 = T->has32;
     }
+    mark("solve-order operators, cost");
     if (p->tuned64) {
         for (int k = 0; k < p->nlev; ++k) {
             Level &L = p->L[k];
@@ -1291,7 +1306,9 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
         if (p->autotune) autotune_levels(p, false, s);
         plan_sweeps(p, false, s);
     }
+    mark("FP64 kernel choices");
     if (o.precision != GL_FP64) precond_ensure_fp32(p, s);
+    mark("FP32 copies and choices");
 }
 
 // FP32 copies of every level (the coarsest solve stays FP64)

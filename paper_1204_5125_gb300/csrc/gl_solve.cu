@@ -24,6 +24,7 @@ struct MinresDev {
     double gamma, gamma_old, eta, eta0, c, c_old, s, s_old;
     double delta, a1, a2, a3, c_new, eta_prev, gamma_cur;
     double bnorm, tol, est, true_rel;
+    double rho0;      // ||b - J x0||_D / ||b||_D: scales the recurrence's estimate to be relative to b
     int it, maxit, check_true, status, lucky, use_true, replays;
     double stall;     // > 0: stop with ST_STALL once the estimate is below stall * tol while the true
                       // residual is still above tol (0: never)
@@ -416,6 +417,9 @@ __global__ void k_scal_init(MinresDev *S, const double *part) {
     S->lucky = 0;
     S->bnorm = sqrt(bb);
     S->true_rel = (S->bnorm > 0) ? sqrt(vv) / S->bnorm : 0.0;
+    // the tolerance is relative to b, the recurrence's estimate to r0 = b - J x0:
+    // scaled by ||r0||_D / ||b||_D (exactly 1 from x0 = 0)
+    S->rho0 = S->true_rel;
     S->est = 1.0;
     if (!(S->bnorm > 0)) {
         S->status = ST_CONV;
@@ -498,7 +502,7 @@ __global__ void k_scal_givens(MinresDev *S, const double *part) {
     S->s_old = S->s;
     S->s = sn;
     S->it += 1;
-    S->est = fabs(S->eta) / S->eta0;
+    S->est = S->rho0 * fabs(S->eta) / S->eta0;
     S->lucky = (gn == 0);
     S->check_true = (S->est <= S->tol) || S->lucky;
 }

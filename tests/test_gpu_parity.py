@@ -330,3 +330,30 @@ def test_device_loop_matches_host_replays(precision):
     finally:
         gl.gl_precond_destroy(G)
         gl.gl_mesh_destroy(m)
+
+
+def test_warm_started_solve_matches_oracle(oracle_mod):
+    """From a nonzero initial guess the tolerance stays relative to b (Sec. 4): the
+    GPU and the oracle, started from the same guess with residual 1e-3 of b, take
+    the same number of iterations (+-1), fewer than from zero, and end at the
+    tolerance."""
+    om = oracle_mod.Mesh(2, 40, 1.0)
+    g = gl.gl_mesh_create(2, 40, 1.0)
+    try:
+        psi, b = gi.disk(om.n, 71), gi.complex_normal(om.n, 72)
+        xz, _ = om.solve(psi, b, max_coarse=64, tol=1e-12)
+        vol = om.volumes()
+        dn = lambda v: np.sqrt(np.sum(vol * np.abs(v) ** 2))  # noqa: E731
+        e = np.exp(1j * np.linspace(0, 3, om.n))
+        x0 = xz + (1e-3 * dn(b) / dn(om.jacobian(psi, e))) * e
+        xo, oinfo = om.solve(psi, b, x0=x0, max_coarse=64, tol=1e-10)
+        _, oinfo0 = om.solve(psi, b, max_coarse=64, tol=1e-10)
+        x = dev(x0)
+        st, info = gl.gl_jacobian_solve(g, dev(psi), None, dev(b), x, gl.options(max_coarse=64, tol=1e-10))
+        assert st == 0 and info.converged and oinfo.converged
+        assert abs(info.iters - oinfo.iters) <= 1, (info.iters, oinfo.iters)
+        assert info.iters <= oinfo0.iters - 3
+        r = b - om.jacobian(psi, host(x))
+        assert dn(r) / dn(b) <= 1.01e-10
+    finally:
+        gl.gl_mesh_destroy(g)
