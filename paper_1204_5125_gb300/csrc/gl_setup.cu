@@ -869,37 +869,48 @@ __global__ void k_symmetrize(int64_t n, const int64_t *rp, const int32_t *ci, do
 }
 
 // ------------------------------------------------------------------ coarsest level
+// the stored entries of a CSR matrix into a zeroed dense row-major one
 __global__ void k_to_dense(int64_t n, const int64_t *rp, const int32_t *ci, const double2 *v, double2 *M) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    for (int64_t j = 0; j < n; ++j) M[i * n + j] = make_double2(0, 0);
     for (int64_t q = rp[i]; q < rp[i + 1]; ++q) M[i * n + ci[q]] = v[q];
 }
-__global__ void k_gj_snap(int64_t n, int64_t k, const double2 *M, double2 *rowk, double2 *colk) {
+// the pivot row scaled by 1 / pivot and the pivot column, as they are before
+// step k (the pivot of an HPD matrix stays real positive; a non-positive one is
+// reported)
+__global__ void k_gj_snap(int64_t n, int64_t k, const double2 *M, double2 *rowk, double2 *colk, double *ipiv,
+                          int *err) {
+    const double piv = M[k * n + k].x;
+    const double ip = 1.0 / piv;
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t < n) {
-        rowk[t] = M[k * n + t];
+        const double2 r = M[k * n + t];
+        rowk[t] = make_double2(r.x * ip, r.y * ip);
         colk[t] = M[t * n + k];
     }
+    if (t == 0) {
+        *ipiv = ip;
+        if (!(piv > 0)) atomicExch(err, 1);
+    }
 }
-// one Gauss-Jordan step on pivot k (in place inversion, no pivoting: A is HPD)
-__global__ void k_gj_step(int64_t n, int64_t k, double2 *M, const double2 *rowk, const double2 *colk, int *err) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n * n) return;
-    int64_t i = t / n, j = t % n;
-    double2 piv = rowk[k];
-    if (!(piv.x > 0) && i == 0 && j == 0) atomicExch(err, 1);
-    double ip = 1.0 / piv.x;  // the pivot of an HPD matrix stays real positive
+// one Gauss-Jordan step on pivot k (in-place inversion, no pivoting: A is HPD):
+// row i = blockIdx.y, columns blockIdx.x * blockDim.x + threadIdx.x; one complex
+// product per entry off the pivot row and column
+__global__ void __launch_bounds__(256) k_gj_step(int64_t n, int64_t k, double2 *M, const double2 *__restrict__ rowk,
+                                                 const double2 *__restrict__ colk, const double *__restrict__ ipiv) {
+    const int64_t i = blockIdx.y;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int64_t t = i * n + j;
     double2 r;
-    if (i == k && j == k)
-        r = make_double2(ip, 0);
-    else if (i == k)
-        r = make_double2(rowk[j].x * ip, rowk[j].y * ip);
-    else if (j == k)
+    if (i == k) {
+        r = (j == k) ? make_double2(*ipiv, 0.0) : rowk[j];
+    } else if (j == k) {
+        const double ip = *ipiv;
         r = make_double2(-colk[i].x * ip, -colk[i].y * ip);
-    else {
-        double2 cr = cmul(colk[i], rowk[j]);
-        r = make_double2(M[t].x - cr.x * ip, M[t].y - cr.y * ip);
+    } else {
+        const double2 cr = cmul(colk[i], rowk[j]);
+        r = make_double2(M[t].x - cr.x, M[t].y - cr.y);
     }
     M[t] = r;
 }
@@ -909,12 +920,15 @@ static void dense_inverse(const CsrDev &A, DBuf<double2> &Ainv, cudaStream_t s) 
     GL_REQUIRE(n <= MAX_COARSE_DENSE, GL_ERR_CAPACITY, "coarsest level too large for the dense solve");
     Ainv.alloc(n * n);
     DBuf<double2> rowk(n), colk(n);
+    DBuf<double> ipiv(1);
     DBuf<int> err(1);
     GL_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    GL_CUDA(cudaMemsetAsync(Ainv.get(), 0, (size_t)n * n * sizeof(double2), s));
     k_to_dense<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp.get(), A.ci.get(), A.v.get(), Ainv.get());
+    const dim3 step_grid((unsigned)((n + 255) / 256), (unsigned)n);
     for (int64_t k = 0; k < n; ++k) {
-        k_gj_snap<<<grid_for(n, 256), 256, 0, s>>>(n, k, Ainv.get(), rowk.get(), colk.get());
-        k_gj_step<<<grid_for(n * n, 256), 256, 0, s>>>(n, k, Ainv.get(), rowk.get(), colk.get(), err.get());
+        k_gj_snap<<<grid_for(n, 256), 256, 0, s>>>(n, k, Ainv.get(), rowk.get(), colk.get(), ipiv.get(), err.get());
+        k_gj_step<<<step_grid, 256, 0, s>>>(n, k, Ainv.get(), rowk.get(), colk.get(), ipiv.get());
     }
     GL_LAUNCH_CHECK();
     int herr = 0;
