@@ -372,9 +372,10 @@ def run_continuation(args):
     Newton step takes over the previous one's symbolic part).  Every Newton system
     has a hint: the correction of the same Newton step at the previous mu.  The warm
     start is trained on the systems of the first half; on the second half every
-    system is solved from zero, from the hint's multiple alone and from hint +
-    network, with the same preconditioner; iterations and device time (inference
-    and fallback check included) are summed."""
+    system is solved from zero, from the hint's minimal-residual multiple alone
+    (no network: one FP64 Jacobian apply and three inner products) and from hint +
+    network, with the same preconditioner; iterations and device time (the guess,
+    inference and fallback check included) are summed."""
     import torch
 
     import paper_1204_5125_gb300 as gl
@@ -428,7 +429,7 @@ def run_continuation(args):
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
         trained = gl.gl_warmstart_get_params(ws)
-        forms = {"zero guess": None, "hint alone": np.zeros(gl.GL_WS_NPARAM, np.float32), "hint + network": trained}
+        forms = {"zero guess": None, "hint multiple": "hint", "hint + network": trained}
         res = {k: {"iters": 0, "ms": 0.0, "used": 0, "max_true_relres": 0.0} for k in forms}
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for mu, p, b, hint in held:
@@ -438,9 +439,10 @@ def run_continuation(args):
                 for k, params in forms.items():
                     oo = gl.options(precision=gl.GL_MIXED_PRECOND, max_coarse=args.max_coarse, tol=1e-8)
                     if params is not None:
+                        oo.warmstart_hint = hint.data_ptr()
+                    if params is not None and not isinstance(params, str):
                         gl.gl_warmstart_set_params(ws, params)
                         oo.warmstart = ws.value
-                        oo.warmstart_hint = hint.data_ptr()
                     x = torch.zeros_like(b)
                     ev0.record()
                     st, inf = gl.gl_jacobian_solve(mesh, p, P, b, x, oo)

@@ -130,11 +130,14 @@ typedef struct {
                             status word between replays (for profilers that cannot see inside
                             conditional graphs).  Solves that time a kernel class with gl_profile_begin,
                             and R_inf, always use 0 (default 1) */
-    const void *warmstart_hint; /* with warmstart: a device vector (n complex FP64, node order) the solution
-                            is expected to resemble, e.g. the same Newton step's correction at the
-                            previous mu of a continuation; the guess is then its minimal-residual
-                            multiple plus the network's correction (see gl_warmstart_predict)
-                            (default NULL) */
+    const void *warmstart_hint; /* a device vector (n complex FP64, node order) the solution is expected to
+                            resemble, e.g. the same Newton step's correction at the previous mu of a
+                            continuation.  With warmstart: the guess is the hint's minimal-residual
+                            multiple plus the network's correction (see gl_warmstart_predict).
+                            Without (warmstart NULL): gl_jacobian_solve ignores the x passed in and
+                            starts from the multiple alone, alpha a with alpha = <J a, b>_R /
+                            <J a, J a>_R (one FP64 Jacobian apply and three inner products; never a
+                            worse guess than zero); warmstart_used reports 1 (default NULL) */
 } gl_options;
 
 #define GL_COLOR_SL 0
@@ -376,7 +379,11 @@ GL_API gl_status gl_newton_step(gl_mesh mesh, void *psi_dev, const gl_options *o
  * a device-side WHILE conditional node until its own stopping test holds (same
  * test as gl_jacobian_solve); x_dev[s] holds the initial guess on entry.  With
  * precision GL_MIXED or GL_MIXED_PRECOND the V-cycles run in FP32 inside FP64
- * MINRES.  The graph is built on the first run and rebuilt when the b/x pointers
+ * MINRES, and instances on lattice meshes with the checked stencil (even N) apply
+ * J in double-FP32 arithmetic as gl_jacobian_solve does; an instance whose true
+ * residual that ~48-bit apply holds above tol continues after the graph from its
+ * x with the FP64 Jacobian (infos[s].stall_restarts = 1).  The graph is built on
+ * the first run and rebuilt when the b/x pointers
  * change.  infos (nullable): count entries.  Returns the first non-GL_OK status.
  * Synchronises `stream`. */
 GL_API gl_status gl_batch_create(int count, const gl_mesh *meshes, const void *const *psi_dev, const gl_options *opt,

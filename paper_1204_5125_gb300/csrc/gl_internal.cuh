@@ -60,10 +60,10 @@ constexpr int STATUS_TIMEOUT = 6;
 constexpr long long SWEEP_WAIT_NS = 1000000000ll;
 
 // Partition and dependency lists of the neighbour-flag sweep of one level in one
-// precision: CTA b owns, in every colour, the rows whose level node id lies in
-// [floor(b n / nb), floor((b + 1) n / nb)), so its rows in all colours sit in
-// one spatial block; before a phase it waits only for the CTAs owning columns
-// of its rows in that phase's colour.
+// precision: CTA b owns chunk b of nb equal contiguous chunks of every colour's
+// positions (ascending node ids within a colour, so chunk b of every colour lies
+// in about the same part of the level); before a phase it waits only for the
+// CTAs owning columns of its rows in that phase's colour.
 struct FlagPlan {
     int nb = 0;                  // CTAs of the launch (0: no plan)
     int G = 0;                   // lanes per row the plan was built for
@@ -264,6 +264,8 @@ void precond_apply_p64_via32(gl_prec_s *p, const double2 *v, double2 *z, const i
 // warmstart_used() reads that decision (after a sync)
 void warmstart_apply_p(gl_warmstart_s *w, gl_mesh_s *m, const double2 *psi_p, const double2 *b_p, double2 *x_p,
                        cudaStream_t s, const double2 *hint_nat = nullptr);
+void hint_guess_p(gl_mesh_s *m, const double2 *psi_p, const double2 *b_p, const double2 *hint_nat, double2 *x_p,
+                  cudaStream_t s);
 int warmstart_used(gl_warmstart_s *w, cudaStream_t s);
 
 // gl_solve.cu

@@ -1092,6 +1092,7 @@ struct BatchInst {
     gl_prec_s *p = nullptr;
     MinresWork<double> W;
     DBuf<double2> b, x;  // solve ordering
+    bool df = false;     // double-float Jacobian (FP32 V-cycle on a lattice mesh)
 };
 
 }  // namespace gl
@@ -1135,6 +1136,10 @@ void batch_create(gl_batch_s *B, int count, gl_mesh_s *const *meshes, const doub
         I->p = new gl_prec_s();
         precond_setup(I->p, I->m, psi[i], so, s);
         I->W.ensure(I->m->n);
+        // as in a single mixed solve: the double-float Jacobian wherever the mesh
+        // has the checked lattice stencil
+        I->df = B->vc32 && I->p->lattice && I->m->lat_ok;
+        if (I->df) I->W.ensure_df();
         I->b.alloc(I->m->n);
         I->x.alloc(I->m->n);
         B->inst.push_back(std::move(I));
@@ -1167,8 +1172,9 @@ static void batch_build(gl_batch_s *B, const double2 *const *b, double2 *const *
             GL_CUDA(cudaStreamWaitEvent(si, B->ev[0], 0));
             permute_in(n, I.m->perm.get(), b[i], I.b.get(), si);
             permute_in(n, I.m->perm.get(), x[i], I.x.get(), si);
-            k_set_params<<<1, 1, 0, si>>>(S, B->o.tol, B->o.maxit, 1, 0.0);
-            enqueue_init<double>(I.m, I.p, I.p->psi_p.get(), I.b.get(), I.x.get(), B->vc32, false, I.W, si);
+            // the double-float Jacobian's stall test, as in a single solve
+            k_set_params<<<1, 1, 0, si>>>(S, B->o.tol, B->o.maxit, 1, I.df ? 1e-3 : 0.0);
+            enqueue_init<double>(I.m, I.p, I.p->psi_p.get(), I.b.get(), I.x.get(), B->vc32, I.df, I.W, si);
             // the WHILE node: its handle lives in the graph being captured
             cudaStreamCaptureStatus cst;
             cudaGraph_t cg = nullptr;
@@ -1191,7 +1197,7 @@ static void batch_build(gl_batch_s *B, const double2 *const *b, double2 *const *
             cudaGraph_t body = cp.conditional.phGraph_out[0];
             GL_CUDA(cudaStreamUpdateCaptureDependencies(si, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
             GL_CUDA(cudaStreamBeginCaptureToGraph(B->sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-            enqueue_body<double>(I.m, I.p, I.p->psi_p.get(), I.b.get(), I.x.get(), B->vc32, false, I.W, B->sb);
+            enqueue_body<double>(I.m, I.p, I.p->psi_p.get(), I.b.get(), I.x.get(), B->vc32, I.df, I.W, B->sb);
             k_set_cond<<<1, 1, 0, B->sb>>>(h, S, max_replays);
             GL_LAUNCH_CHECK();
             GL_CUDA(cudaStreamEndCapture(B->sb, &body));
@@ -1235,16 +1241,36 @@ gl_status batch_run(gl_batch_s *B, const double2 *const *b, double2 *const *x, g
     double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     gl_status first = GL_OK;
     for (size_t i = 0; i < k; ++i) {
+        BatchInst &I = *B->inst[i];
         MinresDev h;
-        GL_CUDA(cudaMemcpy(&h, B->inst[i]->W.S.get(), sizeof(MinresDev), cudaMemcpyDeviceToHost));
+        GL_CUDA(cudaMemcpy(&h, I.W.S.get(), sizeof(MinresDev), cudaMemcpyDeviceToHost));
+        int restarts = 0, its = h.it;
+        if (h.status == ST_STALL) {
+            // the double-float Jacobian's ~48-bit apply held the true residual above
+            // tol: this instance continues from its x with the FP64 Jacobian, as a
+            // single solve does
+            const auto t1 = std::chrono::steady_clock::now();
+            MinresResult r = minres<double>(I.m, I.p, I.p->psi_p.get(), I.b.get(), I.x.get(), B->o.tol,
+                                            std::max(B->o.maxit - its, 1), true, B->vc32, I.W, s, false, true);
+            permute_out(I.m->n, I.m->perm.get(), I.x.get(), x[i], s);
+            GL_CUDA(cudaStreamSynchronize(s));
+            ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+            h.status = r.status;
+            h.true_rel = r.true_rel;
+            h.est = r.est;
+            its += r.iters;
+            restarts = 1;
+        }
         if (infos) {
             gl_solve_info inf{};
-            inf.iters = h.it;
+            inf.iters = its;
             inf.outer_iters = 1;
             inf.converged = (h.status == ST_CONV && h.true_rel <= B->o.tol);
             inf.true_relres = h.true_rel;
             inf.est_relres = h.est;
             inf.solve_ms = ms;
+            inf.df_jacobian = I.df ? 1 : 0;
+            inf.stall_restarts = restarts;
             infos[i] = inf;
         }
         gl_status st = (h.status == ST_CONV) ? (h.true_rel <= B->o.tol ? GL_OK : GL_ERR_NOT_CONVERGED)
@@ -1268,7 +1294,10 @@ gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, con
     gl_solve_info inf{};
     GL_REQUIRE(!(p && p->rinf) || o.precision == GL_FP64, GL_ERR_ARG, "R_inf needs precision GL_FP64");
     rinf_reset(p, s);
-    if (o.warmstart) warmstart_apply_p(o.warmstart, m, psi_p, b_p, x_p, s, (const double2 *)o.warmstart_hint);
+    if (o.warmstart)
+        warmstart_apply_p(o.warmstart, m, psi_p, b_p, x_p, s, (const double2 *)o.warmstart_hint);
+    else if (o.warmstart_hint)
+        hint_guess_p(m, psi_p, b_p, (const double2 *)o.warmstart_hint, x_p, s);
     bool mixed = (o.precision == GL_MIXED) && p;
     if (!mixed) {
         bool vc32 = (o.precision == GL_MIXED_PRECOND) && p;
@@ -1370,7 +1399,7 @@ gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, con
         inf.converged = 0;
     }
     inf.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
-    inf.warmstart_used = o.warmstart ? warmstart_used(o.warmstart, s) : 0;
+    inf.warmstart_used = o.warmstart ? warmstart_used(o.warmstart, s) : (o.warmstart_hint ? 1 : 0);
     inf.lattice_stencil = (p && p->has32 && o.precision != GL_FP64 && p->lattice && m->lat_ok) ? 1 : 0;
     if (p && p->rinf) {
         // measured: every application ran its own number of cycles, each followed by a residual

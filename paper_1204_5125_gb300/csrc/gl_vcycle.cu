@@ -113,6 +113,101 @@ __global__ void __launch_bounds__(256) k_gs_lat(int64_t lo, int64_t hi, LatticeV
         }
     }
 }
+// k_gs_lat with two consecutive positions of a colour per thread: for N % 4 == 0
+// positions 2t and 2t + 1 of a colour are the nodes v and v + 2 of one x-line,
+// so b, diag, |V| and the written x move as 16- and 8-byte vectors, and the
+// neighbours of the pair along y and z (and two of the three along x) are
+// adjacent positions of the other colour, read as one 16-byte vector each.
+// Per row the edges are summed in the order of lattice_row_f.  (Node v of
+// colour c sits at position v >> 1; with p even, v = 2p + a, a = 1 when the
+// parity of the line start differs from c.)
+__global__ void __launch_bounds__(256) k_gs_lat2(int64_t lo, int64_t hi, LatticeView L,
+                                                     const float *__restrict__ diag, const float2 *__restrict__ b,
+                                                     float2 *__restrict__ x, int first, const int *__restrict__ stop) {
+    if (stop && *stop) return;
+    const int64_t p = lo + 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (p >= hi) return;
+    const bool none = first && lo == 0;
+    const uint32_t c = p >= L.nred ? 1u : 0u;
+    const int64_t base = c ? L.nred : 0;
+    const int64_t other = c ? 0 : L.nred;
+    const uint32_t N = (uint32_t)L.N;
+    const uint32_t r = (uint32_t)(p - base);  // even
+    const uint32_t v0 = 2u * r;
+    const uint32_t i0 = v0 % N, row = v0 / N, j = row % N, k = row / N;
+    const uint32_t a = ((i0 + j + k) & 1u) != c ? 1u : 0u;
+    const uint32_t i = i0 + a;
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+    if (!none) {
+        const float2 *xo = x + other;
+        auto e = [](float2 &acc, float2 t, float2 xv, bool plus) {
+            const float ty = plus ? t.y : -t.y;
+            acc.x += t.x * xv.x - ty * xv.y;
+            acc.y += t.x * xv.y + ty * xv.x;
+        };
+        // x-direction: positions r - 1 + a .. r + 1 + a of the other colour
+        const float4 xm = *reinterpret_cast<const float4 *>(xo + r);  // r, r + 1
+        const float2 xlo = make_float2(xm.x, xm.y), xhi = make_float2(xm.z, xm.w);
+        float2 xe = make_float2(0.f, 0.f);
+        if (a == 0u) {
+            if (i > 0) xe = xo[r - 1];
+        } else {
+            if (i + 3 < N) xe = xo[r + 2];
+        }
+        // node 1 (v0 + a): x+ -> (v + 1) >> 1, x- -> (v - 1) >> 1
+        // a = 0: x+ = r, x- = r - 1; a = 1: x+ = r + 1, x- = r
+        // node 2 (v + 2): a = 0: x+ = r + 1, x- = r; a = 1: x+ = r + 2, x- = r + 1
+        const float2 t = __ldg(L.tx + (j + N * k));
+        if (a == 0u) {
+            e(acc0, t, xlo, true);
+            if (i > 0) e(acc0, t, xe, false);
+            if (i + 3 < N) e(acc1, t, xhi, true);
+            e(acc1, t, xlo, false);
+        } else {
+            e(acc0, t, xhi, true);
+            e(acc0, t, xlo, false);
+            if (i + 3 < N) e(acc1, t, xe, true);
+            e(acc1, t, xhi, false);
+        }
+        const uint32_t hN = N / 2;
+        {
+            const float2 t0 = __ldg(L.ty + (i + N * k)), t1 = __ldg(L.ty + (i + 2 + N * k));
+            if (j + 1 < N) {
+                const float4 q = *reinterpret_cast<const float4 *>(xo + r + hN);
+                e(acc0, t0, make_float2(q.x, q.y), true);
+                e(acc1, t1, make_float2(q.z, q.w), true);
+            }
+            if (j > 0) {
+                const float4 q = *reinterpret_cast<const float4 *>(xo + r - hN);
+                e(acc0, t0, make_float2(q.x, q.y), false);
+                e(acc1, t1, make_float2(q.z, q.w), false);
+            }
+        }
+        if (L.dim == 3) {
+            const uint32_t hP = N * N / 2;
+            const float2 t0 = __ldg(L.tz + (i + N * j)), t1 = __ldg(L.tz + (i + 2 + N * j));
+            if (k + 1 < N) {
+                const float4 q = *reinterpret_cast<const float4 *>(xo + r + hP);
+                e(acc0, t0, make_float2(q.x, q.y), true);
+                e(acc1, t1, make_float2(q.z, q.w), true);
+            }
+            if (k > 0) {
+                const float4 q = *reinterpret_cast<const float4 *>(xo + (int64_t)r - hP);
+                e(acc0, t0, make_float2(q.x, q.y), false);
+                e(acc1, t1, make_float2(q.z, q.w), false);
+            }
+        }
+        const float2 vv = *reinterpret_cast<const float2 *>(L.vol + p);
+        const float iv0 = 1.f / vv.x, iv1 = 1.f / vv.y;
+        acc0 = make_float2(acc0.x * iv0, acc0.y * iv0);
+        acc1 = make_float2(acc1.x * iv1, acc1.y * iv1);
+    }
+    const float4 bb = *reinterpret_cast<const float4 *>(b + p);
+    const float2 dd = *reinterpret_cast<const float2 *>(diag + p);
+    const float d0 = 1.f / dd.x, d1 = 1.f / dd.y;
+    *reinterpret_cast<float4 *>(x + p) =
+        make_float4((bb.x - acc0.x) * d0, (bb.y - acc0.y) * d0, (bb.z - acc1.x) * d1, (bb.w - acc1.y) * d1);
+}
 // the first two half-sweeps from x = 0 in one launch: red rows x = b / diag,
 // black rows relaxed against their red neighbours' b / diag (the values those
 // rows get in the same launch)
@@ -435,7 +530,7 @@ __global__ void __launch_bounds__(coop_threads<R>()) k_sgs_coop(CsrGView<C> A, c
 }
 
 // The same symmetric step with neighbour flags instead of the grid barrier.
-// CTA b owns a spatial block of the level's nodes (FlagPlan) and after each
+// CTA b owns a chunk of every colour's rows (FlagPlan) and after each
 // phase publishes, with a release store, the number of phases it has
 // completed; before phase ph (colour c) it waits, with acquiring loads by one
 // warp, only until every CTA owning a column of its colour-c rows has
@@ -443,7 +538,7 @@ __global__ void __launch_bounds__(coop_threads<R>()) k_sgs_coop(CsrGView<C> A, c
 // phase <= ph - 1, and its reads of b's colour-c rows since their previous
 // relaxation also lie in phases <= ph - 1, so every row reads exactly the
 // values the grid-barrier sweep gives it: the two forms are bit-identical for
-// the same G.  Blocks far apart may then run several phases apart.  Counters
+// the same G.  CTAs far apart may then run several phases apart.  Counters
 // only grow: a launch adds 2 nc - 1 to each, so all CTAs of a launch start from
 // the same value (a CTA reads its own at the start); a CTA without rows in a
 // colour only counts the phase.
@@ -518,38 +613,45 @@ __global__ void __launch_bounds__(coop_threads<R>()) k_sgs_flags(CsrGView<C> A, 
 }
 
 // ---- partition of the neighbour-flag sweep
-// owner CTA of level node v when CTA b owns node ids [floor(b n / nb), floor((b + 1) n / nb))
-__device__ __forceinline__ int flag_owner(int64_t v, int64_t n, int nb) {
-    int64_t o = v * nb / n;
-    while (o + 1 < nb && (o + 1) * n / nb <= v) ++o;
-    while (o > 0 && o * n / nb > v) --o;
+// Each colour's positions are split into nb equal contiguous chunks: CTA b owns
+// positions [cstart[c] + floor(b m_c / nb), cstart[c] + floor((b + 1) m_c / nb))
+// of colour c (m_c its size).  The positions of a colour hold ascending node
+// ids, so chunk b of every colour covers about the same part of the level
+// (node ids follow space), and no CTA has more than ceil(m_c / nb) rows of a
+// colour, which keeps every phase to one round of rows where a partition by
+// node id would give some CTAs a second one.
+__device__ __forceinline__ int64_t chunk_start(int64_t m, int nb, int b) { return m * b / nb; }
+// owner CTA of solve position q
+__device__ __forceinline__ int flag_owner(int64_t q, const int64_t *__restrict__ cstart, int ncolors, int nb) {
+    int lo = 0, hi = ncolors - 1;  // colour c with cstart[c] <= q < cstart[c + 1]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (cstart[mid] <= q)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const int64_t m = cstart[lo + 1] - cstart[lo], r = q - cstart[lo];
+    int64_t o = m > 0 ? r * nb / m : 0;
+    while (o + 1 < nb && chunk_start(m, nb, (int)o + 1) <= r) ++o;
+    while (o > 0 && chunk_start(m, nb, (int)o) > r) --o;
     return (int)o;
 }
-// rstart[c (nb + 1) + b] = first solve position of colour c whose node id is
-// >= floor(b n / nb) (positions of a colour hold ascending node ids)
-__global__ void k_flag_rstart(int64_t n, int nb, int ncolors, const int64_t *__restrict__ cstart,
-                              const int32_t *__restrict__ perm, int64_t *__restrict__ rstart) {
+// rstart[c (nb + 1) + b] = first position of CTA b's chunk of colour c
+__global__ void k_flag_rstart(int nb, int ncolors, const int64_t *__restrict__ cstart,
+                              int64_t *__restrict__ rstart) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= (int64_t)ncolors * (nb + 1)) return;
     const int c = (int)(i / (nb + 1));
     const int bb = (int)(i % (nb + 1));
-    const int64_t key = (int64_t)bb * n / nb;
-    int64_t lo = cstart[c], hi = cstart[c + 1];
-    while (lo < hi) {
-        const int64_t mid = lo + (hi - lo) / 2;
-        if (perm[mid] < key)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    rstart[i] = lo;
+    rstart[i] = cstart[c] + chunk_start(cstart[c + 1] - cstart[c], nb, bb);
 }
 // the CTAs owning a column of CTA b's colour-c rows (b itself left out); the
 // list length is stored even when it exceeds FLAG_MAXN (the host then drops
 // the plan)
 template <typename C>
-__global__ void __launch_bounds__(256) k_flag_nbrs(CsrGView<C> A, int64_t n, int nb, int ncolors,
-                                                   const int32_t *__restrict__ perm,
+__global__ void __launch_bounds__(256) k_flag_nbrs(CsrGView<C> A, int nb, int ncolors,
+                                                   const int64_t *__restrict__ cstart,
                                                    const int64_t *__restrict__ rstart, int32_t *__restrict__ nbr,
                                                    int32_t *__restrict__ nbrc) {
     __shared__ unsigned bits[MAX_FLAG_CTAS / 32];
@@ -559,7 +661,7 @@ __global__ void __launch_bounds__(256) k_flag_nbrs(CsrGView<C> A, int64_t n, int
     const int64_t lo = rstart[(int64_t)c * (nb + 1) + bb], hi = rstart[(int64_t)c * (nb + 1) + bb + 1];
     for (int64_t row = lo + threadIdx.x; row < hi; row += blockDim.x)
         for (int64_t q = A.rp[row]; q < A.rp[row + 1]; ++q) {
-            const int o = flag_owner(perm[A.col[q]], n, nb);
+            const int o = flag_owner(A.col[q], cstart, ncolors, nb);
             if (o != bb) atomicOr(&bits[o >> 5], 1u << (o & 31));
         }
     __syncthreads();
@@ -647,10 +749,9 @@ static int build_flag_plan(const Level &L, const CsrG<C> &A, int G, int nb, Flag
     F.rstart.alloc((size_t)nc * (nb + 1));
     F.nbr.alloc((size_t)nb * nc * FLAG_MAXN);
     F.nbrc.alloc((size_t)nb * nc);
-    k_flag_rstart<<<grid_for((int64_t)nc * (nb + 1), 256), 256, 0, s>>>(L.n, nb, nc, L.cstart_dev.get(), L.perm,
-                                                                         F.rstart.get());
+    k_flag_rstart<<<grid_for((int64_t)nc * (nb + 1), 256), 256, 0, s>>>(nb, nc, L.cstart_dev.get(), F.rstart.get());
     GL_LAUNCH_CHECK();
-    k_flag_nbrs<C><<<dim3(nb, nc), 256, 0, s>>>(A.view(), L.n, nb, nc, L.perm, F.rstart.get(), F.nbr.get(),
+    k_flag_nbrs<C><<<dim3(nb, nc), 256, 0, s>>>(A.view(), nb, nc, L.cstart_dev.get(), F.rstart.get(), F.nbr.get(),
                                                 F.nbrc.get());
     GL_LAUNCH_CHECK();
     std::vector<int32_t> cnt((size_t)nb * nc);
@@ -1079,8 +1180,12 @@ static void gs_sweep(Level &L, int level, const typename LevelOps<T>::C *b, type
             if (!(first && lo == 0))
                 bytes += (double)(L.n - (hi - lo)) * sizeof(C) + (double)lat->N * lat->N * lat->dim * 8.0;
             ProfScope ps("gs0", bytes, s);
-            k_gs_lat<<<grid_for(hi - lo, 256 * LAT_RPT), 256, 0, s>>>(lo, hi, *lat, O::diag(L), b, x, first ? 1 : 0,
-                                                                     stop);
+            if (lat->N % 4 == 0)  // colour ranges of even length, pairs within one x-line
+                k_gs_lat2<<<grid_for((hi - lo) / 2, 256), 256, 0, s>>>(lo, hi, *lat, O::diag(L), b, x, first ? 1 : 0,
+                                                                       stop);
+            else
+                k_gs_lat<<<grid_for(hi - lo, 256 * LAT_RPT), 256, 0, s>>>(lo, hi, *lat, O::diag(L), b, x,
+                                                                         first ? 1 : 0, stop);
             return;
         }
     }

@@ -318,6 +318,14 @@ __global__ void k_hint_resid(int64_t n, const double *__restrict__ hs, const dou
     const double al = hs[0];
     r[i] = make_double2(b[i].x - al * q[i].x, b[i].y - al * q[i].y);
 }
+// x0 = alpha a
+__global__ void k_hint_set(int64_t n, const double *__restrict__ hs, const double2 *__restrict__ a,
+                           double2 *__restrict__ x0) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double al = hs[0];
+    x0[i] = make_double2(al * a[i].x, al * a[i].y);
+}
 // x0 += alpha a
 __global__ void k_hint_add(int64_t n, const double *__restrict__ hs, const double2 *__restrict__ a,
                            double2 *__restrict__ x0) {
@@ -1193,6 +1201,33 @@ void warmstart_apply_p(gl_warmstart_s *w, gl_mesh_s *m, const double2 *psi_p, co
                                                        x_p, w->fpart.get());
     k_fallback_decide<<<1, 1024, 0, s>>>(w->fpart.get(), RED_BLOCKS, w->used.get());
     k_fallback_apply<<<grid_for(m->n, 256, 4 * NUM_SMS_HINT), 256, 0, s>>>(m->n, w->used.get(), x_p);
+    GL_LAUNCH_CHECK();
+}
+
+// the hint's minimal-residual multiple alone (no network): x_p = alpha a with
+// alpha = <J a, b>_R / <J a, J a>_R, which is never a worse guess than zero
+void hint_guess_p(gl_mesh_s *m, const double2 *psi_p, const double2 *b_p, const double2 *hint_nat, double2 *x_p,
+                  cudaStream_t s) {
+    struct HintWork {
+        DBuf<double2> a, q;
+        DBuf<double> part, hs;
+    };
+    static thread_local HintWork H;
+    const int64_t n = m->n;
+    if (H.a.n != (size_t)n) {
+        H.a.alloc(n);
+        H.q.alloc(n);
+    }
+    if (!H.part.get()) {
+        H.part.alloc(3 * RED_BLOCKS);
+        H.hs.alloc(2);
+    }
+    permute_in(n, m->perm.get(), hint_nat, H.a.get(), s);
+    jacobian_apply_p(m, psi_p, H.a.get(), H.q.get(), s);
+    note_launch(3);
+    k_hint_part<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, m->volp.get(), H.q.get(), b_p, H.a.get(), H.part.get());
+    k_hint_final<<<1, 1024, 0, s>>>(H.part.get(), H.hs.get());
+    k_hint_set<<<grid_for(n, 256), 256, 0, s>>>(n, H.hs.get(), H.a.get(), x_p);
     GL_LAUNCH_CHECK();
 }
 

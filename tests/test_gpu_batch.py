@@ -58,11 +58,12 @@ def test_batch_matches_single_solves(oracle_mod, precision):
             x1 = torch.zeros_like(bs[k])
             st1, info1 = gl.gl_jacobian_solve(meshes[k], psis[k], None, bs[k], x1, opts)
             # iteration counts: within one in FP64; with the FP32 V-cycle the count
-            # depends on FP32 rounding (the batch keeps the FP64 Jacobian where a
-            # single solve on an even-N lattice takes the double-FP32 one, and the
-            # setup timing may pick other lanes per row), so a few more may differ
+            # depends on FP32 rounding (the setup timing may pick other lanes per
+            # row for the batch's preconditioner), so a few more may differ
             slack = 1 if precision == gl.GL_FP64 else 3
             assert st1 == 0 and abs(info1.iters - infos[k].iters) <= slack, (N, info1.iters, infos[k].iters)
+            # the batch applies J as the single solve does (double-FP32 on even-N lattices)
+            assert infos[k].df_jacobian == info1.df_jacobian == (precision != gl.GL_FP64 and N % 2 == 0)
             assert torch.linalg.norm(x1 - xs[k]) <= 1e-8 * torch.linalg.norm(x1)
     finally:
         for m in meshes:

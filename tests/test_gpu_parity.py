@@ -357,3 +357,39 @@ def test_warm_started_solve_matches_oracle(oracle_mod):
         assert dn(r) / dn(b) <= 1.01e-10
     finally:
         gl.gl_mesh_destroy(g)
+
+
+def test_hint_alone_guess_matches_oracle(oracle_mod):
+    """A hint without a network: the solve starts from the hint's multiple with the
+    smallest residual, alpha a with alpha = <J a, b>_R / <J a, J a>_R (real, since
+    J is R-linear and the inner product is the real one of Sec. 3).  The GPU's
+    solve and the oracle's solve from that guess take the same number of
+    iterations (+-1), fewer than from zero, and end at the tolerance; the x
+    passed in is ignored."""
+    om = oracle_mod.Mesh(2, 40, 1.0)
+    g = gl.gl_mesh_create(2, 40, 1.0)
+    try:
+        psi, b = gi.disk(om.n, 81), gi.complex_normal(om.n, 82)
+        xz, _ = om.solve(psi, b, max_coarse=64, tol=1e-12)
+        vol = om.volumes()
+        inner = lambda u, v: float(np.sum(vol * (u.conj() * v).real))  # noqa: E731
+        # a hint off by a factor 0.7 and a modulation of relative size 1e-5 (the
+        # multiple's residual is then about 1e-3 of b: J amplifies the modulation)
+        a = 0.7 * xz * (1 + 1e-5 * np.exp(1j * np.linspace(0, 5, om.n)))
+        q = om.jacobian(psi, a)
+        x0 = (inner(q, b) / inner(q, q)) * a
+        dn = lambda v: np.sqrt(np.sum(vol * np.abs(v) ** 2))  # noqa: E731
+        assert dn(b - om.jacobian(psi, x0)) <= 3e-3 * dn(b)
+        xo, oinfo = om.solve(psi, b, x0=x0, max_coarse=64, tol=1e-10)
+        _, oinfo0 = om.solve(psi, b, max_coarse=64, tol=1e-10)
+        x = dev(gi.complex_normal(om.n, 83))  # ignored
+        hint = dev(a)
+        o = gl.options(max_coarse=64, tol=1e-10)
+        o.warmstart_hint = hint.data_ptr()
+        st, info = gl.gl_jacobian_solve(g, dev(psi), None, dev(b), x, o)
+        assert st == 0 and info.converged and oinfo.converged and info.warmstart_used == 1
+        assert abs(info.iters - oinfo.iters) <= 1, (info.iters, oinfo.iters)
+        assert info.iters <= oinfo0.iters - 3, (info.iters, oinfo0.iters)
+        assert dn(b - om.jacobian(psi, host(x))) / dn(b) <= 1.01e-10
+    finally:
+        gl.gl_mesh_destroy(g)

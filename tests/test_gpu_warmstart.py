@@ -209,7 +209,8 @@ def test_continuation_gain(oracle_mod):
     previous mu.  The network is trained on the systems of the first half of the
     continuation and used on the second half; every warm-started solve is
     compared with the zero-guess solve of the same system and with the guess the
-    hint alone gives (its minimal-residual multiple, a zero network).  Reported:
+    hint alone gives (its minimal-residual multiple; the solve then runs no
+    network, and the multiple equals the zero network's guess).  Reported:
     the guesses' relative residuals and the iterations and time they save."""
     N, steps = 64, 24
     mus = [2.0 * (s + 1) / steps for s in range(steps)]
@@ -268,7 +269,8 @@ def test_continuation_gain(oracle_mod):
                     pn, bn = p.cpu().numpy(), b.cpu().numpy()
                     res.append(true_relres(om, pn, bn, x0.cpu().numpy()))
                     wopts = gl.options(max_coarse=64)
-                    wopts.warmstart = ws.value
+                    if label != "hint alone":
+                        wopts.warmstart = ws.value
                     wopts.warmstart_hint = hint.data_ptr()
                     x = torch.zeros_like(b)
                     st, inf = gl.gl_jacobian_solve(m, p, None, b, x, wopts)
