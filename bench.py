@@ -95,7 +95,10 @@ def peaks():
 
 
 class Clocks:
-    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+    """Samples SM clocks and throttle reasons with nvidia-smi every 50 ms.  The
+    sampler is started, and its first sample awaited, before the region; the
+    summary keeps the samples that arrived inside the region (all of them if none
+    did)."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -105,21 +108,32 @@ class Clocks:
         self.idx = gpu_index
         self.rows = []
         self.proc = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            deadline = time.perf_counter() + 5.0
+            while not self.rows and time.perf_counter() < deadline and self.proc.poll() is None:
+                time.sleep(0.01)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.perf_counter(), [x.strip() for x in line.split(",")]))
+
+    def start(self):
+        self.t0 = time.perf_counter()
+
+    def stop(self):
+        self.t1 = time.perf_counter()
+        time.sleep(0.06)  # the sample taken at the end of the region
 
     def __exit__(self, *exc):
         if self.proc:
@@ -132,16 +146,20 @@ class Clocks:
     def summary(self):
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        inside = [r for t, r in self.rows
+                  if self.t0 is not None and self.t1 is not None and self.t0 <= t <= self.t1 + 0.06]
+        rows = inside or [r for _, r in self.rows]
+        sm = [float(r[1]) for r in rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
-        for r in self.rows:
+        for r in rows:
             for k, name in enumerate(names):
                 if len(r) > 5 + k and "Active" in r[5 + k] and "Not" not in r[5 + k]:
                     reasons.add(name)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.rows)}
+                "reasons": sorted(reasons), "samples": len(rows), "samples_in_region": len(inside),
+                "interval_ms": 50}
 
 
 def recorded_traffic(cls):
@@ -527,9 +545,10 @@ def main():
             raise RuntimeError(f"solve failed: status {st} {info.as_dict()}")
         return info
 
-    def timed(opts, steps, warm, profile_class=None, count=False):
+    def timed(opts, steps, warm, profile_class=None, count=False, clocks=None):
         """Times `steps` solves after `warm` untimed ones.  profile_class: time every
-        launch of that kernel class with CUDA events; count: only count launches."""
+        launch of that kernel class with CUDA events; count: only count launches;
+        clocks: the sampler whose window is the timed region."""
         profiling = bool(profile_class) or count
         if profiling:
             # before the warm-up, so graphs it makes the solver re-capture are captured there
@@ -543,10 +562,14 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if clocks:
+            clocks.start()
         ev0.record(stream)
         infos = [solve(opts) for _ in range(steps)]
         ev1.record(stream)
         torch.cuda.synchronize()
+        if clocks:
+            clocks.stop()
         prof = gl.gl_profile_end() if profiling else None
         ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
         return ms, infos, prof
@@ -610,7 +633,7 @@ def main():
     # headline: the chosen form, with the dominant kernel timed live by CUDA events
     # launches are counted during the timed solves; nothing is timed per kernel
     with Clocks(dev.index if world == 1 else local) as clk:
-        ms, infos, count = timed(opts_final, args.steps, args.warmup, count=True)
+        ms, infos, count = timed(opts_final, args.steps, args.warmup, count=True, clocks=clk)
     x_mixed = x.clone()
     err_mixed_vs_fp64 = float(torch.linalg.norm(x_mixed - x64) / torch.linalg.norm(x64))
 
@@ -654,15 +677,19 @@ def main():
         "setup_like": {"setup_s": like_s, "solves_per_s": 1.0 / (like_s + ms / 1e3 / args.steps)},
     }
 
-    # measured arithmetic peaks of this GPU (own FMA kernel, CUDA events)
+    # measured arithmetic peaks of this GPU (own FMA kernel, CUDA events) and the
+    # latencies that bound a phase of the coarse sweeps (own probe kernels)
     fp64_gflops = gl.gl_measure_fma_peak(gl.GL_FP64)
     fp32_gflops = gl.gl_measure_fma_peak(gl.GL_MIXED)
+    sync_lat = gl.gl_measure_sync_latency()
 
     # live per-class timing (CUDA events around every launch of the class, on the
     # launching stream): the finest-level sweep from the headline run, then the
     # coarse-level sweeps and the Jacobian in two short runs of the same form
     KERNELS = {
-        "gs0": ("k_gs_lat (Gauss-Seidel colour sweep, finest level, FP32, tabulated lattice stencil)"
+        "gs0": (("k_gs_lat2 (Gauss-Seidel colour sweep, finest level, FP32, tabulated lattice stencil, two "
+                 "positions per thread)" if N % 4 == 0 else
+                 "k_gs_lat (Gauss-Seidel colour sweep, finest level, FP32, tabulated lattice stencil)")
                 if infos[-1].lattice_stencil else "k_gs (Gauss-Seidel colour sweep, finest level, FP32)"),
         "gs": "k_sgs_flags / k_sgs_coop / k_sgs_cluster (symmetric Gauss-Seidel step, coarse levels, FP32)",
         "jz": ("k_jz_latdf (double-FP32 Jacobian apply fused with the Lanczos dot; SM-pipe bound)"
@@ -685,6 +712,20 @@ def main():
             "launches_timed": pr["timed"], "avg_launch_us": 1e3 * pr["ms"] / pr["timed"],
             "ms_per_solve": pr["ms"] / nsolves, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
         }
+    # the coarse sweep is a chain of dependent phases: each waits for a hand-off
+    # from the CTAs it reads (release store -> acquiring poll), gathers the
+    # neighbours' x from L2, and publishes its own writes behind a GPU-scope fence;
+    # its floor per phase is the sum of those three measured latencies
+    sweep_levels = [lv for lv in levels[1:-1]]
+    if "gs" in rooflines and sweep_levels:
+        phases = sum(2 * lv["ncolors"] - 1 for lv in sweep_levels)  # per pre- or post-smoothing
+        us_phase = rooflines["gs"]["avg_launch_us"] * len(sweep_levels) / phases
+        floor_us = (sync_lat["handoff_ns"] + sync_lat["l2_load_ns"] + sync_lat["fence_ns"]) / 1e3
+        rooflines["gs"]["latency"] = {
+            "bound": "latency", "phases_per_launch": phases / len(sweep_levels), "us_per_phase": us_phase,
+            "floor_us_per_phase": floor_us, "frac": floor_us / us_phase, **sync_lat,
+            "how": "floor = median one-way CTA hand-off + dependent L2 load + store and GPU-scope fence, "
+                   "measured by gl_measure_sync_latency"}
     # the double-FP32 Jacobian is bounded by the FP32 pipe: its min(HBM, ALU) roofline
     if "jz" in rooflines and profs["jz"][0]["flops"] > 0 and infos[-1].df_jacobian:
         rooflines["jz"]["alu"] = alu_roofline(profs["jz"][0], 2, peak, fp32_gflops,
@@ -735,7 +776,7 @@ def main():
             "err_mixed_vs_fp64_oracle": err_vs_oracle,
             "setup_s": {"mesh": t1 - t0, "precond": t2 - t1}, "setup_inclusive": setup_inclusive,
             "peaks": {"hbm_gbs": peak, "hbm_kind": peak_kind, "fp64_gflops_measured": fp64_gflops,
-                      "fp32_gflops_measured": fp32_gflops},
+                      "fp32_gflops_measured": fp32_gflops, "sync_latency_ns": sync_lat},
             "roofline": roofline, "rooflines": rooflines, "rooflines_fp64": rooflines_fp64,
             "workloads": extra, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": count["launches"] if count else None, "clocks": clk.summary(),

@@ -403,6 +403,15 @@ GL_API gl_status gl_batch_solve(int count, const gl_mesh *meshes, const void *co
  * `stream`. */
 GL_API gl_status gl_measure_fma_peak(int precision, double *gflops_host, void *stream);
 
+/* Measured latencies that bound one phase of the coarse-level Gauss-Seidel
+ * sweeps (not a paper quantity), in ns, into ns4_host[4]: [0] the median and
+ * [1] the largest one-way hand-off between CTA 0 and every other SM's CTA (a
+ * release store seen by an acquiring poll, 200 round trips per pair); [2] one
+ * dependent L2 load (__ldcg along a 1 MiB chain); [3] a store followed by a
+ * GPU-scope fence.  Every wait is bounded (1 s; GL_ERR_TIMEOUT).  Synchronises
+ * `stream`. */
+GL_API gl_status gl_measure_sync_latency(double *ns4_host, void *stream);
+
 /* Measurement instrumentation (no counterpart in the paper).
  * gl_profile_begin resets the count of hot-path kernel launches and, when
  * kernel_class is not NULL, records a pair of CUDA events on the launching

@@ -31,6 +31,7 @@ __all__ = [
     "gl_mesh_set_mu", "gl_residual_dmu", "gl_energy", "cont_options", "gl_continuation", "gl_precond_setup_like",
     "GL_COLOR_SL", "GL_COLOR_JP", "GL_COLOR_PSL", "gl_mesh_create_dipole", "gl_precond_apply_precision", "gl_precond_debug",
     "GL_DEBUG_STALL_SWEEPS", "GL_DEBUG_NEGATE_COARSEST", "gl_precond_level_sweep", "gl_measure_fma_peak",
+    "gl_measure_sync_latency",
     "gl_profile_flops",
 ]
 
@@ -53,6 +54,7 @@ EXPORTED = [
     "gl_warmstart_adam_step", "gl_last_error", "gl_mesh_create_edge", "gl_mesh_set_mu", "gl_residual_dmu",
     "gl_energy", "gl_cont_options_default", "gl_continuation", "gl_precond_setup_like", "gl_mesh_create_dipole",
     "gl_precond_apply_precision", "gl_precond_debug", "gl_precond_level_sweep", "gl_measure_fma_peak",
+    "gl_measure_sync_latency",
     "gl_profile_flops",
 ]
 
@@ -137,6 +139,7 @@ def library(build_if_missing: bool = True):
             "gl_precond_apply_precision": [vp, vp, vp, C.c_int, vp],
             "gl_precond_debug": [vp, C.c_int],
             "gl_measure_fma_peak": [C.c_int, C.POINTER(C.c_double), vp],
+            "gl_measure_sync_latency": [C.POINTER(C.c_double), vp],
             "gl_profile_flops": [C.POINTER(C.c_double)],
             "gl_precond_level_sweep": [vp, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                        C.POINTER(C.c_int)],
@@ -389,6 +392,13 @@ def gl_measure_fma_peak(precision=GL_FP64, stream=None) -> float:
     g = C.c_double()
     _check(library().gl_measure_fma_peak(precision, C.byref(g), _stream(stream)))
     return g.value
+
+
+def gl_measure_sync_latency(stream=None) -> dict:
+    """Hand-off (median, max), dependent L2 load and store + fence latencies in ns."""
+    out = (C.c_double * 4)()
+    _check(library().gl_measure_sync_latency(out, _stream(stream)))
+    return dict(handoff_ns=out[0], handoff_max_ns=out[1], l2_load_ns=out[2], fence_ns=out[3])
 
 
 def gl_precond_destroy(prec):

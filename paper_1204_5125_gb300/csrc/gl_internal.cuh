@@ -70,7 +70,25 @@ struct FlagPlan {
     DBuf<int64_t> rstart;        // [colour][nb + 1]: first solve position of each CTA's rows in the colour
     DBuf<int32_t> nbr;           // [cta][colour][FLAG_MAXN]: CTAs whose rows those rows read
     DBuf<int32_t> nbrc;          // [cta][colour]: lengths of those lists
+    // the row pointers of each CTA's rows, colour after colour (each colour's
+    // rows and their end), which the sweep keeps in shared memory: CTA b's list
+    // starts at rbase[b]; its colour c part at roff[b (nc + 1) + c]
+    DBuf<int64_t> rpl, rbase;
+    DBuf<int32_t> roff;
+    int smem = 0;                // dynamic shared memory of the launch (bytes)
 };
+// what the sweep kernel reads of a FlagPlan
+struct FlagView {
+    const int64_t *rstart;
+    const int32_t *nbr, *nbrc;
+    const int64_t *rpl, *rbase;
+    const int32_t *roff;
+};
+inline FlagView flag_view(const FlagPlan &F) {
+    return FlagView{F.rstart.get(), F.nbr.get(), F.nbrc.get(), F.rpl.get(), F.rbase.get(), F.roff.get()};
+}
+constexpr int FLAG_SMEM_MAX = 40 * 1024;  // bound of a plan's shared-memory row pointers (bytes; with the
+                                          // kernel's static shared memory below the 48 KiB default)
 
 struct Level {
     int64_t n = 0;

@@ -437,10 +437,17 @@ struct SweepRows {
     }
     // loads the x-independent data of row `row` (first round of a phase)
     __device__ __forceinline__ void prefetch(int64_t row, bool ok) {
+        if (ok)
+            prefetch_q(row, true, A.rp[row], A.rp[row + 1]);
+        else
+            prefetch_q(row, false, 0, 0);
+    }
+    // the same with the row's entry range [q0, q1) given
+    __device__ __forceinline__ void prefetch_q(int64_t row, bool ok, int64_t q0, int64_t q1) {
         pq0 = pq1 = 0;
         if (ok) {
-            pq0 = A.rp[row];
-            pq1 = A.rp[row + 1];
+            pq0 = q0;
+            pq1 = q1;
             pb = b[row];
             pd = diag[row];
         }
@@ -532,30 +539,44 @@ __global__ void __launch_bounds__(coop_threads<R>()) k_sgs_coop(CsrGView<C> A, c
 // The same symmetric step with neighbour flags instead of the grid barrier.
 // CTA b owns a chunk of every colour's rows (FlagPlan) and after each
 // phase publishes, with a release store, the number of phases it has
-// completed; before phase ph (colour c) it waits, with acquiring loads by one
-// warp, only until every CTA owning a column of its colour-c rows has
-// completed phase ph - 1.  That CTA's last write of any such column came in a
-// phase <= ph - 1, and its reads of b's colour-c rows since their previous
-// relaxation also lie in phases <= ph - 1, so every row reads exactly the
-// values the grid-barrier sweep gives it: the two forms are bit-identical for
-// the same G.  CTAs far apart may then run several phases apart.  Counters
-// only grow: a launch adds 2 nc - 1 to each, so all CTAs of a launch start from
-// the same value (a CTA reads its own at the start); a CTA without rows in a
-// colour only counts the phase.
+// completed; before phase ph (colour c) it waits, with acquiring loads, only
+// until every CTA owning a column of its colour-c rows has completed phase
+// ph - 1.  That CTA's last write of any such column came in a phase <= ph - 1,
+// and its reads of b's colour-c rows since their previous relaxation also lie
+// in phases <= ph - 1, so every row reads exactly the values the grid-barrier
+// sweep gives it: the two forms are bit-identical for the same G.  CTAs far
+// apart may then run several phases apart.  Counters only grow: a launch adds
+// 2 nc - 1 to each, so all CTAs of a launch start from the same value (a CTA
+// reads its own at the start); a CTA without rows in a colour only counts the
+// phase.
+//
+// The phase is a chain of latencies (the hand-off from the CTAs it reads, the
+// gathers of their x, the fence behind this CTA's writes), so the kernel keeps
+// everything else off it: warp 0 holds no rows and only publishes and polls,
+// starting its poll right after the release; the other warps relax the rows
+// and, before the phase is published, issue the loads of the next phase's
+// x-independent data (columns, values, b, diagonal) with row pointers from
+// shared memory, where the CTA's row pointers of all colours sit for the whole
+// launch, so no load waits on another.
 template <int G, typename C, typename R>
 __global__ void __launch_bounds__(coop_threads<R>()) k_sgs_flags(CsrGView<C> A, const R *__restrict__ diag,
                                                                  const int64_t *__restrict__ cstart, int ncolors,
-                                                                 const int64_t *__restrict__ rstart,
-                                                                 const int32_t *__restrict__ nbr,
-                                                                 const int32_t *__restrict__ nbrc,
-                                                                 const C *__restrict__ b, C *x, int zero_start,
-                                                                 unsigned long long *flags,
+                                                                 FlagView F, const C *__restrict__ b, C *x,
+                                                                 int zero_start, unsigned long long *flags,
                                                                  const unsigned long long *extra_p, int *err,
                                                                  int *stop) {
     if (sweep_halted(stop, err)) return;
-    constexpr int GPB = coop_threads<R>() / G;  // groups (rows per round) of a CTA
+    constexpr int NT = coop_threads<R>();
+    constexpr int GPB = (NT - 32) / G;  // row groups (rows per round) of the worker warps
+    // dynamic shared memory: this CTA's rows [s_lo[c], s_hi[c]) of every colour,
+    // the offsets s_roff[c] of their row pointers in s_rp, and the row pointers
+    extern __shared__ int64_t s_dyn[];
+    int64_t *s_lo = s_dyn, *s_hi = s_dyn + ncolors;
+    int32_t *s_roff = reinterpret_cast<int32_t *>(s_dyn + 2 * ncolors);
+    int64_t *s_rp = s_dyn + 2 * ncolors + (ncolors + 2) / 2;
     const int nb = gridDim.x, cta = blockIdx.x;
-    const int grp = threadIdx.x / G;
+    const bool worker = threadIdx.x >= 32;
+    const int grp = worker ? (int)(threadIdx.x - 32) / G : 0;
     unsigned long long *mine = flags + (size_t)cta * FLAG_STRIDE;
     // the launch's starting count, and the offset of every wait target (nonzero
     // only when a test asks for waits that cannot end), kept in shared memory
@@ -565,28 +586,59 @@ __global__ void __launch_bounds__(coop_threads<R>()) k_sgs_flags(CsrGView<C> A, 
         s_base = *(volatile unsigned long long *)mine;
         s_target0 = s_base + *extra_p;
     }
+    for (int c = threadIdx.x; c <= ncolors; c += NT) {
+        s_roff[c] = F.roff[(int64_t)cta * (ncolors + 1) + c];
+        if (c < ncolors) {
+            s_lo[c] = F.rstart[(int64_t)c * (nb + 1) + cta];
+            s_hi[c] = F.rstart[(int64_t)c * (nb + 1) + cta + 1];
+        }
+    }
+    __syncthreads();
+    {
+        const int64_t *src = F.rpl + F.rbase[cta];
+        const int total = s_roff[ncolors];
+        for (int i0 = threadIdx.x; i0 < total; i0 += 4 * NT) {
+            int64_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i0 + u * NT < total) v[u] = __ldg(src + i0 + u * NT);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i0 + u * NT < total) s_rp[i0 + u * NT] = v[u];
+        }
+    }
     __syncthreads();
     SweepRows<G, C, R> S(A, diag, b, x, (int)(threadIdx.x % G));
     const int nphase = 2 * ncolors - 1;
     auto colour_of = [&](int ph) { return ph < ncolors ? ph : 2 * ncolors - 2 - ph; };
-    {
-        const int c = colour_of(0);
-        const int64_t lo = rstart[(int64_t)c * (nb + 1) + cta], hi = rstart[(int64_t)c * (nb + 1) + cta + 1];
-        S.prefetch(lo + grp, lo + grp < hi);
-    }
+    auto rows_of = [&](int c, int64_t &lo, int64_t &hi) {
+        lo = s_lo[c];
+        hi = s_hi[c];
+    };
+    // the x-independent data of this group's first row of colour c (later rounds
+    // of a phase, rare, load their own)
+    auto prefetch = [&](int c) {
+        int64_t lo, hi;
+        rows_of(c, lo, hi);
+        const bool ok = lo + grp < hi;
+        const int32_t i = s_roff[c] + grp;
+        S.prefetch_q(lo + grp, ok, ok ? s_rp[i] : 0, ok ? s_rp[i + 1] : 0);
+    };
+    if (worker) prefetch(colour_of(0));
     for (int ph = 0; ph < nphase; ++ph) {
         const int c = colour_of(ph);
         const bool first = zero_start && ph < ncolors;
         const int64_t clo = cstart[c];
         const int64_t lim = first ? clo : INT64_MAX;
-        const int64_t lo = rstart[(int64_t)c * (nb + 1) + cta], hi = rstart[(int64_t)c * (nb + 1) + cta + 1];
+        int64_t lo, hi;
+        rows_of(c, lo, hi);
         if (ph > 0 && hi > lo) {
-            if (threadIdx.x < 32) {
+            if (!worker) {
                 const int64_t li = (int64_t)cta * ncolors + c;
-                const int cnt = nbrc[li];
+                const int cnt = F.nbrc[li];
                 bool ok = true;
                 if ((int)threadIdx.x < cnt)
-                    ok = spin_geq(flags + (size_t)nbr[li * FLAG_MAXN + threadIdx.x] * FLAG_STRIDE,
+                    ok = spin_geq(flags + (size_t)F.nbr[li * FLAG_MAXN + threadIdx.x] * FLAG_STRIDE,
                                   s_target0 + (unsigned long long)ph);
                 ok = __all_sync(0xffffffffu, ok);
                 if (threadIdx.x == 0) {
@@ -597,18 +649,17 @@ __global__ void __launch_bounds__(coop_threads<R>()) k_sgs_flags(CsrGView<C> A, 
             __syncthreads();
             if (!s_ok) return;
         }
-        const int64_t rounds = (hi - lo + GPB - 1) / GPB;
-        for (int64_t k = 0; k < rounds; ++k) {
-            const int64_t row = lo + k * GPB + grp;
-            S.relax(row, row < hi, k, lim, first && clo == 0);
+        if (worker) {
+            const int64_t rounds = (hi - lo + GPB - 1) / GPB;
+            for (int64_t k = 0; k < rounds; ++k) {
+                const int64_t row = lo + k * GPB + grp;
+                S.relax(row, row < hi, k, lim, first && clo == 0);
+            }
+            // the next phase's x-independent data, before this phase is published
+            if (ph + 1 < nphase) prefetch(colour_of(ph + 1));
         }
         __syncthreads();
         if (threadIdx.x == 0) st_release_u64(mine, s_base + (unsigned long long)ph + 1);
-        if (ph + 1 < nphase) {
-            const int cn = colour_of(ph + 1);
-            const int64_t nlo = rstart[(int64_t)cn * (nb + 1) + cta], nhi = rstart[(int64_t)cn * (nb + 1) + cta + 1];
-            S.prefetch(nlo + grp, nlo + grp < nhi);
-        }
     }
 }
 
@@ -681,21 +732,34 @@ __global__ void __launch_bounds__(256) k_flag_nbrs(CsrGView<C> A, int nb, int nc
     }
 }
 
+// rpl[rbase[b] + roff[b][c] + i] = A.rp[lo + i], i = 0 .. hi - lo, for CTA b's
+// rows [lo, hi) of colour c
+template <typename C>
+__global__ void __launch_bounds__(256) k_flag_rpl(CsrGView<C> A, int nb, int ncolors,
+                                                  const int64_t *__restrict__ rstart, const int32_t *__restrict__ roff,
+                                                  const int64_t *__restrict__ rbase, int64_t *__restrict__ rpl) {
+    const int bb = blockIdx.x, c = blockIdx.y;
+    const int64_t lo = rstart[(int64_t)c * (nb + 1) + bb], hi = rstart[(int64_t)c * (nb + 1) + bb + 1];
+    int64_t *dst = rpl + rbase[bb] + roff[(int64_t)bb * (ncolors + 1) + c];
+    for (int64_t i = threadIdx.x; i <= hi - lo; i += blockDim.x) dst[i] = A.rp[lo + i];
+}
+
 // resident CTAs per SM of a sweep kernel and the SM count (queried once per kernel)
 template <typename K>
-static void sweep_residency(K kern, int threads, int &per_sm, int &nsm) {
+static void sweep_residency(K kern, int threads, int &per_sm, int &nsm, size_t smem = 0) {
     int dev = 0;
     GL_CUDA(cudaGetDevice(&dev));
     GL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    GL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
+    GL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     GL_REQUIRE(per_sm > 0, GL_ERR_CUDA, "cooperative sweep kernel cannot be resident");
 }
 
 template <typename K, typename... Args>
-static void launch_coop(K kern, int grid, int threads, cudaStream_t s, Args... args) {
+static void launch_coop_smem(K kern, int grid, int threads, size_t smem, cudaStream_t s, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -703,6 +767,10 @@ static void launch_coop(K kern, int grid, int threads, cudaStream_t s, Args... a
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     GL_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
+}
+template <typename K, typename... Args>
+static void launch_coop(K kern, int grid, int threads, cudaStream_t s, Args... args) {
+    launch_coop_smem(kern, grid, threads, 0, s, args...);
 }
 
 template <int G, typename C, typename R>
@@ -718,11 +786,12 @@ static void launch_sgs_coop(const CsrG<C> &A, const R *diag, const int64_t *csta
                 stop);
 }
 
-// most CTAs a neighbour-flag sweep of G lanes per row may use (all resident)
+// most CTAs a neighbour-flag sweep of G lanes per row may use (all resident,
+// with the largest shared memory a plan may ask for)
 template <int G, typename C, typename R>
 static int flags_max_ctas() {
     static int per_sm = -1, nsm = 0;
-    if (per_sm < 0) sweep_residency(k_sgs_flags<G, C, R>, coop_threads<R>(), per_sm, nsm);
+    if (per_sm < 0) sweep_residency(k_sgs_flags<G, C, R>, coop_threads<R>(), per_sm, nsm, FLAG_SMEM_MAX);
     return std::min(per_sm * nsm, MAX_FLAG_CTAS);
 }
 
@@ -730,11 +799,10 @@ template <int G, typename C, typename R>
 static void launch_sgs_flags(const CsrG<C> &A, const R *diag, const int64_t *cstart, int nc, const FlagPlan &F,
                              const C *b, C *x, int zero_start, unsigned long long *flags,
                              const unsigned long long *extra, int *err, int *stop, cudaStream_t s) {
-    const bool matches = F.nb > 0 && F.nb <= flags_max_ctas<G, C, R>() && F.G == G;
+    const bool matches = F.nb > 0 && F.nb <= flags_max_ctas<G, C, R>() && F.G == G && F.smem <= FLAG_SMEM_MAX;
     GL_REQUIRE(matches, GL_ERR_ARG, "neighbour-flag sweep without a matching partition");
-    launch_coop(k_sgs_flags<G, C, R>, F.nb, coop_threads<R>(), s, A.view(), diag, cstart, nc,
-                (const int64_t *)F.rstart.get(), (const int32_t *)F.nbr.get(), (const int32_t *)F.nbrc.get(), b, x,
-                zero_start, flags, extra, err, stop);
+    launch_coop_smem(k_sgs_flags<G, C, R>, F.nb, coop_threads<R>(), (size_t)F.smem, s, A.view(), diag, cstart, nc,
+                     flag_view(F), b, x, zero_start, flags, extra, err, stop);
 }
 
 // Builds the neighbour-flag partition of a coarse level for nb CTAs of G lanes
@@ -755,12 +823,39 @@ static int build_flag_plan(const Level &L, const CsrG<C> &A, int G, int nb, Flag
                                                 F.nbrc.get());
     GL_LAUNCH_CHECK();
     std::vector<int32_t> cnt((size_t)nb * nc);
+    std::vector<int64_t> rs((size_t)nc * (nb + 1));
     GL_CUDA(cudaMemcpyAsync(cnt.data(), F.nbrc.get(), cnt.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaMemcpyAsync(rs.data(), F.rstart.get(), rs.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     GL_CUDA(cudaStreamSynchronize(s));
     int mx = 0;
     for (int32_t v : cnt) mx = std::max(mx, (int)v);
-    if (mx <= FLAG_MAXN) F.nb = nb;
-    return mx;
+    // each CTA's row pointers, colour after colour: its rows of colour c and their end
+    std::vector<int32_t> roff((size_t)nb * (nc + 1));
+    std::vector<int64_t> rbase(nb + 1);
+    int64_t most = 0;
+    rbase[0] = 0;
+    for (int bb = 0; bb < nb; ++bb) {
+        int32_t o = 0;
+        for (int c = 0; c < nc; ++c) {
+            roff[(size_t)bb * (nc + 1) + c] = o;
+            o += (int32_t)(rs[(size_t)c * (nb + 1) + bb + 1] - rs[(size_t)c * (nb + 1) + bb]) + 1;
+        }
+        roff[(size_t)bb * (nc + 1) + nc] = o;
+        rbase[bb + 1] = rbase[bb] + o;
+        most = std::max<int64_t>(most, o);
+    }
+    // the kernel's layout: lo and hi per colour, nc + 1 offsets (int32), the row pointers
+    F.smem = (int)std::min<int64_t>((2 * nc + (nc + 2) / 2 + most) * (int64_t)sizeof(int64_t), INT32_MAX);
+    F.roff.alloc(roff.size());
+    F.rbase.alloc(nb + 1);
+    F.rpl.alloc((size_t)std::max<int64_t>(rbase[nb], 1));
+    GL_CUDA(cudaMemcpyAsync(F.roff.get(), roff.data(), roff.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    GL_CUDA(cudaMemcpyAsync(F.rbase.get(), rbase.data(), rbase.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    k_flag_rpl<<<dim3(nb, nc), 256, 0, s>>>(A.view(), nb, nc, F.rstart.get(), F.roff.get(), F.rbase.get(), F.rpl.get());
+    GL_LAUNCH_CHECK();
+    GL_CUDA(cudaStreamSynchronize(s));
+    if (mx <= FLAG_MAXN && F.smem <= FLAG_SMEM_MAX) F.nb = nb;
+    return F.smem <= FLAG_SMEM_MAX ? mx : FLAG_MAXN + 1;
 }
 
 // ---------------------------------------------------------------- cluster sweeps
@@ -1579,7 +1674,8 @@ template <typename T>
 static int flags_default_nb(const Level &L, int G, int max_ctas) {
     int64_t maxc = 0;
     for (int c = 0; c < L.ncolors; ++c) maxc = std::max(maxc, L.cstart[c + 1] - L.cstart[c]);
-    const int64_t per = std::max<int64_t>(1, (int64_t)(coop_threads<T>() / G) * 3 / 4);
+    // rows per round of the flag sweep (its warp 0 only synchronises), three quarters full
+    const int64_t per = std::max<int64_t>(1, (int64_t)((coop_threads<T>() - 32) / G) * 3 / 4);
     return (int)std::min<int64_t>(std::max<int64_t>((maxc + per - 1) / per, 1), max_ctas);
 }
 
