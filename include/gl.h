@@ -67,7 +67,8 @@ typedef enum {
     GL_FP64 = 0,          /* everything in FP64 complex */
     GL_MIXED = 1,         /* FP64 defect correction around inner MINRES solves whose vectors,
                              Jacobian applies and V-cycles are FP32 complex */
-    GL_MIXED_PRECOND = 2  /* FP64 MINRES and Jacobian applies; the V-cycle of R_k runs in FP32 */
+    GL_MIXED_PRECOND = 2, /* FP64 MINRES and Jacobian applies; the V-cycle of R_k runs in FP32 */
+    GL_APPLY_FP64_TABLES = 3 /* gl_jacobian_apply only: the FP64 apply from the lattice stencil's FP64 tables */
 } gl_precision;
 
 /* options.cycles value selecting R_inf = P^-1 D (Eq. prec1), realised as the
@@ -95,7 +96,11 @@ typedef struct {
     int lattice;         /* 1: on a mesh with an even number of nodes per side, the FP32 finest-level
                             sweeps and residuals of the V-cycle use the closed-form lattice stencil (checked
                             entry by entry against the assembled K at setup) instead of the stored one;
-                            0: always the stored stencil (default 1) */
+                            2: as 1, and MINRES's FP64 Jacobian also runs matrix-free from the stencil's
+                            FP64 tables where they match the stored K to 16 ulp of its largest entry (it
+                            reads a quarter of the bytes but is bound by this GPU's FP64 rate, and took
+                            longer than the stored form when measured); 0: always the stored stencil
+                            (default 1) */
     int cluster_sweeps;  /* 1: FP32 coarse-level Gauss-Seidel steps whose level vector fits the shared memory
                             of one thread-block cluster may run in that cluster (hardware barrier between
                             colours) instead of a cooperative grid: with autotune, where the setup timing
@@ -164,6 +169,9 @@ typedef struct {
                             (cycles applied) x (one V-cycle + one finest residual) */
     double cycles_per_apply; /* V-cycles per preconditioner application: k for R_k, the average for R_inf,
                             0 without a preconditioner */
+    int jacobian_tables; /* 1 if MINRES's FP64 Jacobian applies ran from the lattice stencil's FP64 tables
+                            (gl_options.lattice = 2 on an even-N lattice whose stored K matches them to 16
+                            ulp of its largest entry) instead of the stored K */
 } gl_solve_info;
 
 /* Default options (values listed in gl_options).  Returns GL_ERR_ARG on NULL. */
@@ -234,8 +242,12 @@ GL_API gl_status gl_energy(gl_mesh mesh, const void *psi_dev, double *energy_hos
 
 /* Discrete Jacobian (Sec. 3):
  *   y_i = (K phi)_i + (-1 + 2|psi_i|^2) phi_i + psi_i^2 conj(phi_i).
- * psi, phi, y: n complex FP64; y may not alias psi or phi.  With GL_MIXED the
- * operator and arithmetic are FP32 (inputs rounded to FP32, output widened).
+ * psi, phi, y: n complex FP64; y may not alias psi or phi.  GL_FP64: the stored
+ * K.  GL_APPLY_FP64_TABLES: the same operator formed matrix-free from the lattice
+ * stencil's FP64 tables (meshes with an even number of nodes per side whose
+ * stored K matches the tables to 16 ulp of its largest entry; GL_ERR_ARG on
+ * others).  With GL_MIXED the operator and arithmetic are FP32 (inputs rounded
+ * to FP32, output widened).
  * With GL_MIXED_PRECOND: the double-FP32 form that GL_MIXED_PRECOND solves use on
  * meshes with an even number of nodes per side (edge magnitudes and phases of
  * the checked lattice stencil as FP32 hi + lo pairs, error-free transformations,

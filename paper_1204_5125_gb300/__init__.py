@@ -31,11 +31,12 @@ __all__ = [
     "gl_mesh_set_mu", "gl_residual_dmu", "gl_energy", "cont_options", "gl_continuation", "gl_precond_setup_like",
     "GL_COLOR_SL", "GL_COLOR_JP", "GL_COLOR_PSL", "gl_mesh_create_dipole", "gl_precond_apply_precision", "gl_precond_debug",
     "GL_DEBUG_STALL_SWEEPS", "GL_DEBUG_NEGATE_COARSEST", "gl_precond_level_sweep", "gl_measure_fma_peak",
-    "gl_measure_sync_latency",
+    "gl_measure_sync_latency", "GL_APPLY_FP64_TABLES",
     "gl_profile_flops",
 ]
 
 GL_FP64, GL_MIXED, GL_MIXED_PRECOND = 0, 1, 2
+GL_APPLY_FP64_TABLES = 3  # gl_jacobian_apply: the FP64 apply from the lattice stencil's FP64 tables
 GL_CYCLES_INF = -1  # options.cycles: R_inf, the V-cycle repeated until the 1e-12 residual test
 GL_COLOR_SL, GL_COLOR_JP, GL_COLOR_PSL = 0, 1, 2  # options.coloring of the coarse levels
 GL_DEBUG_STALL_SWEEPS, GL_DEBUG_NEGATE_COARSEST = 1, 2  # gl_precond_debug actions (fault injection for tests)
@@ -84,6 +85,7 @@ class SolveInfo(C.Structure):
         ("est_relres", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
         ("warmstart_used", C.c_int), ("lattice_stencil", C.c_int), ("df_jacobian", C.c_int),
         ("stall_restarts", C.c_int), ("matvec_equiv", C.c_double), ("cycles_per_apply", C.c_double),
+        ("jacobian_tables", C.c_int),
     ]
 
     def as_dict(self):

@@ -43,6 +43,7 @@ void check_opts(const gl_options *o) {
     GL_REQUIRE(o->coloring == GL_COLOR_SL || o->coloring == GL_COLOR_JP || o->coloring == GL_COLOR_PSL, GL_ERR_ARG,
                "unknown coloring");
     GL_REQUIRE(o->sweep_sync >= 0 && o->sweep_sync <= 2, GL_ERR_ARG, "sweep_sync must be 0, 1 or 2");
+    GL_REQUIRE(o->lattice >= 0 && o->lattice <= 2, GL_ERR_ARG, "lattice must be 0, 1 or 2");
 }
 
 void ensure_tmp(gl_mesh_s *m) {
@@ -201,8 +202,9 @@ gl_status gl_jacobian_apply(gl_mesh m, const void *psi, const void *phi, void *y
     return guard([&] {
         GL_REQUIRE(m && psi && phi && y, GL_ERR_ARG, "NULL argument");
         GL_REQUIRE(y != psi && y != phi, GL_ERR_ARG, "y must not alias psi or phi");
-        GL_REQUIRE(precision == GL_FP64 || precision == GL_MIXED || precision == GL_MIXED_PRECOND, GL_ERR_ARG,
-                   "unknown precision");
+        GL_REQUIRE(precision == GL_FP64 || precision == GL_MIXED || precision == GL_MIXED_PRECOND ||
+                       precision == GL_APPLY_FP64_TABLES,
+                   GL_ERR_ARG, "unknown precision");
         cudaStream_t s = as_stream(stream);
         ensure_tmp(m);
         permute_in(m->n, m->perm.get(), (const double2 *)psi, m->t0.get(), s);
@@ -212,6 +214,8 @@ gl_status gl_jacobian_apply(gl_mesh m, const void *psi, const void *phi, void *y
         } else if (precision == GL_MIXED) {
             mesh_ensure_fp32(m, s);
             jacobian_apply_p32(m, m->t0.get(), m->t1.get(), m->t2.get(), s);
+        } else if (precision == GL_APPLY_FP64_TABLES) {
+            jacobian_apply_lat64_p(m, m->t0.get(), m->t1.get(), m->t2.get(), s);
         } else {
             jacobian_apply_p(m, m->t0.get(), m->t1.get(), m->t2.get(), s);
         }

@@ -31,6 +31,10 @@ struct gl_mesh_s {
     bool lat_checked = false, lat_ok = false;
     int64_t lat_per_axis = 0;
     gl::DBuf<float2> lat_tab;
+    // the FP64 tables, used by the FP64 Jacobian when every stored entry of K
+    // matches them to 16 ulp of the largest entry (lat64_ok)
+    bool lat64_ok = false;
+    gl::DBuf<double2> lat_tab64;
     // the same tables as double-float magnitude a = |K-hat| / h^d and unit phase,
     // the FP64 remainders K_ii - sum_k |K_ik| (solve ordering) and h^d
     gl::DBuf<float2> lat_a;
@@ -156,6 +160,7 @@ struct gl_prec_s {
     bool has32 = false;
     bool autotune = true;
     bool lattice = true;              // closed-form finest-level stencil in the FP32 V-cycle when available
+    bool lattice64 = false;           // and MINRES's FP64 Jacobian from its FP64 tables (options.lattice = 2)
     bool cluster_sweeps = true;       // FP32 coarse sweeps by one thread-block cluster when the level fits
     gl::Level L[gl::MAX_LEVELS];
     gl::DBuf<double2> psi_p;          // psi in solve ordering
@@ -205,8 +210,33 @@ void build_csrg(int64_t nrows, const int32_t *perm, const int32_t *icol, const C
 
 // gl_lattice.cu: validates the closed-form finest-level stencil against the
 // assembled K and builds its phase tables (sets lat_ok)
+// Unsigned 32-bit division by a divisor fixed on the host, by a multiply-high
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994): with l = ceil(log2 d) and the round-up multiplier
+// m = floor(2^32 (2^l - d) / d) + 1 (< 2^32), n / d = (mulhi(m, n) + n) >> l for
+// every 32-bit n (the sum formed in 64 bits).  The lattice kernels split node
+// numbers into coordinates with it instead of the hardware-less integer division.
+struct DivU32 {
+    uint32_t d = 1, m = 1;
+    int l = 0;
+    static DivU32 make(uint32_t d_) {
+        DivU32 r;
+        r.d = d_;
+        r.l = 0;
+        while ((1ull << r.l) < d_) ++r.l;
+        r.m = (uint32_t)((((1ull << 32) * ((1ull << r.l) - d_)) / d_) + 1);
+        return r;
+    }
+#ifdef __CUDACC__
+    __device__ __forceinline__ uint32_t div(uint32_t n) const {
+        return (uint32_t)(((uint64_t)__umulhi(m, n) + n) >> l);
+    }
+#endif
+};
+
 struct LatticeView {
     int dim, N;
+    DivU32 dN;                     // division by N
     int64_t nred;
     const float *vol;              // |V| in the solve ordering
     const float2 *tx, *ty, *tz;    // K-hat of the +x, +y, +z edges by perpendicular position
@@ -216,9 +246,20 @@ void mesh_ensure_lattice(gl_mesh_s *m, cudaStream_t s);
 // a failed check turns the stencil off)
 void mesh_refresh_lattice(gl_mesh_s *m, cudaStream_t s);
 LatticeView lattice_view(const gl_mesh_s *m);
+// the FP64 tables and |V| (solve ordering) for the FP64 Jacobian
+struct LatticeView64 {
+    int dim, N;
+    DivU32 dN;
+    int64_t nred;
+    const double *vol;
+    const double2 *tx, *ty, *tz;
+    double ihd;        // 1 / h^d: |V_p| = h^d 2^-b_p (b_p boundary coordinates), so 1 / |V_p| = 2^b_p / h^d
+};
+LatticeView64 lattice_view64(const gl_mesh_s *m);
 // double-float view of the same stencil (row scaled by 2^b / h^d, b = boundary coordinates)
 struct LatticeDfView {
     int dim, N;
+    DivU32 dN;
     int64_t nred;
     int64_t per_axis;
     const float2 *a;   // |K-hat| / h^d as (hi, lo), axis-major tables
@@ -246,6 +287,7 @@ void precond_negate_coarsest(gl_prec_s *p, cudaStream_t s);
 void permute_in(int64_t n, const int32_t *perm, const double2 *nat, double2 *sol, cudaStream_t s);
 void permute_out(int64_t n, const int32_t *perm, const double2 *sol, double2 *nat, cudaStream_t s);
 void jacobian_apply_p(const gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s);
+void jacobian_apply_lat64_p(const gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s);
 void jacobian_apply_p32(const gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s);
 // gl_solve.cu: the double-float lattice Jacobian of the GL_MIXED_PRECOND solve on
 // phi rounded to FP32 (solve ordering; GL_ERR_ARG without a lattice stencil)

@@ -115,8 +115,9 @@ __device__ __forceinline__ float2 lattice_row_f(const LatticeView &L, int64_t p,
     const uint32_t c = p >= L.nred ? 1u : 0u;
     const uint32_t N = (uint32_t)L.N;
     uint32_t v = 2u * (uint32_t)(p - (c ? L.nred : 0));
-    uint32_t i = v % N;
-    const uint32_t r = v / N, j = r % N, k = r / N;
+    const uint32_t r = L.dN.div(v), k = L.dN.div(r);
+    uint32_t i = v - r * N;
+    const uint32_t j = r - k * N;
     if (((i + j + k) & 1u) != c) {
         ++v;
         ++i;
@@ -147,6 +148,48 @@ __device__ __forceinline__ float2 lattice_row_f(const LatticeView &L, int64_t p,
     }
     const float iv = 1.f / L.vol[p];
     return make_float2(acc.x * iv, acc.y * iv);
+}
+
+// sum_{k != p} K_pk x_k in FP64 from the FP64 tables (same layout, edge order and
+// conjugation as lattice_row_f), the row scaled by 1 / |V_p| = 2^b / h^d (b the
+// node's boundary coordinates; no division: this kernel is bound by the FP64 pipe)
+__device__ __forceinline__ double2 lattice_row64(const LatticeView64 &L, int64_t p, const double2 *__restrict__ x) {
+    const uint32_t c = p >= L.nred ? 1u : 0u;
+    const uint32_t N = (uint32_t)L.N;
+    uint32_t v = 2u * (uint32_t)(p - (c ? L.nred : 0));
+    const uint32_t r = L.dN.div(v), k = L.dN.div(r);
+    uint32_t i = v - r * N;
+    const uint32_t j = r - k * N;
+    if (((i + j + k) & 1u) != c) {
+        ++v;
+        ++i;
+    }
+    const int64_t other = c ? 0 : L.nred;
+    double2 acc = make_double2(0.0, 0.0);
+    auto edge = [&](double2 t, uint32_t u, bool plus) {
+        const double2 xv = x[(int64_t)(u >> 1) + other];
+        const double ty = plus ? t.y : -t.y;
+        acc.x += t.x * xv.x - ty * xv.y;
+        acc.y += t.x * xv.y + ty * xv.x;
+    };
+    {
+        const double2 t = __ldg(L.tx + (j + N * k));
+        if (i + 1 < N) edge(t, v + 1, true);
+        if (i > 0) edge(t, v - 1, false);
+    }
+    {
+        const double2 t = __ldg(L.ty + (i + N * k));
+        if (j + 1 < N) edge(t, v + N, true);
+        if (j > 0) edge(t, v - N, false);
+    }
+    if (L.dim == 3) {
+        const double2 t = __ldg(L.tz + (i + N * j));
+        if (k + 1 < N) edge(t, v + N * N, true);
+        if (k > 0) edge(t, v - N * N, false);
+    }
+    const int b = (i == 0 || i == N - 1) + (j == 0 || j == N - 1) + (L.dim == 3 && (k == 0 || k == N - 1));
+    const double iv = L.ihd * (double)(1 << b);
+    return make_double2(acc.x * iv, acc.y * iv);
 }
 
 }  // namespace gl

@@ -27,6 +27,11 @@
 // entry of the assembled FP64 operator K has been found equal to the table
 // value (relative difference <= 1e-12 of the largest entry) and every row to
 // hold exactly its lattice neighbours; otherwise the sliced-ELL kernels stay.
+// The FP64 Jacobian takes the FP64 tables under a tighter test: every entry within
+// 16 ulp of the largest and every control volume h^d 2^-b to 2 ulp (its row
+// scale 2^b / h^d then needs no division).
+#include <cfloat>
+
 #include "gl_internal.cuh"
 
 namespace gl {
@@ -80,15 +85,23 @@ __global__ void k_lat_tables(LatDev L, const int64_t *__restrict__ rp, const int
 }
 
 // compares every stored entry of K (solve ordering, FP64) with the table value
+// (bad: beyond tol); bad64 also counts entries beyond tol64 and control volumes
+// other than h^d 2^-b (b the node's boundary coordinates), the scale the FP64
+// stencil applies
 __global__ void k_lat_check(LatDev L, SellView<double2> K, const int32_t *__restrict__ perm,
                             const double *__restrict__ vol, const double2 *__restrict__ tab, int64_t per_axis,
-                            double tol, unsigned *bad) {
+                            double tol, unsigned *bad, double tol64, unsigned *bad64, double hd) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= L.n) return;
     const int N = L.N;
     const int64_t v = perm[p];
     int cc[3];
     lat_coords(L, v, cc);
+    {
+        int b = 0;
+        for (int e = 0; e < L.dim; ++e) b += (cc[e] == 0 || cc[e] == N - 1);
+        if (fabs(vol[v] - hd / (double)(1 << b)) > 2.0 * DBL_EPSILON * vol[v]) atomicAdd(bad64, 1u);
+    }
     const int64_t stride[3] = {1, N, (int64_t)N * N};
     int expect = 0;
     for (int e = 0; e < L.dim; ++e) {
@@ -119,6 +132,7 @@ __global__ void k_lat_check(LatDev L, SellView<double2> K, const int32_t *__rest
         double2 t = tab[e * per_axis + lat_perp(L, e, cc)];
         double ex = t.x / vol[v], ey = (sg > 0 ? t.y : -t.y) / vol[v];
         if (fabs(val.x - ex) > tol || fabs(val.y - ey) > tol) ok = false;
+        if (fabs(val.x - ex) > tol64 || fabs(val.y - ey) > tol64) atomicAdd(bad64, 1u);
         ++found;
     }
     if (!ok || found != expect) atomicAdd(bad, 1u);
@@ -174,8 +188,8 @@ static bool lattice_tables(gl_mesh_s *m, bool reuse, cudaStream_t s) {
     k_lat_tables<<<grid_for(per_axis * m->dim, 256), 256, 0, s>>>(L, m->khat.rp.get(), m->khat.ci.get(), m->khat.v.get(),
                                                                    tab64.get(), per_axis);
     GL_LAUNCH_CHECK();
-    DBuf<unsigned> bad(1);
-    GL_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(unsigned), s));
+    DBuf<unsigned> bad(2);
+    GL_CUDA(cudaMemsetAsync(bad.get(), 0, 2 * sizeof(unsigned), s));
     double kmax = 0;
     {
         // largest |K| entry bounds the tolerance: the row sums of |K| are the diagonal
@@ -185,13 +199,16 @@ static bool lattice_tables(gl_mesh_s *m, bool reuse, cudaStream_t s) {
         for (double v : kd) kmax = std::max(kmax, std::fabs(v));
     }
     k_lat_check<<<grid_for(m->n, 256), 256, 0, s>>>(L, m->K.view(), m->perm.get(), m->vol.get(), tab64.get(),
-                                                    per_axis, 1e-12 * kmax, bad.get());
+                                                    per_axis, 1e-12 * kmax, bad.get(), 16.0 * DBL_EPSILON * kmax,
+                                                    bad.get() + 1, m->dim == 2 ? m->h * m->h : m->h * m->h * m->h);
     GL_LAUNCH_CHECK();
-    unsigned nb = 0;
-    GL_CUDA(cudaMemcpyAsync(&nb, bad.get(), sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    unsigned nbad[2] = {0, 0};
+    GL_CUDA(cudaMemcpyAsync(nbad, bad.get(), 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     GL_CUDA(cudaStreamSynchronize(s));
-    if (nb != 0) return false;
+    m->lat64_ok = false;
+    if (nbad[0] != 0) return false;
     if (!reuse) {
+        m->lat_tab64.alloc((size_t)per_axis * m->dim);
         m->lat_tab.alloc((size_t)per_axis * m->dim);
         m->lat_a.alloc((size_t)per_axis * m->dim);
         m->lat_u.alloc((size_t)per_axis * m->dim);
@@ -199,6 +216,9 @@ static bool lattice_tables(gl_mesh_s *m, bool reuse, cudaStream_t s) {
     }
     k_lat_round<<<grid_for(per_axis * m->dim, 256), 256, 0, s>>>(per_axis * m->dim, tab64.get(), m->lat_tab.get());
     GL_LAUNCH_CHECK();
+    GL_CUDA(cudaMemcpyAsync(m->lat_tab64.get(), tab64.get(), (size_t)per_axis * m->dim * sizeof(double2),
+                            cudaMemcpyDeviceToDevice, s));
+    m->lat64_ok = nbad[1] == 0;
     // double-float tables: the control volumes are h^d 2^-b exactly (b boundary
     // coordinates), so K_ik = 2^b (K-hat_ik / h^d) with an exact power-of-2 factor
     m->lat_hd = m->dim == 2 ? m->h * m->h : m->h * m->h * m->h;
@@ -228,6 +248,7 @@ LatticeDfView lattice_df_view(const gl_mesh_s *m) {
     LatticeDfView v{};
     v.dim = m->dim;
     v.N = m->N;
+    v.dN = DivU32::make((uint32_t)m->N);
     v.nred = m->nred;
     v.per_axis = m->lat_per_axis;
     v.a = m->lat_a.get();
@@ -235,10 +256,25 @@ LatticeDfView lattice_df_view(const gl_mesh_s *m) {
     return v;
 }
 
+LatticeView64 lattice_view64(const gl_mesh_s *m) {
+    LatticeView64 v{};
+    v.dim = m->dim;
+    v.N = m->N;
+    v.dN = DivU32::make((uint32_t)m->N);
+    v.nred = m->nred;
+    v.vol = m->volp.get();
+    v.tx = m->lat_tab64.get();
+    v.ty = v.tx + m->lat_per_axis;
+    v.tz = m->dim == 3 ? v.ty + m->lat_per_axis : nullptr;
+    v.ihd = 1.0 / m->lat_hd;
+    return v;
+}
+
 LatticeView lattice_view(const gl_mesh_s *m) {
     LatticeView v{};
     v.dim = m->dim;
     v.N = m->N;
+    v.dN = DivU32::make((uint32_t)m->N);
     v.nred = m->nred;
     v.vol = m->volp32.get();
     v.tx = m->lat_tab.get();

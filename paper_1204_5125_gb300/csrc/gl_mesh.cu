@@ -724,6 +724,8 @@ void mesh_create(gl_mesh_s *m, int dim, int N, double edge, double mu, const dou
     k_permute_real<<<grid_for(n, 256), 256, 0, s>>>(n, m->perm.get(), m->vol.get(), m->volp.get());
     GL_LAUNCH_CHECK();
     GL_CUDA(cudaStreamSynchronize(s));
+    // the matrix-free lattice stencil, checked against K (even N)
+    mesh_ensure_lattice(m, s);
 }
 
 // rewrites the values of a sliced ELL built by build_sell from a CSR of the same
@@ -747,10 +749,9 @@ void mesh_set_mu(gl_mesh_s *m, double mu, cudaStream_t s) {
         k_edges_set_mu<<<grid_for(m->nedges, 256), 256, 0, s>>>(m->nedges, mu, m->etheta1.get(), m->etheta.get());
     GL_LAUNCH_CHECK();
     refill_sell<double2>(n, n, m->perm.get(), m->iperm.get(), m->khat, m->vol.get(), true, m->K, m->kdiag.get(), s);
-    if (m->has32) {
+    if (m->has32)
         refill_sell<float2>(n, n, m->perm.get(), m->iperm.get(), m->khat, m->vol.get(), true, m->K32, nullptr, s);
-        mesh_refresh_lattice(m, s);
-    }
+    mesh_refresh_lattice(m, s);
     GL_CUDA(cudaStreamSynchronize(s));
     m->mu = mu;
     m->version += 1;

@@ -38,6 +38,16 @@ __global__ void k_jacobian64(int64_t n, SellView<double2> K, const double *__res
     y[p] = jacobian_epilogue(acc, kdiag[p], psi[p], phi[p]);
 }
 
+// the same from the FP64 lattice tables (meshes whose stored K matches them)
+__global__ void k_jacobian_lat64(int64_t n, LatticeView64 L, const double *__restrict__ kdiag,
+                                 const double2 *__restrict__ psi, const double2 *__restrict__ phi,
+                                 double2 *__restrict__ y) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double2 acc = lattice_row64(L, p, phi);
+    y[p] = jacobian_epilogue(acc, kdiag[p], psi[p], phi[p]);
+}
+
 // y = J(psi) phi with the FP32 operator and FP32 arithmetic (FP64 in/out)
 __global__ void k_jacobian32(int64_t n, SellView<float2> K, const float *__restrict__ kdiag,
                              const double2 *__restrict__ psi, const double2 *__restrict__ phi,
@@ -112,6 +122,13 @@ void newton_update(int64_t n, const double2 *d, double2 *psi, cudaStream_t s) {
 
 void jacobian_apply_p(const gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s) {
     k_jacobian64<<<grid_for(m->n, 256), 256, 0, s>>>(m->n, m->K.view(), m->kdiag.get(), psi, phi, y);
+    GL_LAUNCH_CHECK();
+}
+// the same matrix-free from the lattice stencil's FP64 tables (meshes whose stored
+// K matches them to 16 ulp of its largest entry: the same operator up to rounding)
+void jacobian_apply_lat64_p(const gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s) {
+    GL_REQUIRE(m->lat64_ok, GL_ERR_ARG, "the mesh has no FP64 lattice stencil (odd N, or K does not match it)");
+    k_jacobian_lat64<<<grid_for(m->n, 256), 256, 0, s>>>(m->n, lattice_view64(m), m->kdiag.get(), psi, phi, y);
     GL_LAUNCH_CHECK();
 }
 void jacobian_apply_p32(const gl_mesh_s *m, const double2 *psi, const double2 *phi, double2 *y, cudaStream_t s) {

@@ -1282,6 +1282,7 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
     GL_CUDA(cudaStreamSynchronize(s));
     p->autotune = o.autotune != 0;
     p->lattice = o.lattice != 0;
+    p->lattice64 = o.lattice == 2;
     p->cluster_sweeps = o.cluster_sweeps != 0;
     p->sweep_sync = o.sweep_sync;
     p->coarse_df = o.coarse_df != 0;

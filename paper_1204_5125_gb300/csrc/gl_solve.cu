@@ -110,6 +110,24 @@ __global__ void __launch_bounds__(RED_THREADS) k_jz(int64_t n, SellView<C> K, co
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
+// the same from the FP64 lattice tables (the matrix-free stencil of a lattice mesh)
+__global__ void __launch_bounds__(RED_THREADS) k_jz_lat64(int64_t n, LatticeView64 L, const double *kd,
+                                                          const double2 *psi, const double2 *z, double2 *q,
+                                                          double *part, const int *stop) {
+    __shared__ double sh[32];
+    if (*stop) return;
+    double a = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const double2 acc = lattice_row64(L, p, z);
+        const double2 zz = z[p];
+        const double2 jz = jacobian_epilogue(acc, kd[p], psi[p], zz);
+        q[p] = jz;
+        a += L.vol[p] * redot(jz, zz);
+    }
+    double t = block_sum(a, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
 // ------------------------------------------------------------------ double-float Jacobian apply
 // In the mixed-precision solve (FP64 MINRES, FP32 V-cycle) every z that meets
 // the Jacobian is the FP64 image of the V-cycle's FP32 output, so its FP32 copy
@@ -148,8 +166,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_jz_latdf(int64_t n, LatticeDfVi
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t c = p >= L.nred ? 1u : 0u;
         uint32_t v = 2u * (uint32_t)(p - (c ? L.nred : 0));
-        uint32_t i = v % N;
-        const uint32_t r = v / N, j = r % N, k = r / N;
+        const uint32_t r = L.dN.div(v), k = L.dN.div(r);
+        uint32_t i = v - r * N;
+        const uint32_t j = r - k * N;
         if (((i + j + k) & 1u) != c) {
             ++v;
             ++i;
@@ -824,11 +843,25 @@ static void enqueue_body(gl_mesh_s *m, gl_prec_s *p, const cplx_t<T> *psi, const
                                                                W.jp2.get(), p->mp_out.get(), (double2 *)W.q.get(),
                                                                part, stop);
             } else {
-                double jb = (double)nnz * (sizeof(C) + 4) + (double)n * (2 * sizeof(T) + 3 * sizeof(C));
-                // a complex FMA (8 flops) per stored entry; per row the local terms
-                // (K_ii - 1 + 2|psi|^2) z + psi^2 conj(z) (20) and the dot (5)
-                ProfScope ps("jz", jb, ks, 8.0 * (double)nnz + 25.0 * (double)n);
-                k_jz<C, T><<<RED_BLOCKS, RED_THREADS, 0, ks>>>(n, K, kd, vol, psi, z, W.q.get(), part, stop);
+                bool lat64 = false;
+                if constexpr (std::is_same<T, double>::value) lat64 = m->lat64_ok && p && p->lattice64;
+                if (lat64) {
+                    // own z, K_ii, |V|, psi and the written q per row (48 + 16 B); the
+                    // neighbours' z and the tables from cache; per row the six
+                    // complex FMAs, the 1 / |V| scaling, the local terms and the dot
+                    if constexpr (std::is_same<T, double>::value) {
+                        ProfScope ps("jz", (double)n * (3 * sizeof(C) + 2 * sizeof(T)), ks,
+                                     8.0 * (double)nnz + 28.0 * (double)n);
+                        k_jz_lat64<<<RED_BLOCKS, RED_THREADS, 0, ks>>>(n, lattice_view64(m), kd, psi, z, W.q.get(),
+                                                                      part, stop);
+                    }
+                } else {
+                    double jb = (double)nnz * (sizeof(C) + 4) + (double)n * (2 * sizeof(T) + 3 * sizeof(C));
+                    // a complex FMA (8 flops) per stored entry; per row the local terms
+                    // (K_ii - 1 + 2|psi|^2) z + psi^2 conj(z) (20) and the dot (5)
+                    ProfScope ps("jz", jb, ks, 8.0 * (double)nnz + 25.0 * (double)n);
+                    k_jz<C, T><<<RED_BLOCKS, RED_THREADS, 0, ks>>>(n, K, kd, vol, psi, z, W.q.get(), part, stop);
+                }
             }
         }
         note_launch(2);
@@ -1401,6 +1434,11 @@ gl_status jacobian_solve_p(gl_mesh_s *m, gl_prec_s *p, const double2 *psi_p, con
     inf.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     inf.warmstart_used = o.warmstart ? warmstart_used(o.warmstart, s) : (o.warmstart_hint ? 1 : 0);
     inf.lattice_stencil = (p && p->has32 && o.precision != GL_FP64 && p->lattice && m->lat_ok) ? 1 : 0;
+    // MINRES's FP64 Jacobian (FP64 solves; mixed-preconditioner solves without the
+    // double-float apply or after its stall) read the FP64 tables
+    const bool fp64_j = o.precision == GL_FP64 ||
+                        (o.precision == GL_MIXED_PRECOND && (!inf.df_jacobian || inf.stall_restarts));
+    inf.jacobian_tables = (fp64_j && m->lat64_ok && p && p->lattice64) ? 1 : 0;
     if (p && p->rinf) {
         // measured: every application ran its own number of cycles, each followed by a residual
         const RinfDev R = rinf_read(p, s);

@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(256) k_gs_lat2(int64_t lo, int64_t hi, Lattice
     const uint32_t N = (uint32_t)L.N;
     const uint32_t r = (uint32_t)(p - base);  // even
     const uint32_t v0 = 2u * r;
-    const uint32_t i0 = v0 % N, row = v0 / N, j = row % N, k = row / N;
+    const uint32_t row = L.dN.div(v0), k = L.dN.div(row);
+    const uint32_t i0 = v0 - row * N, j = row - k * N;
     const uint32_t a = ((i0 + j + k) & 1u) != c ? 1u : 0u;
     const uint32_t i = i0 + a;
     float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);

@@ -128,6 +128,44 @@ def test_double_fp32_jacobian_matches_oracle(oracle_mod, dim, N):
         gl.gl_mesh_destroy(m)
 
 
+@pytest.mark.parametrize("dim,N", EVEN, ids=lambda p: str(p))
+def test_fp64_lattice_jacobian_matches_oracle(oracle_mod, dim, N):
+    """The FP64 Jacobian from the lattice tables (matrix-free; gl_jacobian_apply with
+    GL_APPLY_FP64_TABLES, and MINRES's FP64 apply with options.lattice = 2) against
+    the oracle's J, element by element at 64 eps64 of the row's magnitude sum; an
+    FP64 solve with lattice = 2 reports that it ran from the tables, with lattice =
+    1 from the stored K; the two solves (to 1e-10) agree within one iteration and
+    1e-8 in the solution."""
+    om = oracle_mod.Mesh(dim, N, 1.0, bhat(dim))
+    m = gl.gl_mesh_create(dim, N, 1.0, bhat(dim))
+    n = om.n
+    try:
+        psi, phi = gi.disk(n, 37), gi.complex_normal(n, 38)
+        y = torch.empty(n, dtype=torch.complex128, device=DEV)
+        gl.gl_jacobian_apply(m, dev(psi), dev(phi), y, precision=gl.GL_APPLY_FP64_TABLES)
+        ref = om.jacobian(psi, phi)
+        rp, ci, v = om.khat_csr()
+        row = np.add.reduceat(np.abs(v) * np.abs(phi)[ci], rp[:-1]) / om.volumes() + \
+            (1 + 3 * np.abs(psi) ** 2) * np.abs(phi)
+        rel = np.abs(host(y) - ref) / row
+        print(f"{dim}d N={N}: FP64 lattice J, max |y - y_ref| / |row| = {rel.max():.2e} eps64 x "
+              f"{rel.max() / 2.0 ** -52:.1f}")
+        assert rel.max() <= 64 * 2.0 ** -52
+        b = dev(gi.complex_normal(n, 39))
+        xs, infos = [], []
+        for lat in (2, 1):
+            x = torch.zeros(n, dtype=torch.complex128, device=DEV)
+            st, info = gl.gl_jacobian_solve(m, dev(psi), None, b, x, gl.options(max_coarse=64, lattice=lat))
+            assert st == 0 and info.converged
+            xs.append(x)
+            infos.append(info)
+        assert infos[0].jacobian_tables == 1 and infos[1].jacobian_tables == 0
+        assert abs(infos[0].iters - infos[1].iters) <= 1
+        assert float(torch.linalg.norm(xs[0] - xs[1]) / torch.linalg.norm(xs[1])) <= 1e-8
+    finally:
+        gl.gl_mesh_destroy(m)
+
+
 def test_double_fp32_jacobian_needs_even_n():
     m = gl.gl_mesh_create(2, 17, 1.0)
     try:
@@ -135,6 +173,13 @@ def test_double_fp32_jacobian_needs_even_n():
         y = torch.empty_like(x)
         with pytest.raises(gl.GLError):
             gl.gl_jacobian_apply(m, x, x, y, precision=gl.GL_MIXED_PRECOND)
+        with pytest.raises(gl.GLError):
+            gl.gl_jacobian_apply(m, x, x, y, precision=gl.GL_APPLY_FP64_TABLES)
+        # an odd-N mesh has no lattice stencil: the FP64 solve streams the stored K
+        b = dev(gi.complex_normal(17 * 17, 40))
+        z = torch.zeros_like(b)
+        st, info = gl.gl_jacobian_solve(m, x, None, b, z, gl.options(max_coarse=64, lattice=2))
+        assert st == 0 and info.jacobian_tables == 0
     finally:
         gl.gl_mesh_destroy(m)
 
