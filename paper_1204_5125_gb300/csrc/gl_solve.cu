@@ -6,7 +6,11 @@
 // The Lanczos/Givens scalars live on the device; every reduction writes one
 // partial per block of a fixed grid and is summed in index order, so results do
 // not depend on scheduling.  A device status word stops all kernels once the
-// solve has converged or failed; the host polls it every few iterations.
+// solve has converged or failed.  A solve is one CUDA graph that loops on the
+// device (a WHILE conditional node over bodies of six iterations, the later
+// ones in IF nodes that the previous iteration's scalar kernel opens), so the
+// host waits once; options.device_loop = 0 replays the body graph from the host
+// instead, reading the status word between replays.
 //
 // GL_MIXED: FP64 defect correction x <- x + e around inner MINRES solves of
 // J e = r whose vectors, Jacobian applies and V-cycles are FP32 (dots and

@@ -278,8 +278,26 @@ __device__ __forceinline__ C group_row(const CsrGView<C> &A, int64_t row, int la
     acc.x = 0;
     acc.y = 0;
     if (row >= 0) {
-        int64_t q1 = A.rp[row + 1];
-        for (int64_t q = A.rp[row] + lane; q < q1; q += G) {
+        const int64_t q1 = A.rp[row + 1];
+        int64_t q = A.rp[row] + lane;
+        // four entries per step with all their loads issued first (long rows, such
+        // as a restriction to a small coarse level, would otherwise wait for one
+        // column and one gather per entry in turn); the sum runs in the same order
+        for (; q + 3 * G < q1; q += 4 * G) {
+            int32_t c[4];
+            C v[4], xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) c[u] = __ldg(A.col + q + u * G);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                v[u] = A.val[q + u * G];
+                if (c[u] < lim) xv[u] = x[c[u]];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c[u] < lim) cfma(acc, v[u], xv[u]);
+        }
+        for (; q < q1; q += G) {
             int32_t c = __ldg(A.col + q);
             if (c < lim) cfma(acc, A.val[q], x[c]);
         }
