@@ -226,3 +226,34 @@ def test_setup_like_reuses_the_symbolic_hierarchy(autotune):
     finally:
         gl.gl_precond_destroy(G1)
         gl.gl_mesh_destroy(m)
+
+
+def test_resume_from_checkpoint(tmp_path):
+    """A continuation stopped after a few points, saved (mu, psi, the points so
+    far) and reloaded, restarts from exactly the saved state on a mesh made from
+    the saved description, and continues."""
+    from paper_1204_5125_gb300 import state
+
+    N, edge = 33, 10.0
+    kw = dict(ds=0.1, ds_max=0.3, mu_max=1.2, newton_tol=1e-9, newton_maxit=8, solver=dict(tol=1e-8, max_coarse=512))
+    m = gl.gl_mesh_create(2, N, 0.0, edge=edge)
+    try:
+        psi = torch.ones(N * N, dtype=torch.complex128, device=DEV)
+        st, pts = gl.gl_continuation(m, psi, gl.cont_options(max_steps=4, **kw), max_points=16)
+        assert st == 0 and len(pts) == 5
+        state.save_state(str(tmp_path), dim=2, N=N, mu=pts[-1]["mu"], psi=psi, edge=edge, points=pts)
+    finally:
+        gl.gl_mesh_destroy(m)
+    s = state.load_state(str(tmp_path))
+    assert s["points"][-1]["mu"] == pts[-1]["mu"]
+    m = gl.gl_mesh_create(2, s["N"], s["mu"], edge=s["edge"])
+    try:
+        psi2 = torch.from_numpy(s["psi"]).to(DEV)
+        assert float(gl.gl_energy(m, psi2)) == pytest.approx(pts[-1]["energy"], rel=1e-12)
+        st, more = gl.gl_continuation(m, psi2, gl.cont_options(max_steps=3, **kw), max_points=16)
+        assert st == 0 and len(more) == 4
+        assert more[0]["mu"] == pytest.approx(pts[-1]["mu"], abs=1e-14)
+        assert more[0]["energy"] == pytest.approx(pts[-1]["energy"], rel=1e-12)
+        assert all(p["newton_steps"] <= 8 for p in more)
+    finally:
+        gl.gl_mesh_destroy(m)
