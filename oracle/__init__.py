@@ -86,6 +86,10 @@ def lib():
             L.glref_mesh_create_edge.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _f64p, _f64p]
             L.glref_mesh_create_dipole.restype = vp
             L.glref_mesh_create_dipole.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _f64p, _f64p]
+            L.glref_mesh_create_simplicial.restype = vp
+            L.glref_mesh_create_simplicial.argtypes = [C.c_int, C.c_int64, _f64p, C.c_int64,
+                                                       np.ctypeslib.ndpointer(np.int32, flags="C"), C.c_double,
+                                                       vp, vp, vp]
             L.glref_set_threads.argtypes = [C.c_int]
             L.glref_get_threads.restype = C.c_int
             L.glref_max_threads.restype = C.c_int
@@ -182,9 +186,17 @@ class Mesh:
     square/cube of side `edge` centred at the origin, with A(x) = (mu/2) bhat x x + a0."""
 
     def __init__(self, dim: int, N: int, mu: float, bhat=(0.0, 0.0, 1.0), a0=(0.0, 0.0, 0.0), edge: float = 1.0,
-                 dipole=None):
+                 dipole=None, _ptr=None):
         """dipole=(x0, m): A = mu A_d, the field of a dipole of moment m at x0 (bhat, a0 unused)."""
         self._lib = lib()
+        if _ptr is not None:  # made by from_simplices
+            self.ptr = _ptr
+            self.dim, self.N, self.mu, self.edge = dim, 0, float(mu), 0.0
+            self.bhat, self.a0 = tuple(float(c) for c in bhat), (0.0, 0.0, 0.0)
+            self.n = self._lib.glref_mesh_n(self.ptr)
+            self.nedges = self._lib.glref_mesh_nedges(self.ptr)
+            self.nnz = self._lib.glref_mesh_nnz(self.ptr)
+            return
         b = np.ascontiguousarray(bhat, dtype=np.float64)
         a = np.ascontiguousarray(a0, dtype=np.float64)
         if dipole is None:
@@ -200,6 +212,28 @@ class Mesh:
         self.n = self._lib.glref_mesh_n(self.ptr)
         self.nedges = self._lib.glref_mesh_nedges(self.ptr)
         self.nnz = self._lib.glref_mesh_nnz(self.ptr)
+
+    @classmethod
+    def from_simplices(cls, dim: int, x, simplices, mu: float, bhat=(0.0, 0.0, 1.0), dipole=None):
+        """A general simplicial mesh: x (n x 3, or n x dim), simplices (m x (dim + 1))
+        node ids; A = (mu/2) bhat x x, or mu A_d with dipole=(x0, m)."""
+        L = lib()
+        x = np.asarray(x, dtype=np.float64)
+        if x.shape[1] == 2:
+            x = np.hstack([x, np.zeros((x.shape[0], 1))])
+        x = np.ascontiguousarray(x)
+        sp = np.ascontiguousarray(simplices, dtype=np.int32)
+        b = np.ascontiguousarray(bhat, dtype=np.float64)
+        xd = md = None
+        if dipole is not None:
+            xd = np.ascontiguousarray(dipole[0], dtype=np.float64)
+            md = np.ascontiguousarray(dipole[1], dtype=np.float64)
+        ptr = L.glref_mesh_create_simplicial(dim, x.shape[0], x.ravel(), sp.shape[0], sp.ravel(), float(mu),
+                                             b.ctypes.data, xd.ctypes.data if xd is not None else None,
+                                             md.ctypes.data if md is not None else None)
+        if not ptr:
+            raise ValueError("glref_mesh_create_simplicial failed")
+        return cls(dim, 0, mu, bhat=bhat, _ptr=ptr)
 
     def __del__(self):
         p = getattr(self, "ptr", None)

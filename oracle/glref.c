@@ -294,7 +294,7 @@ int glref_simplex_alpha_cot(const double *p, double *alpha) {
 /* ------------------------------------------------------------------ */
 
 typedef struct glref_mesh {
-    int dim, N;
+    int dim, N;                 /* N = 0: a general simplicial mesh (glref_mesh_create_simplicial) */
     int64_t n;
     double h, mu, bhat[3], a0[3], edge;
     int dipole;                 /* 0: A = (mu/2) bhat x x + a0; 1: A = mu A_d (dipole at xd, moment md) */
@@ -402,9 +402,10 @@ double glref_edge_integral1(const glref_mesh *m, const double *xa, const double 
 /* per-node neighbour table used while summing simplex contributions */
 typedef struct {
     int64_t n;
+    int cap;        /* neighbours per node */
     int32_t *cnt;
-    int32_t *nb;    /* n x MAXDEG */
-    double *al;     /* n x MAXDEG */
+    int32_t *nb;    /* n x cap */
+    double *al;     /* n x cap */
 } edge_table;
 
 static void table_add(edge_table *t, int64_t a, int64_t b, double alpha) {
@@ -413,15 +414,15 @@ static void table_add(edge_table *t, int64_t a, int64_t b, double alpha) {
         a = b;
         b = s;
     }
-    int32_t *nb = t->nb + a * GLREF_MAXDEG;
-    double *al = t->al + a * GLREF_MAXDEG;
+    int32_t *nb = t->nb + a * t->cap;
+    double *al = t->al + a * t->cap;
     for (int s = 0; s < t->cnt[a]; ++s)
         if (nb[s] == b) {
             al[s] += alpha;
             return;
         }
-    if (t->cnt[a] >= GLREF_MAXDEG) {
-        fprintf(stderr, "glref: node degree above %d\n", GLREF_MAXDEG);
+    if (t->cnt[a] >= t->cap) {
+        fprintf(stderr, "glref: node degree above %d\n", t->cap);
         abort();
     }
     nb[t->cnt[a]] = (int32_t)b;
@@ -491,75 +492,21 @@ glref_mesh *glref_mesh_create_dipole(int dim, int N, double edge, double mu, con
     return mesh_assemble(m);
 }
 
-static glref_mesh *mesh_assemble(glref_mesh *m) {
-    const int dim = m->dim, N = m->N;
-    const double edge = m->edge;
-    m->n = (dim == 2) ? (int64_t)N * N : (int64_t)N * N * N;
-    m->h = edge / (N - 1);
-    int64_t n = m->n;
-    int nz = (dim == 2) ? 1 : N;
-
-    /* nodes of the square/cube centred at the origin */
-    const double x0 = -0.5 * edge;
-    m->x = xcalloc((size_t)n * 3, sizeof(double));
-    for (int k = 0; k < nz; ++k)
-        for (int j = 0; j < N; ++j)
-            for (int i = 0; i < N; ++i) {
-                int64_t id = node_id(m, i, j, k);
-                m->x[3 * id + 0] = x0 + i * m->h;
-                m->x[3 * id + 1] = x0 + j * m->h;
-                m->x[3 * id + 2] = (dim == 3) ? x0 + k * m->h : 0.0;
-            }
-
-    /* control volumes: the Voronoi cell of a lattice node is the cube of side h
-     * around it, clipped to the domain: h^d 2^(-number of boundary coordinates) */
-    m->vol = xcalloc((size_t)n, sizeof(double));
-    for (int k = 0; k < nz; ++k)
-        for (int j = 0; j < N; ++j)
-            for (int i = 0; i < N; ++i) {
-                int nb = (i == 0 || i == N - 1) + (j == 0 || j == N - 1);
-                if (dim == 3) nb += (k == 0 || k == N - 1);
-                m->vol[node_id(m, i, j, k)] = pow(m->h, dim) / (double)(1 << nb);
-            }
-
-    /* Eq. fhat: alpha_jk = sum over the simplices adjacent to edge jk of the
-     * simplex coefficients */
-    edge_table t;
-    t.n = n;
-    t.cnt = xcalloc((size_t)n, sizeof(int32_t));
-    t.nb = xcalloc((size_t)n * GLREF_MAXDEG, sizeof(int32_t));
-    t.al = xcalloc((size_t)n * GLREF_MAXDEG, sizeof(double));
-    int ncell_z = (dim == 2) ? 1 : N - 1;
-    int ea[6], eb[6];
-    int nse = simplex_edges(dim, ea, eb);
-    for (int k = 0; k < ncell_z; ++k)
-        for (int j = 0; j < N - 1; ++j)
-            for (int i = 0; i < N - 1; ++i) {
-                int64_t vid[6][4];
-                int ns = cell_simplices(m, i, j, k, vid);
-                for (int s = 0; s < ns; ++s) {
-                    double p[12];
-                    for (int v = 0; v <= dim; ++v)
-                        for (int c = 0; c < 3; ++c) p[3 * v + c] = m->x[3 * vid[s][v] + c];
-                    double al[6];
-                    int rc = (dim == 2) ? glref_simplex_alpha_cot(p, al) : glref_simplex_alpha_linsys(3, p, al);
-                    if (rc) {
-                        fprintf(stderr, "glref: degenerate simplex\n");
-                        abort();
-                    }
-                    for (int e = 0; e < nse; ++e) table_add(&t, vid[s][ea[e]], vid[s][eb[e]], al[e]);
-                }
-            }
-
+/* From the per-node table of summed edge coefficients: the kept edges (those
+ * with |alpha| > 1e-12 max |alpha|; O2), their link phases (Eq. link variable)
+ * and K-hat (Eq. discr kin energy with Remark rmk:dk).  Frees the table. */
+static void mesh_edges_khat(glref_mesh *m, edge_table *tp) {
+    edge_table t = *tp;
+    const int64_t n = m->n;
     /* edges whose coefficient vanishes (|alpha| <= 1e-12 max |alpha|) are dropped */
     double amax = 0;
     for (int64_t a = 0; a < n; ++a)
-        for (int s = 0; s < t.cnt[a]; ++s) amax = fmax(amax, fabs(t.al[a * GLREF_MAXDEG + s]));
+        for (int s = 0; s < t.cnt[a]; ++s) amax = fmax(amax, fabs(t.al[a * t.cap + s]));
     double cut = 1e-12 * amax;
     int64_t ne = 0;
     for (int64_t a = 0; a < n; ++a)
         for (int s = 0; s < t.cnt[a]; ++s)
-            if (fabs(t.al[a * GLREF_MAXDEG + s]) > cut) ++ne;
+            if (fabs(t.al[a * t.cap + s]) > cut) ++ne;
     m->ne = ne;
     m->ej = xcalloc((size_t)ne, sizeof(int32_t));
     m->ek = xcalloc((size_t)ne, sizeof(int32_t));
@@ -568,8 +515,8 @@ static glref_mesh *mesh_assemble(glref_mesh *m) {
     int64_t q = 0;
     for (int64_t a = 0; a < n; ++a) {
         /* neighbours of a in ascending order */
-        int32_t *nb = t.nb + a * GLREF_MAXDEG;
-        double *al = t.al + a * GLREF_MAXDEG;
+        int32_t *nb = t.nb + a * t.cap;
+        double *al = t.al + a * t.cap;
         int c = t.cnt[a];
         for (int s = 1; s < c; ++s) {
             int32_t kb = nb[s];
@@ -648,6 +595,148 @@ static glref_mesh *mesh_assemble(glref_mesh *m) {
     }
     free(fill);
     free(deg);
+}
+
+static glref_mesh *mesh_assemble(glref_mesh *m) {
+    const int dim = m->dim, N = m->N;
+    const double edge = m->edge;
+    m->n = (dim == 2) ? (int64_t)N * N : (int64_t)N * N * N;
+    m->h = edge / (N - 1);
+    int64_t n = m->n;
+    int nz = (dim == 2) ? 1 : N;
+
+    /* nodes of the square/cube centred at the origin */
+    const double x0 = -0.5 * edge;
+    m->x = xcalloc((size_t)n * 3, sizeof(double));
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < N; ++j)
+            for (int i = 0; i < N; ++i) {
+                int64_t id = node_id(m, i, j, k);
+                m->x[3 * id + 0] = x0 + i * m->h;
+                m->x[3 * id + 1] = x0 + j * m->h;
+                m->x[3 * id + 2] = (dim == 3) ? x0 + k * m->h : 0.0;
+            }
+
+    /* control volumes: the Voronoi cell of a lattice node is the cube of side h
+     * around it, clipped to the domain: h^d 2^(-number of boundary coordinates) */
+    m->vol = xcalloc((size_t)n, sizeof(double));
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < N; ++j)
+            for (int i = 0; i < N; ++i) {
+                int nb = (i == 0 || i == N - 1) + (j == 0 || j == N - 1);
+                if (dim == 3) nb += (k == 0 || k == N - 1);
+                m->vol[node_id(m, i, j, k)] = pow(m->h, dim) / (double)(1 << nb);
+            }
+
+    /* Eq. fhat: alpha_jk = sum over the simplices adjacent to edge jk of the
+     * simplex coefficients */
+    edge_table t;
+    t.n = n;
+    t.cap = GLREF_MAXDEG;
+    t.cnt = xcalloc((size_t)n, sizeof(int32_t));
+    t.nb = xcalloc((size_t)n * GLREF_MAXDEG, sizeof(int32_t));
+    t.al = xcalloc((size_t)n * GLREF_MAXDEG, sizeof(double));
+    int ncell_z = (dim == 2) ? 1 : N - 1;
+    int ea[6], eb[6];
+    int nse = simplex_edges(dim, ea, eb);
+    for (int k = 0; k < ncell_z; ++k)
+        for (int j = 0; j < N - 1; ++j)
+            for (int i = 0; i < N - 1; ++i) {
+                int64_t vid[6][4];
+                int ns = cell_simplices(m, i, j, k, vid);
+                for (int s = 0; s < ns; ++s) {
+                    double p[12];
+                    for (int v = 0; v <= dim; ++v)
+                        for (int c = 0; c < 3; ++c) p[3 * v + c] = m->x[3 * vid[s][v] + c];
+                    double al[6];
+                    int rc = (dim == 2) ? glref_simplex_alpha_cot(p, al) : glref_simplex_alpha_linsys(3, p, al);
+                    if (rc) {
+                        fprintf(stderr, "glref: degenerate simplex\n");
+                        abort();
+                    }
+                    for (int e = 0; e < nse; ++e) table_add(&t, vid[s][ea[e]], vid[s][eb[e]], al[e]);
+                }
+            }
+
+    mesh_edges_khat(m, &t);
+    return m;
+}
+
+/* A mesh given by its nodes and simplices (the paper's Delaunay meshes of its
+ * test domains, Sec. 4; any conforming simplicial mesh).  x: n x 3 coordinates
+ * (z = 0 in 2D); simp: ns x (dim + 1) node ids.  The coefficient of each edge of
+ * each simplex (the cotangent formula in 2D, the linear system of the corollary
+ * in 3D) is summed per edge in simplex order (Eq. fhat).  The control volumes
+ * come from the same coefficients: by the corollary's identity taken over an
+ * orthonormal basis, a simplex's volume is sum_e alpha_e |e|^2 / d, and the part
+ * alpha_e |e|^2 / d of edge e lies half at each end, so |V_j| = sum_k alpha_jk
+ * |x_j - x_k|^2 / (2 d) over the kept edges of j (the Voronoi region of x_j
+ * within the mesh, for well-centred simplices; Eq. mass lumping).  Link phases
+ * of A = (mu / 2) bhat x x, or of mu A_d when xd and md are given.  Returns NULL
+ * on invalid input. */
+void glref_mesh_destroy(glref_mesh *m);
+glref_mesh *glref_mesh_create_simplicial(int dim, int64_t n, const double *x, int64_t ns, const int32_t *simp,
+                                         double mu, const double *bhat, const double *xd, const double *md) {
+    if ((dim != 2 && dim != 3) || n < 2 || ns < 1 || !x || !simp) return NULL;
+    for (int64_t q = 0; q < ns * (dim + 1); ++q)
+        if (simp[q] < 0 || simp[q] >= n) return NULL;
+    glref_mesh *m = xcalloc(1, sizeof *m);
+    m->dim = dim;
+    m->N = 0;
+    m->n = n;
+    m->mu = mu;
+    double b[3] = {0, 0, 1}, nb = 1;
+    if (bhat) {
+        nb = sqrt(dot3(bhat, bhat));
+        for (int c = 0; c < 3; ++c) b[c] = bhat[c] / nb;
+    }
+    for (int c = 0; c < 3; ++c) m->bhat[c] = b[c];
+    if (xd && md) {
+        m->dipole = 1;
+        for (int c = 0; c < 3; ++c) {
+            m->xd[c] = xd[c];
+            m->md[c] = md[c];
+        }
+    }
+    m->x = xcalloc((size_t)n * 3, sizeof(double));
+    memcpy(m->x, x, sizeof(double) * 3 * (size_t)n);
+    if (dim == 2)
+        for (int64_t j = 0; j < n; ++j) m->x[3 * j + 2] = 0.0;
+    edge_table t;
+    t.n = n;
+    t.cap = 64;
+    t.cnt = xcalloc((size_t)n, sizeof(int32_t));
+    t.nb = xcalloc((size_t)n * t.cap, sizeof(int32_t));
+    t.al = xcalloc((size_t)n * t.cap, sizeof(double));
+    int ea[6], eb[6];
+    const int nse = simplex_edges(dim, ea, eb);
+    for (int64_t q = 0; q < ns; ++q) {
+        const int32_t *v = simp + q * (dim + 1);
+        double p[12], al[6];
+        for (int k = 0; k <= dim; ++k)
+            for (int c = 0; c < 3; ++c) p[3 * k + c] = m->x[3 * (int64_t)v[k] + c];
+        int rc = (dim == 2) ? glref_simplex_alpha_cot(p, al) : glref_simplex_alpha_linsys(3, p, al);
+        if (rc) {
+            free(t.cnt);
+            free(t.nb);
+            free(t.al);
+            glref_mesh_destroy(m);
+            return NULL;
+        }
+        for (int e = 0; e < nse; ++e) table_add(&t, v[ea[e]], v[eb[e]], al[e]);
+    }
+    mesh_edges_khat(m, &t);
+    /* control volumes: the kept edges in lexicographic order reach each node in
+     * the order of its neighbours' ids (those below it first) */
+    m->vol = xcalloc((size_t)n, sizeof(double));
+    for (int64_t e = 0; e < m->ne; ++e) {
+        const int64_t a = m->ej[e], b = m->ek[e];
+        double d[3];
+        for (int c = 0; c < 3; ++c) d[c] = m->x[3 * b + c] - m->x[3 * a + c];
+        const double part = m->alpha[e] * dot3(d, d) / (2.0 * dim);
+        m->vol[a] += part;
+        m->vol[b] += part;
+    }
     return m;
 }
 
@@ -1173,8 +1262,9 @@ void glref_precond_destroy(glref_prec *p) {
  *   tentative P_tent[i, agg(i)] = B_i / ||B restricted to agg(i)||;
  *   P = (I - omega D^-1 A) P_tent with omega = 4 / (3 rho(D^-1 A));
  *   Galerkin A_c = P^H A P, made exactly Hermitian as (A_c + A_c^H)/2;
- *   colours: red-black (i+j+k mod 2) on the finest lattice level,
- *   Jones-Plassmann below; coarsest level factored by dense Cholesky. */
+ *   colours: red-black (i+j+k mod 2) on the finest lattice level, the
+ *   options' colouring below and on the finest level of a general simplicial
+ *   mesh; coarsest level factored by dense Cholesky. */
 glref_prec *glref_precond_setup(const glref_mesh *m, const cplx *psi, const glref_options *o) {
     glref_prec *p = xcalloc(1, sizeof *p);
     p->mesh = m;
@@ -1209,7 +1299,7 @@ glref_prec *glref_precond_setup(const glref_mesh *m, const cplx *psi, const glre
         int64_t nl = L->A.n;
         /* colours */
         L->color = xcalloc((size_t)nl, sizeof(int32_t));
-        if (l == 0) {
+        if (l == 0 && m->N > 0) {
             int nz = (m->dim == 2) ? 1 : m->N;
             for (int k = 0; k < nz; ++k)
                 for (int j = 0; j < m->N; ++j)
