@@ -196,6 +196,25 @@ GL_API gl_status gl_mesh_create(int dim, int n_per_side, double mu, const double
  * square of edge 10). */
 GL_API gl_status gl_mesh_create_edge(int dim, int n_per_side, double edge, double mu, const double *bhat_host,
                                      void *stream, gl_mesh *out);
+/* A general simplicial mesh (Sec. 3: any conforming Delaunay triangulation; the
+ * paper's test domains of Sec. 4 are meshed this way).  x_host: n x 3 node
+ * coordinates (the third ignored in 2D); simplices_host: ns x (dim + 1) node ids
+ * (int32).  Per simplex the edge coefficients (the cotangent formula in 2D, the
+ * linear system of the corollary in 3D) are summed per edge (Eq. fhat); edges
+ * with |alpha| <= 1e-12 max |alpha| are dropped; the link phases are those of
+ * A = (mu/2) bhat x x (bhat NULL: e_z; normalised) or, with dipole_x0 and
+ * dipole_m, of mu A_d (8-point Gauss-Legendre along each edge); the control
+ * volumes are the dual of the coefficients, |V_j| = sum_k alpha_jk
+ * |x_j - x_k|^2 / (2 dim) (the Voronoi region of x_j for well-centred Delaunay
+ * simplices; Eq. mass lumping).  The finest level is coloured like a coarse level
+ * (round-based smallest-last) instead of red-black, and the lattice stencil is
+ * off.  GL_ERR_ARG on bad ids or a degenerate simplex, GL_ERR_CAPACITY on a node
+ * with more than 64 neighbours.  Synchronises `stream`. */
+GL_API gl_status gl_mesh_create_simplicial(int dim, int64_t n, const double *x_host, int64_t ns,
+                                           const int32_t *simplices_host, double mu, const double *bhat,
+                                           const double *dipole_x0, const double *dipole_m, void *stream,
+                                           gl_mesh *out);
+
 /* The same domain in mu A_d, the field of a magnetic dipole (Sec. 4):
  * A_d(x) = m x (x - x0) / |x - x0|^3, m = mom_host, x0 = x0_host (3 doubles
  * each; the paper takes m = e_z and x0 = (0,0,1) in 2D, (0,0,6) in 3D).  The

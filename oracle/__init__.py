@@ -113,6 +113,8 @@ def lib():
             L.glref_inner_r.argtypes = [vp, _c128p, _c128p]
             L.glref_simplex_alpha_linsys.restype = C.c_int
             L.glref_simplex_alpha_linsys.argtypes = [C.c_int, _f64p, _f64p]
+            L.glref_simplex_alpha_dihedral.restype = C.c_int
+            L.glref_simplex_alpha_dihedral.argtypes = [_f64p, _f64p]
             L.glref_simplex_alpha_cot.restype = C.c_int
             L.glref_simplex_alpha_cot.argtypes = [_f64p, _f64p]
             L.glref_hash32.restype = C.c_uint32
@@ -501,6 +503,9 @@ def simplex_alpha(dim: int, verts, method: str = "linsys"):
     if method == "cot":
         assert dim == 2
         rc = lib().glref_simplex_alpha_cot(p, a)
+    elif method == "dihedral":
+        assert dim == 3
+        rc = lib().glref_simplex_alpha_dihedral(p, a)
     else:
         rc = lib().glref_simplex_alpha_linsys(dim, p, a)
     if rc:

@@ -272,6 +272,46 @@ int glref_simplex_alpha_linsys(int dim, const double *p, double *alpha) {
 /* Triangle edge coefficients from the cotangent formula of the Remark after
  * Cor. "simplex": alpha_ij = 1/2 t / sqrt(1 - t^2), t = cosine of the angle at
  * the vertex opposite edge (i, j). */
+/* Tetrahedron: the closed form of the same coefficients, alpha_ij = |e_kl|
+ * cot(theta_kl) / 6, with e_kl the edge opposite ij and theta_kl the dihedral
+ * angle there (between the faces kli and klj): these weights satisfy
+ * sum_e alpha_e e e^T = |S| I, the corollary's identity, so they are its
+ * system's unique solution, without forming the (for flat tetrahedra badly
+ * conditioned) 6 x 6 system.  cot theta = (a . b) / |a x b| with a, b the parts of
+ * x_i - x_k and x_j - x_k perpendicular to e_kl. */
+int glref_simplex_alpha_dihedral(const double *p, double *alpha) {
+    int ea[6], eb[6];
+    simplex_edges(3, ea, eb);
+    for (int s = 0; s < 6; ++s) {
+        int i = ea[s], j = eb[s], k = -1, l = -1;
+        for (int t = 0; t < 4; ++t)
+            if (t != i && t != j) {
+                if (k < 0)
+                    k = t;
+                else
+                    l = t;
+            }
+        double e[3], a[3], b[3];
+        for (int c = 0; c < 3; ++c) {
+            e[c] = p[3 * l + c] - p[3 * k + c];
+            a[c] = p[3 * i + c] - p[3 * k + c];
+            b[c] = p[3 * j + c] - p[3 * k + c];
+        }
+        const double ee = dot3(e, e), L = sqrt(ee);
+        if (!(ee > 0)) return -1;
+        const double ae = dot3(a, e) / ee, be = dot3(b, e) / ee;
+        for (int c = 0; c < 3; ++c) {
+            a[c] -= ae * e[c];
+            b[c] -= be * e[c];
+        }
+        double x[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+        const double sn = sqrt(dot3(x, x));
+        if (!(sn > 0)) return -1;
+        alpha[s] = L * dot3(a, b) / (6.0 * sn);
+    }
+    return 0;
+}
+
 int glref_simplex_alpha_cot(const double *p, double *alpha) {
     int ea[6], eb[6];
     simplex_edges(2, ea, eb);
@@ -665,8 +705,8 @@ static glref_mesh *mesh_assemble(glref_mesh *m) {
 /* A mesh given by its nodes and simplices (the paper's Delaunay meshes of its
  * test domains, Sec. 4; any conforming simplicial mesh).  x: n x 3 coordinates
  * (z = 0 in 2D); simp: ns x (dim + 1) node ids.  The coefficient of each edge of
- * each simplex (the cotangent formula in 2D, the linear system of the corollary
- * in 3D) is summed per edge in simplex order (Eq. fhat).  The control volumes
+ * each simplex (the cotangent formula in 2D, its dihedral form in 3D) is summed
+ * per edge in simplex order (Eq. fhat).  The control volumes
  * come from the same coefficients: by the corollary's identity taken over an
  * orthonormal basis, a simplex's volume is sum_e alpha_e |e|^2 / d, and the part
  * alpha_e |e|^2 / d of edge e lies half at each end, so |V_j| = sum_k alpha_jk
@@ -715,7 +755,7 @@ glref_mesh *glref_mesh_create_simplicial(int dim, int64_t n, const double *x, in
         double p[12], al[6];
         for (int k = 0; k <= dim; ++k)
             for (int c = 0; c < 3; ++c) p[3 * k + c] = m->x[3 * (int64_t)v[k] + c];
-        int rc = (dim == 2) ? glref_simplex_alpha_cot(p, al) : glref_simplex_alpha_linsys(3, p, al);
+        int rc = (dim == 2) ? glref_simplex_alpha_cot(p, al) : glref_simplex_alpha_dihedral(p, al);
         if (rc) {
             free(t.cnt);
             free(t.nb);

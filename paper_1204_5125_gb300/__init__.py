@@ -29,7 +29,7 @@ __all__ = [
     "gl_warmstart_predict", "gl_warmstart_grad", "gl_warmstart_train", "gl_warmstart_adam_step", "GL_WS_NPARAM",
     "gl_last_error", "EXPORTED", "GL_CYCLES_INF", "ContOptions", "ContPoint", "gl_mesh_create_edge",
     "gl_mesh_set_mu", "gl_residual_dmu", "gl_energy", "cont_options", "gl_continuation", "gl_precond_setup_like",
-    "GL_COLOR_SL", "GL_COLOR_JP", "GL_COLOR_PSL", "gl_mesh_create_dipole", "gl_precond_apply_precision", "gl_precond_debug",
+    "GL_COLOR_SL", "GL_COLOR_JP", "GL_COLOR_PSL", "gl_mesh_create_dipole", "gl_mesh_create_simplicial", "gl_precond_apply_precision", "gl_precond_debug",
     "GL_DEBUG_STALL_SWEEPS", "GL_DEBUG_NEGATE_COARSEST", "gl_precond_level_sweep", "gl_measure_fma_peak",
     "gl_measure_sync_latency", "GL_APPLY_FP64_TABLES",
     "gl_profile_flops",
@@ -54,6 +54,7 @@ EXPORTED = [
     "gl_warmstart_set_params", "gl_warmstart_predict", "gl_warmstart_grad", "gl_warmstart_train",
     "gl_warmstart_adam_step", "gl_last_error", "gl_mesh_create_edge", "gl_mesh_set_mu", "gl_residual_dmu",
     "gl_energy", "gl_cont_options_default", "gl_continuation", "gl_precond_setup_like", "gl_mesh_create_dipole",
+    "gl_mesh_create_simplicial",
     "gl_precond_apply_precision", "gl_precond_debug", "gl_precond_level_sweep", "gl_measure_fma_peak",
     "gl_measure_sync_latency",
     "gl_profile_flops",
@@ -175,6 +176,8 @@ def library(build_if_missing: bool = True):
             "gl_mesh_create_edge": [C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_double), vp,
                                     C.POINTER(vp)],
             "gl_mesh_set_mu": [vp, C.c_double, vp],
+            "gl_mesh_create_simplicial": [C.c_int, C.c_int64, vp, C.c_int64, vp, C.c_double, vp, vp, vp, vp,
+                                          C.POINTER(vp)],
             "gl_mesh_create_dipole": [C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), vp, C.POINTER(vp)],
             "gl_precond_setup_like": [vp, vp, C.POINTER(Options), vp, vp, C.POINTER(vp)],
@@ -263,6 +266,25 @@ def gl_mesh_create_dipole(dim: int, n_per_side: int, edge: float, mu: float, x0=
     out = C.c_void_p()
     _check(library().gl_mesh_create_dipole(dim, n_per_side, float(edge), float(mu), a, b, _stream(stream),
                                            C.byref(out)))
+    return out
+
+
+def gl_mesh_create_simplicial(dim: int, x, simplices, mu: float, bhat=None, dipole=None, stream=None):
+    """A general simplicial mesh: x (n x 3, or n x dim), simplices (m x (dim + 1)) node
+    ids (host arrays); A = (mu/2) bhat x x, or mu A_d with dipole=(x0, m)."""
+    x = np.asarray(x, dtype=np.float64)
+    if x.shape[1] == 2:
+        x = np.hstack([x, np.zeros((x.shape[0], 1))])
+    x = np.ascontiguousarray(x)
+    sp = np.ascontiguousarray(simplices, dtype=np.int32)
+    b = None if bhat is None else (C.c_double * 3)(*bhat)
+    xd = md = None
+    if dipole is not None:
+        xd = (C.c_double * 3)(*dipole[0])
+        md = (C.c_double * 3)(*dipole[1])
+    out = C.c_void_p()
+    _check(library().gl_mesh_create_simplicial(dim, x.shape[0], x.ctypes.data, sp.shape[0], sp.ctypes.data,
+                                               float(mu), b, xd, md, _stream(stream), C.byref(out)))
     return out
 
 

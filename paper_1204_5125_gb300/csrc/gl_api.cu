@@ -102,6 +102,27 @@ gl_status gl_mesh_set_mu(gl_mesh m, double mu, void *stream) {
     });
 }
 
+gl_status gl_mesh_create_simplicial(int dim, int64_t n, const double *x_host, int64_t ns, const int32_t *simplices_host,
+                                    double mu, const double *bhat, const double *dipole_x0, const double *dipole_m,
+                                    void *stream, gl_mesh *out) {
+    return guard([&] {
+        GL_REQUIRE(out, GL_ERR_ARG, "NULL argument");
+        GL_REQUIRE((dipole_x0 == nullptr) == (dipole_m == nullptr), GL_ERR_ARG,
+                   "dipole_x0 and dipole_m must both be given or both be NULL");
+        *out = nullptr;
+        auto *m = new gl_mesh_s();
+        try {
+            mesh_create_simplicial(m, dim, n, x_host, ns, simplices_host, mu, bhat, dipole_x0, dipole_m,
+                                   as_stream(stream));
+        } catch (...) {
+            delete m;
+            throw;
+        }
+        *out = m;
+        return GL_OK;
+    });
+}
+
 gl_status gl_mesh_create_dipole(int dim, int n_per_side, double edge, double mu, const double *x0, const double *mom,
                                 void *stream, gl_mesh *out) {
     return guard([&] {

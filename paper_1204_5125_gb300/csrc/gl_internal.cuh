@@ -18,9 +18,13 @@ struct gl_mesh_s {
     gl::DBuf<int32_t> ej, ek;             // edges j < k, lexicographic
     gl::DBuf<double> ealpha, etheta, etheta1;  // etheta1: phase per unit mu
     gl::DBuf<double> kal, kth1;           // per stored K-hat entry: alpha and phase per unit mu (0 on the diagonal)
-    gl::DBuf<int32_t> color0;             // red-black colour of each node
-    // solve ordering: position p holds node perm[p]; red nodes occupy [0, nred)
+    gl::DBuf<int32_t> color0;             // finest-level colour of each node (red-black on a lattice)
+    // solve ordering: position p holds node perm[p]; red nodes occupy [0, nred);
+    // colour c occupies [cstart0[c], cstart0[c + 1]) (ncolors0 colours: 2 on a
+    // lattice, more on a general simplicial mesh)
     int64_t nred = 0;
+    int ncolors0 = 2;
+    std::vector<int64_t> cstart0;
     gl::DBuf<int32_t> perm, iperm;
     gl::Sell<double2> K;                  // off-diagonals of K = D^-1 K-hat (solve ordering)
     gl::DBuf<double> kdiag, volp;         // K_ii and |V_i| (solve ordering)
@@ -199,6 +203,12 @@ void mesh_create(gl_mesh_s *m, int dim, int N, double edge, double mu, const dou
 // new field strength: rewrites every phase-dependent value in place (K-hat, K, the
 // FP32 copy and the lattice tables); bumps m->version
 void mesh_set_mu(gl_mesh_s *m, double mu, cudaStream_t s);
+// a general simplicial mesh from host arrays (gl_mesh.cu)
+void mesh_create_simplicial(gl_mesh_s *m, int dim, int64_t n, const double *xyz_host, int64_t ns,
+                            const int32_t *simp_host, double mu, const double *bhat, const double *dip_x0,
+                            const double *dip_m, cudaStream_t s);
+// round-based smallest-last colouring of a graph (gl_setup.cu); returns the colour count
+int colour_graph_psl(const CsrDev &A, int32_t *color, cudaStream_t s);
 void mesh_ensure_fp32(gl_mesh_s *m, cudaStream_t s);
 template <typename C>
 void build_sell(int64_t nrows, int64_t ncols, const int32_t *perm, const int32_t *icol, const CsrDev &A,

@@ -716,6 +716,8 @@ void mesh_create(gl_mesh_s *m, int dim, int N, double edge, double mu, const dou
     k_rb_perm<<<grid_for(n, 256), 256, 0, s>>>(n, m->color0.get(), isred.get(), m->nred, m->perm.get(),
                                                m->iperm.get());
     GL_LAUNCH_CHECK();
+    m->ncolors0 = n > 1 ? 2 : 1;
+    m->cstart0 = n > 1 ? std::vector<int64_t>{0, m->nred, n} : std::vector<int64_t>{0, n};
 
     // K = D^-1 K-hat, off-diagonals as sliced ELL in the solve ordering
     m->kdiag.alloc(n);
@@ -770,4 +772,446 @@ void mesh_ensure_fp32(gl_mesh_s *m, cudaStream_t s) {
     m->has32 = true;
 }
 
+
+// ---------------------------------------------------------------- general simplicial meshes
+// Any conforming simplicial mesh (the paper's Delaunay meshes of its test domains,
+// Sec. 4): the coefficient of every edge of every simplex (the cotangent formula
+// in 2D, its dihedral form in 3D), summed
+// per edge over the simplices at the edge's first node in ascending simplex order
+// (Eq. fhat; a deterministic order), the edges with |alpha| <= 1e-12 max |alpha|
+// dropped (O2), the link phases of the uniform field or the dipole (Eq. link
+// variable), K-hat in node order (Eq. discr kin energy with Remark rmk:dk), and the
+// control volumes from the same coefficients (Eq. mass lumping, read as the dual of
+// the coefficients): |V_j| = sum_k alpha_jk |x_j - x_k|^2 / (2 d), the Voronoi
+// region of x_j for well-centred Delaunay simplices.  The finest level has no
+// lattice colouring: the nodes are coloured like a coarse level (round-based
+// smallest-last) and put in colour-major order.
+constexpr int GEN_MAXDEG = 64;  // neighbours of one node
+
+__global__ void k_gen_check(int64_t q, const int32_t *simp, int64_t n, int *bad) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < q && (simp[i] < 0 || simp[i] >= n)) atomicExch(bad, 1);
+}
+// Tetrahedron coefficients in closed form: alpha_ij = |e_kl| cot(theta_kl) / 6,
+// e_kl the opposite edge, theta_kl the dihedral angle there (the unique solution
+// of simplex_alpha's system, since these weights satisfy sum_e alpha_e e e^T =
+// |S| I, without its 6 x 6 system, badly conditioned for flat tetrahedra);
+// cot theta = (a . b) / |a x b| with a, b the parts of x_i - x_k, x_j - x_k
+// perpendicular to e_kl.
+__device__ void simplex_alpha_dihedral(const double p[4][3], double *alpha) {
+    for (int s = 0; s < 6; ++s) {
+        int i, j;
+        simplex_edge(3, s, i, j);
+        int k = -1, l = -1;
+        for (int t = 0; t < 4; ++t)
+            if (t != i && t != j) {
+                if (k < 0)
+                    k = t;
+                else
+                    l = t;
+            }
+        double e[3], a[3], b[3];
+        for (int c = 0; c < 3; ++c) {
+            e[c] = p[l][c] - p[k][c];
+            a[c] = p[i][c] - p[k][c];
+            b[c] = p[j][c] - p[k][c];
+        }
+        const double ee = e[0] * e[0] + e[1] * e[1] + e[2] * e[2], L = sqrt(ee);
+        const double ae = (a[0] * e[0] + a[1] * e[1] + a[2] * e[2]) / ee;
+        const double be = (b[0] * e[0] + b[1] * e[1] + b[2] * e[2]) / ee;
+        for (int c = 0; c < 3; ++c) {
+            a[c] -= ae * e[c];
+            b[c] -= be * e[c];
+        }
+        const double x0 = a[1] * b[2] - a[2] * b[1], x1 = a[2] * b[0] - a[0] * b[2], x2 = a[0] * b[1] - a[1] * b[0];
+        const double sn = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
+        alpha[s] = L * (a[0] * b[0] + a[1] * b[1] + a[2] * b[2]) / (6.0 * sn);
+    }
+}
+// alphaT[s * ne + e]: coefficient of local edge e of simplex s
+__global__ void k_gen_alpha(int dim, int64_t ns, const double *xyz, const int32_t *simp, double *alphaT, int *bad) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    double p[4][3];
+    for (int v = 0; v <= dim; ++v) {
+        const int64_t id = simp[s * (dim + 1) + v];
+        for (int c = 0; c < 3; ++c) p[v][c] = xyz[3 * id + c];
+    }
+    double al[6];
+    if (dim == 2)
+        simplex_alpha(2, p, al);
+    else
+        simplex_alpha_dihedral(p, al);
+    const int ne = dim == 2 ? 3 : 6;
+    for (int e = 0; e < ne; ++e) {
+        if (!isfinite(al[e])) atomicExch(bad, 1);
+        alphaT[s * ne + e] = al[e];
+    }
+}
+// simplices at each node: counts, then the lists (sorted afterwards)
+__global__ void k_gen_inc_count(int dim, int64_t ns, const int32_t *simp, unsigned long long *cnt) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    for (int v = 0; v <= dim; ++v) atomicAdd(cnt + simp[s * (dim + 1) + v], 1ull);
+}
+__global__ void k_gen_inc_fill(int dim, int64_t ns, const int32_t *simp, const int64_t *irp, unsigned long long *fill,
+                               int32_t *inc) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    for (int v = 0; v <= dim; ++v) {
+        const int32_t a = simp[s * (dim + 1) + v];
+        const unsigned long long k = atomicAdd(fill + a, 1ull);
+        inc[irp[a] + (int64_t)k] = (int32_t)s;
+    }
+}
+// node a: its neighbours b > a with the coefficients summed over a's simplices in
+// ascending order, sorted by b, into slots [a GEN_MAXDEG, (a + 1) GEN_MAXDEG)
+__global__ void k_gen_node_edges(int dim, int64_t n, const int32_t *simp, const int64_t *irp, const int32_t *inc,
+                                 const double *alphaT, int32_t *nb_out, double *al_out, int32_t *cnt_out, int *bad) {
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    int32_t nb[GEN_MAXDEG];
+    double al[GEN_MAXDEG];
+    int c = 0;
+    const int ne = dim == 2 ? 3 : 6;
+    for (int64_t q = irp[a]; q < irp[a + 1]; ++q) {
+        const int64_t s = inc[q];
+        for (int e = 0; e < ne; ++e) {
+            int u, w;
+            simplex_edge(dim, e, u, w);
+            int32_t gu = simp[s * (dim + 1) + u], gw = simp[s * (dim + 1) + w];
+            if (gu > gw) {
+                const int32_t t = gu;
+                gu = gw;
+                gw = t;
+            }
+            if (gu != (int32_t)a) continue;
+            int k = 0;
+            while (k < c && nb[k] != gw) ++k;
+            if (k == c) {
+                if (c == GEN_MAXDEG) {
+                    atomicExch(bad, 2);
+                    continue;
+                }
+                nb[c] = gw;
+                al[c] = 0.0;
+                ++c;
+            }
+            al[k] += alphaT[s * ne + e];
+        }
+    }
+    for (int i = 1; i < c; ++i) {
+        const int32_t kb = nb[i];
+        const double ka = al[i];
+        int r = i - 1;
+        while (r >= 0 && nb[r] > kb) {
+            nb[r + 1] = nb[r];
+            al[r + 1] = al[r];
+            --r;
+        }
+        nb[r + 1] = kb;
+        al[r + 1] = ka;
+    }
+    for (int i = 0; i < GEN_MAXDEG; ++i) {
+        nb_out[a * GEN_MAXDEG + i] = i < c ? nb[i] : -1;
+        al_out[a * GEN_MAXDEG + i] = i < c ? al[i] : 0.0;
+    }
+    cnt_out[a] = c;
+}
+// kept edges of each node (forward) and of the nodes they reach (backward)
+__global__ void k_gen_keep_count(int64_t n, const int32_t *nb, const double *al, const int32_t *cnt, double cut,
+                                 int64_t *fwd, unsigned long long *back) {
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    int64_t f = 0;
+    for (int i = 0; i < cnt[a]; ++i)
+        if (fabs(al[a * GEN_MAXDEG + i]) > cut) {
+            ++f;
+            atomicAdd(back + nb[a * GEN_MAXDEG + i], 1ull);
+        }
+    fwd[a] = f;
+}
+// the edge list (j < k, lexicographic) with coefficients and phases
+__global__ void k_gen_edges(int64_t n, const int32_t *nb, const double *al, const int32_t *cnt, double cut,
+                            const int64_t *erp, const double *xyz, Lattice L, int32_t *ej, int32_t *ek, double *eal,
+                            double *eth, double *eth1) {
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    int64_t e = erp[a];
+    const double *xa = xyz + 3 * a;
+    for (int i = 0; i < cnt[a]; ++i) {
+        const double alpha = al[a * GEN_MAXDEG + i];
+        if (!(fabs(alpha) > cut)) continue;
+        const int32_t b = nb[a * GEN_MAXDEG + i];
+        const double *xb = xyz + 3 * (int64_t)b;
+        ej[e] = (int32_t)a;
+        ek[e] = b;
+        eal[e] = alpha;
+        eth1[e] = edge_phase1(L, xa, xb);
+        eth[e] = edge_phase(L, xa, xb);
+        ++e;
+    }
+}
+// the edges ending at each node (by edge id; sorted afterwards)
+__global__ void k_gen_back_fill(int64_t ne, const int32_t *ek, const int64_t *brp, unsigned long long *fill, int32_t *bl) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const int32_t b = ek[e];
+    const unsigned long long k = atomicAdd(fill + b, 1ull);
+    bl[brp[b] + (int64_t)k] = (int32_t)e;
+}
+__global__ void k_gen_row_max(int64_t n, const int64_t *rp, int *mx) {
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a < n) atomicMax(mx, (int)(rp[a + 1] - rp[a]));
+}
+// the longest row of a row-pointer array (synchronises s)
+static int64_t longest_row(int64_t n, const int64_t *rp, cudaStream_t s) {
+    DBuf<int> mx(1);
+    GL_CUDA(cudaMemsetAsync(mx.get(), 0, sizeof(int), s));
+    k_gen_row_max<<<grid_for(n, 256), 256, 0, s>>>(n, rp, mx.get());
+    GL_LAUNCH_CHECK();
+    int h = 0;
+    GL_CUDA(cudaMemcpyAsync(&h, mx.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+__global__ void k_gen_row_len(int64_t n, const int64_t *erp, const int64_t *brp, int64_t *len) {
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a < n) len[a] = (erp[a + 1] - erp[a]) + (brp[a + 1] - brp[a]) + 1;
+}
+// row a of K-hat: the edges ending at a (neighbours below a), the diagonal, the
+// edges starting at a (neighbours above a): columns ascending
+__global__ void k_gen_khat(int64_t n, const int64_t *krp, const int64_t *brp, const int32_t *bl, const int64_t *erp,
+                           const int32_t *ej, const int32_t *ek, const double *eal, const double *eth,
+                           const double *eth1, int32_t *ci, double2 *v, double *kal, double *kth1) {
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    double diag = 0;
+    for (int64_t q = brp[a]; q < brp[a + 1]; ++q) diag += eal[bl[q]];
+    for (int64_t e = erp[a]; e < erp[a + 1]; ++e) diag += eal[e];
+    int64_t q = krp[a];
+    for (int64_t r = brp[a]; r < brp[a + 1]; ++r) {
+        const int32_t e = bl[r];
+        // K-hat_{a c} = -alpha exp(-i theta_{a c}), theta_{a c} = -theta_{c a}
+        double sn, cs;
+        sincos(eth[e], &sn, &cs);
+        ci[q] = ej[e];
+        kal[q] = eal[e];
+        kth1[q] = -eth1[e];
+        v[q++] = make_double2(-eal[e] * cs, -eal[e] * sn);
+    }
+    ci[q] = (int32_t)a;
+    kal[q] = 0.0;
+    kth1[q] = 0.0;
+    v[q++] = make_double2(diag, 0.0);
+    for (int64_t e = erp[a]; e < erp[a + 1]; ++e) {
+        double sn, cs;
+        sincos(eth[e], &sn, &cs);
+        ci[q] = ek[e];
+        kal[q] = eal[e];
+        kth1[q] = eth1[e];
+        v[q++] = make_double2(-eal[e] * cs, eal[e] * sn);
+    }
+}
+__global__ void k_gen_volumes(int64_t n, int dim, const int64_t *krp, const int32_t *ci, const double *kal,
+                              const double *xyz, double *vol) {
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    double s = 0;
+    for (int64_t q = krp[a]; q < krp[a + 1]; ++q) {
+        const int64_t c = ci[q];
+        if (c == a) continue;
+        const double d0 = xyz[3 * c] - xyz[3 * a], d1 = xyz[3 * c + 1] - xyz[3 * a + 1],
+                     d2 = xyz[3 * c + 2] - xyz[3 * a + 2];
+        s += kal[q] * (d0 * d0 + d1 * d1 + d2 * d2) / (2.0 * dim);
+    }
+    vol[a] = s;
+}
+// colour-major order: the nodes of colour c at [base, base + count), in node order
+__global__ void k_gen_flag_colour(int64_t n, const int32_t *color, int c, int64_t *flag) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = color[i] == c ? 1 : 0;
+}
+__global__ void k_gen_place(int64_t n, const int32_t *color, int c, const int64_t *rank, int64_t base, int32_t *perm,
+                            int32_t *iperm) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || color[i] != c) return;
+    const int64_t p = base + rank[i];
+    perm[p] = (int32_t)i;
+    iperm[i] = (int32_t)p;
+}
+
+void mesh_create_simplicial(gl_mesh_s *m, int dim, int64_t n, const double *xyz_host, int64_t ns,
+                            const int32_t *simp_host, double mu, const double *bhat, const double *dip_x0,
+                            const double *dip_m, cudaStream_t s) {
+    GL_REQUIRE(dim == 2 || dim == 3, GL_ERR_ARG, "dim must be 2 or 3");
+    GL_REQUIRE(n >= 2 && n < 2147483647, GL_ERR_ARG, "node count out of range");
+    GL_REQUIRE(ns >= 1 && ns * (dim + 1) < 2147483647, GL_ERR_ARG, "simplex count out of range");
+    GL_REQUIRE(xyz_host && simp_host, GL_ERR_ARG, "NULL mesh arrays");
+    GL_REQUIRE(std::isfinite(mu), GL_ERR_ARG, "mu must be finite");
+    Lattice L{};
+    L.dim = dim;
+    L.N = 0;
+    L.h = 0;
+    L.mu = mu;
+    L.dipole = (dip_x0 && dip_m) ? 1 : 0;
+    for (int c = 0; c < 3; ++c) {
+        L.xd[c] = L.dipole ? dip_x0[c] : 0.0;
+        L.md[c] = L.dipole ? dip_m[c] : 0.0;
+    }
+    legendre_rule(GL_QUAD, L.gx, L.gw);
+    double b[3] = {0, 0, 1};
+    if (bhat) {
+        double nb = std::sqrt(bhat[0] * bhat[0] + bhat[1] * bhat[1] + bhat[2] * bhat[2]);
+        GL_REQUIRE(nb > 0, GL_ERR_ARG, "bhat must be nonzero");
+        for (int c = 0; c < 3; ++c) b[c] = bhat[c] / nb;
+    }
+    for (int c = 0; c < 3; ++c) L.b[c] = m->bhat[c] = b[c];
+    m->dim = dim;
+    m->N = 0;
+    m->h = 0;
+    m->edge = 0;
+    m->mu = mu;
+    m->dipole = L.dipole;
+    m->n = n;
+    const int ne = dim == 2 ? 3 : 6;
+    DBuf<double> xyz(3 * n);
+    DBuf<int32_t> simp(ns * (dim + 1));
+    GL_CUDA(cudaMemcpyAsync(xyz.get(), xyz_host, 3 * n * sizeof(double), cudaMemcpyHostToDevice, s));
+    GL_CUDA(cudaMemcpyAsync(simp.get(), simp_host, ns * (dim + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    DBuf<int> bad(1);
+    GL_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
+    k_gen_check<<<grid_for(ns * (dim + 1), 256), 256, 0, s>>>(ns * (dim + 1), simp.get(), n, bad.get());
+    GL_LAUNCH_CHECK();
+    int hb = 0;
+    GL_CUDA(cudaMemcpyAsync(&hb, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaStreamSynchronize(s));
+    GL_REQUIRE(hb == 0, GL_ERR_ARG, "simplex node id out of range");
+    if (dim == 2) {
+        // z = 0 in 2D
+        std::vector<double> xh(xyz_host, xyz_host + 3 * n);
+        for (int64_t j = 0; j < n; ++j) xh[3 * j + 2] = 0.0;
+        GL_CUDA(cudaMemcpyAsync(xyz.get(), xh.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, s));
+        GL_CUDA(cudaStreamSynchronize(s));
+    }
+    // coefficients per simplex edge, then per edge summed at its first node
+    DBuf<double> alphaT(ns * ne);
+    k_gen_alpha<<<grid_for(ns, 128), 128, 0, s>>>(dim, ns, xyz.get(), simp.get(), alphaT.get(), bad.get());
+    GL_LAUNCH_CHECK();
+    DBuf<int64_t> irp(n + 1);
+    {
+        DBuf<unsigned long long> cnt(n);
+        GL_CUDA(cudaMemsetAsync(cnt.get(), 0, n * sizeof(unsigned long long), s));
+        k_gen_inc_count<<<grid_for(ns, 256), 256, 0, s>>>(dim, ns, simp.get(), cnt.get());
+        GL_LAUNCH_CHECK();
+        scan_exclusive(reinterpret_cast<const int64_t *>(cnt.get()), irp.get(), n, true, s);
+    }
+    const int64_t ninc = ns * (dim + 1);
+    DBuf<int32_t> inc(ninc);
+    {
+        DBuf<unsigned long long> fill(n);
+        GL_CUDA(cudaMemsetAsync(fill.get(), 0, n * sizeof(unsigned long long), s));
+        k_gen_inc_fill<<<grid_for(ns, 256), 256, 0, s>>>(dim, ns, simp.get(), irp.get(), fill.get(), inc.get());
+        GL_LAUNCH_CHECK();
+        DBuf<double2> dummy(ninc);
+        sort_rows_by_col(n, irp.get(), inc.get(), dummy.get(), longest_row(n, irp.get(), s), s);
+    }
+    DBuf<int32_t> nbs(n * GEN_MAXDEG), cnts(n);
+    DBuf<double> als(n * GEN_MAXDEG);
+    k_gen_node_edges<<<grid_for(n, 128), 128, 0, s>>>(dim, n, simp.get(), irp.get(), inc.get(), alphaT.get(),
+                                                       nbs.get(), als.get(), cnts.get(), bad.get());
+    GL_LAUNCH_CHECK();
+    GL_CUDA(cudaMemcpyAsync(&hb, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaStreamSynchronize(s));
+    GL_REQUIRE(hb != 1, GL_ERR_ARG, "a degenerate simplex (its coefficients are not finite)");
+    GL_REQUIRE(hb != 2, GL_ERR_CAPACITY, "a node has more than 64 neighbours");
+    const double amax = reduce_max_abs(als.get(), n * GEN_MAXDEG, s);
+    const double cut = 1e-12 * amax;
+    DBuf<int64_t> fwd(n + 1), erp(n + 1), brp(n + 1);
+    DBuf<unsigned long long> back(n);
+    GL_CUDA(cudaMemsetAsync(back.get(), 0, n * sizeof(unsigned long long), s));
+    k_gen_keep_count<<<grid_for(n, 256), 256, 0, s>>>(n, nbs.get(), als.get(), cnts.get(), cut, fwd.get(), back.get());
+    GL_LAUNCH_CHECK();
+    scan_exclusive(fwd.get(), erp.get(), n, true, s);
+    scan_exclusive(reinterpret_cast<const int64_t *>(back.get()), brp.get(), n, true, s);
+    GL_CUDA(cudaMemcpyAsync(&m->nedges, erp.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaStreamSynchronize(s));
+    const int64_t nem = m->nedges > 0 ? m->nedges : 1;
+    m->ej.alloc(nem);
+    m->ek.alloc(nem);
+    m->ealpha.alloc(nem);
+    m->etheta.alloc(nem);
+    m->etheta1.alloc(nem);
+    k_gen_edges<<<grid_for(n, 128), 128, 0, s>>>(n, nbs.get(), als.get(), cnts.get(), cut, erp.get(), xyz.get(), L,
+                                                  m->ej.get(), m->ek.get(), m->ealpha.get(), m->etheta.get(),
+                                                  m->etheta1.get());
+    GL_LAUNCH_CHECK();
+    DBuf<int32_t> bl(nem);
+    {
+        DBuf<unsigned long long> fill(n);
+        GL_CUDA(cudaMemsetAsync(fill.get(), 0, n * sizeof(unsigned long long), s));
+        k_gen_back_fill<<<grid_for(nem, 256), 256, 0, s>>>(m->nedges, m->ek.get(), brp.get(), fill.get(), bl.get());
+        GL_LAUNCH_CHECK();
+        DBuf<double2> dummy(nem);
+        sort_rows_by_col(n, brp.get(), bl.get(), dummy.get(), longest_row(n, brp.get(), s), s);
+    }
+    // K-hat: row a holds its backward and forward edges and the diagonal
+    CsrDev &K = m->khat;
+    K.n = K.m = n;
+    K.rp.alloc(n + 1);
+    {
+        DBuf<int64_t> len(n + 1);
+        k_gen_row_len<<<grid_for(n, 256), 256, 0, s>>>(n, erp.get(), brp.get(), len.get());
+        GL_LAUNCH_CHECK();
+        scan_exclusive(len.get(), K.rp.get(), n, true, s);
+    }
+    GL_CUDA(cudaMemcpyAsync(&K.nnz, K.rp.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaStreamSynchronize(s));
+    K.ci.alloc(K.nnz);
+    K.v.alloc(K.nnz);
+    m->kal.alloc(K.nnz);
+    m->kth1.alloc(K.nnz);
+    k_gen_khat<<<grid_for(n, 128), 128, 0, s>>>(n, K.rp.get(), brp.get(), bl.get(), erp.get(), m->ej.get(),
+                                                 m->ek.get(), m->ealpha.get(), m->etheta.get(), m->etheta1.get(),
+                                                 K.ci.get(), K.v.get(), m->kal.get(), m->kth1.get());
+    GL_LAUNCH_CHECK();
+    m->vol.alloc(n);
+    k_gen_volumes<<<grid_for(n, 256), 256, 0, s>>>(n, dim, K.rp.get(), K.ci.get(), m->kal.get(), xyz.get(),
+                                                    m->vol.get());
+    GL_LAUNCH_CHECK();
+    // finest-level colours and the colour-major solve ordering
+    m->color0.alloc(n);
+    const int nc = colour_graph_psl(K, m->color0.get(), s);
+    m->perm.alloc(n);
+    m->iperm.alloc(n);
+    m->cstart0.assign(1, 0);
+    {
+        DBuf<int64_t> flag(n + 1), rank(n + 1);
+        int64_t base = 0;
+        for (int c = 0; c < nc; ++c) {
+            k_gen_flag_colour<<<grid_for(n, 256), 256, 0, s>>>(n, m->color0.get(), c, flag.get());
+            GL_LAUNCH_CHECK();
+            scan_exclusive(flag.get(), rank.get(), n, true, s);
+            int64_t cnt = 0;
+            GL_CUDA(cudaMemcpyAsync(&cnt, rank.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            GL_CUDA(cudaStreamSynchronize(s));
+            k_gen_place<<<grid_for(n, 256), 256, 0, s>>>(n, m->color0.get(), c, rank.get(), base, m->perm.get(),
+                                                          m->iperm.get());
+            GL_LAUNCH_CHECK();
+            base += cnt;
+            m->cstart0.push_back(base);
+        }
+    }
+    m->ncolors0 = nc;
+    m->nred = m->cstart0.size() > 1 ? m->cstart0[1] : n;
+    // K = D^-1 K-hat, off-diagonals as sliced ELL in the solve ordering
+    m->kdiag.alloc(n);
+    build_sell<double2>(n, n, m->perm.get(), m->iperm.get(), K, m->vol.get(), true, m->K, m->kdiag.get(), s);
+    m->volp.alloc(n);
+    k_permute_real<<<grid_for(n, 256), 256, 0, s>>>(n, m->perm.get(), m->vol.get(), m->volp.get());
+    GL_LAUNCH_CHECK();
+    GL_CUDA(cudaStreamSynchronize(s));
+    m->lat_checked = true;  // no lattice stencil
+    m->lat_ok = false;
+}
 }  // namespace gl

@@ -350,6 +350,8 @@ static int color_psl(const CsrDev &A, int32_t *color, cudaStream_t s) {
 // head of the bucket one degree lower.  Colouring runs from the last vertex to
 // leave to the first, each taking the smallest colour none of its coloured
 // neighbours has.
+int colour_graph_psl(const CsrDev &A, int32_t *color, cudaStream_t s) { return color_psl(A, color, s); }
+
 static int color_smallest_last(const CsrDev &A, int32_t *color_dev, cudaStream_t s) {
     const int64_t n = A.n;
     std::vector<int64_t> rp(n + 1);
@@ -1058,7 +1060,7 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
     k_fill_d<<<grid_for(n, 256), 256, 0, s>>>(n, L0.B.get(), 1.0);
     L0.color.alloc(n);
     GL_CUDA(cudaMemcpyAsync(L0.color.get(), m->color0.get(), n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    L0.ncolors = n > 1 ? 2 : 1;
+    L0.ncolors = m->ncolors0;
 
     int l = 0;
     for (;;) {
@@ -1161,8 +1163,7 @@ void precond_setup(gl_prec_s *p, gl_mesh_s *m, const double2 *psi_nat, const gl_
         if (k == 0) {
             L.perm = m->perm.get();
             L.iperm = m->iperm.get();
-            L.cstart = {0, m->nred, n};
-            if (L.ncolors == 1) L.cstart = {0, n};
+            L.cstart = m->cstart0;
             L.A = &m->K;
         } else if (coarsest) {
             L.perm_own.alloc(L.n);

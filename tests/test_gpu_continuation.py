@@ -249,7 +249,10 @@ def test_resume_from_checkpoint(tmp_path):
     m = gl.gl_mesh_create(2, s["N"], s["mu"], edge=s["edge"])
     try:
         psi2 = torch.from_numpy(s["psi"]).to(DEV)
-        assert float(gl.gl_energy(m, psi2)) == pytest.approx(pts[-1]["energy"], rel=1e-12)
+        vol = torch.zeros(N * N, dtype=torch.float64, device=DEV)
+        gl.gl_mesh_info(m, vol)
+        # the points carry F / |Omega|
+        assert float(gl.gl_energy(m, psi2)) / float(vol.sum()) == pytest.approx(pts[-1]["energy"], rel=1e-12)
         st, more = gl.gl_continuation(m, psi2, gl.cont_options(max_steps=3, **kw), max_points=16)
         assert st == 0 and len(more) == 4
         assert more[0]["mu"] == pytest.approx(pts[-1]["mu"], abs=1e-14)

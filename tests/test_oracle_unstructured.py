@@ -1,8 +1,12 @@
 """The oracle's assembly on general simplicial meshes (glref_mesh_create_simplicial;
 the paper's Delaunay meshes of its six test domains, Sec. 4), pinned to:
 
+* the tetrahedron coefficients in closed form (|e_kl| cot(theta_kl) / 6): the
+  corollary's identity |S| |u|^2 = sum_e alpha_e <e, u>^2 on random tetrahedra,
+  and the linear-system solution of the structured path on well-shaped ones;
 * the structured assembly: the Kuhn lattice fed in as a list of simplices gives
-  K-hat bit for bit (2D and 3D) and the control volumes h^d 2^-b to rounding (2D;
+  K-hat bit for bit in 2D and to 4e-16 of its largest entry in 3D (the closed
+  form against the linear system), the control volumes h^d 2^-b to rounding (2D;
   3D at interior nodes: at the cube's boundary the Kuhn split is not well-centred
   and the circumcentric dual differs from the lattice Voronoi cell);
 * the Voronoi regions of an equilateral triangulation: regular hexagons of area
@@ -46,6 +50,21 @@ def kuhn_simplices(dim, N):
     return np.array(out)
 
 
+def test_dihedral_coefficients(oracle_mod):
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        p = rng.standard_normal((4, 3))
+        a = oracle_mod.simplex_alpha(3, p, method="dihedral")
+        vol = abs(np.linalg.det(p[1:] - p[0])) / 6
+        edges = [(i, j) for i in range(4) for j in range(i + 1, 4)]
+        S = sum(a[k] * np.outer(p[j] - p[i], p[j] - p[i]) for k, (i, j) in enumerate(edges))
+        assert np.abs(S - vol * np.eye(3)).max() <= 1e-12 * max(1.0, vol)
+    # a well-shaped tetrahedron: the structured path's linear system agrees
+    p = np.array([[0.0, 0, 0], [1.0, 0.1, 0], [0.2, 1.0, 0.1], [0.1, 0.2, 1.1]])
+    np.testing.assert_allclose(oracle_mod.simplex_alpha(3, p, method="dihedral"),
+                               oracle_mod.simplex_alpha(3, p, method="linsys"), rtol=1e-12, atol=1e-14)
+
+
 @pytest.mark.parametrize("dim,N", [(2, 9), (3, 6)])
 def test_kuhn_lattice_as_simplices(oracle_mod, dim, N):
     bh = (0.0, 0.0, 1.0) if dim == 2 else tuple(np.array([0.3, 0.4, 0.866]) / np.linalg.norm([0.3, 0.4, 0.866]))
@@ -53,7 +72,12 @@ def test_kuhn_lattice_as_simplices(oracle_mod, dim, N):
     mg = oracle_mod.Mesh.from_simplices(dim, ms.nodes(), kuhn_simplices(dim, N), 1.3, bhat=bh)
     rp, ci, v = ms.khat_csr()
     rp2, ci2, v2 = mg.khat_csr()
-    assert np.array_equal(rp, rp2) and np.array_equal(ci, ci2) and np.array_equal(v, v2)
+    assert np.array_equal(rp, rp2) and np.array_equal(ci, ci2)
+    if dim == 2:
+        assert np.array_equal(v, v2)  # the same cotangent formula
+    else:
+        # the dihedral closed form against the structured path's linear system
+        assert np.abs(v - v2).max() <= 4e-16 * np.abs(v).max()
     vs, vg = ms.volumes(), mg.volumes()
     assert vg.sum() == pytest.approx(2.0 ** dim, rel=1e-14)
     if dim == 2:
