@@ -117,3 +117,42 @@ def test_disc_counts_flat_and_bad_input():
     flat[0, 1] = flat[0, 0]
     with pytest.raises(gl.GLError):
         gl.gl_mesh_create_simplicial(dim, x, flat, 1.0)
+
+
+SIZES = {"tri": (0.5, 0.25, 0.125), "sq": (0.5, 0.25, 0.125), "circ": (0.5, 0.25, 0.125),
+         "tet": (1.0, 0.6, 0.4), "cube": (1.0, 0.6, 0.4), "ball": (1.0, 0.6, 0.4)}
+
+
+@pytest.mark.parametrize("field", ["A_z", "A_d"])
+@pytest.mark.parametrize("name", list(SIZES))
+def test_fig2_fig3_counts_on_delaunay_domains(name, field):
+    """Figs. 2-3 in the paper's setting on Delaunay meshes of its domains: psi = 1,
+    right-hand side 1, phi_0 = 0, tol 1e-11, mu = 1, A_z or A_d (dipole at
+    (0,0,1) in 2D, (0,0,6) in 3D), R_1 and R_inf, three refinements.  The counts
+    stay bounded as n grows (max <= 2 min + 2; R_inf's do not grow by more than 3,
+    and fall on the finer, more regular meshes) and R_inf takes no more
+    iterations than R_1.  They are printed."""
+    r1, rinf, ns = [], [], []
+    for h in SIZES[name]:
+        dim, x, s = gi.delaunay_domain(name, h, seed=9)
+        dip = DIPOLE[dim] if field == "A_d" else None
+        m = gl.gl_mesh_create_simplicial(dim, x, s, 1.0, dipole=dip)
+        try:
+            n = x.shape[0]
+            psi = torch.ones(n, dtype=torch.complex128, device=DEV)
+            b = torch.ones(n, dtype=torch.complex128, device=DEV)
+            its = []
+            for k in (1, gl.GL_CYCLES_INF):
+                xg = torch.zeros_like(b)
+                st, info = gl.gl_jacobian_solve(m, psi, None, b, xg, gl.options(tol=1e-11, cycles=k, max_coarse=64))
+                assert st == 0 and info.converged, (name, field, h, k, info.as_dict())
+                its.append(info.iters)
+            r1.append(its[0])
+            rinf.append(its[1])
+            ns.append(2 * n)
+        finally:
+            gl.gl_mesh_destroy(m)
+    print(f"{name} {field}: real dimension {ns}: R_1 {r1}, R_inf {rinf}")
+    assert max(r1) <= 2 * min(r1) + 2, r1
+    assert max(rinf) <= 2 * min(rinf) + 2 and rinf[-1] <= rinf[0] + 3, rinf
+    assert all(a >= b for a, b in zip(r1, rinf)), (r1, rinf)
