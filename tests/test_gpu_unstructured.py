@@ -156,3 +156,28 @@ def test_fig2_fig3_counts_on_delaunay_domains(name, field):
     assert max(r1) <= 2 * min(r1) + 2, r1
     assert max(rinf) <= 2 * min(rinf) + 2 and rinf[-1] <= rinf[0] + 3, rinf
     assert all(a >= b for a, b in zip(r1, rinf)), (r1, rinf)
+
+
+@pytest.mark.parametrize("precision", [gl.GL_FP64, gl.GL_MIXED_PRECOND])
+def test_batch_of_unstructured_meshes(oracle_mod, precision):
+    """Meshes of three domains in one batched launch: every instance reaches the
+    true residual 1e-10 with the oracle's Jacobian, as its single solve does."""
+    cases = [gi.delaunay_domain(name, h, seed=10) for name, h in (("tri", 0.3), ("circ", 0.3), ("tet", 0.8))]
+    meshes = [gl.gl_mesh_create_simplicial(dim, x, s, 0.9) for dim, x, s in cases]
+    try:
+        psis = [dev(gi.psi_noisy_one(x.shape[0], 20 + k)) for k, (_, x, _) in enumerate(cases)]
+        bs = [dev(gi.complex_normal(x.shape[0], 30 + k)) for k, (_, x, _) in enumerate(cases)]
+        xs = [torch.zeros_like(b) for b in bs]
+        opts = gl.options(precision=precision, max_coarse=64)
+        st, infos = gl.gl_batch_solve(meshes, psis, bs, xs, opts)
+        assert st == 0
+        for k, (dim, x, s) in enumerate(cases):
+            om = oracle_mod.Mesh.from_simplices(dim, x, s, 0.9)
+            assert infos[k].converged
+            assert true_relres(om, psis[k].cpu().numpy(), bs[k].cpu().numpy(), xs[k].cpu().numpy()) <= 1.01e-10
+            x1 = torch.zeros_like(bs[k])
+            st1, info1 = gl.gl_jacobian_solve(meshes[k], psis[k], None, bs[k], x1, opts)
+            assert st1 == 0 and abs(info1.iters - infos[k].iters) <= (1 if precision == gl.GL_FP64 else 3)
+    finally:
+        for m in meshes:
+            gl.gl_mesh_destroy(m)
