@@ -694,9 +694,10 @@ def main():
         "gs": "k_sgs_flags / k_sgs_coop / k_sgs_cluster (symmetric Gauss-Seidel step, coarse levels, FP32)",
         "jz": ("k_jz_latdf (double-FP32 Jacobian apply fused with the Lanczos dot; SM-pipe bound)"
                if infos[-1].df_jacobian else "k_jz (Jacobian apply fused with the Lanczos dot, FP64)"),
+        "coarse": "k_dense_mv_df (double-FP32 dense coarsest product)",
     }
     profs = {}
-    for cls in ("gs0", "gs", "jz"):
+    for cls in ("gs0", "gs", "jz", "coarse"):
         _, _, pr = timed(opts_final, 2, 1, profile_class=cls)
         profs[cls] = (pr, 2)
     prof = profs["gs0"][0]

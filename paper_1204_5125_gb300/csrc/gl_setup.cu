@@ -1395,6 +1395,7 @@ void precond_negate_coarsest(gl_prec_s *p, cudaStream_t s) {
     const int64_t nn = L.n * L.n;
     k_negate<<<grid_for(nn, 256), 256, 0, s>>>(nn, L.Ainv.get());
     GL_LAUNCH_CHECK();
+    if (L.Ainv_df.get()) coarse_inverse_df(L, s);  // the FP32 V-cycle's copy follows
     GL_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -96,6 +96,30 @@ def test_indefinite_preconditioner_is_a_breakdown():
         gl.gl_mesh_destroy(m)
 
 
+def test_negated_coarsest_reaches_the_fp32_vcycle():
+    # two levels: the FP32 V-cycle's double-FP32 copy of the coarsest inverse is
+    # rebuilt from the negated FP64 inverse, so both V-cycles apply the same
+    # (indefinite) operator afterwards
+    m = gl.gl_mesh_create(2, 40, 1.0)
+    n = 1600
+    psi, b = dev(gi.disk(n, 25)), dev(gi.complex_normal(n, 26))
+    P = gl.gl_precond_setup(m, psi, gl.options(precision=gl.GL_MIXED_PRECOND, max_coarse=256))
+    try:
+        assert gl.gl_precond_levels(P) >= 2
+        z64, z32 = torch.empty_like(psi), torch.empty_like(psi)
+        gl.gl_precond_apply_precision(P, b, z32, gl.GL_MIXED_PRECOND)
+        before = z32.clone()
+        gl.gl_precond_debug(P, gl.GL_DEBUG_NEGATE_COARSEST)
+        gl.gl_precond_apply_precision(P, b, z64, gl.GL_FP64)
+        gl.gl_precond_apply_precision(P, b, z32, gl.GL_MIXED_PRECOND)
+        rel = lambda a, c: float(torch.linalg.vector_norm(a - c) / torch.linalg.vector_norm(c))
+        assert rel(z32, z64) <= 2 ** 8 * 2.0 ** -24
+        assert rel(before, z64) > 1e-3
+    finally:
+        gl.gl_precond_destroy(P)
+        gl.gl_mesh_destroy(m)
+
+
 def test_debug_rejects_unknown_action():
     m = gl.gl_mesh_create(2, 8, 1.0)
     psi = torch.ones(64, dtype=torch.complex128, device=DEV)

@@ -92,6 +92,46 @@ def test_fp32_vcycle_matches_oracle_r1(oracle_mod, dim, N, cycles):
         gl.gl_mesh_destroy(m)
 
 
+# meshes whose coarsest level (max_coarse 4096, two levels) has 1294 and 1661
+# nodes: rows longer than a block's threads with a ragged tail
+LARGE_COARSEST = [(2, 96), (3, 26)]
+
+
+@pytest.mark.parametrize("dim,N", LARGE_COARSEST, ids=lambda p: str(p))
+def test_fp32_vcycle_large_coarsest_matches_oracle(oracle_mod, dim, N):
+    """The FP32 V-cycle with the double-FP32 coarsest product on a coarsest level
+    of the benchmark's size class: against the oracle's R_1 at the FP32
+    V-cycle's bound, and against the same V-cycle with the FP64 coarsest
+    product, which differs only where the FP32 roundings of a 48-bit and a
+    53-bit value of the same product differ (a few u32)."""
+    om = oracle_mod.Mesh(dim, N, 1.0, bhat(dim))
+    m = gl.gl_mesh_create(dim, N, 1.0, bhat(dim))
+    n = om.n
+    psi, v = gi.disk(n, 31), gi.complex_normal(n, 32)
+    P = oracle_mod.Precond(om, psi, max_coarse=4096)
+    Gs = [gl.gl_precond_setup(m, dev(psi), gl.options(precision=gl.GL_MIXED_PRECOND, max_coarse=4096,
+                                                      coarse_df=df)) for df in (1, 0)]
+    try:
+        nc = gl.gl_precond_level_info(Gs[0], 1)["n"]
+        assert gl.gl_precond_levels(Gs[0]) == 2 and nc > 1024 and nc % 32 != 0
+        zs = []
+        for G in Gs:
+            z = torch.empty(n, dtype=torch.complex128, device=DEV)
+            gl.gl_precond_apply_precision(G, dev(v), z, gl.GL_MIXED_PRECOND)
+            zs.append(host(z))
+        ref = P.apply(v.astype(np.complex64).astype(np.complex128))
+        vol = om.volumes()
+        err = dnorm(vol, zs[0] - ref) / dnorm(vol, ref)
+        dif = dnorm(vol, zs[0] - zs[1]) / dnorm(vol, zs[1])
+        print(f"{dim}d N={N} coarsest {nc}: vs oracle {err / U32:.1f} u32, vs FP64 coarsest product {dif / U32:.2f} u32")
+        assert err <= 2 ** 8 * U32
+        assert dif <= 4 * U32
+    finally:
+        for G in Gs:
+            gl.gl_precond_destroy(G)
+        gl.gl_mesh_destroy(m)
+
+
 @pytest.mark.parametrize("dim,N", EVEN, ids=lambda p: str(p))
 def test_double_fp32_jacobian_matches_oracle(oracle_mod, dim, N):
     om = oracle_mod.Mesh(dim, N, 1.0, bhat(dim))
