@@ -131,6 +131,7 @@ struct Level {
     DBuf<float> diag32;
     Sell<float2> P32, PH32;
     CsrG<float2> Ag32, PHg32;
+    CsrG<float2> PHg32b;            // level 0 with two colours: P^H without the colour-0 columns
     DBuf<float2> b32, x32, r32;
     DBuf<float4> Ainv_df;           // coarsest: the dense inverse as double-FP32 (re hi, re lo, im hi, im lo)
     int cl_size = 0, cl_chunk = 0;  // FP32 sweeps by one thread-block cluster (0: cooperative grid)
@@ -214,9 +215,11 @@ template <typename C>
 void build_sell(int64_t nrows, int64_t ncols, const int32_t *perm, const int32_t *icol, const CsrDev &A,
                 const double *row_scale, bool drop_diag, Sell<C> &out, double *diag_out, cudaStream_t s);
 void to_float(const double *in, float *out, int64_t n, cudaStream_t s);
+// grouped CSR of A's rows perm[0..nrows) with columns mapped by icol; columns
+// (after the map) below col_lo are left out
 template <typename C>
 void build_csrg(int64_t nrows, const int32_t *perm, const int32_t *icol, const CsrDev &A, bool drop_diag,
-                CsrG<C> &out, double *diag_out, cudaStream_t s);
+                CsrG<C> &out, double *diag_out, cudaStream_t s, int64_t col_lo = 0);
 
 // gl_lattice.cu: validates the closed-form finest-level stencil against the
 // assembled K and builds its phase tables (sets lat_ok)

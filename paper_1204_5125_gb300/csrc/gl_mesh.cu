@@ -510,22 +510,25 @@ template void build_sell<float2>(int64_t, int64_t, const int32_t *, const int32_
                                  bool, Sell<float2> &, double *, cudaStream_t);
 
 // ---------------------------------------------------------------- grouped CSR builder
-__global__ void k_csrg_len(int64_t nrows, const int32_t *perm, const int64_t *rp, const int32_t *ci, bool drop_diag,
-                           int64_t *len) {
+__global__ void k_csrg_len(int64_t nrows, const int32_t *perm, const int32_t *icol, const int64_t *rp,
+                           const int32_t *ci, bool drop_diag, int64_t col_lo, int64_t *len) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= nrows) return;
     int64_t r = perm ? perm[p] : p;
-    int64_t l = rp[r + 1] - rp[r];
-    if (drop_diag)
-        for (int64_t q = rp[r]; q < rp[r + 1]; ++q)
-            if (ci[q] == r) --l;
+    int64_t l = 0;
+    for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
+        const int64_t c = ci[q];
+        if (drop_diag && c == r) continue;
+        if ((icol ? icol[c] : c) < col_lo) continue;
+        ++l;
+    }
     len[p] = l;
 }
 
 template <typename C>
 __global__ void k_csrg_fill(int64_t nrows, const int32_t *perm, const int32_t *icol, const int64_t *rp,
-                            const int32_t *ci, const double2 *v, bool drop_diag, const int64_t *orp, int32_t *ocol,
-                            C *oval, double *diag_out) {
+                            const int32_t *ci, const double2 *v, bool drop_diag, int64_t col_lo, const int64_t *orp,
+                            int32_t *ocol, C *oval, double *diag_out) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= nrows) return;
     int64_t r = perm ? perm[p] : p;
@@ -537,7 +540,9 @@ __global__ void k_csrg_fill(int64_t nrows, const int32_t *perm, const int32_t *i
             dg = v[q].x;
             continue;
         }
-        ocol[o] = icol ? icol[c] : (int32_t)c;
+        const int32_t oc = icol ? icol[c] : (int32_t)c;
+        if (oc < col_lo) continue;
+        ocol[o] = oc;
         C val;
         val.x = v[q].x;
         val.y = v[q].y;
@@ -549,10 +554,11 @@ __global__ void k_csrg_fill(int64_t nrows, const int32_t *perm, const int32_t *i
 
 template <typename C>
 void build_csrg(int64_t nrows, const int32_t *perm, const int32_t *icol, const CsrDev &A, bool drop_diag,
-                CsrG<C> &out, double *diag_out, cudaStream_t s) {
+                CsrG<C> &out, double *diag_out, cudaStream_t s, int64_t col_lo) {
     out.nrows = nrows;
     DBuf<int64_t> len(nrows + 1);
-    k_csrg_len<<<grid_for(nrows, 256), 256, 0, s>>>(nrows, perm, A.rp.get(), A.ci.get(), drop_diag, len.get());
+    k_csrg_len<<<grid_for(nrows, 256), 256, 0, s>>>(nrows, perm, icol, A.rp.get(), A.ci.get(), drop_diag, col_lo,
+                                                     len.get());
     GL_LAUNCH_CHECK();
     out.rp.alloc(nrows + 1);
     scan_exclusive(len.get(), out.rp.get(), nrows, true, s);
@@ -561,8 +567,8 @@ void build_csrg(int64_t nrows, const int32_t *perm, const int32_t *icol, const C
     out.col.alloc(out.nnz > 0 ? out.nnz : 1);
     out.val.alloc(out.nnz > 0 ? out.nnz : 1);
     k_csrg_fill<C><<<grid_for(nrows, 256), 256, 0, s>>>(nrows, perm, icol, A.rp.get(), A.ci.get(), A.v.get(),
-                                                        drop_diag, out.rp.get(), out.col.get(), out.val.get(),
-                                                        diag_out);
+                                                        drop_diag, col_lo, out.rp.get(), out.col.get(),
+                                                        out.val.get(), diag_out);
     GL_LAUNCH_CHECK();
     GL_CUDA(cudaStreamSynchronize(s));
     // lanes per row: the power of two nearest a quarter of the mean row length
@@ -573,9 +579,9 @@ void build_csrg(int64_t nrows, const int32_t *perm, const int32_t *icol, const C
 }
 
 template void build_csrg<double2>(int64_t, const int32_t *, const int32_t *, const CsrDev &, bool, CsrG<double2> &,
-                                  double *, cudaStream_t);
+                                  double *, cudaStream_t, int64_t);
 template void build_csrg<float2>(int64_t, const int32_t *, const int32_t *, const CsrDev &, bool, CsrG<float2> &,
-                                 double *, cudaStream_t);
+                                 double *, cudaStream_t, int64_t);
 
 __global__ void k_d2f(int64_t n, const double *in, float *out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

@@ -1351,6 +1351,10 @@ void precond_ensure_fp32(gl_prec_s *p, cudaStream_t s) {
             transpose_conj(L.P_can, PH, s);
             build_sell<float2>(Lc.n, L.n, Lc.perm, L.iperm, PH, nullptr, false, L.PH32, nullptr, s);
             build_csrg<float2>(Lc.n, Lc.perm, L.iperm, PH, false, L.PHg32, nullptr, s);
+            // after the pre-smoothing of a red-black level 0 the residual of every
+            // colour-0 row is zero, so its restriction needs only the other columns
+            if (k == 0 && L.ncolors == 2)
+                build_csrg<float2>(Lc.n, Lc.perm, L.iperm, PH, false, L.PHg32b, nullptr, s, L.cstart[1]);
         }
         L.b32.alloc(L.n);
         L.x32.alloc(L.n);

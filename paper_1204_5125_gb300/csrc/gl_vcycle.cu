@@ -230,12 +230,13 @@ __global__ void __launch_bounds__(256) k_gs_lat_first2(int64_t n, LatticeView L,
     x[p] = make_float2((bb.x - acc.x) * d, (bb.y - acc.y) * d);
 }
 
-__global__ void __launch_bounds__(256) k_resid_lat(int64_t n, LatticeView L, const float *__restrict__ diag,
-                                                   const float2 *__restrict__ b, const float2 *__restrict__ x,
-                                                   const float *__restrict__ scale, float2 *__restrict__ r,
-                                                   const int *__restrict__ stop) {
+// the residual of the rows [lo, n) (the rows below lo are not written)
+__global__ void __launch_bounds__(256) k_resid_lat(int64_t lo, int64_t n, LatticeView L,
+                                                   const float *__restrict__ diag, const float2 *__restrict__ b,
+                                                   const float2 *__restrict__ x, const float *__restrict__ scale,
+                                                   float2 *__restrict__ r, const int *__restrict__ stop) {
     if (stop && *stop) return;
-    const int64_t p0 = (int64_t)blockIdx.x * blockDim.x * LAT_RPT + threadIdx.x;
+    const int64_t p0 = lo + (int64_t)blockIdx.x * blockDim.x * LAT_RPT + threadIdx.x;
     float2 acc[LAT_RPT];
 #pragma unroll
     for (int u = 0; u < LAT_RPT; ++u) {
@@ -1416,6 +1417,7 @@ static void vcycle(gl_prec_s *p, int l, const typename LevelOps<T>::C *b, typena
     Level &Lc = p->L[l + 1];
     smooth<T>(p, l, b, x, true, stop, s);
     C *r = O::r(L);
+    bool restrict_black = false;
     if (l == 0) {
         const T *scale;
         if constexpr (sizeof(T) == 8)
@@ -1426,12 +1428,19 @@ static void vcycle(gl_prec_s *p, int l, const typename LevelOps<T>::C *b, typena
         LatticeView lv;
         bool lat = lattice_for<T>(p, lv);
         if constexpr (sizeof(T) == 4) {
-            if (lat)
-                k_resid_lat<<<grid_for(L.n, 256 * LAT_RPT), 256, 0, s>>>(L.n, lv, O::diag(L), b, x, scale, r,
-                                                                         stop);
+            if (lat) {
+                // the pre-smoothing ended by relaxing the red rows against black
+                // neighbours it left unchanged, so their residual is zero (up to the
+                // rounding of that relaxation): only the black rows are formed, and
+                // the restriction below reads only black columns
+                const int64_t lo = L.PHg32b.nrows > 0 ? L.cstart[1] : 0;
+                k_resid_lat<<<grid_for(L.n - lo, 256 * LAT_RPT), 256, 0, s>>>(lo, L.n, lv, O::diag(L), b, x, scale,
+                                                                              r, stop);
+            }
         }
         if (!lat)
             k_resid<C, T><<<grid_for(L.n, 256), 256, 0, s>>>(L.n, O::A(L).view(), O::diag(L), b, x, scale, r, stop);
+        restrict_black = lat && sizeof(T) == 4 && L.PHg32b.nrows > 0;
     } else {
         const CsrG<C> &A = O::Ag(L);
         ProfScope ps("resid", 0, s);
@@ -1440,7 +1449,15 @@ static void vcycle(gl_prec_s *p, int l, const typename LevelOps<T>::C *b, typena
     }
     {
         ProfScope ps("restrict", 0, s);
-        spmv_g<C>(O::PHg(L), r, O::b(Lc), 0, stop, s);
+        if constexpr (sizeof(T) == 4) {
+            if (restrict_black) {
+                spmv_g<C>(L.PHg32b, r, O::b(Lc), 0, stop, s);
+            } else {
+                spmv_g<C>(O::PHg(L), r, O::b(Lc), 0, stop, s);
+            }
+        } else {
+            spmv_g<C>(O::PHg(L), r, O::b(Lc), 0, stop, s);
+        }
     }
     vcycle<T>(p, l + 1, O::b(Lc), O::x(Lc), stop, s);
     {
